@@ -1,0 +1,1113 @@
+/*
+ * mcrt_oracle.c -- plain, slow, FP64 CPU reference of the polarized Monte-Carlo
+ * transport and two-step imaging of Kratos-polrad (arXiv:2512.01283).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or calls
+ * this file; only the tests, the package smoke check and the benchmark's CPU
+ * baseline leg do.  It shares no code, header, table or constant with the CUDA
+ * path: every formula is written here a second time, directly from the paper, in
+ * the paper's order and notation, with no blocking or fusion.
+ *
+ * Passages followed (paper sections / equations):
+ *   Sec. 2.1  eq. (grain-quaternion)   q_B from (theta_B, phi_B)
+ *             eq. (vector-transform)   (0, n_GF) = q_B^* (0, n) q_B
+ *             Stokes basis theta-hat, phi-hat; Q > 0 along theta-hat
+ *             eq. (rotation-angle), eq. (stokes-rotation): basis rotation by eta.
+ *             Here the rotation is done by projecting the coherency matrix onto
+ *             the new basis vectors, which needs no angle convention; the signed
+ *             eta of the CUDA path is checked against it.
+ *   Sec. 2.2  eq. (polarized-rt), eq. (mfp-matrices), eq. (scattering-source);
+ *             exponential scattering optical depth drawn at emission and after
+ *             each scattering; cell-to-cell traversal; rejection sampling of the
+ *             polarization-aware differential cross section.
+ *   Sec. 2.3  eq. (scat-disc-sum): every path segment adds Z(Omega_cam;Omega_pp) I_pp
+ *             to S(Omega_cam, x); step 2 ray-marches toward the camera with the
+ *             same cell-by-cell analytic integration.
+ *   App. A    analytic in-cell solution (the printed I_s..V_s and cosh/sinh,
+ *             cos/sin solution; the extinction matrix is taken as the one that
+ *             solution solves, K = [[a1,a2,0,0],[a2,a1,0,0],[0,0,a1,a3],[0,0,-a3,a1]]).
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - Random numbers: Philox4x32-10 (Salmon et al. 2011), key = (seed, stream),
+ *     counter = (pid_lo, pid_hi, event, slot); u = ((x >> 8) | 1) * 2^-24.
+ *   - Scattering optical depth is sampled with the scalar kappa_sca; between
+ *     events the Stokes vector is attenuated by K - omega*1 (absorption and all
+ *     dichroism) and the absorbed I is tallied.
+ *   - The step-1 tally uses the exact path integral of the attenuated Stokes
+ *     vector over the segment (length units); step 2 uses S = omega/V * tally.
+ *   - Rayleigh: isotropic proposal in the grain frame with envelope 2*max Z11.
+ *     Tables: proposal from a piecewise-constant envelope of P11 over the
+ *     tabulated scattering-angle intervals, azimuth uniform about n.
+ *
+ * All arithmetic is double precision.  Tallies from several threads are added
+ * with compare-and-swap; with one thread the results are deterministic.
+ */
+#include <complex.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Problem description (mirrored field by field in oracle.py).               */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t type;       /* 0 point, 1 plane beam, 2 thermal emission of the grid */
+    int32_t beam_dir;   /* beam: +1 travels +z from the lo_z face, -1 travels -z from hi_z */
+    double luminosity;  /* total power of this source; thermal: <= 0 means computed */
+    double pos[3];      /* point source position */
+    int64_t n_packets;
+} orc_source;
+
+typedef struct {
+    double dir[3];      /* unit vector pointing from the model toward the observer */
+    double center[3];   /* image centre */
+    double fov[2];      /* image extent along e_x, e_y (length units) */
+    int32_t npix[2];    /* nx, ny */
+} orc_camera;
+
+typedef struct {
+    int32_t n[3];
+    double lo[3], hi[3];
+    const float *kappa_abs;   /* [nz][ny][nx], 1/length */
+    const float *kappa_sca;   /* [nz][ny][nx], 1/length */
+    const float *bfield;      /* [nz][ny][nx][3] or NULL (no alignment) */
+    const float *emissivity;  /* [nz][ny][nx] B_lambda(T) or NULL */
+    int32_t scat_model;       /* 0 Rayleigh (analytic dipole), 1 tables */
+    int32_t n_bins, n_theta;
+    const float *mueller;     /* [n_bins][n_theta][6] P11,P12,P22,P33,P34,P44 */
+    const float *bin_weight;  /* [n_bins] */
+    int32_t n_ktheta;
+    const float *kext;        /* [n_ktheta][3] alpha1, alpha2, alpha3 on theta' in [0, pi] */
+    int32_t n_sources;
+    const orc_source *sources;
+    int32_t n_cam;
+    const orc_camera *cams;
+    uint32_t seed, stream;
+    int64_t pid_begin, pid_end;
+    double roulette_threshold, roulette_survival;
+    int64_t max_events;
+    int32_t max_trials;
+    int32_t n_threads;
+    int64_t n_trace;
+} orc_problem;
+
+typedef struct {
+    double *S;          /* [ncell][n_cam][4] path-integral tally, caller zeroes */
+    double *absorbed;   /* [ncell] */
+    double *trace;      /* [n_trace][16] final packet states, or NULL */
+    double stats[16];
+} orc_result;
+
+enum {
+    ST_EMITTED_E = 0, ST_ESCAPED_E, ST_ABSORBED_E, ST_ROULETTE_LOST, ST_ROULETTE_GAIN,
+    ST_CAP_LOST, ST_EVENTS, ST_SEGMENTS, ST_SCATTERS, ST_EMITTED_N, ST_ESCAPED_N,
+    ST_KILLED_N, ST_CAP_N, ST_TRIALS, ST_STATUS, ST_SPARE
+};
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, Salmon, Moraes, Dror & Shaw (SC'11), Sec. 5.                */
+/* ------------------------------------------------------------------------- */
+void orc_philox(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double orc_uniform(uint32_t x)
+{
+    return (double)((x >> 8) | 1u) * (1.0 / 16777216.0);
+}
+
+/* Four uniforms of (pid, event, slot). */
+static void draw4(const orc_problem *P, int64_t pid, uint32_t event, uint32_t slot, double u[4])
+{
+    uint32_t ctr[4] = {(uint32_t)((uint64_t)pid & 0xffffffffu), (uint32_t)((uint64_t)pid >> 32), event, slot};
+    uint32_t key[2] = {P->seed, P->stream};
+    uint32_t x[4];
+    orc_philox(ctr, key, x);
+    for (int i = 0; i < 4; ++i) u[i] = orc_uniform(x[i]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Vectors and Hamilton quaternions (Sec. 2.1).                              */
+/* ------------------------------------------------------------------------- */
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    double x = a[1] * b[2] - a[2] * b[1];
+    double y = a[2] * b[0] - a[0] * b[2];
+    double z = a[0] * b[1] - a[1] * b[0];
+    c[0] = x; c[1] = y; c[2] = z;
+}
+
+/* Hamilton product with i^2 = j^2 = k^2 = ijk = -1. */
+static void qmul(const double a[4], const double b[4], double c[4])
+{
+    double r0 = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    double r1 = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    double r2 = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    double r3 = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    c[0] = r0; c[1] = r1; c[2] = r2; c[3] = r3;
+}
+
+/* eq. (grain-quaternion): q_B from the field direction angles (theta_B, phi_B);
+ * phi_B = 0 when B is along z, q_B = 1 when B = 0. */
+void orc_grain_quaternion(double bx, double by, double bz, double q[4])
+{
+    double b = sqrt(bx * bx + by * by + bz * bz);
+    if (b == 0.0) {
+        q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
+        return;
+    }
+    double c = bz / b;
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    double thetaB = acos(c);
+    double phiB = (bx == 0.0 && by == 0.0) ? 0.0 : atan2(by, bx);
+    q[0] = cos(phiB / 2) * cos(thetaB / 2);
+    q[1] = -sin(phiB / 2) * sin(thetaB / 2);
+    q[2] = cos(phiB / 2) * sin(thetaB / 2);
+    q[3] = sin(phiB / 2) * cos(thetaB / 2);
+}
+
+/* eq. (vector-transform): (0, v_GF) = q^* (0, v) q. */
+void orc_to_grain(const double q[4], const double v[3], double out[3])
+{
+    double qc[4] = {q[0], -q[1], -q[2], -q[3]};
+    double pv[4] = {0.0, v[0], v[1], v[2]};
+    double t[4], r[4];
+    qmul(qc, pv, t);
+    qmul(t, q, r);
+    out[0] = r[1]; out[1] = r[2]; out[2] = r[3];
+}
+
+/* Inverse of eq. (vector-transform): (0, v) = q (0, v_GF) q^*. */
+void orc_to_lab(const double q[4], const double v[3], double out[3])
+{
+    double qc[4] = {q[0], -q[1], -q[2], -q[3]};
+    double pv[4] = {0.0, v[0], v[1], v[2]};
+    double t[4], r[4];
+    qmul(q, pv, t);
+    qmul(t, qc, r);
+    out[0] = r[1]; out[1] = r[2]; out[2] = r[3];
+}
+
+/* Sec. 2.1 Stokes reference basis for light travelling along n = (theta, phi):
+ * theta-hat = (cos t cos p, cos t sin p, -sin t), phi-hat = (-sin p, cos p, 0);
+ * at the poles phi = 0. */
+void orc_stokes_basis(const double n[3], double th[3], double ph[3])
+{
+    double c = n[2];
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    double t = acos(c);
+    double p = (n[0] == 0.0 && n[1] == 0.0) ? 0.0 : atan2(n[1], n[0]);
+    th[0] = cos(t) * cos(p); th[1] = cos(t) * sin(p); th[2] = -sin(t);
+    ph[0] = -sin(p); ph[1] = cos(p); ph[2] = 0.0;
+}
+
+/* Re-express a Stokes vector given in the basis (a1, a2) in the basis (b1, b2),
+ * both orthonormal and perpendicular to the propagation direction.  The field
+ * components transform as E_b = T E_a with T_jk = b_j . a_k; the coherency matrix
+ * C = <E E^dagger> = 1/2 [[I+Q, U+iV], [U-iV, I-Q]] transforms as T C T^T.  This is
+ * the explicit projection behind eq. (stokes-rotation). */
+void orc_change_basis(const double X[4], const double a1[3], const double a2[3],
+                      const double b1[3], const double b2[3], double out[4])
+{
+    double T[2][2] = {{dot3(b1, a1), dot3(b1, a2)}, {dot3(b2, a1), dot3(b2, a2)}};
+    double complex C[2][2];
+    C[0][0] = 0.5 * (X[0] + X[1]);
+    C[1][1] = 0.5 * (X[0] - X[1]);
+    C[0][1] = 0.5 * (X[2] + I * X[3]);
+    C[1][0] = 0.5 * (X[2] - I * X[3]);
+    double complex D[2][2];
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) {
+            double complex s = 0.0;
+            for (int l = 0; l < 2; ++l)
+                for (int m = 0; m < 2; ++m) s += T[j][l] * C[l][m] * T[k][m];
+            D[j][k] = s;
+        }
+    out[0] = creal(D[0][0] + D[1][1]);
+    out[1] = creal(D[0][0] - D[1][1]);
+    out[2] = 2.0 * creal(D[0][1]);
+    out[3] = 2.0 * cimag(D[0][1]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* App. A: analytic solution inside one cell.                                */
+/* ------------------------------------------------------------------------- */
+
+/* The printed solution with source (S1..S4) per unit extinction optical depth,
+ * entering Stokes X0 and cell optical depth dtau. */
+void orc_cell_solution(const double X0[4], double alpha1, double alpha2, double alpha3,
+                       const double S[4], double dtau, double out[4])
+{
+    double Is = (alpha1 * S[0] - alpha2 * S[1]) / (alpha1 * alpha1 - alpha2 * alpha2);
+    double Qs = (alpha1 * S[1] - alpha2 * S[0]) / (alpha1 * alpha1 - alpha2 * alpha2);
+    double Us = (alpha1 * S[2] - alpha3 * S[3]) / (alpha1 * alpha1 + alpha3 * alpha3);
+    double Vs = (alpha1 * S[3] + alpha3 * S[2]) / (alpha1 * alpha1 + alpha3 * alpha3);
+    double e = exp(-alpha1 * dtau);
+    double ch = cosh(-alpha2 * dtau), sh = sinh(-alpha2 * dtau);
+    double co = cos(-alpha3 * dtau), si = sin(-alpha3 * dtau);
+    out[0] = Is + (X0[0] - Is) * e * ch + (X0[1] - Qs) * e * sh;
+    out[1] = Qs + (X0[0] - Is) * e * sh + (X0[1] - Qs) * e * ch;
+    out[2] = Us + (X0[2] - Us) * e * co + (X0[3] - Vs) * e * si;
+    out[3] = Vs - (X0[2] - Us) * e * si + (X0[3] - Vs) * e * co;
+}
+
+/* App. A with S = 0 and diagonal rate a (= alpha1 - omega in step 1). */
+void orc_attenuate(const double X0[4], double a, double alpha2, double alpha3, double dtau, double out[4])
+{
+    double e = exp(-a * dtau);
+    double ch = cosh(-alpha2 * dtau), sh = sinh(-alpha2 * dtau);
+    double co = cos(-alpha3 * dtau), si = sin(-alpha3 * dtau);
+    out[0] = X0[0] * e * ch + X0[1] * e * sh;
+    out[1] = X0[0] * e * sh + X0[1] * e * ch;
+    out[2] = X0[2] * e * co + X0[3] * e * si;
+    out[3] = -X0[2] * e * si + X0[3] * e * co;
+}
+
+/* Integral over t in [0, dtau] of exp(-M t) X0 with M = [[a,a2,0,0],[a2,a,0,0],
+ * [0,0,a,a3],[0,0,-a3,a]], from the eigen-decomposition of the two blocks:
+ * I+Q and I-Q decay at a+a2 and a-a2, U+iV at a-i a3; int_0^T e^{-z t} dt =
+ * (1 - e^{-z T})/z, equal to T when z = 0. */
+static double complex decay_integral(double complex z, double T)
+{
+    if (z == 0.0) return T;
+    /* 1 - e^{-w} for w = x + i y, written with expm1 and 1 - cos y = 2 sin^2(y/2)
+     * so that small |w| keeps full relative precision */
+    double x = creal(z) * T, y = cimag(z) * T;
+    double s = sin(0.5 * y);
+    double re = -expm1(-x) + 2.0 * exp(-x) * s * s;
+    double im = exp(-x) * sin(y);
+    return (re + I * im) / z;
+}
+
+void orc_segment_integral(const double X0[4], double a, double alpha2, double alpha3, double dtau, double out[4])
+{
+    double p = creal(decay_integral(a + alpha2, dtau)) * (X0[0] + X0[1]);
+    double m = creal(decay_integral(a - alpha2, dtau)) * (X0[0] - X0[1]);
+    double complex w = decay_integral(a - I * alpha3, dtau) * (X0[2] + I * X0[3]);
+    out[0] = 0.5 * (p + m);
+    out[1] = 0.5 * (p - m);
+    out[2] = creal(w);
+    out[3] = cimag(w);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Grain optics.                                                             */
+/* ------------------------------------------------------------------------- */
+
+/* Dipole (Rayleigh) scattering matrix normalised to int P11 dOmega = 1, in the
+ * scattering-plane basis (e_par, e_perp): P11,P12,P22,P33,P34,P44. */
+void orc_rayleigh(double mu, double P[6])
+{
+    double f = 3.0 / (16.0 * M_PI);
+    P[0] = f * (1.0 + mu * mu);
+    P[1] = f * (mu * mu - 1.0);
+    P[2] = f * (1.0 + mu * mu);
+    P[3] = f * 2.0 * mu;
+    P[4] = 0.0;
+    P[5] = f * 2.0 * mu;
+}
+
+/* Table row interpolation, linear in the scattering angle on a uniform grid. */
+static void table_mueller(const float *tab, int n_theta, double mu, double P[6])
+{
+    if (mu > 1.0) mu = 1.0;
+    if (mu < -1.0) mu = -1.0;
+    double x = acos(mu) / M_PI * (n_theta - 1);
+    int j = (int)floor(x);
+    if (j > n_theta - 2) j = n_theta - 2;
+    if (j < 0) j = 0;
+    double f = x - j;
+    for (int e = 0; e < 6; ++e)
+        P[e] = (1.0 - f) * tab[j * 6 + e] + f * tab[(j + 1) * 6 + e];
+}
+
+/* Scattering matrix of the bin mixture used by the step-1 tally. */
+static void mixture_mueller(const orc_problem *P, double mu, double Z[6])
+{
+    if (P->scat_model == 0) {
+        orc_rayleigh(mu, Z);
+        return;
+    }
+    double wsum = 0.0;
+    for (int k = 0; k < P->n_bins; ++k) wsum += P->bin_weight[k];
+    for (int e = 0; e < 6; ++e) Z[e] = 0.0;
+    for (int k = 0; k < P->n_bins; ++k) {
+        double Pk[6];
+        table_mueller(P->mueller + (size_t)k * P->n_theta * 6, P->n_theta, mu, Pk);
+        for (int e = 0; e < 6; ++e) Z[e] += P->bin_weight[k] / wsum * Pk[e];
+    }
+}
+
+/* Extinction elements alpha1..3 at grain-frame polar angle theta', linear in theta'. */
+static void kext_eval(const orc_problem *P, double thetap, double al[3])
+{
+    double x = thetap / M_PI * (P->n_ktheta - 1);
+    int j = (int)floor(x);
+    if (j > P->n_ktheta - 2) j = P->n_ktheta - 2;
+    if (j < 0) j = 0;
+    double f = x - j;
+    for (int e = 0; e < 3; ++e) al[e] = (1.0 - f) * P->kext[j * 3 + e] + f * P->kext[(j + 1) * 3 + e];
+}
+
+/* Average of alpha1 over the sphere, 1/2 int alpha1(theta') sin theta' dtheta',
+ * integrating the linear interpolant exactly on each interval. */
+static double kext_alpha1_mean(const orc_problem *P)
+{
+    double h = M_PI / (P->n_ktheta - 1), s = 0.0;
+    for (int j = 0; j + 1 < P->n_ktheta; ++j) {
+        double ta = j * h, tb = (j + 1) * h;
+        double A = P->kext[j * 3], B = (P->kext[(j + 1) * 3] - A) / h;
+        s += A * (cos(ta) - cos(tb)) + B * (-(tb - ta) * cos(tb) + sin(tb) - sin(ta));
+    }
+    return 0.5 * s;
+}
+
+/* Apply a scattering matrix Z (block form) for the scattering n -> n2 to X given
+ * in the Stokes basis of n; the result is in the Stokes basis of n2.  The
+ * scattering plane basis is e_perp = n x n2 / |n x n2|, e_par = e_perp x n on
+ * the incident side and e_perp x n2 on the scattered side (Q = I_par - I_perp).
+ * For n2 parallel to n, e_perp is the phi-hat of n. */
+void orc_mueller_apply(const double X[4], const double n[3], const double n2[3], const double Z[6], double out[4])
+{
+    double th[3], ph[3], th2[3], ph2[3];
+    orc_stokes_basis(n, th, ph);
+    orc_stokes_basis(n2, th2, ph2);
+    double ep[3];
+    cross3(n, n2, ep);
+    double len = sqrt(dot3(ep, ep));
+    if (len <= 1e-300) {
+        ep[0] = ph[0]; ep[1] = ph[1]; ep[2] = ph[2];
+    } else {
+        ep[0] /= len; ep[1] /= len; ep[2] /= len;
+    }
+    double epar_in[3], epar_out[3];
+    cross3(ep, n, epar_in);
+    cross3(ep, n2, epar_out);
+    double Xs[4], Y[4];
+    orc_change_basis(X, th, ph, epar_in, ep, Xs);
+    Y[0] = Z[0] * Xs[0] + Z[1] * Xs[1];
+    Y[1] = Z[1] * Xs[0] + Z[2] * Xs[1];
+    Y[2] = Z[3] * Xs[2] + Z[4] * Xs[3];
+    Y[3] = -Z[4] * Xs[2] + Z[5] * Xs[3];
+    orc_change_basis(Y, epar_out, ep, th2, ph2, out);
+}
+
+/* (Z X)_0 / I for the proposal n -> n2: the polarization-aware differential
+ * cross section relative to its unpolarized value, evaluated in the
+ * scattering-plane basis. */
+static double scattered_I(const double X[4], const double n[3], const double n2[3], const double Z[6])
+{
+    double th[3], ph[3];
+    orc_stokes_basis(n, th, ph);
+    double ep[3];
+    cross3(n, n2, ep);
+    double len = sqrt(dot3(ep, ep));
+    if (len <= 1e-300) {
+        ep[0] = ph[0]; ep[1] = ph[1]; ep[2] = ph[2];
+    } else {
+        ep[0] /= len; ep[1] /= len; ep[2] /= len;
+    }
+    double epar_in[3];
+    cross3(ep, n, epar_in);
+    double Xs[4];
+    orc_change_basis(X, th, ph, epar_in, ep, Xs);
+    return Z[0] * Xs[0] + Z[1] * Xs[1];
+}
+
+/* ------------------------------------------------------------------------- */
+/* Grid and cell-to-cell traversal.                                          */
+/* ------------------------------------------------------------------------- */
+static double cell_size(const orc_problem *P, int a) { return (P->hi[a] - P->lo[a]) / P->n[a]; }
+
+/* Cell holding p for travel along n; a point on a face belongs to the cell that
+ * n points into.  Returns 0 when that cell is outside the grid. */
+static int locate(const int n3[3], const double lo[3], const double hi[3], const double p[3],
+                  const double n[3], int idx[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        double d = (hi[a] - lo[a]) / n3[a];
+        double x = (p[a] - lo[a]) / d;
+        int i = (int)floor(x);
+        if ((double)i == x && n[a] < 0.0) i -= 1;
+        idx[a] = i;
+        if (i < 0 || i >= n3[a]) return 0;
+    }
+    return 1;
+}
+
+/* Distance to the exit face of cell idx along n and the axis crossed; equal
+ * distances go to the lowest axis. */
+static double exit_distance(const int n3[3], const double lo[3], const double hi[3], const int idx[3],
+                            const double p[3], const double n[3], int *axis)
+{
+    double best = INFINITY;
+    *axis = -1;
+    for (int a = 0; a < 3; ++a) {
+        double d = (hi[a] - lo[a]) / n3[a];
+        double t;
+        if (n[a] > 0.0)
+            t = (lo[a] + (idx[a] + 1) * d - p[a]) / n[a];
+        else if (n[a] < 0.0)
+            t = (lo[a] + idx[a] * d - p[a]) / n[a];
+        else
+            continue;
+        if (t < 0.0) t = 0.0;
+        if (t < best) {
+            best = t;
+            *axis = a;
+        }
+    }
+    return best;
+}
+
+/* Move p to the exit face and step the cell index; returns 0 on leaving the grid. */
+static int cross_face(const int n3[3], const double lo[3], const double hi[3], int idx[3], double p[3],
+                      const double n[3], double ell, int axis)
+{
+    double d = (hi[axis] - lo[axis]) / n3[axis];
+    for (int a = 0; a < 3; ++a) p[a] += ell * n[a];
+    if (n[axis] > 0.0) {
+        p[axis] = lo[axis] + (idx[axis] + 1) * d;
+        idx[axis] += 1;
+    } else {
+        p[axis] = lo[axis] + idx[axis] * d;
+        idx[axis] -= 1;
+    }
+    return idx[axis] >= 0 && idx[axis] < n3[axis];
+}
+
+/* Brute list of cells and chord lengths along a ray (for the DDA pins). */
+int64_t orc_dda_walk(const int32_t n3[3], const double lo[3], const double hi[3], const double p0[3],
+                     const double n[3], int64_t max_cells, int64_t *cells, double *lengths)
+{
+    int idx[3];
+    double p[3] = {p0[0], p0[1], p0[2]};
+    if (!locate(n3, lo, hi, p, n, idx)) return 0;
+    int64_t k = 0;
+    while (k < max_cells) {
+        int axis;
+        double ell = exit_distance(n3, lo, hi, idx, p, n, &axis);
+        cells[k] = ((int64_t)idx[2] * n3[1] + idx[1]) * n3[0] + idx[0];
+        lengths[k] = ell;
+        ++k;
+        if (!cross_face(n3, lo, hi, idx, p, n, ell, axis)) break;
+    }
+    return k;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Per-cell local frame: grain quaternion, grain-meridian basis, K elements.  */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double th[3], ph[3];   /* lab Stokes basis of n */
+    double gth[3], gph[3]; /* grain-meridian basis of n, in lab coordinates */
+    double alpha[3];       /* alpha1..3 at theta' */
+    double thetap;
+} local_frame;
+
+static void cell_quaternion(const orc_problem *P, int64_t c, double q[4])
+{
+    if (!P->bfield) {
+        q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
+        return;
+    }
+    orc_grain_quaternion(P->bfield[3 * c], P->bfield[3 * c + 1], P->bfield[3 * c + 2], q);
+}
+
+static void make_local_frame(const orc_problem *P, int64_t c, const double n[3], local_frame *F)
+{
+    double q[4], nGF[3], th_g[3], ph_g[3];
+    cell_quaternion(P, c, q);
+    orc_stokes_basis(n, F->th, F->ph);
+    orc_to_grain(q, n, nGF);
+    orc_stokes_basis(nGF, th_g, ph_g);
+    orc_to_lab(q, th_g, F->gth);
+    orc_to_lab(q, ph_g, F->gph);
+    double cz = nGF[2];
+    if (cz > 1.0) cz = 1.0;
+    if (cz < -1.0) cz = -1.0;
+    F->thetap = acos(cz);
+    kext_eval(P, F->thetap, F->alpha);
+}
+
+/* Public wrapper for the frame tests: grain-meridian basis and theta'. */
+void orc_grain_meridian(const double q[4], const double n[3], double gth[3], double gph[3], double *thetap)
+{
+    double nGF[3], th_g[3], ph_g[3];
+    orc_to_grain(q, n, nGF);
+    orc_stokes_basis(nGF, th_g, ph_g);
+    orc_to_lab(q, th_g, gth);
+    orc_to_lab(q, ph_g, gph);
+    double cz = nGF[2];
+    if (cz > 1.0) cz = 1.0;
+    if (cz < -1.0) cz = -1.0;
+    *thetap = acos(cz);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tallies (compare-and-swap when several threads run).                      */
+/* ------------------------------------------------------------------------- */
+static int g_threads_shared = 0;
+
+static void add_double(double *dst, double v)
+{
+    if (!g_threads_shared) {
+        *dst += v;
+        return;
+    }
+    uint64_t *p = (uint64_t *)dst;
+    uint64_t old = __atomic_load_n(p, __ATOMIC_RELAXED);
+    for (;;) {
+        double cur;
+        memcpy(&cur, &old, 8);
+        double nv = cur + v;
+        uint64_t nb;
+        memcpy(&nb, &nv, 8);
+        if (__atomic_compare_exchange_n(p, &old, nb, 0, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) return;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Step 1: Monte-Carlo transport of one packet.                              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    const orc_problem *P;
+    orc_result *R;
+    const double *cdf;     /* thermal emission CDF over cells (unnormalised), or NULL */
+    double cdf_total;
+    double alpha1_mean;
+    double thermal_L;
+    double stats[16];
+} run_ctx;
+
+static int find_source(const orc_problem *P, int64_t pid, int64_t *first)
+{
+    int64_t start = 0;
+    for (int s = 0; s < P->n_sources; ++s) {
+        if (pid < start + P->sources[s].n_packets) {
+            *first = start;
+            return s;
+        }
+        start += P->sources[s].n_packets;
+    }
+    *first = start;
+    return -1;
+}
+
+static double source_luminosity(const run_ctx *C, int s)
+{
+    const orc_source *src = &C->P->sources[s];
+    if (src->type == 2 && src->luminosity <= 0.0) return C->thermal_L;
+    return src->luminosity;
+}
+
+static void isotropic(double u_cos, double u_phi, double n[3])
+{
+    double ct = 2.0 * u_cos - 1.0;
+    double st = sqrt(fmax(0.0, 1.0 - ct * ct));
+    double ph = 2.0 * M_PI * u_phi;
+    n[0] = st * cos(ph); n[1] = st * sin(ph); n[2] = ct;
+}
+
+/* Packet birth, event 0 (Sec. 2.2): position, direction and Stokes vector in the
+ * lab basis of n.  Slot 0 = (tau, cos theta, phi, cell), slot 1 = (x, y, z, -). */
+static int emit_packet(const run_ctx *C, int64_t pid, int s, double eps, double p[3], double n[3],
+                       double X[4], int idx[3], double *tau)
+{
+    const orc_problem *P = C->P;
+    const orc_source *src = &P->sources[s];
+    const int64_t ncell = (int64_t)P->n[0] * P->n[1] * P->n[2];
+    double u0[4], u1[4];
+    draw4(P, pid, 0, 0, u0);
+    draw4(P, pid, 0, 1, u1);
+    X[0] = eps; X[1] = X[2] = X[3] = 0.0;
+    int inside;
+    if (src->type == 0) {
+        p[0] = src->pos[0]; p[1] = src->pos[1]; p[2] = src->pos[2];
+        isotropic(u0[1], u0[2], n);
+        inside = locate(P->n, P->lo, P->hi, p, n, idx);
+    } else if (src->type == 1) {
+        p[0] = P->lo[0] + u1[0] * (P->hi[0] - P->lo[0]);
+        p[1] = P->lo[1] + u1[1] * (P->hi[1] - P->lo[1]);
+        p[2] = src->beam_dir > 0 ? P->lo[2] : P->hi[2];
+        n[0] = 0.0; n[1] = 0.0; n[2] = src->beam_dir > 0 ? 1.0 : -1.0;
+        inside = locate(P->n, P->lo, P->hi, p, n, idx);
+    } else {
+        /* thermal: first cell whose cumulative weight exceeds u * total */
+        double target = u0[3] * C->cdf_total;
+        int64_t lo = 0, hi = ncell - 1;
+        while (lo < hi) {
+            int64_t mid = lo + (hi - lo) / 2;
+            if (C->cdf[mid] > target) hi = mid; else lo = mid + 1;
+        }
+        int64_t c = lo;
+        idx[0] = (int)(c % P->n[0]);
+        idx[1] = (int)((c / P->n[0]) % P->n[1]);
+        idx[2] = (int)(c / ((int64_t)P->n[0] * P->n[1]));
+        for (int a = 0; a < 3; ++a) p[a] = P->lo[a] + (idx[a] + u1[a]) * cell_size(P, a);
+        isotropic(u0[1], u0[2], n);
+        inside = 1;
+        /* emission alpha_abs B with alpha_abs = K - omega 1 acting on (1,0,0,0), in the
+         * grain-meridian basis; weight (alpha1(theta') - omega) / (mean alpha1 - omega) */
+        local_frame F;
+        make_local_frame(P, c, n, &F);
+        double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+        double omega = (ka + ks) > 0.0 ? ks / (ka + ks) : 0.0;
+        double w = (F.alpha[0] - omega) / (C->alpha1_mean - omega);
+        double Xg[4] = {eps * w, eps * w * F.alpha[1] / (F.alpha[0] - omega), 0.0, 0.0};
+        orc_change_basis(Xg, F.gth, F.gph, F.th, F.ph, X);
+    }
+    *tau = -log(u0[0]);
+    return inside;
+}
+
+/* Rejection sampling of the polarization-aware differential cross section at
+ * scattering number n_sca (Sec. 2.2 and Sec. 3).  Trial t uses slot 1 + t.
+ * On acceptance n2 is the new direction and Y the scattered Stokes vector in the
+ * lab basis of n2, renormalised to the incident I.  Returns the number of trials,
+ * negative when no proposal was accepted within max_trials. */
+static int scatter_sample(const orc_problem *P, int64_t pid, uint32_t n_sca, int bin, const double X[4],
+                          const double n[3], const double q[4], double n2[3], double Y[4])
+{
+    const float *tab = NULL;
+    double *env_cdf = NULL, env_cdf_total = 0.0;
+    if (P->scat_model == 1) {
+        tab = P->mueller + (size_t)bin * P->n_theta * 6;
+        /* piecewise-constant envelope of P11 over [theta_j, theta_j+1] */
+        env_cdf = (double *)malloc(sizeof(double) * (P->n_theta - 1));
+        for (int j = 0; j + 1 < P->n_theta; ++j) {
+            double t0 = M_PI * j / (P->n_theta - 1), t1 = M_PI * (j + 1) / (P->n_theta - 1);
+            double env = fmax(tab[j * 6], tab[(j + 1) * 6]);
+            env_cdf_total += env * (cos(t0) - cos(t1));
+            env_cdf[j] = env_cdf_total;
+        }
+    }
+    int result = -P->max_trials;
+    for (int t = 0; t < P->max_trials; ++t) {
+        double ut[4];
+        draw4(P, pid, n_sca, (uint32_t)(1 + t), ut);
+        double Z[6], bound;
+        if (P->scat_model == 0) {
+            /* isotropic proposal in the grain frame, envelope 2 max Z11 */
+            double nGF2[3];
+            isotropic(ut[0], ut[1], nGF2);
+            orc_to_lab(q, nGF2, n2);
+            orc_rayleigh(dot3(n, n2), Z);
+            bound = ut[2] * 2.0 * (3.0 / (8.0 * M_PI)) * X[0];
+        } else {
+            int j = P->n_theta - 2;
+            for (int jj = 0; jj + 1 < P->n_theta; ++jj)
+                if (ut[0] < env_cdf[jj] / env_cdf_total) {
+                    j = jj;
+                    break;
+                }
+            double t0 = M_PI * j / (P->n_theta - 1), t1 = M_PI * (j + 1) / (P->n_theta - 1);
+            double mu = cos(t0) - ut[1] * (cos(t0) - cos(t1));
+            double sn = sqrt(fmax(0.0, 1.0 - mu * mu));
+            double az = 2.0 * M_PI * ut[2];
+            double th[3], ph[3];
+            orc_stokes_basis(n, th, ph);
+            for (int a = 0; a < 3; ++a) n2[a] = mu * n[a] + sn * (cos(az) * th[a] + sin(az) * ph[a]);
+            table_mueller(tab, P->n_theta, mu, Z);
+            double env = fmax(tab[j * 6], tab[(j + 1) * 6]);
+            bound = ut[3] * 2.0 * env * X[0];
+        }
+        if (bound < scattered_I(X, n, n2, Z)) {
+            orc_mueller_apply(X, n, n2, Z, Y);
+            double norm = X[0] / Y[0];
+            for (int e = 0; e < 4; ++e) Y[e] *= norm;
+            result = t + 1;
+            break;
+        }
+    }
+    free(env_cdf);
+    return result;
+}
+
+/* Grain bin k with probability proportional to its weight: the first k whose
+ * cumulative normalised weight exceeds u. */
+static int choose_bin(const orc_problem *P, double u)
+{
+    if (P->scat_model != 1) return 0;
+    double wsum = 0.0, acc = 0.0;
+    for (int k = 0; k < P->n_bins; ++k) wsum += P->bin_weight[k];
+    for (int k = 0; k < P->n_bins; ++k) {
+        acc += P->bin_weight[k];
+        if (u < acc / wsum) return k;
+    }
+    return P->n_bins - 1;
+}
+
+static void transport_packet(run_ctx *C, int64_t pid)
+{
+    const orc_problem *P = C->P;
+    orc_result *R = C->R;
+    int64_t first;
+    int s = find_source(P, pid, &first);
+    if (s < 0) return;
+    const orc_source *src = &P->sources[s];
+    double eps = source_luminosity(C, s) / (double)src->n_packets;
+
+    double p[3], n[3], X[4], tau_rem;
+    int idx[3];
+    int inside = emit_packet(C, pid, s, eps, p, n, X, idx, &tau_rem);
+    double I_birth = X[0];
+    C->stats[ST_EMITTED_E] += X[0];
+    C->stats[ST_EMITTED_N] += 1.0;
+    C->stats[ST_EVENTS] += 1.0;
+
+    int64_t n_seg = 0, n_sca = 0, events = 1;
+    int flag = 0; /* 1 escaped, 2 roulette, 3 event cap, 4 trial cap */
+    if (!inside) flag = 1;
+
+    while (!flag) {
+        if (events >= P->max_events) {
+            flag = 3;
+            break;
+        }
+        int64_t c = ((int64_t)idx[2] * P->n[1] + idx[1]) * P->n[0] + idx[0];
+        double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+        double kext = ka + ks;
+        double omega = kext > 0.0 ? ks / kext : 0.0;
+        int axis;
+        double ell_exit = exit_distance(P->n, P->lo, P->hi, idx, p, n, &axis);
+        double dtau_sca_exit = ks * ell_exit;
+        int scatter_here = (ks > 0.0 && tau_rem < dtau_sca_exit);
+        double ell = scatter_here ? tau_rem / ks : ell_exit;
+
+        /* ---- extinction, absorption and the step-1 tally over the segment ---- */
+        if (kext > 0.0) {
+            local_frame F;
+            make_local_frame(P, c, n, &F);
+            double dtau = kext * ell;
+            double a = F.alpha[0] - omega;
+            double Xg[4], Yg[4], Wg[4], Y[4];
+            orc_change_basis(X, F.th, F.ph, F.gth, F.gph, Xg);
+            orc_attenuate(Xg, a, F.alpha[1], F.alpha[2], dtau, Yg);
+            orc_change_basis(Yg, F.gth, F.gph, F.th, F.ph, Y);
+            double dI = X[0] - Y[0];
+            if (ks > 0.0 && P->n_cam > 0) {
+                double W[4];
+                orc_segment_integral(Xg, a, F.alpha[1], F.alpha[2], dtau, Wg);
+                for (int e = 0; e < 4; ++e) Wg[e] /= kext;
+                orc_change_basis(Wg, F.gth, F.gph, F.th, F.ph, W);
+                for (int k = 0; k < P->n_cam; ++k) {
+                    double Z[6], Sc[4];
+                    mixture_mueller(P, dot3(n, P->cams[k].dir), Z);
+                    /* eq. (scat-disc-sum): Z(Omega_cam; Omega_pp) applied to the path
+                     * integral of I_pp, in the Stokes basis of Omega_cam */
+                    orc_mueller_apply(W, n, P->cams[k].dir, Z, Sc);
+                    for (int e = 0; e < 4; ++e) add_double(&R->S[((size_t)c * P->n_cam + k) * 4 + e], Sc[e]);
+                }
+            }
+            if (dI != 0.0) {
+                add_double(&R->absorbed[c], dI);
+                C->stats[ST_ABSORBED_E] += dI;
+            }
+            for (int e = 0; e < 4; ++e) X[e] = Y[e];
+        }
+        n_seg++;
+        events++;
+        C->stats[ST_SEGMENTS] += 1.0;
+        C->stats[ST_EVENTS] += 1.0;
+
+        if (!scatter_here) {
+            tau_rem -= dtau_sca_exit;
+            if (!cross_face(P->n, P->lo, P->hi, idx, p, n, ell_exit, axis)) {
+                flag = 1;
+                break;
+            }
+            continue;
+        }
+
+        /* ---- scattering event: the packet stays in cell idx ---- */
+        for (int a = 0; a < 3; ++a) p[a] += ell * n[a];
+        n_sca++;
+        events++;
+        C->stats[ST_SCATTERS] += 1.0;
+        C->stats[ST_EVENTS] += 1.0;
+        double us[4];
+        draw4(P, pid, (uint32_t)n_sca, 0, us);
+        if (P->roulette_threshold > 0.0 && X[0] < P->roulette_threshold * I_birth) {
+            if (us[1] < P->roulette_survival) {
+                double g = 1.0 / P->roulette_survival;
+                C->stats[ST_ROULETTE_GAIN] += X[0] * (g - 1.0);
+                for (int e = 0; e < 4; ++e) X[e] *= g;
+            } else {
+                C->stats[ST_ROULETTE_LOST] += X[0];
+                flag = 2;
+                break;
+            }
+        }
+        double q[4], n2[3], Y[4];
+        cell_quaternion(P, c, q);
+        int trials = scatter_sample(P, pid, (uint32_t)n_sca, choose_bin(P, us[2]), X, n, q, n2, Y);
+        C->stats[ST_TRIALS] += (double)(trials > 0 ? trials : -trials);
+        if (trials < 0) {
+            flag = 4;
+            break;
+        }
+        for (int e = 0; e < 4; ++e) X[e] = Y[e];
+        for (int a = 0; a < 3; ++a) n[a] = n2[a];
+        tau_rem = -log(us[0]);
+    }
+
+    if (flag == 1) {
+        C->stats[ST_ESCAPED_E] += X[0];
+        C->stats[ST_ESCAPED_N] += 1.0;
+    } else if (flag == 2) {
+        C->stats[ST_KILLED_N] += 1.0;
+    } else if (flag == 3 || flag == 4) {
+        C->stats[ST_CAP_LOST] += X[0];
+        C->stats[ST_CAP_N] += 1.0;
+    }
+    if (R->trace && pid < P->n_trace) {
+        double *tr = R->trace + (size_t)pid * 16;
+        tr[0] = X[0]; tr[1] = X[1]; tr[2] = X[2]; tr[3] = X[3];
+        tr[4] = p[0]; tr[5] = p[1]; tr[6] = p[2];
+        tr[7] = n[0]; tr[8] = n[1]; tr[9] = n[2];
+        tr[10] = (double)n_sca; tr[11] = (double)n_seg; tr[12] = (double)flag;
+        tr[13] = I_birth; tr[14] = (double)s; tr[15] = (double)events;
+    }
+}
+
+typedef struct {
+    run_ctx *C;
+    int64_t b, e;
+} thread_arg;
+
+static void *thread_main(void *arg)
+{
+    thread_arg *A = (thread_arg *)arg;
+    for (int64_t pid = A->b; pid < A->e; ++pid) transport_packet(A->C, pid);
+    return NULL;
+}
+
+/* Thermal source set-up: cell weights kappa_ext (mean alpha1 - omega) B V and the
+ * luminosity 4 pi sum of them. */
+static int thermal_setup(run_ctx *C)
+{
+    const orc_problem *P = C->P;
+    int need = 0;
+    for (int s = 0; s < P->n_sources; ++s)
+        if (P->sources[s].type == 2) need = 1;
+    C->alpha1_mean = kext_alpha1_mean(P);
+    if (!need) return 0;
+    if (!P->emissivity) return -1;
+    const int64_t ncell = (int64_t)P->n[0] * P->n[1] * P->n[2];
+    const double V = cell_size(P, 0) * cell_size(P, 1) * cell_size(P, 2);
+    double *cdf = (double *)malloc(sizeof(double) * ncell);
+    double acc = 0.0;
+    for (int64_t c = 0; c < ncell; ++c) {
+        double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+        double kext = ka + ks;
+        double omega = kext > 0.0 ? ks / kext : 0.0;
+        double w = kext * (C->alpha1_mean - omega) * P->emissivity[c] * V;
+        if (w < 0.0) w = 0.0;
+        acc += w;
+        cdf[c] = acc;
+    }
+    C->cdf = cdf;
+    C->cdf_total = acc;
+    C->thermal_L = 4.0 * M_PI * acc;
+    return 0;
+}
+
+double orc_thermal_luminosity(const orc_problem *P)
+{
+    run_ctx C;
+    memset(&C, 0, sizeof C);
+    C.P = P;
+    if (thermal_setup(&C) != 0) return -1.0;
+    free((void *)C.cdf);
+    return C.thermal_L;
+}
+
+int orc_transport(const orc_problem *P, orc_result *R)
+{
+    if (P->n_cam > 64) return -1;
+    run_ctx C;
+    memset(&C, 0, sizeof C);
+    C.P = P;
+    C.R = R;
+    if (thermal_setup(&C) != 0) return -2;
+    int nt = P->n_threads > 0 ? P->n_threads : 1;
+    int64_t total = P->pid_end - P->pid_begin;
+    if (nt > total) nt = total > 0 ? (int)total : 1;
+    if (nt == 1) {
+        g_threads_shared = 0;
+        for (int64_t pid = P->pid_begin; pid < P->pid_end; ++pid) transport_packet(&C, pid);
+        memcpy(R->stats, C.stats, sizeof C.stats);
+    } else {
+        g_threads_shared = 1;
+        pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nt);
+        thread_arg *A = (thread_arg *)malloc(sizeof(thread_arg) * nt);
+        run_ctx *Cs = (run_ctx *)malloc(sizeof(run_ctx) * nt);
+        for (int t = 0; t < nt; ++t) {
+            Cs[t] = C;
+            A[t].C = &Cs[t];
+            A[t].b = P->pid_begin + total * t / nt;
+            A[t].e = P->pid_begin + total * (t + 1) / nt;
+            pthread_create(&th[t], NULL, thread_main, &A[t]);
+        }
+        memset(R->stats, 0, sizeof R->stats);
+        for (int t = 0; t < nt; ++t) {
+            pthread_join(th[t], NULL);
+            for (int k = 0; k < 16; ++k) R->stats[k] += Cs[t].stats[k];
+        }
+        g_threads_shared = 0;
+        free(th);
+        free(A);
+        free(Cs);
+    }
+    free((void *)C.cdf);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Step 2: deterministic ray-march toward the camera (Sec. 2.3, App. A).     */
+/* ------------------------------------------------------------------------- */
+
+/* S is the step-1 tally [ncell][n_cam][4]; scale_S multiplies it (1 / number of
+ * packet batches or similar, normally 1).  out is [4][ny][nx]. */
+int orc_image(const orc_problem *P, const double *S, int cam, double scale_S, double *out)
+{
+    const orc_camera *K = &P->cams[cam];
+    const int64_t ncell = (int64_t)P->n[0] * P->n[1] * P->n[2];
+    (void)ncell;
+    const double V = cell_size(P, 0) * cell_size(P, 1) * cell_size(P, 2);
+    double Om[3] = {K->dir[0], K->dir[1], K->dir[2]};
+    double cth[3], cph[3];
+    orc_stokes_basis(Om, cth, cph);
+    double ex[3] = {cph[0], cph[1], cph[2]};
+    double ey[3] = {-cth[0], -cth[1], -cth[2]};
+    const int nx = K->npix[0], ny = K->npix[1];
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double a = ((i + 0.5) / nx - 0.5) * K->fov[0];
+            double b = ((j + 0.5) / ny - 0.5) * K->fov[1];
+            double o[3];
+            for (int d = 0; d < 3; ++d) o[d] = K->center[d] + a * ex[d] + b * ey[d];
+            /* entry and exit of the box along Om */
+            double tin = -INFINITY, tout = INFINITY;
+            int miss = 0;
+            for (int d = 0; d < 3; ++d) {
+                if (Om[d] != 0.0) {
+                    double t1 = (P->lo[d] - o[d]) / Om[d], t2 = (P->hi[d] - o[d]) / Om[d];
+                    if (t1 > t2) { double tt = t1; t1 = t2; t2 = tt; }
+                    if (t1 > tin) tin = t1;
+                    if (t2 < tout) tout = t2;
+                } else if (o[d] < P->lo[d] || o[d] > P->hi[d]) {
+                    miss = 1;
+                }
+            }
+            double X[4] = {0.0, 0.0, 0.0, 0.0};
+            if (!miss && tin < tout) {
+                double p[3];
+                int idx[3];
+                for (int d = 0; d < 3; ++d) p[d] = o[d] + tin * Om[d];
+                for (int d = 0; d < 3; ++d) {
+                    double dd = cell_size(P, d);
+                    double x = (p[d] - P->lo[d]) / dd;
+                    int ii = (int)floor(x);
+                    if ((double)ii == x && Om[d] < 0.0) ii -= 1;
+                    if (ii < 0) ii = 0;
+                    if (ii >= P->n[d]) ii = P->n[d] - 1;
+                    idx[d] = ii;
+                }
+                for (;;) {
+                    int axis;
+                    double ell = exit_distance(P->n, P->lo, P->hi, idx, p, Om, &axis);
+                    int64_t c = ((int64_t)idx[2] * P->n[1] + idx[1]) * P->n[0] + idx[0];
+                    double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+                    double kext = ka + ks;
+                    if (kext > 0.0 && ell > 0.0) {
+                        double omega = ks / kext;
+                        local_frame F;
+                        make_local_frame(P, c, Om, &F);
+                        double Bc = P->emissivity ? P->emissivity[c] : 0.0;
+                        double Sg[4] = {(F.alpha[0] - omega) * Bc, F.alpha[1] * Bc, 0.0, 0.0};
+                        if (S && ks > 0.0) {
+                            double Sc[4], Sgs[4];
+                            for (int e = 0; e < 4; ++e)
+                                Sc[e] = scale_S * omega / V * S[((size_t)c * P->n_cam + cam) * 4 + e];
+                            orc_change_basis(Sc, F.th, F.ph, F.gth, F.gph, Sgs);
+                            for (int e = 0; e < 4; ++e) Sg[e] += Sgs[e];
+                        }
+                        double Xg[4], Yg[4];
+                        orc_change_basis(X, F.th, F.ph, F.gth, F.gph, Xg);
+                        orc_cell_solution(Xg, F.alpha[0], F.alpha[1], F.alpha[2], Sg, kext * ell, Yg);
+                        orc_change_basis(Yg, F.gth, F.gph, F.th, F.ph, X);
+                    }
+                    if (!cross_face(P->n, P->lo, P->hi, idx, p, Om, ell, axis)) break;
+                }
+            }
+            for (int e = 0; e < 4; ++e) out[((size_t)e * ny + j) * nx + i] = X[e];
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exported pieces for the tests.                                            */
+/* ------------------------------------------------------------------------- */
+
+/* Birth of packet pid: out = [x,y,z, nx,ny,nz, I,Q,U,V, tau, inside, source]. */
+int orc_emit(const orc_problem *P, int64_t pid, double out[13])
+{
+    run_ctx C;
+    memset(&C, 0, sizeof C);
+    C.P = P;
+    if (thermal_setup(&C) != 0) return -2;
+    int64_t first;
+    int s = find_source(P, pid, &first);
+    if (s < 0) {
+        free((void *)C.cdf);
+        return -1;
+    }
+    double eps = source_luminosity(&C, s) / (double)P->sources[s].n_packets;
+    double p[3], n[3], X[4], tau;
+    int idx[3];
+    int inside = emit_packet(&C, pid, s, eps, p, n, X, idx, &tau);
+    for (int a = 0; a < 3; ++a) { out[a] = p[a]; out[3 + a] = n[a]; }
+    for (int e = 0; e < 4; ++e) out[6 + e] = X[e];
+    out[10] = tau; out[11] = inside; out[12] = s;
+    free((void *)C.cdf);
+    return 0;
+}
+
+/* One scattering of packet pid at scattering number n_sca with cell quaternion q:
+ * out = [n2x,n2y,n2z, I,Q,U,V]; returns the trial count (negative: no acceptance). */
+int orc_scatter(const orc_problem *P, int64_t pid, uint32_t n_sca, int bin, const double X[4],
+                const double n[3], const double q[4], double out[7])
+{
+    double n2[3], Y[4];
+    int t = scatter_sample(P, pid, n_sca, bin, X, n, q, n2, Y);
+    for (int a = 0; a < 3; ++a) out[a] = n2[a];
+    for (int e = 0; e < 4; ++e) out[3 + e] = Y[e];
+    return t;
+}

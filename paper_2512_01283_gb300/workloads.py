@@ -1,0 +1,225 @@
+"""Seeded synthetic inputs for the transport: grids, field directions, grain optics
+tables, sources and cameras.
+
+This module only builds input arrays (numpy, FP32 fields, FP64 geometry).  It holds
+none of the transport or imaging arithmetic, and is the one module that both the CPU
+oracle's tests and the CUDA path draw their inputs from.
+
+Workloads (sizes as stated):
+  rayleigh_sphere   uniform sphere of radius 1 on a 32^3 grid over [-1,1]^3, radial
+                    optical depth 1, albedo 1, dipole (Rayleigh) grains, central
+                    isotropic unpolarized point source, 1e5 packets, one 64^2 camera.
+  dichroic_slab     aligned-grain slab on a 64^3 grid over [0,1]^3, uniform field at
+                    45 deg to the line of sight, alpha2/alpha1 = -0.05, alpha3 = 0,
+                    no scattering, plane beam along +z, 1e6 packets.
+  disk              flared disk on a 192^3 grid over [-1,1]^3: rho ~ (R/R0)^-1
+                    exp(-z^2/2H^2), H/R = 0.1 (R/R0)^0.25, inner radius 0.1, outer 1,
+                    midplane radial optical depth 1e3; toroidal+poloidal field with a
+                    30 deg pitch; 8 grain-size bins of tabulated scattering matrices
+                    (181 angles); star plus thermal emission; 8 cameras at 256^2.
+  twisted_slab      slab with a field rotating by 2 pi per unit optical depth (the
+                    twisted-field test of Sec. 3.2).
+
+The grain tables are synthetic (no measured optical constants are available): per bin
+a Henyey-Greenstein P11, P12/P11 = -p (1-c^2)/(1+c^2), P22 = P11,
+P33/P11 = P44/P11 = 2c/(1+c^2), P34 = 0, which is a realizable scattering matrix for
+0 <= p <= 1.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+N_THETA = 181
+
+
+def _centres(n, lo, hi):
+    d = (hi - lo) / n
+    return lo + (np.arange(n) + 0.5) * d
+
+
+def cell_centres(shape_zyx, lo, hi):
+    nz, ny, nx = shape_zyx
+    z = _centres(nz, lo[2], hi[2])[:, None, None]
+    y = _centres(ny, lo[1], hi[1])[None, :, None]
+    x = _centres(nx, lo[0], hi[0])[None, None, :]
+    return x, y, z
+
+
+# ----------------------------------------------------------------------------------
+# grain optics inputs
+# ----------------------------------------------------------------------------------
+def kext_isotropic():
+    """alpha1 = 1, alpha2 = alpha3 = 0 on theta' in [0, pi] (spherical grains)."""
+    return np.array([[1.0, 0.0, 0.0], [1.0, 0.0, 0.0]], dtype=np.float32)
+
+
+def kext_constant(alpha2, alpha3=0.0):
+    return np.array([[1.0, alpha2, alpha3], [1.0, alpha2, alpha3]], dtype=np.float32)
+
+
+def kext_dipole(p_max, alpha3_over_alpha2=0.0, n=N_THETA):
+    """alpha1 = 1, alpha2 = -p_max sin^2 theta', alpha3 = ratio * alpha2."""
+    t = np.linspace(0.0, math.pi, n)
+    a2 = -p_max * np.sin(t) ** 2
+    return np.stack([np.ones(n), a2, alpha3_over_alpha2 * a2], axis=1).astype(np.float32)
+
+
+def _interp_norm(p11, n_theta):
+    """2 pi int P11(theta) sin(theta) dtheta of the interpolant linear in theta."""
+    h = math.pi / (n_theta - 1)
+    ta = np.arange(n_theta - 1) * h
+    tb = ta + h
+    A = p11[:-1]
+    B = (p11[1:] - p11[:-1]) / h
+    return 2 * math.pi * np.sum(A * (np.cos(ta) - np.cos(tb)) + B * (-(tb - ta) * np.cos(tb) + np.sin(tb) - np.sin(ta)))
+
+
+def synthetic_bins(n_bins=8, n_theta=N_THETA):
+    """Per-bin scattering tables [n_bins][n_theta][6] (P11,P12,P22,P33,P34,P44),
+    normalised so that the theta-linear interpolant of P11 integrates to 1 over the
+    sphere, and the bin weights (fractions of the scattering cross section)."""
+    x = np.logspace(-1, 1, n_bins)
+    g = np.linspace(0.0, 0.8, n_bins)
+    p = np.linspace(1.0, 0.3, n_bins)
+    th = np.linspace(0.0, math.pi, n_theta)
+    c = np.cos(th)
+    tabs = np.zeros((n_bins, n_theta, 6))
+    for k in range(n_bins):
+        p11 = (1 - g[k] ** 2) / (4 * math.pi * (1 + g[k] ** 2 - 2 * g[k] * c) ** 1.5)
+        p11 = p11 / _interp_norm(p11, n_theta)
+        tabs[k, :, 0] = p11
+        tabs[k, :, 1] = -p[k] * (1 - c * c) / (1 + c * c) * p11
+        tabs[k, :, 2] = p11
+        tabs[k, :, 3] = 2 * c / (1 + c * c) * p11
+        tabs[k, :, 4] = 0.0
+        tabs[k, :, 5] = 2 * c / (1 + c * c) * p11
+    w = np.sqrt(x)
+    w = w / w.sum()
+    return tabs.astype(np.float32), w.astype(np.float32), x
+
+
+def rayleigh_optics():
+    return {"model": "rayleigh", "kext": kext_isotropic()}
+
+
+def table_optics(n_bins=8, p_max=0.05):
+    tabs, w, _ = synthetic_bins(n_bins)
+    return {"model": "table", "mueller": tabs, "bin_weight": w, "kext": kext_dipole(p_max)}
+
+
+# ----------------------------------------------------------------------------------
+# cameras
+# ----------------------------------------------------------------------------------
+def camera(direction, npix, fov, center=None):
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    cam = {"dir": tuple(float(v) for v in d), "npix": (int(npix[0]), int(npix[1])),
+           "fov": (float(fov[0]), float(fov[1]))}
+    if center is not None:
+        cam["center"] = tuple(float(v) for v in center)
+    return cam
+
+
+def inclination_cameras(n_cam=8, npix=256, fov=2.0):
+    """Cameras at inclinations linspace(0, 90 deg, n_cam), azimuth 0."""
+    cams = []
+    for i in np.linspace(0.0, math.pi / 2, n_cam):
+        cams.append(camera((math.sin(i), 0.0, math.cos(i)), (npix, npix), (fov, fov)))
+    return cams
+
+
+# ----------------------------------------------------------------------------------
+# models
+# ----------------------------------------------------------------------------------
+def rayleigh_sphere(n=32, tau=1.0, radius=1.0, bfield=None):
+    """Uniform Rayleigh sphere: kappa_ext = tau/radius where the cell centre lies
+    within ``radius`` of the origin, albedo 1."""
+    lo, hi = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    x, y, z = cell_centres((n, n, n), lo, hi)
+    r = np.sqrt(x * x + y * y + z * z)
+    ks = np.where(r <= radius, tau / radius, 0.0).astype(np.float32)
+    model = {"lo": lo, "hi": hi, "kappa_abs": np.zeros_like(ks), "kappa_sca": ks,
+             "bfield": bfield, "emissivity": None, "optics": rayleigh_optics()}
+    return model
+
+
+def rayleigh_sphere_run(n_packets=100000, seed=0, npix=64):
+    return {"sources": [{"type": "point", "pos": (0.0, 0.0, 0.0), "luminosity": 1.0, "n_packets": n_packets}],
+            "cameras": [camera((1.0, 0.0, 0.0), (npix, npix), (2.0, 2.0))],
+            "seed": seed, "roulette_threshold": 1e-4, "roulette_survival": 0.1}
+
+
+def dichroic_slab(n=64, tau=1.0, p=0.05, b_angle_deg=45.0, albedo=0.0, emissivity=None):
+    """Aligned-grain slab over [0,1]^3 with uniform kappa_ext = tau and a uniform
+    field in the x-z plane at ``b_angle_deg`` from +z."""
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    kext = np.full((n, n, n), tau, dtype=np.float32)
+    a = math.radians(b_angle_deg)
+    bf = np.zeros((n, n, n, 3), dtype=np.float32)
+    bf[..., 0] = math.sin(a)
+    bf[..., 2] = math.cos(a)
+    em = None if emissivity is None else np.full((n, n, n), emissivity, dtype=np.float32)
+    return {"lo": lo, "hi": hi, "kappa_abs": (kext * (1 - albedo)).astype(np.float32),
+            "kappa_sca": (kext * albedo).astype(np.float32), "bfield": bf, "emissivity": em,
+            "optics": {"model": "rayleigh", "kext": kext_constant(-p, 0.0)}}
+
+
+def beam_run(n_packets, seed=1, direction=+1, cameras=None, roulette_threshold=0.0):
+    return {"sources": [{"type": "beam", "beam_dir": direction, "luminosity": 1.0, "n_packets": n_packets}],
+            "cameras": cameras or [], "seed": seed, "roulette_threshold": roulette_threshold,
+            "roulette_survival": 0.1}
+
+
+def twisted_slab(tau, p0=0.01, nz_per_tau=200, nxy=2, coupling=True):
+    """Slab of optical depth ``tau`` (kappa = 1) over z in [0, tau]; the field lies
+    in the x-y plane at angle 2 pi z from +x, i.e. 2 pi tau' with tau' the optical
+    depth above the z = 0 face.  alpha2 = -p0 (field perpendicular to the beam);
+    alpha3 = -alpha2 when ``coupling`` (the artificial U-V term of Sec. 3.2)."""
+    nz = max(1, int(round(nz_per_tau * tau)))
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, float(tau))
+    z = _centres(nz, 0.0, tau)
+    bf = np.zeros((nz, nxy, nxy, 3), dtype=np.float32)
+    bf[..., 0] = np.cos(2 * math.pi * z)[:, None, None]
+    bf[..., 1] = np.sin(2 * math.pi * z)[:, None, None]
+    ka = np.ones((nz, nxy, nxy), dtype=np.float32)
+    a3 = p0 if coupling else 0.0
+    return {"lo": lo, "hi": hi, "kappa_abs": ka, "kappa_sca": np.zeros_like(ka), "bfield": bf,
+            "emissivity": None, "optics": {"model": "rayleigh", "kext": kext_constant(-p0, a3)}}
+
+
+def disk(n=192, tau_mid=1e3, r_in=0.1, r_out=1.0, albedo=0.6, pitch_deg=30.0, T0=1000.0,
+         lam_um=1.0, n_bins=8, p_max=0.05):
+    """Flared disk; see the module docstring."""
+    lo, hi = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    x, y, z = cell_centres((n, n, n), lo, hi)
+    R = np.sqrt(x * x + y * y) + 0.0 * z
+    H = 0.1 * np.maximum(R, 1e-30) ** 1.25
+    rho = np.where((R >= r_in) & (R <= r_out), np.maximum(R, 1e-30) ** -1.0 * np.exp(-z * z / (2 * H * H)), 0.0)
+    k0 = tau_mid / math.log(r_out / r_in)
+    kext = (k0 * rho).astype(np.float32)
+    ks = (albedo * kext).astype(np.float32)
+    ka = (kext - ks).astype(np.float32)
+    pitch = math.radians(pitch_deg)
+    Rs = np.maximum(R, 1e-30)
+    bf = np.zeros((n, n, n, 3), dtype=np.float32)
+    bf[..., 0] = (math.cos(pitch) * (-y / Rs)) * (R > 0)
+    bf[..., 1] = (math.cos(pitch) * (x / Rs)) * (R > 0)
+    bf[..., 2] = math.sin(pitch)
+    T = T0 * Rs ** -0.5
+    hc_k = 14387.77 / lam_um
+    em = np.where(rho > 0, 1.0 / np.expm1(np.minimum(hc_k / T, 700.0)), 0.0)
+    em = (em / max(em.max(), 1e-300)).astype(np.float32)
+    return {"lo": lo, "hi": hi, "kappa_abs": ka, "kappa_sca": ks, "bfield": bf, "emissivity": em,
+            "optics": table_optics(n_bins, p_max)}
+
+
+def disk_run(n_packets=100_000_000, seed=2, n_cam=8, npix=256, star_luminosity=1.0):
+    """Half of the packets from the star at the origin, half from thermal emission."""
+    n_star = n_packets // 2
+    return {"sources": [{"type": "point", "pos": (0.0, 0.0, 0.0), "luminosity": star_luminosity,
+                         "n_packets": n_star},
+                        {"type": "thermal", "luminosity": 0.0, "n_packets": n_packets - n_star}],
+            "cameras": inclination_cameras(n_cam, npix, 2.0), "seed": seed,
+            "roulette_threshold": 1e-4, "roulette_survival": 0.1}
