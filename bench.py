@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Throughput of the polarized Monte-Carlo transport + two-step imaging on one GB300.
+
+Workload (default): flared protoplanetary disk on a 192^3 grid, 8 grain-size bins of
+tabulated scattering matrices (181 angles), aligned grains (toroidal + poloidal field,
+30 deg pitch), star plus thermal emission, 1e8 packets per step, 8 cameras at 256^2.
+A step = step 1 (all packets emitted, transported, tallied) + step 2 (all 8 images).
+Metric: packet-events/s (emission + cell segments + scatterings), inputs resident in
+HBM.  Synthetic seeded inputs (paper_2512_01283_gb300.workloads).
+
+``--impl reference`` times the FP64 CPU oracle on bounded samples of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "packet-events/s on 1 GB300 at fixed Stokes-map error; surrogate vs table path"
+UNIT = "packet-events/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--packets", type=float, default=1e8)
+    ap.add_argument("--grid", type=int, default=192)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args):
+    return {"workload": "flared disk %d^3, 8 grain-size bins (181-angle scattering tables), aligned grains, "
+                        "star + thermal emission, %.0e packets, 8 cameras at 256^2" % (args.grid, args.packets),
+            "grid": args.grid, "packets_per_step": int(args.packets), "n_cameras": 8, "npix": 256,
+            "precision": "fp32 per-step transport math, fp64 optical-depth sum and tallies",
+            "l2": "no flush: the source tally (1.81 GB) and grid (226 MB) exceed the 129 MB L2"}
+
+
+def oracle_sample(model, run, seconds, n_threads, pid_offset=0):
+    """Oracle on growing pid samples (half star ids, half thermal ids) until about
+    ``seconds`` of wall time; returns (events, wall, packets)."""
+    from oracle import oracle as O
+
+    n_star = run["sources"][0]["n_packets"]
+    chunk, events, wall, packets = 256, 0.0, 0.0, 0
+    start = pid_offset
+    while wall < seconds:
+        for base in (start, n_star + start):
+            t0 = time.perf_counter()
+            out = O.transport(model, dict(run, pid_begin=base, pid_end=base + chunk, n_threads=n_threads,
+                                          cameras=run["cameras"]))
+            wall += time.perf_counter() - t0
+            events += out["stats"]["events"]
+            packets += chunk
+        start += chunk
+        if wall < seconds / 4:
+            chunk *= 2
+    return events, wall, packets
+
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", os.environ.get("LOCAL_RANK", "0")],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), p[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 CPU oracle timed on bounded samples of the workload."""
+    if rank != 0:
+        return
+    from paper_2512_01283_gb300 import workloads as W
+
+    model = W.disk(n=args.grid)
+    run = W.disk_run(n_packets=int(args.packets))
+    cores = os.cpu_count() or 1
+    per_step = max(2.0, 90.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for s in range(args.warmup + args.steps):
+        ev, wall, npk = oracle_sample(model, run, per_step, cores, pid_offset=s * 100000)
+        if s >= args.warmup:
+            vals.append((ev, wall, npk))
+    ev = sum(v[0] for v in vals)
+    wall = sum(v[1] for v in vals)
+    value = ev / wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d packets per step (half star, half thermal ids) of the %.0e-packet "
+                                       "workload" % (vals[0][2], args.packets)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+
+    from paper_2512_01283_gb300 import build as B
+    from paper_2512_01283_gb300 import mcrt as M
+    from paper_2512_01283_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    B.build()
+
+    model = W.disk(n=args.grid)
+    run = W.disk_run(n_packets=int(args.packets))
+    run["stream"] = rank  # independent packets per rank (weak scaling), no data-path collective
+    n_cam = len(run["cameras"])
+    npix = run["cameras"][0]["npix"]
+    mdl = M.Model(model)
+    imgs = torch.empty((n_cam, 4, npix[1], npix[0]), dtype=torch.float64, device="cuda")
+
+    def step(seed):
+        st = M.launch(mdl, dict(run, seed=seed), precision="fp32")
+        for k in range(n_cam):
+            mdl.image(k, imgs[k])
+        return st
+
+    for w in range(args.warmup):
+        step(1000 + w)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stats = []
+    clocks_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
+    os.makedirs(os.path.dirname(clocks_path), exist_ok=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(clocks_path) as cs:
+        e0.record()
+        for s in range(args.steps):
+            stats.append(step(2000 + s))
+        e1.record()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    events = sum(s["events"] for s in stats)
+    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    ev_t = torch.tensor([events], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
+    ms_max, ev_all = float(ms_t.item()), float(ev_t.item())
+    value = ev_all / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (transport): algorithmic bytes per launch /
+    # its CUDA-event duration measured inside the library on the launching stream
+    seg = sum(s["segments"] for s in stats)
+    tal = sum(s["tally_segments"] for s in stats)
+    ab = sum(s["absorb_segments"] for s in stats)
+    kms = sum(s["kernel_ms"] for s in stats)
+    alg_bytes = 32.0 * seg + 16.0 * ab + 64.0 * n_cam * tal
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / (kms * 1e-3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "transport_disk_traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("dram_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "kernel": "k_transport<float, table>", "bytes_per_segment": "32 cell + 16 absorbed RMW (if absorbing) "
+                "+ 64 x n_cam source RMW (if scattering)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
+            "roofline": roofline, "gpu_launches": args.steps * (1 + n_cam),
+            "clocks": cs.summary(),
+            "detail": {"events_per_step": events / args.steps, "segments_per_step": seg / args.steps,
+                       "scatterings_per_step": sum(s["scatterings"] for s in stats) / args.steps,
+                       "transport_ms_per_step": kms / args.steps,
+                       "imaging_ms_per_step": ms / args.steps - kms / args.steps}}
+
+    # end to end through the public API with host buffers: H2D of the model, both
+    # steps, D2H of the images, every step
+    if not args.no_e2e:
+        host_imgs = np.zeros((n_cam, 4, npix[1], npix[0]))
+        h2d = sum(np.asarray(model[k]).nbytes for k in ("kappa_abs", "kappa_sca", "bfield", "emissivity"))
+        h2d += sum(np.asarray(model["optics"][k]).nbytes for k in ("mueller", "bin_weight", "kext"))
+        d2h = host_imgs.nbytes
+        e_ev, e_t = 0.0, 0.0
+        for s in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m2 = M.Model(model)
+            st = M.launch(m2, dict(run, seed=3000 + s), precision="fp32")
+            for k in range(n_cam):
+                m2.image(k, host_imgs[k])
+            m2.close()
+            torch.cuda.synchronize()
+            e_t += time.perf_counter() - t0
+            e_ev += st["events"]
+        e_val = e_ev / e_t
+        line["e2e"] = {"value": e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        line["gpu_launches_e2e_per_step"] = 1 + n_cam + 5
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        ev, wall, npk = oracle_sample(model, run, args.cpu_seconds, cores)
+        line["cpu_baseline"] = {"value": ev / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "%d packets (first ids of the star and of the thermal halves) of the "
+                                          "%.0e-packet workload, %.1f s" % (npk, args.packets, wall)}
+    mdl.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,235 @@
+/*
+ * mcrt.h -- C ABI of the GB300 polarized Monte-Carlo radiative transfer library.
+ *
+ * The library transports photon packets that carry the full Stokes vector
+ * (I,Q,U,V) through a Cartesian grid of dust with magnetically aligned grains and
+ * tallies them into the two-step polarimetry images of Kratos-polrad
+ * (arXiv:2512.01283).  All compute runs in hand-written CUDA kernels for sm_103a;
+ * nothing falls back to the CPU.  Every function returns an mcrt_status; no C++
+ * exception crosses this boundary.
+ *
+ * Conventions shared by all calls
+ *  - Grids are C-ordered [nz][ny][nx]; cell (i,j,k) spans
+ *    [lo + (i,j,k) d, lo + (i+1,j+1,k+1) d] with d = (hi - lo) / (nx,ny,nz).
+ *  - Stokes vectors of light travelling along n are given in the basis
+ *    theta-hat = (cos t cos p, cos t sin p, -sin t), phi-hat = (-sin p, cos p, 0)
+ *    of n = (t, p) (paper Sec. 2.1); Q > 0 means polarization along theta-hat;
+ *    at the poles p = 0.
+ *  - Pointer arguments may be host or device memory (detected with
+ *    cudaPointerGetAttributes) unless stated otherwise.  Inputs are copied; the
+ *    caller keeps ownership of every buffer it passes.
+ *  - Work is queued on the stream given to mcrt_create_grid (NULL: the legacy
+ *    default stream).  Calls that return data to host memory synchronize that
+ *    stream before returning.
+ *  - Errors: a failing call returns a negative mcrt_status and leaves a message
+ *    readable with mcrt_last_error(ctx) (or mcrt_last_error(NULL) for failures
+ *    without a context); the context stays usable unless the status is
+ *    MCRT_E_CUDA from a sticky CUDA error.
+ *  - Results are deterministic for a given (seed, stream, packet ids) up to the
+ *    order of floating-point atomic additions in the tallies.
+ */
+#ifndef MCRT_H
+#define MCRT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MCRT_API __attribute__((visibility("default")))
+#else
+#define MCRT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcrt_ctx mcrt_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    MCRT_OK = 0,
+    MCRT_E_INVAL = -1,     /* bad argument; nothing was queued */
+    MCRT_E_NOMEM = -2,     /* device or host allocation failed */
+    MCRT_E_CUDA = -3,      /* a CUDA call failed; message holds cudaGetErrorString */
+    MCRT_E_EVENT_CAP = -4, /* some packets hit the per-packet event or trial cap */
+    MCRT_E_TIMEOUT = -5,   /* the launch's time budget ran out; tallies are partial */
+    MCRT_E_STATE = -6      /* call out of order (e.g. image before any launch) */
+} mcrt_status;
+
+enum { MCRT_BOUNDARY_OUTFLOW = 0 };
+enum { MCRT_SRC_POINT = 0, MCRT_SRC_BEAM = 1, MCRT_SRC_THERMAL = 2 };
+enum { MCRT_SCAT_RAYLEIGH = 0, MCRT_SCAT_TABLE = 1 };
+enum { MCRT_FP32 = 0, MCRT_FP64 = 1 };
+enum { MCRT_MAX_SOURCES = 8, MCRT_MAX_CAMERAS = 16 };
+
+/* Status bits reported in mcrt_stats.status_bits. */
+enum {
+    MCRT_STATUS_EVENT_CAP = 1u, /* a packet reached max_events */
+    MCRT_STATUS_TRIAL_CAP = 2u, /* a scattering found no accepted proposal in max_trials */
+    MCRT_STATUS_TIMEOUT = 4u    /* time budget exhausted before the packet pool */
+};
+
+/* A packet source (paper Sec. 2.2: packets are emitted, then transported). */
+typedef struct {
+    int32_t type;       /* MCRT_SRC_POINT: isotropic unpolarized point at pos.
+                           MCRT_SRC_BEAM: unpolarized plane beam entering the lo_z face
+                           along +z (beam_dir = +1) or the hi_z face along -z (-1),
+                           uniform over the face.
+                           MCRT_SRC_THERMAL: emission alpha_abs B of the grid's
+                           emissivity (eq. polarized-rt), cells drawn in proportion to
+                           kappa_ext (mean alpha1 - omega) B V, isotropic directions. */
+    int32_t beam_dir;
+    double luminosity;  /* total power of the source's packets; THERMAL: <= 0 means
+                           4 pi sum kappa_ext (mean alpha1 - omega) B V */
+    double pos[3];      /* POINT: position, inside the grid box */
+    int64_t n_packets;  /* packets of this source; sources take consecutive packet ids */
+} mcrt_source;
+
+/* A camera of the two-step imaging (paper Sec. 2.3). */
+typedef struct {
+    double dir[3];      /* Omega_cam: unit vector from the model toward the observer */
+    double center[3];   /* point of the model imaged at the image centre */
+    double fov[2];      /* image extent along e_x = phi-hat(Omega), e_y = -theta-hat(Omega) */
+    int32_t npix[2];    /* pixels along e_x, e_y */
+} mcrt_camera;
+
+/* One transport launch. */
+typedef struct {
+    int32_t n_sources;
+    const mcrt_source *sources;   /* host memory */
+    int32_t n_cameras;            /* 0..MCRT_MAX_CAMERAS; 0 skips the step-1 tally */
+    const mcrt_camera *cameras;   /* host memory */
+    uint32_t seed;                /* Philox key word 0 */
+    uint32_t stream;              /* Philox key word 1 (job index in batched launches) */
+    int32_t precision;            /* MCRT_FP32 (per-step transport math in FP32) or MCRT_FP64 */
+    int32_t accumulate;           /* 0: zero the tallies first; 1: add to the previous launch
+                                     (resume: launch the remaining packet ids) */
+    int64_t pid_begin, pid_end;   /* packet ids to run; pid_end <= 0 means all ids */
+    double roulette_threshold;    /* Russian roulette when I < threshold * I_birth at a
+                                     scattering; 0 disables */
+    double roulette_survival;     /* survival probability (weight / survival on survival) */
+    int64_t max_events;           /* per-packet event cap (emission + segments + scatterings) */
+    int32_t max_trials;           /* rejection-sampling trial cap per scattering */
+    int32_t block_size;           /* threads per block; 0 = library default */
+    int32_t blocks_per_sm;        /* resident blocks per SM of the persistent grid; 0 = max */
+    double time_budget_s;         /* > 0: stop taking new packets after this many seconds
+                                     of kernel time and return MCRT_E_TIMEOUT */
+    int64_t n_trace;              /* final state of packets with id < n_trace is written */
+    double *trace;                /* [n_trace][16]: I,Q,U,V, x,y,z, nx,ny,nz, scatterings,
+                                     segments, flag (1 escaped, 2 roulette, 3 event cap,
+                                     4 trial cap), I_birth, source, events; host or device;
+                                     nullable */
+} mcrt_launch_desc;
+
+/* Totals of a launch (FP64 sums over packets). */
+typedef struct {
+    double emitted_energy, escaped_energy, absorbed_energy;
+    double roulette_lost, roulette_gain, cap_lost;
+    double events, segments, scatterings, emitted, escaped, roulette_killed, cap_hits, trials;
+    double kernel_ms;             /* device time of the transport kernel(s) */
+    double status_bits;           /* MCRT_STATUS_* bits, as a number */
+    double tally_segments;        /* segments that added to the source tally */
+    double absorb_segments;       /* segments that added to the absorbed-energy tally */
+} mcrt_stats;
+
+/*
+ * Create a model: the grid of inverse mean free paths (eq. mfp-matrices, read per
+ * cell as in Sec. 2.2) and the grain alignment field (Sec. 2.1).
+ *   kappa_abs, kappa_sca  [nz][ny][nx] FP32, 1/length, >= 0
+ *   bfield     [nz][ny][nx][3] FP32 field direction (any norm; zero means no
+ *              alignment, q_B = 1) or NULL for none; converted once to the grain
+ *              quaternion q_B of eq. (grain-quaternion)
+ *   emissivity [nz][ny][nx] FP32 Planck function B per cell, or NULL
+ *   boundary   MCRT_BOUNDARY_OUTFLOW (packets leaving the box escape)
+ *   cuda_stream  cudaStream_t on which this context queues all its work
+ * On success *out owns device copies of the grid (32 bytes per cell).
+ * Errors: MCRT_E_INVAL for bad sizes or NULL required pointers, MCRT_E_NOMEM,
+ * MCRT_E_CUDA.
+ */
+MCRT_API mcrt_status mcrt_create_grid(mcrt_ctx **out, int32_t nx, int32_t ny, int32_t nz, const double lo[3],
+                             const double hi[3], const float *kappa_abs, const float *kappa_sca,
+                             const float *bfield, const float *emissivity, int32_t boundary,
+                             void *cuda_stream);
+
+/*
+ * Grain optics (Sec. 2.2: the Mueller matrix and cross sections are user-defined,
+ * as analytic forms or tables; App. A: extinction elements alpha_i).
+ *   model    MCRT_SCAT_RAYLEIGH: dipole scattering matrix (n_bins, mueller and
+ *            bin_weight ignored); MCRT_SCAT_TABLE: tables below.
+ *   mueller  [n_bins][n_theta][6] FP32 P11,P12,P22,P33,P34,P44 in the scattering-
+ *            plane basis, on scattering angles theta_j = pi j / (n_theta - 1),
+ *            interpolated linearly in theta, each bin normalised so that
+ *            2 pi int P11 sin(theta) dtheta = 1 (1/sr)
+ *   bin_weight [n_bins] FP32 share of the scattering cross section per bin
+ *   kext     [n_ktheta][3] FP32 alpha1, alpha2, alpha3 per unit extinction optical
+ *            depth at grain-frame angles theta'_j = pi j / (n_ktheta - 1), linear in
+ *            theta', in the grain-meridian basis; the extinction matrix is
+ *            K = [[a1,a2,0,0],[a2,a1,0,0],[0,0,a1,a3],[0,0,-a3,a1]]
+ * Limits: 2 <= n_theta <= 721, 1 <= n_bins <= 32, 2 <= n_ktheta <= 721.
+ * Errors: MCRT_E_INVAL, MCRT_E_NOMEM, MCRT_E_CUDA.
+ */
+MCRT_API mcrt_status mcrt_set_dust_tables(mcrt_ctx *ctx, int32_t model, int32_t n_bins, int32_t n_theta,
+                                 const float *mueller, const float *bin_weight, int32_t n_ktheta,
+                                 const float *kext);
+
+/*
+ * Step 1 of the two-step scheme (Sec. 2.2, 2.3): emit and transport packets,
+ * accumulating per model the absorbed energy per cell and the source tally
+ *   T_c[cell] = sum over path segments of Z(Omega_c; Omega_pp) int I_pp ds
+ * (eq. scat-disc-sum, path-integral estimator, FP64) for each camera c.
+ * With n_models > 1 the same description runs once per model in one persistent
+ * launch, model m using Philox stream desc->stream + m.
+ * out_stats (nullable, host) receives the totals summed over models after the
+ * stream has been synchronized.
+ * Errors: MCRT_E_INVAL, MCRT_E_STATE (tables not set), MCRT_E_NOMEM, MCRT_E_CUDA,
+ * MCRT_E_EVENT_CAP (results valid, some packets were cut), MCRT_E_TIMEOUT.
+ */
+MCRT_API mcrt_status mcrt_launch_packets(mcrt_ctx *const *models, int32_t n_models, const mcrt_launch_desc *desc,
+                                mcrt_stats *out_stats);
+
+/*
+ * Step 2 (Sec. 2.3, App. A): ray-march every pixel of camera `camera` of the last
+ * launch from the far side of the grid toward the observer, integrating
+ * dX/dtau = -K X + alpha_abs B + S cell by cell with S = omega / V * T_c.
+ *   out  [4][npix_y][npix_x] FP64 Stokes image (I,Q,U,V) in the basis of Omega_cam;
+ *        host or device.
+ * Errors: MCRT_E_INVAL (camera out of range), MCRT_E_STATE (no launch yet),
+ * MCRT_E_CUDA.
+ */
+MCRT_API mcrt_status mcrt_image_stokes(mcrt_ctx *ctx, int32_t camera, double *out);
+
+/*
+ * Copy the step-1 tallies of the last launch: source [ncell][n_cameras][4] FP64
+ * (length-weighted Stokes sums T_c, camera basis) and absorbed [ncell] FP64.  Either
+ * pointer may be NULL.  Host or device.
+ */
+MCRT_API mcrt_status mcrt_get_tallies(mcrt_ctx *ctx, double *source, double *absorbed);
+
+/* Release the context and its device memory; NULL is accepted. */
+MCRT_API mcrt_status mcrt_destroy(mcrt_ctx *ctx);
+
+/* Last error message of ctx, or of the calling thread's context-less calls when
+ * ctx is NULL.  Never NULL; owned by the library. */
+MCRT_API const char *mcrt_last_error(const mcrt_ctx *ctx);
+
+/*
+ * Diagnostics: evaluate one device building block on n inputs (host buffers),
+ * for unit tests against the CPU reference.  fn selects the block; in/out layouts:
+ *   0 Philox4x32-10: in [n][6] (ctr0..3, key0, key1 as doubles) -> out [n][4]
+ *   1 grain quaternion rotation: in [n][7] (bx,by,bz, vx,vy,vz, unused) ->
+ *     out [n][8] (q0..q3, v in the grain frame)
+ *   2 eta rotation into the grain-meridian basis: in [n][10] (bx,by,bz, nx,ny,nz,
+ *     I,Q,U,V) -> out [n][6] (I,Q,U,V in that basis, cos theta', unused)
+ *   3 in-cell solution: in [n][12] (I,Q,U,V, alpha1,alpha2,alpha3, S1..S4, dtau)
+ *     -> out [n][4]
+ *   4 path integral: in [n][8] (I,Q,U,V, a, alpha2, alpha3, dtau) -> out [n][4]
+ *   5 scattering-matrix transfer: in [n][16] (I,Q,U,V, n, n2, P11,P12,P22,P33,P34,
+ *     P44) -> out [n][4] (Stokes in the basis of n2)
+ * precision selects the FP32 or FP64 instantiation.
+ */
+MCRT_API mcrt_status mcrt_unit_eval(int32_t fn, int32_t precision, int64_t n, const double *in, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCRT_H */

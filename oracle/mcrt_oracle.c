@@ -391,7 +391,9 @@ static double kext_alpha1_mean(const orc_problem *P)
  * in the Stokes basis of n; the result is in the Stokes basis of n2.  The
  * scattering plane basis is e_perp = n x n2 / |n x n2|, e_par = e_perp x n on
  * the incident side and e_perp x n2 on the scattered side (Q = I_par - I_perp).
- * For n2 parallel to n, e_perp is the phi-hat of n. */
+ * The plane is taken as undefined when sin(Theta) = |n x n2| < 1e-6; e_perp is
+ * then the phi-hat of n (for a realizable matrix the result is continuous there:
+ * P12, P34 -> 0 and P33 -> +-P11). */
 void orc_mueller_apply(const double X[4], const double n[3], const double n2[3], const double Z[6], double out[4])
 {
     double th[3], ph[3], th2[3], ph2[3];
@@ -400,7 +402,7 @@ void orc_mueller_apply(const double X[4], const double n[3], const double n2[3],
     double ep[3];
     cross3(n, n2, ep);
     double len = sqrt(dot3(ep, ep));
-    if (len <= 1e-300) {
+    if (len < 1e-6) {
         ep[0] = ph[0]; ep[1] = ph[1]; ep[2] = ph[2];
     } else {
         ep[0] /= len; ep[1] /= len; ep[2] /= len;
@@ -427,7 +429,7 @@ static double scattered_I(const double X[4], const double n[3], const double n2[
     double ep[3];
     cross3(n, n2, ep);
     double len = sqrt(dot3(ep, ep));
-    if (len <= 1e-300) {
+    if (len < 1e-6) {
         ep[0] = ph[0]; ep[1] = ph[1]; ep[2] = ph[2];
     } else {
         ep[0] /= len; ep[1] /= len; ep[2] /= len;

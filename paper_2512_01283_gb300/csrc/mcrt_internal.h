@@ -1,0 +1,101 @@
+// mcrt_internal.h -- device-side layouts shared by the translation units of the
+// library (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mcrt.h"
+
+namespace mcrt {
+
+constexpr int kMaxCams = MCRT_MAX_CAMERAS;
+constexpr int kMaxSources = MCRT_MAX_SOURCES;
+
+// Cell record, 32 bytes = one DRAM sector: q_B (float4) then
+// (kappa_abs, kappa_sca, emissivity, 0).
+struct GridDev {
+    int n[3];
+    double lo[3], hi[3], d[3];
+    long long ncell;
+    const float4* cells;  // [ncell][2]
+};
+
+struct TablesDev {
+    int model;            // MCRT_SCAT_*
+    int n_bins, n_theta, n_ktheta;
+    int k_iso;            // alpha2 = alpha3 = 0 everywhere and alpha1 constant
+    int k_const;          // alpha does not depend on theta'
+    const float4* mix;    // [n_theta][2] (P11,P12,P22,P33),(P34,P44,0,0) of the bin mixture
+    const float4* bins;   // [n_bins][n_theta][2]
+    const double* env_cdf;  // [n_bins][n_theta-1] normalised cumulative envelope weights
+    const float* env;     // [n_bins][n_theta-1] envelope max(P11_j, P11_j+1)
+    const double* bin_cdf;  // [n_bins] normalised cumulative bin weights
+    const float4* kext;   // [n_ktheta] (alpha1, alpha2, alpha3, 0)
+    double alpha1_mean;
+};
+
+struct SourceDev {
+    int type, beam_dir;
+    long long start, count;
+    double eps;  // energy per packet
+    double pos[3];
+};
+
+struct CameraDev {
+    double dir[3], th[3], ph[3];
+};
+
+struct TransportParams {
+    GridDev g;
+    TablesDev t;
+    int n_src;
+    SourceDev src[kMaxSources];
+    int n_cam;
+    CameraDev cam[kMaxCams];
+    const double* thermal_cdf;  // [ncell] inclusive cumulative emission weights
+    double thermal_total;
+    double* S;         // [ncell][n_cam][4]
+    double* absorbed;  // [ncell]
+    unsigned seed, stream;
+    long long pid_begin, pid_end;
+    double roulette_thr, roulette_surv;
+    long long max_events;
+    int max_trials;
+    double time_budget_ns;  // <= 0: none
+    unsigned long long* counter;  // next packet index (relative to pid_begin)
+    double* stats;  // [6] FP64 energy sums, then [10] u64 counters
+    unsigned* status;
+    double* trace;
+    long long n_trace;
+};
+
+struct ImageParams {
+    GridDev g;
+    TablesDev t;
+    CameraDev cam;
+    double center[3], fov[2];
+    int npix[2];
+    int cam_index, n_cam;
+    const double* S;  // [ncell][n_cam][4] or nullptr
+    double* out;      // [4][ny][nx]
+};
+
+// launchers (defined in the .cu files)
+cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s);
+int transport_max_blocks_per_sm(int precision, int model, int block, size_t smem);
+size_t transport_smem_bytes(const TransportParams& p, int precision);
+cudaError_t launch_image(const ImageParams& p, int precision, cudaStream_t s);
+cudaError_t launch_setup_cells(const float* ka, const float* ks, const float* bf, const float* em, long long ncell,
+                               float4* cells, unsigned* bad, cudaStream_t s);
+cudaError_t launch_prepare_tables(int model, int n_bins, int n_theta, int n_ktheta, const float* mueller,
+                                  const float* bin_weight, const float* kext, float4* mix, float4* bins,
+                                  double* env_cdf, float* env, double* bin_cdf, float4* kext4, double* alpha1_mean,
+                                  cudaStream_t s);
+cudaError_t launch_thermal_cdf(const GridDev& g, double alpha1_mean, double* cdf, double* block_sums, int n_blocks,
+                               cudaStream_t s);
+int thermal_cdf_blocks(long long ncell);
+cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s);
+
+}  // namespace mcrt

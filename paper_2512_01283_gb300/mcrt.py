@@ -1,0 +1,265 @@
+"""Python binding of the C ABI in ``include/mcrt.h`` (ctypes; argument marshalling
+only -- every step of the transport and imaging runs in the CUDA kernels of
+``libmcrt.so``).  There is no CPU fallback: if the library is missing or no GPU is
+present the calls raise.
+
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device memory);
+torch is used only as a device-memory and stream container.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmcrt.so")
+
+MCRT_OK, MCRT_E_INVAL, MCRT_E_NOMEM, MCRT_E_CUDA, MCRT_E_EVENT_CAP, MCRT_E_TIMEOUT, MCRT_E_STATE = 0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "MCRT_OK", -1: "MCRT_E_INVAL", -2: "MCRT_E_NOMEM", -3: "MCRT_E_CUDA", -4: "MCRT_E_EVENT_CAP",
+                -5: "MCRT_E_TIMEOUT", -6: "MCRT_E_STATE"}
+SRC = {"point": 0, "beam": 1, "thermal": 2}
+SCAT = {"rayleigh": 0, "table": 1}
+PRECISION = {"fp32": 0, "fp64": 1}
+
+
+class McrtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Source(C.Structure):
+    _fields_ = [("type", C.c_int32), ("beam_dir", C.c_int32), ("luminosity", C.c_double),
+                ("pos", C.c_double * 3), ("n_packets", C.c_int64)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("dir", C.c_double * 3), ("center", C.c_double * 3), ("fov", C.c_double * 2),
+                ("npix", C.c_int32 * 2)]
+
+
+class LaunchDesc(C.Structure):
+    _fields_ = [("n_sources", C.c_int32), ("sources", C.POINTER(Source)),
+                ("n_cameras", C.c_int32), ("cameras", C.POINTER(Camera)),
+                ("seed", C.c_uint32), ("stream", C.c_uint32), ("precision", C.c_int32), ("accumulate", C.c_int32),
+                ("pid_begin", C.c_int64), ("pid_end", C.c_int64),
+                ("roulette_threshold", C.c_double), ("roulette_survival", C.c_double),
+                ("max_events", C.c_int64), ("max_trials", C.c_int32), ("block_size", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("time_budget_s", C.c_double),
+                ("n_trace", C.c_int64), ("trace", C.c_void_p)]
+
+
+STAT_FIELDS = ["emitted_energy", "escaped_energy", "absorbed_energy", "roulette_lost", "roulette_gain", "cap_lost",
+               "events", "segments", "scatterings", "emitted", "escaped", "roulette_killed", "cap_hits", "trials",
+               "kernel_ms", "status_bits", "tally_segments", "absorb_segments"]
+
+
+class Stats(C.Structure):
+    _fields_ = [(f, C.c_double) for f in STAT_FIELDS]
+
+
+_lib = None
+
+# symbols of include/mcrt.h
+SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "mcrt_image_stokes",
+           "mcrt_get_tallies", "mcrt_destroy", "mcrt_last_error", "mcrt_unit_eval"]
+
+
+def lib():
+    """Load ``libmcrt.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libmcrt.so is not built (run paper_2512_01283_gb300.build.build()); "
+                           "there is no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, dp, fp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.c_void_p
+    L.mcrt_create_grid.argtypes = [C.POINTER(C.c_void_p), i32, i32, i32, dp, dp, fp, fp, fp, fp, i32, vp]
+    L.mcrt_set_dust_tables.argtypes = [vp, i32, i32, i32, fp, fp, i32, fp]
+    L.mcrt_launch_packets.argtypes = [C.POINTER(C.c_void_p), i32, C.POINTER(LaunchDesc), C.POINTER(Stats)]
+    L.mcrt_image_stokes.argtypes = [vp, i32, vp]
+    L.mcrt_get_tallies.argtypes = [vp, vp, vp]
+    L.mcrt_destroy.argtypes = [vp]
+    L.mcrt_last_error.argtypes = [vp]
+    L.mcrt_last_error.restype = C.c_char_p
+    L.mcrt_unit_eval.argtypes = [i32, i32, i64, vp, vp]
+    for name in SYMBOLS:
+        if name != "mcrt_last_error":
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != MCRT_OK:
+        msg = lib().mcrt_last_error(ctx).decode(errors="replace")
+        raise McrtError(status, msg)
+
+
+def _ptr(a, dtype):
+    """Pointer and keep-alive object for a numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        assert a.is_contiguous(), "tensor must be contiguous"
+        return C.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    return C.c_void_p(arr.ctypes.data), arr
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class Model:
+    """A device-resident model: grid (mcrt_create_grid) plus optics (mcrt_set_dust_tables)."""
+
+    def __init__(self, model: dict, stream=None):
+        L = lib()
+        ka = model["kappa_abs"]
+        nz, ny, nx = tuple(ka.shape)
+        self.shape = (nz, ny, nx)
+        self.ncell = nx * ny * nz
+        self.center = tuple((float(a) + float(b)) / 2 for a, b in zip(model["lo"], model["hi"]))
+        keep = []
+        pk, k1 = _ptr(ka, np.float32)
+        ps, k2 = _ptr(model["kappa_sca"], np.float32)
+        pb, k3 = _ptr(model.get("bfield"), np.float32)
+        pe, k4 = _ptr(model.get("emissivity"), np.float32)
+        keep += [k1, k2, k3, k4]
+        lo = (C.c_double * 3)(*model["lo"])
+        hi = (C.c_double * 3)(*model["hi"])
+        h = C.c_void_p()
+        st = L.mcrt_create_grid(C.byref(h), nx, ny, nz, lo, hi, pk, ps, pb, pe, 0, _stream_handle(stream))
+        _check(st)
+        self.h = h
+        try:
+            self.set_optics(model["optics"])
+        except Exception:
+            self.close()
+            raise
+
+    def set_optics(self, optics: dict):
+        L = lib()
+        m = SCAT[optics["model"]]
+        pkx, kx = _ptr(optics["kext"], np.float32)
+        n_k = int(np.asarray(optics["kext"]).shape[0]) if not hasattr(optics["kext"], "is_cuda") else optics["kext"].shape[0]
+        if m == 1:
+            pm, km = _ptr(optics["mueller"], np.float32)
+            pw, kw = _ptr(optics["bin_weight"], np.float32)
+            nb, nt = optics["mueller"].shape[0], optics["mueller"].shape[1]
+        else:
+            pm = pw = None
+            nb = nt = 0
+        _check(L.mcrt_set_dust_tables(self.h, m, nb, nt, pm, pw, n_k, pkx), self.h)
+
+    def image(self, camera: int, out=None):
+        """Stokes image [4][ny][nx] (FP64) of a camera of the last launch."""
+        L = lib()
+        if out is None:
+            raise ValueError("pass out (numpy float64 [4][ny][nx] or CUDA tensor)")
+        p, keep = _ptr(out, np.float64)
+        _check(L.mcrt_image_stokes(self.h, int(camera), p), self.h)
+        return out
+
+    def tallies(self, n_cam: int):
+        L = lib()
+        S = np.zeros((self.ncell, max(1, n_cam), 4))
+        A = np.zeros(self.ncell)
+        _check(L.mcrt_get_tallies(self.h, C.c_void_p(S.ctypes.data) if n_cam > 0 else None,
+                                  C.c_void_p(A.ctypes.data)), self.h)
+        return S[:, :n_cam], A
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mcrt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_desc(run: dict, precision="fp32", trace=None, n_trace=0, default_center=(0.0, 0.0, 0.0), **kw):
+    """mcrt_launch_desc from a run dict (sources, cameras, seed, roulette...);
+    cameras without a centre image ``default_center``."""
+    keep = []
+    srcs = run["sources"]
+    sa = (Source * len(srcs))()
+    for i, s in enumerate(srcs):
+        sa[i].type = SRC[s["type"]]
+        sa[i].beam_dir = int(s.get("beam_dir", 1))
+        sa[i].luminosity = float(s.get("luminosity", 1.0))
+        sa[i].pos = (C.c_double * 3)(*s.get("pos", (0.0, 0.0, 0.0)))
+        sa[i].n_packets = int(s["n_packets"])
+    keep.append(sa)
+    cams = run.get("cameras", [])
+    ca = (Camera * max(1, len(cams)))()
+    for i, c in enumerate(cams):
+        ca[i].dir = (C.c_double * 3)(*c["dir"])
+        ca[i].center = (C.c_double * 3)(*c.get("center", default_center))
+        ca[i].fov = (C.c_double * 2)(*c["fov"])
+        ca[i].npix = (C.c_int32 * 2)(*c["npix"])
+    keep.append(ca)
+    d = LaunchDesc()
+    d.n_sources = len(srcs)
+    d.sources = sa
+    d.n_cameras = len(cams)
+    d.cameras = ca
+    d.seed = int(run.get("seed", 0)) & 0xffffffff
+    d.stream = int(run.get("stream", 0)) & 0xffffffff
+    d.precision = PRECISION[precision]
+    d.accumulate = int(kw.get("accumulate", 0))
+    d.pid_begin = int(run.get("pid_begin", 0))
+    d.pid_end = int(run.get("pid_end", 0))
+    d.roulette_threshold = float(run.get("roulette_threshold", 1e-4))
+    d.roulette_survival = float(run.get("roulette_survival", 0.1))
+    d.max_events = int(run.get("max_events", 100000))
+    d.max_trials = int(run.get("max_trials", 1000))
+    d.block_size = int(kw.get("block_size", 0))
+    d.blocks_per_sm = int(kw.get("blocks_per_sm", 0))
+    d.time_budget_s = float(kw.get("time_budget_s", 0.0))
+    if trace is not None:
+        p, k = _ptr(trace, np.float64)
+        keep.append(k)
+        d.trace = p
+        d.n_trace = int(n_trace)
+    return d, keep
+
+
+def launch(models, run: dict, precision="fp32", trace=None, n_trace=0, sync=True, raise_on_cap=True, **kw):
+    """mcrt_launch_packets over one or more Model objects; returns the stats dict
+    (with key ``status`` = returned mcrt_status)."""
+    L = lib()
+    if isinstance(models, Model):
+        models = [models]
+    arr = (C.c_void_p * len(models))(*[m.h for m in models])
+    d, keep = make_desc(run, precision, trace, n_trace, default_center=models[0].center, **kw)
+    st = Stats()
+    status = L.mcrt_launch_packets(arr, len(models), C.byref(d), C.byref(st) if sync else None)
+    if status not in (MCRT_OK, MCRT_E_EVENT_CAP, MCRT_E_TIMEOUT) or (raise_on_cap and status == MCRT_E_EVENT_CAP):
+        _check(status, None if len(models) > 1 else models[0].h)
+    out = {f: getattr(st, f) for f in STAT_FIELDS}
+    out["status"] = status
+    del keep
+    return out
+
+
+def unit_eval(fn: int, inputs, precision="fp32"):
+    """mcrt_unit_eval: evaluate a device building block on host inputs."""
+    L = lib()
+    widths_out = [4, 8, 6, 4, 4, 4]
+    a = np.ascontiguousarray(np.asarray(inputs, dtype=np.float64))
+    n = a.shape[0]
+    out = np.zeros((n, widths_out[fn]))
+    _check(L.mcrt_unit_eval(int(fn), PRECISION[precision], n, C.c_void_p(a.ctypes.data), C.c_void_p(out.ctypes.data)))
+    return out

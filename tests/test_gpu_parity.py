@@ -1,0 +1,368 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, on the same
+seeded inputs.  Needs a GB300: run with ``-m gpu``.
+
+Tolerances (stated per test): FP64 kernels agree with the oracle to rounding
+(<= 1e-9 relative on traces); FP32 kernels to 1e-4 relative per packet trace for
+>= 99.9 % of packets, 1e-3 of the total intensity on integrated image Stokes, and
+closed forms to 1e-5 relative with an absolute floor in Q/I of 64 x 2^-24 (FP32,
+one rounding per cell of a 64-cell slab) or 1e-15 (FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_01283_gb300 import build as B
+from paper_2512_01283_gb300 import mcrt as M
+from paper_2512_01283_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+RNG = np.random.default_rng(2024)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for -m gpu tests")
+    B.build()
+    M.lib()
+
+
+def rand_dirs(k):
+    v = RNG.normal(size=(k, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def gpu_run(model, run, precision="fp32", n_trace=0, **kw):
+    m = M.Model(model)
+    trace = np.zeros((max(1, n_trace), 16))
+    st = M.launch(m, run, precision=precision, trace=trace if n_trace else None, n_trace=n_trace, **kw)
+    n_cam = len(run.get("cameras", []))
+    S, A = m.tallies(n_cam)
+    imgs = []
+    for k, c in enumerate(run.get("cameras", [])):
+        out = np.zeros((4, c["npix"][1], c["npix"][0]))
+        m.image(k, out)
+        imgs.append(out)
+    m.close()
+    return {"stats": st, "trace": trace[:n_trace], "S": S, "absorbed": A, "images": imgs}
+
+
+def oracle_run(model, run, n_trace=0, images=True, n_threads=1):
+    r = dict(run)
+    r["n_trace"] = n_trace
+    r["n_threads"] = n_threads
+    out = O.transport(model, r)
+    out["images"] = [O.image(model, r, out["S"], k) for k in range(len(run.get("cameras", [])))] if images else []
+    return out
+
+
+def trace_match_fraction(tg, to, rtol):
+    """Fraction of packets whose final (I,Q,U,V) agree to rtol relative to I."""
+    I = np.abs(to[:, 0:1]) + 1e-300
+    err = np.max(np.abs(tg[:, 0:4] - to[:, 0:4]) / I, axis=1)
+    same_fate = tg[:, 12] == to[:, 12]
+    return float(np.mean((err < rtol) & same_fate))
+
+
+# ---------------------------------------------------------------------------------
+# building blocks against the oracle
+# ---------------------------------------------------------------------------------
+def test_philox_bitwise():
+    ins = RNG.integers(0, 2 ** 32, size=(4096, 6), dtype=np.uint64).astype(np.float64)
+    for prec in ("fp32", "fp64"):
+        out = M.unit_eval(0, ins, prec)
+        ref = np.array([O.philox(r[:4].astype(np.uint64), r[4:6].astype(np.uint64)) for r in ins], dtype=np.float64)
+        assert np.array_equal(out, ref)
+
+
+def test_grain_quaternion_rotation():
+    b = rand_dirs(500) * RNG.uniform(0.1, 3, size=(500, 1))
+    v = rand_dirs(500)
+    ins = np.concatenate([b, v, np.zeros((500, 1))], axis=1)
+    for prec, tol in (("fp32", 2e-6), ("fp64", 2e-7)):
+        out = M.unit_eval(1, ins, prec)
+        for r, o in zip(ins, out):
+            q = O.grain_quaternion(r[:3].astype(np.float32))
+            assert np.allclose(o[:4], q, atol=1e-7)
+            assert np.allclose(o[4:7], O.to_grain(q, r[3:6]), atol=tol)
+
+
+def test_eta_rotation_equals_projection():
+    """Signed eta of eq. (rotation-angle) applied by eq. (stokes-rotation) equals the
+    oracle's projection of the coherency matrix on the grain-meridian basis."""
+    b = rand_dirs(500)
+    n = rand_dirs(500)
+    X = np.concatenate([np.ones((500, 1)), RNG.uniform(-0.5, 0.5, (500, 3))], axis=1)
+    ins = np.concatenate([b, n, X], axis=1)
+    for prec, tol in (("fp32", 3e-6), ("fp64", 3e-7)):
+        out = M.unit_eval(2, ins, prec)
+        for r, o in zip(ins, out):
+            q = O.grain_quaternion(r[:3].astype(np.float32))
+            th, ph = O.stokes_basis(r[3:6])
+            gth, gph, tp = O.grain_meridian(q, r[3:6])
+            ref = O.change_basis(r[6:10], th, ph, gth, gph)
+            assert np.allclose(o[:4], ref, atol=tol)
+            assert abs(o[4] - math.cos(tp)) < tol
+
+
+def test_cell_solution_and_path_integral():
+    k = 400
+    a1 = RNG.uniform(0.3, 2.0, k)
+    a2 = RNG.uniform(-0.9, 0.9, k) * a1
+    a3 = RNG.uniform(-1.5, 1.5, k)
+    X = np.concatenate([np.ones((k, 1)), RNG.uniform(-0.5, 0.5, (k, 3))], axis=1)
+    S = RNG.uniform(-0.5, 1.0, (k, 4))
+    dt = 10 ** RNG.uniform(-4, 1.5, k)
+    ins = np.concatenate([X, a1[:, None], a2[:, None], a3[:, None], S, dt[:, None]], axis=1)
+    for prec, rtol in (("fp32", 2e-5), ("fp64", 1e-10)):
+        out = M.unit_eval(3, ins, prec)
+        for r, o in zip(ins, out):
+            ref = O.cell_solution(r[:4], r[4:7], r[7:11], r[11])
+            scale = 1.0 + np.abs(ref).max() + np.abs(r[7:11]).max() / r[4]
+            assert np.allclose(o, ref, atol=rtol * scale), (r, o, ref)
+    ins2 = np.concatenate([X, (a1 * 0.7)[:, None], (a2 * 0.5)[:, None], a3[:, None], dt[:, None]], axis=1)
+    for prec, rtol in (("fp32", 2e-5), ("fp64", 1e-11)):
+        out = M.unit_eval(4, ins2, prec)
+        for r, o in zip(ins2, out):
+            ref = O.segment_integral(r[:4], r[4], r[5], r[6], r[7])
+            assert np.allclose(o, ref, rtol=rtol, atol=rtol * r[7])
+
+
+def test_scattering_matrix_transfer():
+    k = 400
+    n, n2 = rand_dirs(k), rand_dirs(k)
+    n2[:5] = n[:5]          # forward, degenerate scattering plane
+    n2[5:10] = -n[5:10]     # backward
+    n[10:12] = [[0, 0, 1], [0, 0, -1]]  # poles
+    X = np.concatenate([np.ones((k, 1)), RNG.uniform(-0.5, 0.5, (k, 3))], axis=1)
+    P = np.array([O.rayleigh(float(np.dot(a, b))) for a, b in zip(n, n2)])
+    # a circular term away from Theta = 0, pi only: a realizable matrix has P34 = 0
+    # where the scattering plane is undefined
+    P[10:, 4] = RNG.uniform(-0.02, 0.02, k - 10)
+    ins = np.concatenate([X, n, n2, P], axis=1)
+    for prec, tol in (("fp32", 3e-6), ("fp64", 1e-12)):
+        out = M.unit_eval(5, ins, prec)
+        for r, o in zip(ins, out):
+            ref = O.mueller_apply(r[:4], r[4:7], r[7:10], r[10:16])
+            assert np.allclose(o, ref, atol=tol), (r, o, ref)
+
+
+# ---------------------------------------------------------------------------------
+# dichroic slab (64^3, 1e6 packets, FP32): closed forms and oracle traces
+# ---------------------------------------------------------------------------------
+@pytest.mark.parametrize("tau", [0.1, 1.0, 10.0, 30.0])
+def test_dichroic_slab_full_size(tau):
+    t, p = f32(tau), -f32(-0.05)
+    model = W.dichroic_slab(n=64, tau=tau)
+    run = W.beam_run(1_000_000, seed=1)
+    g = gpu_run(model, run, "fp32", n_trace=256)
+    st = g["stats"]
+    assert st["emitted"] == 1_000_000 and st["escaped"] == 1_000_000
+    assert st["events"] == 1_000_000 * 65
+    tr = g["trace"]
+    I = tr[:, 0] / tr[:, 13]
+    ref_I = math.exp(-t) * math.cosh(p * t)
+    assert np.allclose(I, ref_I, rtol=2e-5)
+    assert np.allclose(tr[:, 1] / tr[:, 0], math.tanh(p * t), rtol=1e-5, atol=64 * 2.0 ** -24)
+    assert np.all(np.abs(tr[:, 2:4]) <= 1e-6 * tr[:, :1])
+    assert abs(st["escaped_energy"] - ref_I) < 2e-5 * ref_I + 1e-9
+    assert abs(st["absorbed_energy"] + st["escaped_energy"] - 1.0) < 1e-5
+    o = oracle_run(model, dict(run, pid_end=256), n_trace=256, images=False)
+    assert trace_match_fraction(tr, o["trace"], 2e-5) == 1.0
+
+
+# absolute floors in Q/I: FP32 = 64 cells x 2^-24 (one rounding of Q per cell),
+# FP64 = the 1e-15 of the oracle pin
+@pytest.mark.parametrize("prec,floor", [("fp32", 64 * 2.0 ** -24), ("fp64", 1e-15)])
+@pytest.mark.parametrize("tau", [0.1, 1.0, 10.0, 30.0])
+def test_ptau_emission_imaging(tau, prec, floor):
+    """eq. (ptau) through the GPU step-2 kernel (emission source only)."""
+    t, p = f32(tau), -f32(-0.05)
+    model = W.dichroic_slab(n=64, tau=tau, emissivity=1.0)
+    run = W.beam_run(1, cameras=[W.camera((0, 0, 1), (4, 4), (0.5, 0.5))])
+    g = gpu_run(model, run, prec)
+    P = math.exp(-t) * math.sinh(p * t) / (1 - math.exp(-t) * math.cosh(p * t))
+    I, Q, U, V = g["images"][0][:, 1, 2]
+    assert abs(I - (1 - math.exp(-t) * math.cosh(p * t))) < max(1e-5 * I, floor)
+    assert abs(-Q / I - P) <= max(1e-5 * P, floor)
+    assert abs(U) <= floor and abs(V) <= floor
+
+
+# ---------------------------------------------------------------------------------
+# Rayleigh sphere (32^3, 1e5 packets)
+# ---------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def sphere_oracle():
+    model = W.rayleigh_sphere()
+    run = W.rayleigh_sphere_run(100_000, seed=0)
+    return model, run, oracle_run(model, run, n_trace=100_000)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_rayleigh_sphere_parity(sphere_oracle, prec):
+    """Per-packet Stokes traces within 1e-4 relative for >= 99.9 % of packets;
+    integrated I,Q,U,V of the image within 1e-3 of the total I; tallies."""
+    model, run, o = sphere_oracle
+    g = gpu_run(model, run, prec, n_trace=100_000)
+    frac = trace_match_fraction(g["trace"], o["trace"], 1e-4)
+    assert frac >= 0.999, frac
+    if prec == "fp64":
+        assert frac >= 0.9999
+    gi, oi = g["images"][0], o["images"][0]
+    Itot = oi[0].sum()
+    for e in range(4):
+        assert abs(gi[e].sum() - oi[e].sum()) < 1e-3 * Itot, e
+    for key in ("emitted", "escaped", "scatterings", "segments"):
+        assert abs(g["stats"][key] - o["stats"][key]) <= 2e-4 * o["stats"][key] + 2, key
+    dS = np.linalg.norm(g["S"] - o["S"]) / np.linalg.norm(o["S"])
+    assert dS < (1e-9 if prec == "fp64" else 1e-3), dS
+    assert abs(g["stats"]["escaped_energy"] - g["stats"]["emitted_energy"]) < 1e-6
+
+
+def test_rayleigh_sphere_chi2_independent_seeds(sphere_oracle):
+    """Images from independent seeds agree within Monte-Carlo error:
+    chi^2/dof < 1.2 with per-pixel sigma from 32 packet batches of each run."""
+    model, run, _ = sphere_oracle
+    nb, per = 32, 100_000 // 32
+    total = nb * per
+    mdl = M.Model(model)
+    gimgs = []
+    for b in range(nb):
+        r = dict(run, seed=7, pid_begin=b * per, pid_end=(b + 1) * per)
+        r["sources"] = [dict(run["sources"][0], n_packets=total)]
+        M.launch(mdl, r, precision="fp32")
+        out = np.zeros((4, 64, 64))
+        mdl.image(0, out)
+        gimgs.append(out * nb)
+    mdl.close()
+    oimgs = []
+    for b in range(nb):
+        r = dict(run, seed=11, pid_begin=b * per, pid_end=(b + 1) * per)
+        r["sources"] = [dict(run["sources"][0], n_packets=total)]
+        o = O.transport(model, r)
+        oimgs.append(O.image(model, r, o["S"], 0) * nb)
+    G, Oo = np.array(gimgs), np.array(oimgs)
+    for e in range(3):
+        mg, mo = G[:, e].mean(0), Oo[:, e].mean(0)
+        var = G[:, e].var(0, ddof=1) / nb + Oo[:, e].var(0, ddof=1) / nb
+        mask = var > 0
+        chi2 = np.sum((mg - mo)[mask] ** 2 / var[mask]) / mask.sum()
+        assert chi2 < 1.2, (e, chi2)
+
+
+# ---------------------------------------------------------------------------------
+# flared disk with grain tables, star + thermal emission
+# ---------------------------------------------------------------------------------
+def test_small_disk_parity():
+    model = W.disk(n=24)
+    run = W.disk_run(n_packets=20_000, n_cam=4, npix=32)
+    o = oracle_run(model, run, n_trace=20_000)
+    for prec in ("fp64", "fp32"):
+        g = gpu_run(model, run, prec, n_trace=20_000)
+        frac = trace_match_fraction(g["trace"], o["trace"], 1e-4)
+        assert frac >= (0.999 if prec == "fp64" else 0.99), (prec, frac)
+        for k in range(4):
+            Itot = o["images"][k][0].sum()
+            for e in range(4):
+                assert abs(g["images"][k][e].sum() - o["images"][k][e].sum()) < 2e-3 * Itot, (prec, k, e)
+        st = g["stats"]
+        bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
+        assert abs(bal - st["emitted_energy"]) < (1e-9 if prec == "fp64" else 1e-5) * st["emitted_energy"]
+        assert abs(st["emitted_energy"] - o["stats"]["emitted_energy"]) < 1e-6 * o["stats"]["emitted_energy"]
+
+
+def test_full_size_disk_sampled_parity():
+    """192^3 disk, 8 cameras of 256^2, in the benchmark's launch configuration:
+    the first 2000 packet ids of a 2e6-packet launch against the oracle."""
+    model = W.disk(n=192)
+    run = W.disk_run(n_packets=2_000_000)
+    n_s = 2000
+    g = gpu_run(model, run, "fp32", n_trace=n_s)
+    o = O.transport(model, dict(run, pid_end=n_s, n_trace=n_s, n_threads=8))
+    # both halves of the id range: star ids [0, 1e6) only here; thermal ids sampled below
+    frac = trace_match_fraction(g["trace"], o["trace"], 1e-4)
+    assert frac >= 0.99, frac
+    r2 = dict(run, pid_begin=1_000_000, pid_end=1_000_000 + n_s)
+    mdl = M.Model(model)
+    tr = np.zeros((1_000_000 + n_s, 16))
+    M.launch(mdl, r2, precision="fp32", trace=tr, n_trace=1_000_000 + n_s)
+    mdl.close()
+    o2 = O.transport(model, dict(r2, n_trace=1_000_000 + n_s, n_threads=8))
+    frac2 = trace_match_fraction(tr[1_000_000:], o2["trace"][1_000_000:], 1e-4)
+    assert frac2 >= 0.99, frac2
+    st = g["stats"]
+    bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
+    assert abs(bal - st["emitted_energy"]) < 1e-5 * st["emitted_energy"]
+
+
+# ---------------------------------------------------------------------------------
+# edge cases and error paths
+# ---------------------------------------------------------------------------------
+def test_empty_and_degenerate_inputs():
+    # no dust: every packet escapes unchanged after crossing the grid
+    model = W.rayleigh_sphere(n=8)
+    model["kappa_sca"][:] = 0
+    run = W.rayleigh_sphere_run(5000, npix=8)
+    g = gpu_run(model, run, "fp32", n_trace=100)
+    assert g["stats"]["escaped"] == 5000 and g["stats"]["scatterings"] == 0
+    assert np.all(g["images"][0] == 0.0)
+    # one-cell grid
+    model = W.dichroic_slab(n=1, tau=2.0)
+    g = gpu_run(model, W.beam_run(64), "fp64", n_trace=4)
+    t, p = 2.0, -f32(-0.05)
+    assert np.allclose(g["trace"][:, 0] / g["trace"][:, 13], math.exp(-t) * math.cosh(p * t), rtol=1e-12)
+    # zero packets
+    m = M.Model(W.rayleigh_sphere(n=4))
+    st = M.launch(m, W.rayleigh_sphere_run(0, npix=4))
+    assert st["emitted"] == 0
+    m.close()
+
+
+def test_ragged_packet_counts_and_resume():
+    """Odd packet counts (not multiples of a warp) and a launch split into two id
+    ranges with accumulate give the same tallies as one launch."""
+    model = W.rayleigh_sphere(n=16)
+    run = W.rayleigh_sphere_run(12_345, npix=16)
+    one = gpu_run(model, run, "fp64")
+    m = M.Model(model)
+    M.launch(m, dict(run, pid_end=5_001), precision="fp64")
+    M.launch(m, dict(run, pid_begin=5_001), precision="fp64", accumulate=1)
+    S, A = m.tallies(1)
+    m.close()
+    assert np.allclose(S, one["S"], rtol=1e-9, atol=1e-15)
+
+
+def test_invalid_arguments_are_rejected():
+    m = M.Model(W.rayleigh_sphere(n=4))
+    bad = W.rayleigh_sphere_run(10, npix=4)
+    bad["sources"][0]["pos"] = (5.0, 0.0, 0.0)
+    with pytest.raises(M.McrtError) as e:
+        M.launch(m, bad)
+    assert e.value.status == M.MCRT_E_INVAL
+    with pytest.raises(M.McrtError) as e:
+        m.image(3, np.zeros((4, 4, 4)))
+    assert e.value.status in (M.MCRT_E_STATE, M.MCRT_E_INVAL)
+    m.close()
+
+
+def test_event_cap_and_time_budget_report_status():
+    """The per-packet event cap and the launch time budget end the kernel with a
+    status the host reads; the context stays usable afterwards."""
+    model = W.rayleigh_sphere(n=32, tau=20.0)
+    m = M.Model(model)
+    run = dict(W.rayleigh_sphere_run(2000, npix=8), max_events=5)
+    st = M.launch(m, run, raise_on_cap=False)
+    assert st["status"] == M.MCRT_E_EVENT_CAP and st["cap_hits"] > 0
+    st = M.launch(m, W.rayleigh_sphere_run(5_000_000, npix=8), raise_on_cap=False, time_budget_s=1e-6)
+    assert st["status"] == M.MCRT_E_TIMEOUT and st["emitted"] < 5_000_000
+    st = M.launch(m, W.rayleigh_sphere_run(1000, npix=8))
+    assert st["status"] == M.MCRT_OK and st["emitted"] == 1000
+    m.close()
