@@ -109,7 +109,7 @@ typedef struct {
     double roulette_survival;     /* survival probability (weight / survival on survival) */
     int64_t max_events;           /* per-packet event cap (emission + segments + scatterings) */
     int32_t max_trials;           /* rejection-sampling trial cap per scattering */
-    int32_t block_size;           /* threads per block; 0 = library default */
+    int32_t block_size;           /* threads per block (multiple of 32, <= 128); 0 = 128 */
     int32_t blocks_per_sm;        /* resident blocks per SM of the persistent grid; 0 = max */
     double time_budget_s;         /* > 0: stop taking new packets after this many seconds
                                      of kernel time and return MCRT_E_TIMEOUT */

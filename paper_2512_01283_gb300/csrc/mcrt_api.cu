@@ -32,6 +32,8 @@ struct mcrt_ctx {
     // thermal emission CDF
     double* d_cdf = nullptr;
     double* d_block_sums = nullptr;
+    long long* d_guide = nullptr;
+    long long n_guide = 0;
     bool cdf_valid = false;
     double thermal_total = 0.0;
     // tallies of the last launch
@@ -340,6 +342,9 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t
         if (!ctx->d_cdf) CK(ctx, cudaMalloc(&ctx->d_cdf, (size_t)ctx->g.ncell * sizeof(double)));
         if (!ctx->d_block_sums) CK(ctx, cudaMalloc(&ctx->d_block_sums, (size_t)nb * sizeof(double)));
         CK(ctx, launch_thermal_cdf(ctx->g, ctx->t.alpha1_mean, ctx->d_cdf, ctx->d_block_sums, nb, ctx->stream));
+        ctx->n_guide = ctx->g.ncell < (1ll << 22) ? ctx->g.ncell : (1ll << 22);
+        if (!ctx->d_guide) CK(ctx, cudaMalloc(&ctx->d_guide, (size_t)(ctx->n_guide + 1) * sizeof(long long)));
+        CK(ctx, launch_thermal_guide(ctx->d_cdf, ctx->g.ncell, ctx->d_guide, ctx->n_guide, ctx->stream));
         CK(ctx, cudaMemcpyAsync(&ctx->thermal_total, ctx->d_cdf + (ctx->g.ncell - 1), sizeof(double),
                                 cudaMemcpyDeviceToHost, ctx->stream));
         CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -374,6 +379,12 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t
     P.n_cam = d->n_cameras;
     P.thermal_cdf = ctx->d_cdf;
     P.thermal_total = ctx->thermal_total;
+    P.thermal_guide = ctx->d_guide;
+    P.n_guide = ctx->n_guide;
+    for (int a = 0; a < 3; ++a) {
+        P.lo_f[a] = (float)ctx->g.lo[a];
+        P.d_f[a] = (float)ctx->g.d[a];
+    }
 
     long long pb = d->pid_begin, pe = d->pid_end <= 0 ? total : d->pid_end;
     if (pb < 0 || pe > total || pb > pe) return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad packet id range");
@@ -407,7 +418,7 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t
     P.pid_end = pe;
     P.roulette_thr = d->roulette_threshold;
     P.roulette_surv = d->roulette_survival > 0.0 ? d->roulette_survival : 1.0;
-    P.max_events = d->max_events > 0 ? d->max_events : 100000;
+    P.max_events = d->max_events > 0 ? (d->max_events < 2147483647ll ? d->max_events : 2147483647ll) : 100000;
     P.max_trials = d->max_trials > 0 ? d->max_trials : 1000;
     P.time_budget_ns = d->time_budget_s > 0.0 ? d->time_budget_s * 1e9 : 0.0;
     P.counter = reinterpret_cast<unsigned long long*>(ctx->d_work);
@@ -432,10 +443,10 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t
         P.n_trace = d->n_trace;
     }
 
-    const int block = d->block_size > 0 ? d->block_size : 256;
-    if (block % 32 != 0 || block > 256)
-        return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: block_size must be a multiple of 32, <= 256");
-    const size_t smem = transport_smem_bytes(P, d->precision);
+    const int block = d->block_size > 0 ? d->block_size : 128;
+    if (block % 32 != 0 || block > 128)
+        return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: block_size must be a multiple of 32, <= 128");
+    const size_t smem = transport_smem_bytes(P, d->precision, block);
     int bps = transport_max_blocks_per_sm(d->precision, P.t.model, block, smem);
     if (d->blocks_per_sm > 0 && d->blocks_per_sm < bps) bps = d->blocks_per_sm;
     const long long work = pe - pb;
@@ -563,6 +574,7 @@ mcrt_status mcrt_destroy(mcrt_ctx* ctx) {
     cudaFree(ctx->d_cells);
     cudaFree(ctx->d_cdf);
     cudaFree(ctx->d_block_sums);
+    cudaFree(ctx->d_guide);
     cudaFree(ctx->d_S);
     cudaFree(ctx->d_absorbed);
     cudaFree(ctx->d_work);

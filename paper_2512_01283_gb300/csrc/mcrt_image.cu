@@ -397,6 +397,34 @@ cudaError_t launch_thermal_cdf(const GridDev& g, double alpha1_mean, double* cdf
     return cudaGetLastError();
 }
 
+// guide[k] = first cell whose cumulative weight exceeds k * total / n_guide, for
+// k = 0..n_guide (binary search of the definition).
+__global__ void k_thermal_guide(const double* __restrict__ cdf, long long ncell, long long* __restrict__ guide,
+                                long long n_guide) {
+    const double total = cdf[ncell - 1];
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k <= n_guide;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double b = (double)k * total / (double)n_guide;
+        long long lo = 0, hi = ncell - 1;
+        while (lo < hi) {
+            const long long mid = lo + (hi - lo) / 2;
+            if (cdf[mid] > b)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        guide[k] = lo;
+    }
+}
+
+cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* guide, long long n_guide,
+                                 cudaStream_t s) {
+    const long long n = n_guide + 1;
+    const unsigned grid = (unsigned)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
+    k_thermal_guide<<<grid, 256, 0, s>>>(cdf, ncell, guide, n_guide);
+    return cudaGetLastError();
+}
+
 int thermal_cdf_blocks(long long ncell) { return (int)((ncell + (long long)kScanBlock * kScanItems - 1) / ((long long)kScanBlock * kScanItems)); }
 
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s) {

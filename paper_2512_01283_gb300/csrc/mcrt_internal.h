@@ -49,6 +49,7 @@ struct CameraDev {
 
 struct TransportParams {
     GridDev g;
+    float lo_f[3], d_f[3];  // FP32 copies of g.lo, g.d
     TablesDev t;
     int n_src;
     SourceDev src[kMaxSources];
@@ -56,6 +57,8 @@ struct TransportParams {
     CameraDev cam[kMaxCams];
     const double* thermal_cdf;  // [ncell] inclusive cumulative emission weights
     double thermal_total;
+    const long long* thermal_guide;  // [n_guide + 1]: first cell with cdf > k total / n_guide
+    long long n_guide;
     double* S;         // [ncell][n_cam][4]
     double* absorbed;  // [ncell]
     unsigned seed, stream;
@@ -85,7 +88,7 @@ struct ImageParams {
 // launchers (defined in the .cu files)
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s);
 int transport_max_blocks_per_sm(int precision, int model, int block, size_t smem);
-size_t transport_smem_bytes(const TransportParams& p, int precision);
+size_t transport_smem_bytes(const TransportParams& p, int precision, int block);
 cudaError_t launch_image(const ImageParams& p, int precision, cudaStream_t s);
 cudaError_t launch_setup_cells(const float* ka, const float* ks, const float* bf, const float* em, long long ncell,
                                float4* cells, unsigned* bad, cudaStream_t s);
@@ -96,6 +99,8 @@ cudaError_t launch_prepare_tables(int model, int n_bins, int n_theta, int n_kthe
 cudaError_t launch_thermal_cdf(const GridDev& g, double alpha1_mean, double* cdf, double* block_sums, int n_blocks,
                                cudaStream_t s);
 int thermal_cdf_blocks(long long ncell);
+cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* guide, long long n_guide,
+                                 cudaStream_t s);
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s);
 
 }  // namespace mcrt

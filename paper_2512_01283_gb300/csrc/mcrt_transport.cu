@@ -27,30 +27,37 @@ namespace mcrt {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kDefaultBlock = 256;
-
-template <typename T> struct Packet {
-    T p[3], n[3], X[4];
-    double tau;  // remaining scattering optical depth
-    T I_birth;
-    long long pid;
-    long long events, n_seg;
-    unsigned n_sca;
-    int idx[3];
-    int src;
-};
-
-struct LocalStats {
-    double e_emit, e_esc, e_abs, lost, gain, cap_lost;
-    unsigned long long events, seg, sca, emitted, escaped, killed, caps, trials, tally_seg, abs_seg;
-    unsigned status;
-};
+constexpr int kDefaultBlock = 128;
+// resident blocks per SM the FP32 kernels are compiled for (register budget 96);
+// shared memory (tables + 272 B of tally staging per thread) allows 5 such blocks
+#ifndef MCRT_MIN_BLOCKS
+#define MCRT_MIN_BLOCKS 5
+#endif
+// per-thread staging slot for the TMA bulk reduction of one segment's source
+// contributions: up to 8 cameras x 4 Stokes FP64 (256 B), padded to 272 B so that
+// the 16-byte stores of a warp spread over all shared-memory banks
+constexpr int kStageCams = 8;
+constexpr int kStageDoubles = 34;
 
 template <typename T> struct Smem {
     const T* cam;        // [n_cam][9]: Omega, theta-hat, phi-hat
     const float4* mix;   // [n_theta][2]
     const float4* kext;  // [n_ktheta]
+    double* stage;       // [blockDim][kStageDoubles]
 };
+
+// TMA bulk reduction (global += shared, FP64) of one thread's staging slot, and the
+// waits on this thread's bulk groups.
+__device__ __forceinline__ void bulk_reduce_add_f64(double* gdst, const double* ssrc, unsigned bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(gdst), "r"(s),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -122,30 +129,88 @@ __device__ __forceinline__ T group_sum(unsigned mask, unsigned peers, T v, unsig
     return acc;
 }
 
+// Packet state, held in registers for the packet's lifetime (scalar fields only,
+// so that nothing is indexed at run time and nothing lands in local memory).
+template <typename T> struct Packet {
+    T px, py, pz, nx, ny, nz;
+    T X0, X1, X2, X3;
+    T I_birth, e_abs, e_gain;
+    double tau;  // remaining scattering optical depth (FP64 running sum)
+    long long pid;
+    unsigned events, n_seg, n_sca, n_tally, n_abs, trials;
+    int ix, iy, iz, src;
+    float4 cq, cr;  // record of the current cell: q_B and (kappa_abs, kappa_sca, B, 0)
+};
+
+// Launch totals of one block (shared memory), folded in once per packet.
+struct BlockTotals {
+    double e[6];               // emitted, escaped, absorbed, roulette lost, roulette gain, capped
+    unsigned long long n[10];  // events, segments, scatterings, emitted, escaped, killed, capped,
+                               // trials, tally segments, absorbing segments
+    unsigned status;
+};
+
+template <typename T> __device__ __forceinline__ T g_lo(const TransportParams& P, int a);
+template <> __device__ __forceinline__ float g_lo<float>(const TransportParams& P, int a) { return P.lo_f[a]; }
+template <> __device__ __forceinline__ double g_lo<double>(const TransportParams& P, int a) { return P.g.lo[a]; }
+template <typename T> __device__ __forceinline__ T g_d(const TransportParams& P, int a);
+template <> __device__ __forceinline__ float g_d<float>(const TransportParams& P, int a) { return P.d_f[a]; }
+template <> __device__ __forceinline__ double g_d<double>(const TransportParams& P, int a) { return P.g.d[a]; }
+
+// Widening of an FP32 tally contribution to FP64 with integer operations (exact for
+// normal numbers; zero, subnormals, infinities and NaN take the plain conversion).
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)((u & 7u) << 29));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 template <typename T>
-__device__ void finish(const TransportParams& P, const Packet<T>& pk, int flag, LocalStats& st) {
+__device__ __forceinline__ void load_cell(const TransportParams& P, int ix, int iy, int iz, float4& q, float4& r) {
+    const long long c = ((long long)iz * P.g.n[1] + iy) * P.g.n[0] + ix;
+    q = __ldg(&P.g.cells[2 * c]);
+    r = __ldg(&P.g.cells[2 * c + 1]);
+}
+
+// Packet end: optional trace record, then the packet's totals into the block's.
+template <typename T>
+__device__ void finish(const TransportParams& P, const Packet<T>& pk, int flag, BlockTotals& bt) {
+    atomicAdd(&bt.e[0], (double)pk.I_birth);
+    atomicAdd(&bt.e[2], (double)pk.e_abs);
+    if (pk.e_gain != T(0)) atomicAdd(&bt.e[4], (double)pk.e_gain);
     if (flag == 1) {
-        st.e_esc += (double)pk.X[0];
-        st.escaped++;
+        atomicAdd(&bt.e[1], (double)pk.X0);
+        atomicAdd(&bt.n[4], 1ull);
     } else if (flag == 2) {
-        st.killed++;
+        atomicAdd(&bt.e[3], (double)pk.X0);
+        atomicAdd(&bt.n[5], 1ull);
     } else {
-        st.cap_lost += (double)pk.X[0];
-        st.caps++;
-        st.status |= (flag == 3) ? MCRT_STATUS_EVENT_CAP : MCRT_STATUS_TRIAL_CAP;
+        atomicAdd(&bt.e[5], (double)pk.X0);
+        atomicAdd(&bt.n[6], 1ull);
+        atomicOr(&bt.status, flag == 3 ? (unsigned)MCRT_STATUS_EVENT_CAP : (unsigned)MCRT_STATUS_TRIAL_CAP);
     }
+    atomicAdd(&bt.n[0], (unsigned long long)pk.events);
+    atomicAdd(&bt.n[1], (unsigned long long)pk.n_seg);
+    atomicAdd(&bt.n[2], (unsigned long long)pk.n_sca);
+    atomicAdd(&bt.n[3], 1ull);
+    atomicAdd(&bt.n[7], (unsigned long long)pk.trials);
+    atomicAdd(&bt.n[8], (unsigned long long)pk.n_tally);
+    atomicAdd(&bt.n[9], (unsigned long long)pk.n_abs);
     if (P.trace && pk.pid < P.n_trace) {
         double* tr = P.trace + pk.pid * 16;
-        tr[0] = pk.X[0];
-        tr[1] = pk.X[1];
-        tr[2] = pk.X[2];
-        tr[3] = pk.X[3];
-        tr[4] = pk.p[0];
-        tr[5] = pk.p[1];
-        tr[6] = pk.p[2];
-        tr[7] = pk.n[0];
-        tr[8] = pk.n[1];
-        tr[9] = pk.n[2];
+        tr[0] = pk.X0;
+        tr[1] = pk.X1;
+        tr[2] = pk.X2;
+        tr[3] = pk.X3;
+        tr[4] = pk.px;
+        tr[5] = pk.py;
+        tr[6] = pk.pz;
+        tr[7] = pk.nx;
+        tr[8] = pk.ny;
+        tr[9] = pk.nz;
         tr[10] = (double)pk.n_sca;
         tr[11] = (double)pk.n_seg;
         tr[12] = (double)flag;
@@ -155,10 +220,45 @@ __device__ void finish(const TransportParams& P, const Packet<T>& pk, int flag, 
     }
 }
 
+// First cell whose cumulative emission weight exceeds `target`: a guide table over
+// equal steps of the total narrows the search, and the answer is checked against
+// the definition (full binary search when the check fails).
+__device__ __forceinline__ long long thermal_cell(const TransportParams& P, double u) {
+    const double target = u * P.thermal_total;
+    const long long last = P.g.ncell - 1;
+    long long lo = 0, hi = last;
+    if (P.thermal_guide) {
+        long long k = (long long)(u * (double)P.n_guide);
+        k = k < 0 ? 0 : (k >= P.n_guide ? P.n_guide - 1 : k);
+        lo = P.thermal_guide[k];
+        hi = P.thermal_guide[k + 1];
+    }
+    while (lo < hi) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (P.thermal_cdf[mid] > target)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    const bool ok = P.thermal_cdf[lo] > target || lo == last;
+    const bool ok_prev = lo == 0 || !(P.thermal_cdf[lo - 1] > target);
+    if (ok && ok_prev) return lo;
+    lo = 0;
+    hi = last;
+    while (lo < hi) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (P.thermal_cdf[mid] > target)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
 // Packet birth, event 0: slot 0 = (tau, cos theta, phi, cell), slot 1 = (x, y, z, -).
+// Returns false when the packet starts outside the grid (it is then finished).
 template <typename T>
-__device__ bool emit(const TransportParams& P, const GridT<T>& g, const Smem<T>& sm, long long pid, Packet<T>& pk,
-                     LocalStats& st) {
+__device__ bool emit(const TransportParams& P, const Smem<T>& sm, long long pid, Packet<T>& pk, BlockTotals& bt) {
     int s = 0;
     while (s < P.n_src - 1 && pid >= P.src[s].start + P.src[s].count) ++s;
     const SourceDev& src = P.src[s];
@@ -167,93 +267,145 @@ __device__ bool emit(const TransportParams& P, const GridT<T>& g, const Smem<T>&
     pk.pid = pid;
     pk.src = s;
     pk.events = 1;
-    pk.n_seg = 0;
-    pk.n_sca = 0;
+    pk.n_seg = pk.n_sca = pk.n_tally = pk.n_abs = pk.trials = 0;
+    pk.e_abs = pk.e_gain = T(0);
     const T eps = T(src.eps);
-    pk.X[0] = eps;
-    pk.X[1] = pk.X[2] = pk.X[3] = T(0);
+    pk.X0 = eps;
+    pk.X1 = pk.X2 = pk.X3 = T(0);
     bool inside;
-    if (src.type == MCRT_SRC_POINT) {
-        pk.p[0] = T(src.pos[0]);
-        pk.p[1] = T(src.pos[1]);
-        pk.p[2] = T(src.pos[2]);
-        iso_dir(u0.b, u0.c, pk.n);
-        inside = locate(g, pk.p, pk.n, pk.idx);
-    } else if (src.type == MCRT_SRC_BEAM) {
-        pk.p[0] = T(P.g.lo[0] + (double)u1.a * (P.g.hi[0] - P.g.lo[0]));
-        pk.p[1] = T(P.g.lo[1] + (double)u1.b * (P.g.hi[1] - P.g.lo[1]));
-        pk.p[2] = T(src.beam_dir > 0 ? P.g.lo[2] : P.g.hi[2]);
-        pk.n[0] = T(0);
-        pk.n[1] = T(0);
-        pk.n[2] = src.beam_dir > 0 ? T(1) : T(-1);
-        inside = locate(g, pk.p, pk.n, pk.idx);
-    } else {
-        // first cell whose cumulative emission weight exceeds u * total
-        const double target = (double)u0.d * P.thermal_total;
-        long long lo = 0, hi = P.g.ncell - 1;
-        while (lo < hi) {
-            const long long mid = lo + (hi - lo) / 2;
-            if (P.thermal_cdf[mid] > target)
-                hi = mid;
-            else
-                lo = mid + 1;
-        }
-        const long long c = lo;
-        pk.idx[0] = (int)(c % g.n[0]);
-        pk.idx[1] = (int)((c / g.n[0]) % g.n[1]);
-        pk.idx[2] = (int)(c / ((long long)g.n[0] * g.n[1]));
-        const T uu[3] = {u1.a, u1.b, u1.c};
-        for (int a = 0; a < 3; ++a) pk.p[a] = g.lo[a] + (T(pk.idx[a]) + uu[a]) * g.d[a];
-        iso_dir(u0.b, u0.c, pk.n);
+    if (src.type == MCRT_SRC_THERMAL) {
+        const long long c = thermal_cell(P, (double)u0.d);
+        pk.ix = (int)(c % P.g.n[0]);
+        pk.iy = (int)((c / P.g.n[0]) % P.g.n[1]);
+        pk.iz = (int)(c / ((long long)P.g.n[0] * P.g.n[1]));
+        pk.px = g_lo<T>(P, 0) + (T(pk.ix) + u1.a) * g_d<T>(P, 0);
+        pk.py = g_lo<T>(P, 1) + (T(pk.iy) + u1.b) * g_d<T>(P, 1);
+        pk.pz = g_lo<T>(P, 2) + (T(pk.iz) + u1.c) * g_d<T>(P, 2);
+        T n[3];
+        iso_dir(u0.b, u0.c, n);
+        pk.nx = n[0];
+        pk.ny = n[1];
+        pk.nz = n[2];
         inside = true;
-        // emission alpha_abs B (1,0,0,0) in the grain-meridian basis
-        const float4 q = P.g.cells[2 * c];
-        const float4 r = P.g.cells[2 * c + 1];
-        const T kext = T(r.x) + T(r.y);
-        const T omega = kext > T(0) ? T(r.y) / kext : T(0);
-        V3<T> n{pk.n[0], pk.n[1], pk.n[2]}, th, ph;
-        stokes_basis(n, th, ph);
-        const GrainFrame<T> f = grain_frame(q, n, ph);
+        load_cell<T>(P, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
+        // emission alpha_abs B (1,0,0,0) in the grain-meridian basis, weight
+        // (alpha1(theta') - omega) / (mean alpha1 - omega)
+        const T kext = T(pk.cr.x) + T(pk.cr.y);
+        const T omega = kext > T(0) ? T(pk.cr.y) / kext : T(0);
+        const V3<T> nv{pk.nx, pk.ny, pk.nz};
+        V3<T> th, ph;
+        stokes_basis(nv, th, ph);
+        const GrainFrame<T> f = grain_frame(pk.cq, nv, ph);
         T a1, a2, a3;
         kext_eval(P.t, sm.kext, f.cos_tp, a1, a2, a3);
         const T w = (a1 - omega) / (T(P.t.alpha1_mean) - omega);
-        pk.X[0] = eps * w;
-        pk.X[1] = eps * w * a2 / (a1 - omega);
-        rotate_qu(pk.X[1], pk.X[2], f.c2, -f.s2);
+        pk.X0 = eps * w;
+        pk.X1 = eps * w * a2 / (a1 - omega);
+        rotate_qu(pk.X1, pk.X2, f.c2, -f.s2);
+    } else {
+        T p[3], n[3];
+        if (src.type == MCRT_SRC_POINT) {
+            p[0] = T(src.pos[0]);
+            p[1] = T(src.pos[1]);
+            p[2] = T(src.pos[2]);
+            iso_dir(u0.b, u0.c, n);
+        } else {
+            p[0] = T(P.g.lo[0] + (double)u1.a * (P.g.hi[0] - P.g.lo[0]));
+            p[1] = T(P.g.lo[1] + (double)u1.b * (P.g.hi[1] - P.g.lo[1]));
+            p[2] = T(src.beam_dir > 0 ? P.g.lo[2] : P.g.hi[2]);
+            n[0] = T(0);
+            n[1] = T(0);
+            n[2] = src.beam_dir > 0 ? T(1) : T(-1);
+        }
+        GridT<T> g;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            g.n[a] = P.g.n[a];
+            g.lo[a] = g_lo<T>(P, a);
+            g.d[a] = g_d<T>(P, a);
+        }
+        int idx[3];
+        inside = locate(g, p, n, idx);
+        pk.px = p[0];
+        pk.py = p[1];
+        pk.pz = p[2];
+        pk.nx = n[0];
+        pk.ny = n[1];
+        pk.nz = n[2];
+        pk.ix = idx[0];
+        pk.iy = idx[1];
+        pk.iz = idx[2];
+        if (inside) load_cell<T>(P, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
     }
     pk.tau = -(double)t_log(u0.a);
-    pk.I_birth = pk.X[0];
-    st.e_emit += (double)pk.X[0];
-    st.emitted++;
-    st.events++;
-    if (!inside) finish(P, pk, 1, st);
+    pk.I_birth = pk.X0;
+    if (!inside) finish(P, pk, 1, bt);
     return inside;
 }
 
-// One event of a live packet: a cell segment, followed by a scattering when the
-// sampled optical depth runs out inside the cell.  `work` = live lanes of the warp.
+// Exit of the current cell along n: distance, axis (ties to the lowest axis) and the
+// coordinate of the exit face.
+template <typename T>
+__device__ __forceinline__ T exit_face(const TransportParams& P, const Packet<T>& pk, int& axis, T& face) {
+    T best = T(INFINITY);
+    axis = -1;
+    face = T(0);
+    if (pk.nx != T(0)) {
+        const T f = g_lo<T>(P, 0) + T(pk.nx > T(0) ? pk.ix + 1 : pk.ix) * g_d<T>(P, 0);
+        T t = (f - pk.px) / pk.nx;
+        t = t < T(0) ? T(0) : t;
+        if (t < best) {
+            best = t;
+            axis = 0;
+            face = f;
+        }
+    }
+    if (pk.ny != T(0)) {
+        const T f = g_lo<T>(P, 1) + T(pk.ny > T(0) ? pk.iy + 1 : pk.iy) * g_d<T>(P, 1);
+        T t = (f - pk.py) / pk.ny;
+        t = t < T(0) ? T(0) : t;
+        if (t < best) {
+            best = t;
+            axis = 1;
+            face = f;
+        }
+    }
+    if (pk.nz != T(0)) {
+        const T f = g_lo<T>(P, 2) + T(pk.nz > T(0) ? pk.iz + 1 : pk.iz) * g_d<T>(P, 2);
+        T t = (f - pk.pz) / pk.nz;
+        t = t < T(0) ? T(0) : t;
+        if (t < best) {
+            best = t;
+            axis = 2;
+            face = f;
+        }
+    }
+    return best;
+}
+
+// One event of a live packet: a cell segment, then a scattering when the sampled
+// optical depth runs out inside the cell.  `work` = live lanes of the warp.
 template <typename T, int SCAT>
-__device__ void step(const TransportParams& P, const GridT<T>& g, const Smem<T>& sm, Packet<T>& pk, bool& alive,
-                     LocalStats& st, unsigned work) {
-    const long long c = ((long long)pk.idx[2] * g.n[1] + pk.idx[1]) * g.n[0] + pk.idx[0];
-    const bool capped = pk.events >= P.max_events;
-    const float4 q = __ldg(&P.g.cells[2 * c]);
-    const float4 r = __ldg(&P.g.cells[2 * c + 1]);
-    const T ks = T(r.y);
-    const T kext = T(r.x) + ks;
+__device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm, Packet<T>& pk, bool& alive,
+                                     BlockTotals& bt, unsigned work) {
+    const T ks = T(pk.cr.y);
+    const T kext = T(pk.cr.x) + ks;
+    const bool capped = pk.events >= (unsigned)P.max_events;
     int axis;
-    const T ell_exit = exit_distance(g, pk.idx, pk.p, pk.n, axis);
+    T face;
+    const T ell_exit = exit_face(P, pk, axis, face);
     // a packet without a finite exit (non-finite direction) ends as escaped
     const bool lost = !capped && axis < 0;
     const bool want_A = !capped && !lost && kext > T(0);
     const bool want_S = want_A && ks > T(0) && P.n_cam > 0;
+    const unsigned c32 = (unsigned)(((long long)pk.iz * P.g.n[1] + pk.iy) * P.g.n[0] + pk.ix);
     // converged point: same-cell groups for the aggregated tallies; lanes that
     // leave below are outside actA / actS
-    const unsigned peers = __match_any_sync(work, (unsigned)c);
+    const unsigned peers = __match_any_sync(work, c32);
     const unsigned actA = __ballot_sync(work, want_A);
     const unsigned actS = __ballot_sync(work, want_S);
     if (capped || lost) {
-        finish(P, pk, capped ? 3 : 1, st);
+        finish(P, pk, capped ? 3 : 1, bt);
         alive = false;
         return;
     }
@@ -261,12 +413,30 @@ __device__ void step(const TransportParams& P, const GridT<T>& g, const Smem<T>&
     const T dsca_exit = ks * ell_exit;
     const bool scatter_here = (ks > T(0)) && (pk.tau < (double)dsca_exit);
     const T ell = scatter_here ? T(pk.tau) / ks : ell_exit;
-    const V3<T> n{pk.n[0], pk.n[1], pk.n[2]};
+
+    // the next cell's record is requested before the segment arithmetic
+    int nix = pk.ix, niy = pk.iy, niz = pk.iz;
+    bool next_in = true;
+    float4 nq = pk.cq, nr = pk.cr;
+    if (!scatter_here) {
+        if (axis == 0) {
+            nix += pk.nx > T(0) ? 1 : -1;
+            next_in = nix >= 0 && nix < P.g.n[0];
+        } else if (axis == 1) {
+            niy += pk.ny > T(0) ? 1 : -1;
+            next_in = niy >= 0 && niy < P.g.n[1];
+        } else {
+            niz += pk.nz > T(0) ? 1 : -1;
+            next_in = niz >= 0 && niz < P.g.n[2];
+        }
+        if (next_in) load_cell<T>(P, nix, niy, niz, nq, nr);
+    }
+
+    const V3<T> n{pk.nx, pk.ny, pk.nz};
     V3<T> th, ph;
     stokes_basis(n, th, ph);
     const int lane = threadIdx.x & 31;
-    // same-cell lanes that tally (a capped lane may share the cell but has left)
-    const unsigned group = peers & actA;
+    const unsigned group = peers & actA;  // same-cell lanes that tally
     const int leader = __ffs(group) - 1;
 
     if (want_A) {
@@ -276,14 +446,14 @@ __device__ void step(const TransportParams& P, const GridT<T>& g, const Smem<T>&
             a2 = T(0);
             a3 = T(0);
         } else {
-            const GrainFrame<T> f = grain_frame(q, n, ph);
+            const GrainFrame<T> f = grain_frame(pk.cq, n, ph);
             c2 = f.c2;
             s2 = f.s2;
             kext_eval(P.t, sm.kext, f.cos_tp, a1, a2, a3);
         }
         const T a = a1 - omega;
         const T dtau = kext * ell;
-        T Xg[4] = {pk.X[0], pk.X[1], pk.X[2], pk.X[3]};
+        T Xg[4] = {pk.X0, pk.X1, pk.X2, pk.X3};
         rotate_qu(Xg[1], Xg[2], c2, s2);
         T Yg[4], Wg[4];
         transfer(Xg, a, a2, a3, dtau, Yg, Wg, want_S, ell);
@@ -291,74 +461,95 @@ __device__ void step(const TransportParams& P, const GridT<T>& g, const Smem<T>&
         // absorbed energy, one FP64 atomic per same-cell group
         {
             const unsigned gmax = __reduce_max_sync(actA, (unsigned)__popc(group));
-            T dI = pk.X[0] - Yg[0];
-            st.e_abs += (double)dI;
-            if (dI != T(0)) st.abs_seg++;
+            T dI = pk.X0 - Yg[0];
+            pk.e_abs += dI;
+            if (dI != T(0)) pk.n_abs++;
             if (gmax > 1u) dI = group_sum(actA, group, dI, gmax);
-            if (lane == leader && dI != T(0)) atomicAdd(&P.absorbed[c], (double)dI);
+            if (lane == leader && dI != T(0)) atomicAdd(&P.absorbed[c32], widen(dI));
         }
         if (want_S) {
             rotate_qu(Wg[1], Wg[2], c2, -s2);
-            const T W[4] = {Wg[0], Wg[1], Wg[2], Wg[3]};
             const unsigned gmax = __reduce_max_sync(actS, (unsigned)__popc(group));
-            st.tally_seg++;
-            double* Sc = P.S + (size_t)c * (size_t)P.n_cam * 4;
-            for (int k = 0; k < P.n_cam; ++k) {
-                const T* cm = sm.cam + 9 * k;
-                const V3<T> Om{cm[0], cm[1], cm[2]}, thc{cm[3], cm[4], cm[5]}, phc{cm[6], cm[7], cm[8]};
-                const T mu = dot(n, Om);
-                T Pm[6];
-                if (SCAT == MCRT_SCAT_RAYLEIGH)
-                    rayleigh_matrix(mu, Pm);
-                else
-                    table_matrix(sm.mix, P.t.n_theta, mu, Pm);
-                const PlaneRot<T> pr = plane_rotation(n, th, ph, Om, thc, phc);
-                T s[4];
-                apply_plane(pr, Pm, W, s);
-                if (gmax > 1u) {
+            pk.n_tally++;
+            double* Sc = P.S + (size_t)c32 * (size_t)P.n_cam * 4;
+            double* slot = sm.stage + threadIdx.x * kStageDoubles;
+            for (int k0 = 0; k0 < P.n_cam; k0 += kStageCams) {
+                const int kn = P.n_cam - k0 < kStageCams ? P.n_cam - k0 : kStageCams;
+                if (lane == leader) bulk_wait_read();  // the slot's previous reduction has read it
+                for (int k = 0; k < kn; ++k) {
+                    const T* cm = sm.cam + 9 * (k0 + k);
+                    const V3<T> Om{cm[0], cm[1], cm[2]}, thc{cm[3], cm[4], cm[5]}, phc{cm[6], cm[7], cm[8]};
+                    const T mu = dot(n, Om);
+                    T Pm[6];
+                    if (SCAT == MCRT_SCAT_RAYLEIGH)
+                        rayleigh_matrix(mu, Pm);
+                    else
+                        table_matrix(sm.mix, P.t.n_theta, mu, Pm);
+                    const PlaneRot<T> pr = plane_rotation(n, th, ph, Om, thc, phc);
+                    T sv[4];
+                    apply_plane(pr, Pm, Wg, sv);
+                    if (gmax > 1u) {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) s[e] = group_sum(actS, group, s[e], gmax);
+                        for (int e = 0; e < 4; ++e) sv[e] = group_sum(actS, group, sv[e], gmax);
+                    }
+                    if (lane == leader) {
+                        double2* d2 = reinterpret_cast<double2*>(slot + 4 * k);
+                        d2[0] = make_double2(widen(sv[0]), widen(sv[1]));
+                        d2[1] = make_double2(widen(sv[2]), widen(sv[3]));
+                    }
                 }
-                if (lane == leader) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) atomicAdd(Sc + 4 * k + e, (double)s[e]);
-                }
+                if (lane == leader) bulk_reduce_add_f64(Sc + 4 * k0, slot, (unsigned)kn * 32u);
             }
         }
-        pk.X[0] = Yg[0];
-        pk.X[1] = Yg[1];
-        pk.X[2] = Yg[2];
-        pk.X[3] = Yg[3];
+        pk.X0 = Yg[0];
+        pk.X1 = Yg[1];
+        pk.X2 = Yg[2];
+        pk.X3 = Yg[3];
     }
     pk.n_seg++;
     pk.events++;
-    st.seg++;
-    st.events++;
 
     if (!scatter_here) {
         pk.tau -= (double)dsca_exit;
-        if (!cross_face(g, pk.idx, pk.p, pk.n, ell_exit, axis)) {
-            finish(P, pk, 1, st);
+        pk.px += ell_exit * pk.nx;
+        pk.py += ell_exit * pk.ny;
+        pk.pz += ell_exit * pk.nz;
+        if (axis == 0)
+            pk.px = face;
+        else if (axis == 1)
+            pk.py = face;
+        else
+            pk.pz = face;
+        pk.ix = nix;
+        pk.iy = niy;
+        pk.iz = niz;
+        if (!next_in) {
+            finish(P, pk, 1, bt);
             alive = false;
+            return;
         }
+        pk.cq = nq;
+        pk.cr = nr;
         return;
     }
 
     // ---- scattering; the packet keeps its cell ----
-    for (int a = 0; a < 3; ++a) pk.p[a] += ell * pk.n[a];
+    pk.px += ell * pk.nx;
+    pk.py += ell * pk.ny;
+    pk.pz += ell * pk.nz;
     pk.n_sca++;
     pk.events++;
-    st.sca++;
-    st.events++;
     const Draw4<T> us = draw4<T>(pk.pid, pk.n_sca, 0u, P.seed, P.stream);
-    if (P.roulette_thr > 0.0 && (double)pk.X[0] < P.roulette_thr * (double)pk.I_birth) {
+    if (P.roulette_thr > 0.0 && (double)pk.X0 < P.roulette_thr * (double)pk.I_birth) {
         if ((double)us.b < P.roulette_surv) {
             const T gmul = T(1.0 / P.roulette_surv);
-            st.gain += (double)pk.X[0] * ((double)gmul - 1.0);
-            for (int e = 0; e < 4; ++e) pk.X[e] *= gmul;
+            pk.e_gain += pk.X0 * (gmul - T(1));
+            pk.X0 *= gmul;
+            pk.X1 *= gmul;
+            pk.X2 *= gmul;
+            pk.X3 *= gmul;
         } else {
-            st.lost += (double)pk.X[0];
-            finish(P, pk, 2, st);
+            finish(P, pk, 2, bt);
             alive = false;
             return;
         }
@@ -374,19 +565,20 @@ __device__ void step(const TransportParams& P, const GridT<T>& g, const Smem<T>&
             }
         tab = P.t.bins + (size_t)bin * P.t.n_theta * 2;
     }
+    const T X[4] = {pk.X0, pk.X1, pk.X2, pk.X3};
     V3<T> n2;
     T Pm[6];
     bool accepted = false;
     for (int t = 0; t < P.max_trials; ++t) {
         const Draw4<T> ut = draw4<T>(pk.pid, pk.n_sca, 1u + (unsigned)t, P.seed, P.stream);
-        st.trials++;
+        pk.trials++;
         T bound;
         if (SCAT == MCRT_SCAT_RAYLEIGH) {
             T g2[3];
             iso_dir(ut.a, ut.b, g2);
-            n2 = quat_to_lab(q, V3<T>{g2[0], g2[1], g2[2]});
+            n2 = quat_to_lab(pk.cq, V3<T>{g2[0], g2[1], g2[2]});
             rayleigh_matrix(dot(n, n2), Pm);
-            bound = ut.c * T(2) * T(0.11936620731892133) * pk.X[0];  // 2 * 3/(8 pi)
+            bound = ut.c * T(2) * T(0.11936620731892133) * X[0];  // 2 * 3/(8 pi)
         } else {
             // interval j of the piecewise-constant envelope of P11: first j with u < cdf_j
             const int nint = P.t.n_theta - 1;
@@ -411,16 +603,16 @@ __device__ void step(const TransportParams& P, const GridT<T>& g, const Smem<T>&
             n2 = V3<T>{mu * n.x + sn * (ca * th.x + sa * ph.x), mu * n.y + sn * (ca * th.y + sa * ph.y),
                        mu * n.z + sn * (ca * th.z + sa * ph.z)};
             table_matrix(tab, P.t.n_theta, mu, Pm);
-            bound = ut.d * T(2) * T(P.t.env[(size_t)bin * nint + j]) * pk.X[0];
+            bound = ut.d * T(2) * T(P.t.env[(size_t)bin * nint + j]) * X[0];
         }
-        const T Qs = plane_Q(n, th, ph, n2, pk.X);
-        if (bound < Pm[0] * pk.X[0] + Pm[1] * Qs) {
+        const T Qs = plane_Q(n, th, ph, n2, X);
+        if (bound < Pm[0] * X[0] + Pm[1] * Qs) {
             accepted = true;
             break;
         }
     }
     if (!accepted) {
-        finish(P, pk, 4, st);
+        finish(P, pk, 4, bt);
         alive = false;
         return;
     }
@@ -428,23 +620,29 @@ __device__ void step(const TransportParams& P, const GridT<T>& g, const Smem<T>&
     stokes_basis(n2, th2, ph2);
     const PlaneRot<T> pr = plane_rotation(n, th, ph, n2, th2, ph2);
     T Y[4];
-    apply_plane(pr, Pm, pk.X, Y);
-    const T norm = pk.X[0] / Y[0];
-    for (int e = 0; e < 4; ++e) pk.X[e] = Y[e] * norm;
-    pk.n[0] = n2.x;
-    pk.n[1] = n2.y;
-    pk.n[2] = n2.z;
+    apply_plane(pr, Pm, X, Y);
+    const T norm = X[0] / Y[0];
+    pk.X0 = Y[0] * norm;
+    pk.X1 = Y[1] * norm;
+    pk.X2 = Y[2] * norm;
+    pk.X3 = Y[3] * norm;
+    pk.nx = n2.x;
+    pk.ny = n2.y;
+    pk.nz = n2.z;
     pk.tau = -(double)t_log(us.a);
 }
 
 template <typename T, int SCAT>
-__global__ void __launch_bounds__(kDefaultBlock) k_transport(const __grid_constant__ TransportParams P) {
+__global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCKS : 1) k_transport(const __grid_constant__ TransportParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // shared layout: kext table, mixture table (TABLE), cameras
+    __shared__ BlockTotals bt;
+    // shared layout: kext table, mixture table (TABLE), cameras, tally staging
     float4* s_kext = reinterpret_cast<float4*>(smem_raw);
     float4* s_mix = s_kext + P.t.n_ktheta;
     const int n_mix = (SCAT == MCRT_SCAT_TABLE) ? 2 * P.t.n_theta : 0;
     T* s_cam = reinterpret_cast<T*>(s_mix + n_mix);
+    const int cam_bytes = (9 * P.n_cam * (int)sizeof(T) + 15) & ~15;
+    double* s_stage = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(s_cam) + cam_bytes);
     for (int i = threadIdx.x; i < P.t.n_ktheta; i += blockDim.x) s_kext[i] = P.t.kext[i];
     for (int i = threadIdx.x; i < n_mix; i += blockDim.x) s_mix[i] = P.t.mix[i];
     for (int i = threadIdx.x; i < 9 * P.n_cam; i += blockDim.x) {
@@ -452,16 +650,12 @@ __global__ void __launch_bounds__(kDefaultBlock) k_transport(const __grid_consta
         const int e = i % 9;
         s_cam[i] = T(e < 3 ? cd.dir[e] : (e < 6 ? cd.th[e - 3] : cd.ph[e - 6]));
     }
+    if (threadIdx.x < 6) bt.e[threadIdx.x] = 0.0;
+    if (threadIdx.x < 10) bt.n[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) bt.status = 0u;
     __syncthreads();
 
-    GridT<T> g;
-    for (int a = 0; a < 3; ++a) {
-        g.n[a] = P.g.n[a];
-        g.lo[a] = T(P.g.lo[a]);
-        g.d[a] = T(P.g.d[a]);
-    }
-    const Smem<T> sm{s_cam, s_mix, s_kext};
-    LocalStats st = {};
+    const Smem<T> sm{s_cam, s_mix, s_kext, s_stage};
     Packet<T> pk;
     bool alive = false, pool_done = false;
     const unsigned long long t0 = global_ns();
@@ -473,13 +667,12 @@ __global__ void __launch_bounds__(kDefaultBlock) k_transport(const __grid_consta
             if (grp.thread_rank() == 0) base = atomicAdd(P.counter, (unsigned long long)grp.size());
             base = grp.shfl(base, 0);
             const long long pid = P.pid_begin + (long long)(base + grp.thread_rank());
-            bool late = false;
-            if (P.time_budget_ns > 0.0 && (double)(global_ns() - t0) > P.time_budget_ns) late = true;
+            const bool late = P.time_budget_ns > 0.0 && (double)(global_ns() - t0) > P.time_budget_ns;
             if (pid >= P.pid_end || late) {
                 pool_done = true;
-                if (late && pid < P.pid_end) st.status |= MCRT_STATUS_TIMEOUT;
+                if (late && pid < P.pid_end) atomicOr(&bt.status, (unsigned)MCRT_STATUS_TIMEOUT);
             } else {
-                alive = emit<T>(P, g, sm, pid, pk, st);
+                alive = emit<T>(P, sm, pid, pk, bt);
             }
         }
         const unsigned work = __ballot_sync(kFull, alive);
@@ -487,33 +680,27 @@ __global__ void __launch_bounds__(kDefaultBlock) k_transport(const __grid_consta
             if (__all_sync(kFull, pool_done)) break;
             continue;
         }
-        if (alive) step<T, SCAT>(P, g, sm, pk, alive, st, work);
+        if (alive) step<T, SCAT>(P, sm, pk, alive, bt, work);
     }
 
-    // reduce the per-thread totals: warp shuffle, then one atomic per warp
-    double dv[6] = {st.e_emit, st.e_esc, st.e_abs, st.lost, st.gain, st.cap_lost};
-    unsigned long long cv[10] = {st.events, st.seg,    st.sca,   st.emitted,   st.escaped,
-                                 st.killed, st.caps, st.trials, st.tally_seg, st.abs_seg};
-    unsigned status = st.status;
-    for (int off = 16; off > 0; off >>= 1) {
-        for (int i = 0; i < 6; ++i) dv[i] += __shfl_down_sync(kFull, dv[i], off);
-        for (int i = 0; i < 10; ++i) cv[i] += __shfl_down_sync(kFull, cv[i], off);
-        status |= __shfl_down_sync(kFull, status, off);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        for (int i = 0; i < 6; ++i) atomicAdd(&P.stats[i], dv[i]);
+    bulk_wait_all();  // this thread's reductions have completed before the block ends
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        atomicAdd(&P.stats[threadIdx.x], bt.e[threadIdx.x]);
+    } else if (threadIdx.x < 16) {
         unsigned long long* cnt = reinterpret_cast<unsigned long long*>(P.stats + 6);
-        for (int i = 0; i < 10; ++i) atomicAdd(&cnt[i], cv[i]);
-        if (status) atomicOr(P.status, status);
+        atomicAdd(&cnt[threadIdx.x - 6], bt.n[threadIdx.x - 6]);
+    } else if (threadIdx.x == 16 && bt.status) {
+        atomicOr(P.status, bt.status);
     }
 }
-
 }  // namespace
 
-size_t transport_smem_bytes(const TransportParams& p, int precision) {
+size_t transport_smem_bytes(const TransportParams& p, int precision, int block) {
     const size_t tsize = precision == MCRT_FP64 ? sizeof(double) : sizeof(float);
     const size_t mix = p.t.model == MCRT_SCAT_TABLE ? 2 * (size_t)p.t.n_theta * sizeof(float4) : 0;
-    return (size_t)p.t.n_ktheta * sizeof(float4) + mix + 9 * (size_t)p.n_cam * tsize;
+    const size_t cams = (9 * (size_t)p.n_cam * tsize + 15) & ~(size_t)15;
+    return (size_t)p.t.n_ktheta * sizeof(float4) + mix + cams + (size_t)block * kStageDoubles * sizeof(double);
 }
 
 static const void* kernel_ptr(int precision, int model) {
@@ -533,7 +720,7 @@ int transport_max_blocks_per_sm(int precision, int model, int block, size_t smem
 }
 
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s) {
-    const size_t smem = transport_smem_bytes(p, precision);
+    const size_t smem = transport_smem_bytes(p, precision, block);
     const void* k = kernel_ptr(precision, p.t.model);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
