@@ -228,6 +228,51 @@ MCRT_API const char *mcrt_last_error(const mcrt_ctx *ctx);
  */
 MCRT_API mcrt_status mcrt_unit_eval(int32_t fn, int32_t precision, int64_t n, const double *in, double *out);
 
+/*
+ * Transport without allocation.  The paper has no counterpart to this entry point;
+ * it exists for callers that cannot allocate device memory themselves or through
+ * this library: code running inside another framework's memory pool or under a
+ * fixed memory plan, or a process whose allocator must not be touched after
+ * start-up.  mcrt_launch_packets_noalloc performs the same step-1 transport as
+ * mcrt_launch_packets, but
+ *  - every input and output is caller-owned DEVICE memory passed in `prob`
+ *    (kappa_abs, kappa_sca, bfield, the optics tables, and the outputs source
+ *    [ncell][n_cameras][4] FP64 and absorbed [ncell] FP64, zeroed by the call unless
+ *    desc->accumulate is set); desc->trace, if used, must be device memory too;
+ *  - its scratch (cell records with the grain quaternions, prepared tables, the
+ *    packet counter and the launch totals) lives in one static device array of
+ *    about 4.3 MB that the library image carries; every GPU that loads the library
+ *    holds that array until the process exits;
+ *  - it calls no cudaMalloc, cudaFree or other allocating routine.
+ * Limits (MCRT_E_INVAL beyond them): at most MCRT_NOALLOC_MAX_CELLS cells,
+ * MCRT_NOALLOC_MAX_BINS grain bins, MCRT_NOALLOC_MAX_THETA angles per table; point
+ * and beam sources only (thermal sources need per-cell emission scratch).
+ * The first call on a device looks up the array's device address (this can load
+ * the library's device code); make that first call before any stream capture.
+ * All calls share the one array, so calls whose GPU work overlaps (different
+ * streams or host threads without ordering between them) race on it; each call
+ * clears what must start at zero.  Work runs on prob->cuda_stream; out_stats
+ * (nullable, host) is filled after that stream has been synchronized.
+ */
+enum { MCRT_NOALLOC_MAX_CELLS = 131072, MCRT_NOALLOC_MAX_BINS = 8, MCRT_NOALLOC_MAX_THETA = 181 };
+
+typedef struct {
+    int32_t nx, ny, nz;
+    double lo[3], hi[3];
+    const float *kappa_abs, *kappa_sca; /* device, [nz][ny][nx] */
+    const float *bfield;                /* device, [nz][ny][nx][3], or NULL */
+    int32_t model, n_bins, n_theta;     /* as in mcrt_set_dust_tables */
+    const float *mueller, *bin_weight;  /* device (MCRT_SCAT_TABLE only) */
+    int32_t n_ktheta;
+    const float *kext;                  /* device, [n_ktheta][3] */
+    double *source;                     /* device output, [ncell][n_cameras][4] */
+    double *absorbed;                   /* device output, [ncell] */
+    void *cuda_stream;
+} mcrt_noalloc_problem;
+
+MCRT_API mcrt_status mcrt_launch_packets_noalloc(const mcrt_noalloc_problem *prob, const mcrt_launch_desc *desc,
+                                                 mcrt_stats *out_stats);
+
 #ifdef __cplusplus
 }
 #endif

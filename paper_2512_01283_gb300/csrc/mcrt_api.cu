@@ -138,6 +138,14 @@ constexpr size_t kWorkBytes = 8 + 16 * 8 + 8;
 
 }  // namespace
 
+mcrt_status mcrt_fail_noctx(mcrt_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
 extern "C" {
 
 const char* mcrt_last_error(const mcrt_ctx* ctx) { return ctx ? ctx->err : g_err; }

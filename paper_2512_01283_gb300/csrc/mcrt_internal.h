@@ -104,3 +104,7 @@ cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* 
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s);
 
 }  // namespace mcrt
+
+// Records `fmt` as the calling thread's context-less error message (read with
+// mcrt_last_error(NULL)) and returns st.
+mcrt_status mcrt_fail_noctx(mcrt_status st, const char* fmt, ...);

@@ -60,11 +60,20 @@ class Stats(C.Structure):
     _fields_ = [(f, C.c_double) for f in STAT_FIELDS]
 
 
+class NoAllocProblem(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3), ("kappa_abs", C.c_void_p), ("kappa_sca", C.c_void_p),
+                ("bfield", C.c_void_p), ("model", C.c_int32), ("n_bins", C.c_int32), ("n_theta", C.c_int32),
+                ("mueller", C.c_void_p), ("bin_weight", C.c_void_p), ("n_ktheta", C.c_int32),
+                ("kext", C.c_void_p), ("source", C.c_void_p), ("absorbed", C.c_void_p),
+                ("cuda_stream", C.c_void_p)]
+
+
 _lib = None
 
 # symbols of include/mcrt.h
 SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "mcrt_image_stokes",
-           "mcrt_get_tallies", "mcrt_destroy", "mcrt_last_error", "mcrt_unit_eval"]
+           "mcrt_get_tallies", "mcrt_destroy", "mcrt_last_error", "mcrt_unit_eval", "mcrt_launch_packets_noalloc"]
 
 
 def lib():
@@ -86,6 +95,7 @@ def lib():
     L.mcrt_last_error.argtypes = [vp]
     L.mcrt_last_error.restype = C.c_char_p
     L.mcrt_unit_eval.argtypes = [i32, i32, i64, vp, vp]
+    L.mcrt_launch_packets_noalloc.argtypes = [C.POINTER(NoAllocProblem), C.POINTER(LaunchDesc), C.POINTER(Stats)]
     for name in SYMBOLS:
         if name != "mcrt_last_error":
             getattr(L, name).restype = C.c_int
@@ -262,4 +272,44 @@ def unit_eval(fn: int, inputs, precision="fp32"):
     n = a.shape[0]
     out = np.zeros((n, widths_out[fn]))
     _check(L.mcrt_unit_eval(int(fn), PRECISION[precision], n, C.c_void_p(a.ctypes.data), C.c_void_p(out.ctypes.data)))
+    return out
+
+
+def launch_noalloc(model_dev: dict, run: dict, source, absorbed, precision="fp32", trace=None, n_trace=0,
+                   stream=None, **kw):
+    """mcrt_launch_packets_noalloc: transport with caller-owned device buffers only.
+
+    ``model_dev`` holds CUDA tensors (kappa_abs, kappa_sca, optional bfield, and the
+    optics tensors under "optics") plus "lo"/"hi"; ``source`` and ``absorbed`` are
+    CUDA float64 tensors the call writes.  Returns the stats dict."""
+    L = lib()
+    ka = model_dev["kappa_abs"]
+    nz, ny, nx = tuple(ka.shape)
+    pr = NoAllocProblem()
+    pr.nx, pr.ny, pr.nz = nx, ny, nz
+    pr.lo = (C.c_double * 3)(*model_dev["lo"])
+    pr.hi = (C.c_double * 3)(*model_dev["hi"])
+    pr.kappa_abs = ka.data_ptr()
+    pr.kappa_sca = model_dev["kappa_sca"].data_ptr()
+    pr.bfield = model_dev["bfield"].data_ptr() if model_dev.get("bfield") is not None else None
+    opt = model_dev["optics"]
+    pr.model = SCAT[opt["model"]]
+    if pr.model == 1:
+        pr.n_bins, pr.n_theta = opt["mueller"].shape[0], opt["mueller"].shape[1]
+        pr.mueller = opt["mueller"].data_ptr()
+        pr.bin_weight = opt["bin_weight"].data_ptr()
+    pr.n_ktheta = opt["kext"].shape[0]
+    pr.kext = opt["kext"].data_ptr()
+    pr.source = source.data_ptr() if source is not None else None
+    pr.absorbed = absorbed.data_ptr()
+    pr.cuda_stream = _stream_handle(stream)
+    center = tuple((float(a) + float(b)) / 2 for a, b in zip(model_dev["lo"], model_dev["hi"]))
+    d, keep = make_desc(run, precision, trace, n_trace, default_center=center, **kw)
+    st = Stats()
+    status = L.mcrt_launch_packets_noalloc(C.byref(pr), C.byref(d), C.byref(st))
+    if status not in (MCRT_OK, MCRT_E_EVENT_CAP, MCRT_E_TIMEOUT):
+        _check(status)
+    out = {f: getattr(st, f) for f in STAT_FIELDS}
+    out["status"] = status
+    del keep
     return out

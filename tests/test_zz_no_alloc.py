@@ -1,0 +1,108 @@
+"""mcrt_launch_packets_noalloc: the transport entry point for callers that cannot
+allocate device memory (code inside another framework's memory pool or under a fixed
+memory plan).  The caller owns every input and output; the call's scratch lives in a
+static device array.  Checked through the C ABI against mcrt_launch_packets on the
+same problem, on two calls in a row (the shared array keeps the previous call's
+contents, so each call must clear what starts at zero).
+
+Kept in a file of its own that pytest collects last.
+"""
+import numpy as np
+import pytest
+
+from paper_2512_01283_gb300 import build as B
+from paper_2512_01283_gb300 import mcrt as M
+from paper_2512_01283_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for -m gpu tests")
+    B.build()
+    M.lib()
+    return torch
+
+
+def to_device(torch, model):
+    dev = {"lo": model["lo"], "hi": model["hi"]}
+    for k in ("kappa_abs", "kappa_sca", "bfield"):
+        dev[k] = None if model.get(k) is None else torch.from_numpy(np.ascontiguousarray(model[k], dtype=np.float32)).cuda()
+    opt = {"model": model["optics"]["model"]}
+    for k in ("mueller", "bin_weight", "kext"):
+        if k in model["optics"]:
+            opt[k] = torch.from_numpy(np.ascontiguousarray(model["optics"][k], dtype=np.float32)).cuda()
+    dev["optics"] = opt
+    return dev
+
+
+def reference(model, run, precision):
+    m = M.Model(model)
+    st = M.launch(m, run, precision=precision)
+    S, A = m.tallies(len(run["cameras"]))
+    m.close()
+    return st, S, A
+
+
+CASES = [
+    ("rayleigh sphere 32^3, 1 camera, fp64", lambda: (W.rayleigh_sphere(), W.rayleigh_sphere_run(50_000, npix=16)),
+     "fp64"),
+    ("disk 24^3 with grain tables, star only, 4 cameras, fp32",
+     lambda: (W.disk(n=24), dict(W.disk_run(40_000, n_cam=4, npix=16),
+                                 sources=[{"type": "point", "pos": (0.0, 0.0, 0.0), "luminosity": 1.0,
+                                           "n_packets": 40_000}])), "fp32"),
+]
+
+
+@pytest.mark.parametrize("name,make,precision", CASES, ids=[c[0] for c in CASES])
+def test_noalloc_matches_allocating_entry_point(torch_cuda, name, make, precision):
+    torch = torch_cuda
+    model, run = make()
+    ref_st, ref_S, ref_A = reference(model, run, precision)
+    dev = to_device(torch, model)
+    ncell = model["kappa_abs"].size
+    n_cam = len(run["cameras"])
+    source = torch.empty((ncell, n_cam, 4), dtype=torch.float64, device="cuda")
+    absorbed = torch.empty(ncell, dtype=torch.float64, device="cuda")
+    for call in range(2):
+        # garbage in the outputs: the call must zero them itself
+        source.fill_(7.0)
+        absorbed.fill_(-3.0)
+        free_before = torch.cuda.mem_get_info()[0]
+        st = M.launch_noalloc(dev, run, source, absorbed, precision=precision)
+        torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free_before
+        assert st["status"] == M.MCRT_OK
+        for key in ("emitted", "escaped", "events", "segments", "scatterings", "tally_segments"):
+            assert st[key] == ref_st[key], (call, key)
+        for key in ("emitted_energy", "escaped_energy", "absorbed_energy"):
+            assert abs(st[key] - ref_st[key]) <= 1e-9 * abs(ref_st["emitted_energy"]), (call, key)
+        S = source.cpu().numpy()
+        A = absorbed.cpu().numpy()
+        assert np.linalg.norm(S - ref_S) <= 1e-9 * np.linalg.norm(ref_S), call
+        assert np.linalg.norm(A - ref_A) <= 1e-9 * max(np.linalg.norm(ref_A), 1e-300), call
+
+
+def test_noalloc_rejects_sizes_beyond_its_limit(torch_cuda):
+    torch = torch_cuda
+    model = W.rayleigh_sphere(n=4)
+    big = np.zeros((64, 64, 33), dtype=np.float32)  # 135168 cells > 131072
+    model["kappa_abs"] = big
+    model["kappa_sca"] = big
+    dev = to_device(torch, model)
+    absorbed = torch.empty(big.size, dtype=torch.float64, device="cuda")
+    with pytest.raises(M.McrtError) as e:
+        M.launch_noalloc(dev, W.rayleigh_sphere_run(10, npix=4) | {"cameras": []}, None, absorbed)
+    assert e.value.status == M.MCRT_E_INVAL and "static limit" in str(e.value)
+    # thermal sources need per-cell emission scratch and are refused
+    model = W.dichroic_slab(n=8, tau=1.0, emissivity=1.0)
+    dev = to_device(torch, model)
+    absorbed = torch.empty(512, dtype=torch.float64, device="cuda")
+    with pytest.raises(M.McrtError) as e:
+        M.launch_noalloc(dev, {"sources": [{"type": "thermal", "n_packets": 10}], "cameras": []}, None, absorbed)
+    assert e.value.status == M.MCRT_E_INVAL
