@@ -71,6 +71,33 @@ def oracle_sample(model, run, seconds, n_threads, pid_offset=0):
     return events, wall, packets
 
 
+def kernel_source_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("paper_2512_01283_gb300/csrc/mcrt_transport.cu", "paper_2512_01283_gb300/csrc/mcrt_device.cuh",
+              "paper_2512_01283_gb300/csrc/mcrt_internal.h"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(segments_per_launch):
+    """DRAM bytes (read + write) per transport launch from the committed ncu summary:
+    bytes per segment of the captured small launch times this launch's segments;
+    None when the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "k_transport_disk192.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and not line.startswith(("|", "#", "`")):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    if fields.get("kernel_source_sha") != kernel_source_sha() or "traffic_bytes_per_segment" not in fields:
+        return None
+    return float(fields["traffic_bytes_per_segment"]) * segments_per_launch
+
+
 class ClockSampler:
     def __init__(self, path):
         self.path = path
@@ -228,13 +255,7 @@ def main():
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / (kms * 1e-3) / 1e9
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "transport_disk_traffic.json")
-    if os.path.exists(tf):
-        try:
-            traffic = json.load(open(tf)).get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = profiled_traffic(seg / args.steps)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "kernel": "k_transport<float, table>", "bytes_per_segment": "32 cell + 16 absorbed RMW (if absorbing) "

@@ -67,8 +67,9 @@ __host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
 #endif
 }
 
-__host__ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                                     uint32_t k0, uint32_t k1) {
+// kept out of line so that the kernel holds one copy of the ten rounds
+static __host__ __device__ __noinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                                  uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         if (r > 0) {
@@ -132,13 +133,16 @@ template <typename T> __device__ __forceinline__ V3<T> quat_to_grain(const float
 template <typename T> __device__ __forceinline__ void stokes_basis(const V3<T>& n, V3<T>& th, V3<T>& ph) {
     const T r2 = n.x * n.x + n.y * n.y;
     if (r2 > T(0)) {
-        const T r = T(1) / t_sqrt(r2);
+        const T r = t_rsqrt(r2);
         ph = V3<T>{-n.y * r, n.x * r, T(0)};
     } else {
         ph = V3<T>{T(0), T(1), T(0)};
     }
     th = cross(ph, n);
 }
+
+__device__ __forceinline__ float t_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double t_rcp(double x) { return 1.0 / x; }
 
 // (cos 2psi, sin 2psi) from any (A, B) proportional to (cos psi, sin psi); (1, 0)
 // for A = B = 0.  Tiny inputs are rescaled first so that 1/r cannot overflow.
@@ -155,7 +159,7 @@ template <typename T> __device__ __forceinline__ void double_angle(T A, T B, T& 
         B = B / m;
         r = A * A + B * B;
     }
-    const T inv = T(1) / r;
+    const T inv = t_rcp(r);
     c2 = (A * A - B * B) * inv;
     s2 = T(2) * A * B * inv;
 }
@@ -296,13 +300,14 @@ template <typename T> struct PlaneRot {
     T c1, s1, c2, s2;
 };
 
+// With e = n x n2 the rotation inputs are projections: e.phi(n) = n2.theta(n),
+// -e.theta(n) = n2.phi(n), e.phi(n2) = -n.theta(n2), e.theta(n2) = n.phi(n2).
 template <typename T>
 __device__ __forceinline__ PlaneRot<T> plane_rotation(const V3<T>& n, const V3<T>& th, const V3<T>& ph,
                                                       const V3<T>& n2, const V3<T>& th2, const V3<T>& ph2) {
-    const V3<T> e = cross(n, n2);
-    T A1 = dot(e, ph), B1 = -dot(e, th);
-    T A2 = dot(e, ph2), B2 = dot(e, th2);
-    if (A1 * A1 + B1 * B1 < T(1e-12)) {  // sin(Theta) < 1e-6: plane undefined
+    T A1 = dot(n2, th), B1 = dot(n2, ph);
+    T A2 = -dot(n, th2), B2 = dot(n, ph2);
+    if (A1 * A1 + B1 * B1 < T(1e-12)) {  // sin(Theta) < 1e-6: plane undefined, e_perp = phi(n)
         A1 = T(1);
         B1 = T(0);
         A2 = dot(ph, ph2);
@@ -316,9 +321,8 @@ __device__ __forceinline__ PlaneRot<T> plane_rotation(const V3<T>& n, const V3<T
 
 // Incident Q in the scattering-plane basis only (rejection test).
 template <typename T>
-__device__ __forceinline__ T plane_Q(const V3<T>& n, const V3<T>& th, const V3<T>& ph, const V3<T>& n2, const T X[4]) {
-    const V3<T> e = cross(n, n2);
-    T A1 = dot(e, ph), B1 = -dot(e, th);
+__device__ __forceinline__ T plane_Q(const V3<T>& th, const V3<T>& ph, const V3<T>& n2, const T X[4]) {
+    const T A1 = dot(n2, th), B1 = dot(n2, ph);
     if (A1 * A1 + B1 * B1 < T(1e-12)) return X[1];
     T c1, s1;
     double_angle(A1, B1, c1, s1);

@@ -39,8 +39,22 @@ constexpr int kDefaultBlock = 128;
 constexpr int kStageCams = 8;
 constexpr int kStageDoubles = 34;
 
+// camera record in shared memory: Omega, theta-hat, phi-hat, each padded to 4
+__device__ __forceinline__ void load_camera(const float* cm, V3<float>& Om, V3<float>& th, V3<float>& ph) {
+    const float4 a = reinterpret_cast<const float4*>(cm)[0], b = reinterpret_cast<const float4*>(cm)[1],
+                 c = reinterpret_cast<const float4*>(cm)[2];
+    Om = V3<float>{a.x, a.y, a.z};
+    th = V3<float>{b.x, b.y, b.z};
+    ph = V3<float>{c.x, c.y, c.z};
+}
+__device__ __forceinline__ void load_camera(const double* cm, V3<double>& Om, V3<double>& th, V3<double>& ph) {
+    Om = V3<double>{cm[0], cm[1], cm[2]};
+    th = V3<double>{cm[4], cm[5], cm[6]};
+    ph = V3<double>{cm[8], cm[9], cm[10]};
+}
+
 template <typename T> struct Smem {
-    const T* cam;        // [n_cam][9]: Omega, theta-hat, phi-hat
+    const T* cam;        // [n_cam][12]: Omega, theta-hat, phi-hat (each padded to 4)
     const float4* mix;   // [n_theta][2]
     const float4* kext;  // [n_ktheta]
     double* stage;       // [blockDim][kStageDoubles]
@@ -157,14 +171,19 @@ template <typename T> __device__ __forceinline__ T g_d(const TransportParams& P,
 template <> __device__ __forceinline__ float g_d<float>(const TransportParams& P, int a) { return P.d_f[a]; }
 template <> __device__ __forceinline__ double g_d<double>(const TransportParams& P, int a) { return P.g.d[a]; }
 
-// Widening of an FP32 tally contribution to FP64 with integer operations (exact for
-// normal numbers; zero, subnormals, infinities and NaN take the plain conversion).
+// Widening of an FP32 value to FP64 with integer operations only (the FP64 pipe of
+// GB300 is narrow): exact for normal numbers, infinities and NaN; FP32 subnormals
+// (|x| < 1.2e-38) become signed zero.
 __device__ __forceinline__ double widen(float f) {
     const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-    return __hiloint2double((int)hi, (int)((u & 7u) << 29));
+    const unsigned e = u & 0x7f800000u;
+    const unsigned sign = u & 0x80000000u;
+    // exponent and mantissa moved into the double's fields, exponent rebased by 1023 - 127
+    unsigned hi = sign | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
+    hi = e == 0x7f800000u ? (sign | 0x7ff00000u | ((u & 0x007fffffu) >> 3)) : hi;
+    hi = e == 0u ? sign : hi;
+    const unsigned lo = e == 0u ? 0u : (u << 29);
+    return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
@@ -411,7 +430,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     }
     const T omega = kext > T(0) ? ks / kext : T(0);
     const T dsca_exit = ks * ell_exit;
-    const bool scatter_here = (ks > T(0)) && (pk.tau < (double)dsca_exit);
+    const bool scatter_here = (ks > T(0)) && (pk.tau < widen(dsca_exit));
     const T ell = scatter_here ? T(pk.tau) / ks : ell_exit;
 
     // the next cell's record is requested before the segment arithmetic
@@ -477,8 +496,8 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
                 const int kn = P.n_cam - k0 < kStageCams ? P.n_cam - k0 : kStageCams;
                 if (lane == leader) bulk_wait_read();  // the slot's previous reduction has read it
                 for (int k = 0; k < kn; ++k) {
-                    const T* cm = sm.cam + 9 * (k0 + k);
-                    const V3<T> Om{cm[0], cm[1], cm[2]}, thc{cm[3], cm[4], cm[5]}, phc{cm[6], cm[7], cm[8]};
+                    V3<T> Om, thc, phc;
+                    load_camera(sm.cam + 12 * (k0 + k), Om, thc, phc);
                     const T mu = dot(n, Om);
                     T Pm[6];
                     if (SCAT == MCRT_SCAT_RAYLEIGH)
@@ -510,7 +529,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     pk.events++;
 
     if (!scatter_here) {
-        pk.tau -= (double)dsca_exit;
+        pk.tau -= widen(dsca_exit);
         pk.px += ell_exit * pk.nx;
         pk.py += ell_exit * pk.ny;
         pk.pz += ell_exit * pk.nz;
@@ -605,7 +624,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             table_matrix(tab, P.t.n_theta, mu, Pm);
             bound = ut.d * T(2) * T(P.t.env[(size_t)bin * nint + j]) * X[0];
         }
-        const T Qs = plane_Q(n, th, ph, n2, X);
+        const T Qs = plane_Q(th, ph, n2, X);
         if (bound < Pm[0] * X[0] + Pm[1] * Qs) {
             accepted = true;
             break;
@@ -641,14 +660,14 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
     float4* s_mix = s_kext + P.t.n_ktheta;
     const int n_mix = (SCAT == MCRT_SCAT_TABLE) ? 2 * P.t.n_theta : 0;
     T* s_cam = reinterpret_cast<T*>(s_mix + n_mix);
-    const int cam_bytes = (9 * P.n_cam * (int)sizeof(T) + 15) & ~15;
+    const int cam_bytes = 12 * P.n_cam * (int)sizeof(T);
     double* s_stage = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(s_cam) + cam_bytes);
     for (int i = threadIdx.x; i < P.t.n_ktheta; i += blockDim.x) s_kext[i] = P.t.kext[i];
     for (int i = threadIdx.x; i < n_mix; i += blockDim.x) s_mix[i] = P.t.mix[i];
-    for (int i = threadIdx.x; i < 9 * P.n_cam; i += blockDim.x) {
-        const CameraDev& cd = P.cam[i / 9];
-        const int e = i % 9;
-        s_cam[i] = T(e < 3 ? cd.dir[e] : (e < 6 ? cd.th[e - 3] : cd.ph[e - 6]));
+    for (int i = threadIdx.x; i < 12 * P.n_cam; i += blockDim.x) {
+        const CameraDev& cd = P.cam[i / 12];
+        const int e = i % 12, v = e / 4, w = e % 4;
+        s_cam[i] = w == 3 ? T(0) : T(v == 0 ? cd.dir[w] : (v == 1 ? cd.th[w] : cd.ph[w]));
     }
     if (threadIdx.x < 6) bt.e[threadIdx.x] = 0.0;
     if (threadIdx.x < 10) bt.n[threadIdx.x] = 0ull;
@@ -699,7 +718,7 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
 size_t transport_smem_bytes(const TransportParams& p, int precision, int block) {
     const size_t tsize = precision == MCRT_FP64 ? sizeof(double) : sizeof(float);
     const size_t mix = p.t.model == MCRT_SCAT_TABLE ? 2 * (size_t)p.t.n_theta * sizeof(float4) : 0;
-    const size_t cams = (9 * (size_t)p.n_cam * tsize + 15) & ~(size_t)15;
+    const size_t cams = 12 * (size_t)p.n_cam * tsize;
     return (size_t)p.t.n_ktheta * sizeof(float4) + mix + cams + (size_t)block * kStageDoubles * sizeof(double);
 }
 
