@@ -176,8 +176,8 @@ MCRT_API mcrt_status mcrt_set_dust_tables(mcrt_ctx *ctx, int32_t model, int32_t 
  * accumulating per model the absorbed energy per cell and the source tally
  *   T_c[cell] = sum over path segments of Z(Omega_c; Omega_pp) int I_pp ds
  * (eq. scat-disc-sum, path-integral estimator, FP64) for each camera c.
- * With n_models > 1 the same description runs once per model in one persistent
- * launch, model m using Philox stream desc->stream + m.
+ * With n_models > 1 the same description runs for every model in one persistent
+ * launch (see the batch calls below), model m using Philox stream desc->stream + m.
  * out_stats (nullable, host) receives the totals summed over models after the
  * stream has been synchronized.
  * Errors: MCRT_E_INVAL, MCRT_E_STATE (tables not set), MCRT_E_NOMEM, MCRT_E_CUDA,
@@ -227,6 +227,45 @@ MCRT_API const char *mcrt_last_error(const mcrt_ctx *ctx);
  * precision selects the FP32 or FP64 instantiation.
  */
 MCRT_API mcrt_status mcrt_unit_eval(int32_t fn, int32_t precision, int64_t n, const double *in, double *out);
+
+/*
+ * Batched launches (many models, e.g. one grid per wavelength, in one persistent
+ * launch).  The paper runs one model per launch; batching is a throughput layer
+ * over the same transport.  Job m of a batch is model m with Philox stream
+ * desc->stream + m, so its tallies equal those of a single launch of that model
+ * with that stream, up to the order of floating-point additions.
+ *
+ * mcrt_batch_create copies the description, sizes every model's tallies, builds
+ * the job table and captures one CUDA graph holding: zeroing of all tallies, the
+ * transport kernel over all jobs, and step 2 for every (model, camera) into
+ * batch-owned image buffers.  All models need the same scattering model; traces,
+ * accumulation and packet-id ranges are not available in a batch.  Errors of the
+ * batch calls are read with mcrt_last_error(NULL).
+ * mcrt_batch_run replays the graph with `seed` (Philox key word 0) on the batch's
+ * own stream; out_stats (nullable) holds the totals over all jobs after the run.
+ * mcrt_batch_tune runs short trial launches of packets_per_job packets per job for
+ * block sizes 64/96/128, full or one-less resident blocks per SM, and job-major or
+ * interleaved packet order, keeps the fastest and re-captures the graph; the
+ * trials overwrite the models' tallies.  report (nullable) lists the trials.
+ * mcrt_batch_images copies all images, [model][camera][4][ny][nx] FP64 (each
+ * camera with its own npix), to host or device memory.
+ * After a run, mcrt_get_tallies and mcrt_image_stokes work on each model as after
+ * a single launch.
+ */
+typedef struct mcrt_batch mcrt_batch;
+
+typedef struct {
+    int32_t n, best;
+    int32_t block_size[16], blocks_per_sm[16], interleave[16];
+    double events_per_s[16];
+} mcrt_tune_report;
+
+MCRT_API mcrt_status mcrt_batch_create(mcrt_batch **out, mcrt_ctx *const *models, int32_t n_models,
+                                       const mcrt_launch_desc *desc);
+MCRT_API mcrt_status mcrt_batch_run(mcrt_batch *batch, uint32_t seed, mcrt_stats *out_stats);
+MCRT_API mcrt_status mcrt_batch_tune(mcrt_batch *batch, int64_t packets_per_job, mcrt_tune_report *report);
+MCRT_API mcrt_status mcrt_batch_images(mcrt_batch *batch, double *out);
+MCRT_API mcrt_status mcrt_batch_destroy(mcrt_batch *batch); /* NULL-safe */
 
 /*
  * Transport without allocation.  The paper has no counterpart to this entry point;

@@ -63,10 +63,13 @@ mcrt_status fail(mcrt_ctx* ctx, mcrt_status st, const char* fmt, ...) {
     return st;
 }
 
-#define CK(ctx, call)                                                                                     \
-    do {                                                                                                  \
-        cudaError_t e_ = (call);                                                                          \
-        if (e_ != cudaSuccess) return fail((ctx), MCRT_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+#define CK(ctx, call)                                                                             \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            (void)cudaGetLastError();                                                             \
+            return fail((ctx), MCRT_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));             \
+        }                                                                                         \
     } while (0)
 
 bool is_device_ptr(const void* p) {
@@ -311,9 +314,8 @@ mcrt_status mcrt_set_dust_tables(mcrt_ctx* ctx, int32_t model, int32_t n_bins, i
     return MCRT_OK;
 }
 
-static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t stream_key, mcrt_stats* st_out,
-                              bool want_sync) {
-    if (!ctx->tables_set) return fail(ctx, MCRT_E_STATE, "mcrt_launch_packets: mcrt_set_dust_tables not called");
+// Checks of a launch description that do not depend on the model.
+static mcrt_status check_desc(mcrt_ctx* ctx, const mcrt_launch_desc* d) {
     if (d->n_sources < 1 || d->n_sources > kMaxSources || !d->sources)
         return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: need 1..%d sources", kMaxSources);
     if (d->n_cameras < 0 || d->n_cameras > kMaxCams || (d->n_cameras > 0 && !d->cameras))
@@ -323,25 +325,74 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t
     if (d->roulette_threshold < 0.0 || (d->roulette_threshold > 0.0 && !(d->roulette_survival > 0.0 && d->roulette_survival <= 1.0)))
         return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad roulette parameters");
     if (d->n_trace < 0 || (d->n_trace > 0 && !d->trace)) return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad trace");
-
-    TransportParams P{};
-    P.g = ctx->g;
-    P.t = ctx->t;
-    long long total = 0;
-    bool need_thermal = false;
     for (int s = 0; s < d->n_sources; ++s) {
         const mcrt_source& src = d->sources[s];
         if (src.type < MCRT_SRC_POINT || src.type > MCRT_SRC_THERMAL)
             return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad source type %d", src.type);
         if (src.n_packets < 0) return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: negative n_packets");
+        if (src.type == MCRT_SRC_BEAM && src.beam_dir != 1 && src.beam_dir != -1)
+            return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: beam_dir must be +1 or -1");
+    }
+    for (int k = 0; k < d->n_cameras; ++k) {
+        const mcrt_camera& cm = d->cameras[k];
+        const double nn = std::sqrt(cm.dir[0] * cm.dir[0] + cm.dir[1] * cm.dir[1] + cm.dir[2] * cm.dir[2]);
+        if (!(nn > 0.0) || cm.npix[0] < 1 || cm.npix[1] < 1 || !(cm.fov[0] > 0.0) || !(cm.fov[1] > 0.0))
+            return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad camera %d", k);
+    }
+    return MCRT_OK;
+}
+
+static long long desc_total(const mcrt_launch_desc* d) {
+    long long total = 0;
+    for (int s = 0; s < d->n_sources; ++s) total += d->sources[s].n_packets;
+    return total;
+}
+
+// Launch-wide parameters: sources (without energies), cameras, random-number key,
+// roulette, caps.
+static void fill_common(const mcrt_launch_desc* d, TransportParams& P) {
+    long long start = 0;
+    for (int s = 0; s < d->n_sources; ++s) {
+        const mcrt_source& src = d->sources[s];
+        SourceDev& o = P.src[s];
+        o.type = src.type;
+        o.beam_dir = src.beam_dir;
+        o.start = start;
+        o.count = src.n_packets;
+        for (int a = 0; a < 3; ++a) o.pos[a] = src.pos[a];
+        start += src.n_packets;
+    }
+    P.n_src = d->n_sources;
+    for (int k = 0; k < d->n_cameras; ++k) {
+        const mcrt_camera& cm = d->cameras[k];
+        const double nn = std::sqrt(cm.dir[0] * cm.dir[0] + cm.dir[1] * cm.dir[1] + cm.dir[2] * cm.dir[2]);
+        CameraDev& cd = P.cam[k];
+        for (int a = 0; a < 3; ++a) cd.dir[a] = cm.dir[a] / nn;
+        host_basis(cd.dir, cd.th, cd.ph);
+    }
+    P.n_cam = d->n_cameras;
+    P.seed = d->seed;
+    P.stream = d->stream;
+    P.roulette_thr = d->roulette_threshold;
+    P.roulette_surv = d->roulette_survival > 0.0 ? d->roulette_survival : 1.0;
+    P.max_events = d->max_events > 0 ? (d->max_events < 2147483647ll ? d->max_events : 2147483647ll) : 100000;
+    P.max_trials = d->max_trials > 0 ? d->max_trials : 1000;
+    P.time_budget_ns = d->time_budget_s > 0.0 ? d->time_budget_s * 1e9 : 0.0;
+}
+
+// Model part of a launch: checks the description against the model, builds the
+// thermal-emission CDF when a thermal source needs it, sizes the tallies and zeroes
+// them unless accumulating, and fills the model's job record.
+static mcrt_status prepare_model(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t stream_key, JobDev& job) {
+    if (!ctx->tables_set) return fail(ctx, MCRT_E_STATE, "mcrt_launch_packets: mcrt_set_dust_tables not called");
+    bool need_thermal = false;
+    for (int s = 0; s < d->n_sources; ++s) {
+        const mcrt_source& src = d->sources[s];
         if (src.type == MCRT_SRC_POINT)
             for (int a = 0; a < 3; ++a)
                 if (!(src.pos[a] >= ctx->g.lo[a] && src.pos[a] <= ctx->g.hi[a]))
                     return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: point source outside the grid");
-        if (src.type == MCRT_SRC_BEAM && src.beam_dir != 1 && src.beam_dir != -1)
-            return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: beam_dir must be +1 or -1");
         if (src.type == MCRT_SRC_THERMAL) need_thermal = true;
-        total += src.n_packets;
     }
     if (need_thermal && !ctx->has_emissivity)
         return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: thermal source needs an emissivity grid");
@@ -360,44 +411,7 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t
     }
     if (need_thermal && !(ctx->thermal_total > 0.0))
         return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: thermal source but the grid emits nothing");
-    long long start = 0;
-    for (int s = 0; s < d->n_sources; ++s) {
-        const mcrt_source& src = d->sources[s];
-        SourceDev& o = P.src[s];
-        o.type = src.type;
-        o.beam_dir = src.beam_dir;
-        o.start = start;
-        o.count = src.n_packets;
-        double L = src.luminosity;
-        if (src.type == MCRT_SRC_THERMAL && L <= 0.0) L = 4.0 * 3.141592653589793 * ctx->thermal_total;
-        o.eps = src.n_packets > 0 ? L / (double)src.n_packets : 0.0;
-        for (int a = 0; a < 3; ++a) o.pos[a] = src.pos[a];
-        start += src.n_packets;
-    }
-    P.n_src = d->n_sources;
-    for (int k = 0; k < d->n_cameras; ++k) {
-        const mcrt_camera& cm = d->cameras[k];
-        const double nn = std::sqrt(cm.dir[0] * cm.dir[0] + cm.dir[1] * cm.dir[1] + cm.dir[2] * cm.dir[2]);
-        if (!(nn > 0.0) || cm.npix[0] < 1 || cm.npix[1] < 1 || !(cm.fov[0] > 0.0) || !(cm.fov[1] > 0.0))
-            return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad camera %d", k);
-        CameraDev& cd = P.cam[k];
-        for (int a = 0; a < 3; ++a) cd.dir[a] = cm.dir[a] / nn;
-        host_basis(cd.dir, cd.th, cd.ph);
-    }
-    P.n_cam = d->n_cameras;
-    P.thermal_cdf = ctx->d_cdf;
-    P.thermal_total = ctx->thermal_total;
-    P.thermal_guide = ctx->d_guide;
-    P.n_guide = ctx->n_guide;
-    for (int a = 0; a < 3; ++a) {
-        P.lo_f[a] = (float)ctx->g.lo[a];
-        P.d_f[a] = (float)ctx->g.d[a];
-    }
 
-    long long pb = d->pid_begin, pe = d->pid_end <= 0 ? total : d->pid_end;
-    if (pb < 0 || pe > total || pb > pe) return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad packet id range");
-
-    // tallies
     const size_t S_elems = (size_t)ctx->g.ncell * (size_t)(d->n_cameras > 0 ? d->n_cameras : 1) * 4;
     if (d->accumulate && (!ctx->launched || ctx->n_cam != d->n_cameras))
         return fail(ctx, MCRT_E_STATE, "mcrt_launch_packets: accumulate needs a previous launch with the same cameras");
@@ -418,17 +432,92 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t
     ctx->precision = d->precision;
     for (int k = 0; k < d->n_cameras; ++k) ctx->cams[k] = d->cameras[k];
 
-    P.S = ctx->d_S;
-    P.absorbed = ctx->d_absorbed;
-    P.seed = d->seed;
-    P.stream = stream_key;
+    job = JobDev{};
+    for (int a = 0; a < 3; ++a) {
+        job.n[a] = ctx->g.n[a];
+        job.lo[a] = ctx->g.lo[a];
+        job.hi[a] = ctx->g.hi[a];
+        job.d[a] = ctx->g.d[a];
+        job.lo_f[a] = (float)ctx->g.lo[a];
+        job.d_f[a] = (float)ctx->g.d[a];
+    }
+    job.ncell = ctx->g.ncell;
+    job.cells = ctx->d_cells;
+    job.S = ctx->d_S;
+    job.absorbed = ctx->d_absorbed;
+    job.t = ctx->t;
+    job.thermal_cdf = ctx->d_cdf;
+    job.thermal_total = ctx->thermal_total;
+    job.thermal_guide = ctx->d_guide;
+    job.n_guide = ctx->n_guide;
+    for (int s = 0; s < d->n_sources; ++s) {
+        const mcrt_source& src = d->sources[s];
+        double L = src.luminosity;
+        if (src.type == MCRT_SRC_THERMAL && L <= 0.0) L = 4.0 * 3.141592653589793 * ctx->thermal_total;
+        job.src_eps[s] = src.n_packets > 0 ? L / (double)src.n_packets : 0.0;
+    }
+    job.stream = stream_key;
+    return MCRT_OK;
+}
+
+static void add_stats(mcrt_stats* st, const double raw[16], unsigned status, float ms) {
+    const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(raw + 6);
+    st->emitted_energy += raw[0];
+    st->escaped_energy += raw[1];
+    st->absorbed_energy += raw[2];
+    st->roulette_lost += raw[3];
+    st->roulette_gain += raw[4];
+    st->cap_lost += raw[5];
+    st->events += (double)cnt[0];
+    st->segments += (double)cnt[1];
+    st->scatterings += (double)cnt[2];
+    st->emitted += (double)cnt[3];
+    st->escaped += (double)cnt[4];
+    st->roulette_killed += (double)cnt[5];
+    st->cap_hits += (double)cnt[6];
+    st->trials += (double)cnt[7];
+    st->tally_segments += (double)cnt[8];
+    st->absorb_segments += (double)cnt[9];
+    st->kernel_ms += ms;
+    st->status_bits = (double)((unsigned)st->status_bits | status);
+}
+
+static mcrt_status status_of(mcrt_ctx* ctx, unsigned status) {
+    if (status & MCRT_STATUS_TIMEOUT) return fail(ctx, MCRT_E_TIMEOUT, "mcrt_launch_packets: time budget exhausted");
+    if (status & (MCRT_STATUS_EVENT_CAP | MCRT_STATUS_TRIAL_CAP))
+        return fail(ctx, MCRT_E_EVENT_CAP, "mcrt_launch_packets: packets reached the event or trial cap");
+    return MCRT_OK;
+}
+
+static mcrt_status launch_batched(mcrt_ctx* const* models, int32_t n_models, const mcrt_launch_desc* desc,
+                                  mcrt_stats* out_stats);
+
+static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_stats* st_out, bool want_sync) {
+    mcrt_status st = check_desc(ctx, d);
+    if (st != MCRT_OK) return st;
+    JobDev job;
+    st = prepare_model(ctx, d, d->stream, job);
+    if (st != MCRT_OK) return st;
+    TransportParams P{};
+    fill_common(d, P);
+    P.g = ctx->g;
+    P.t = ctx->t;
+    for (int a = 0; a < 3; ++a) {
+        P.lo_f[a] = job.lo_f[a];
+        P.d_f[a] = job.d_f[a];
+    }
+    for (int s = 0; s < d->n_sources; ++s) P.src[s].eps = job.src_eps[s];
+    P.thermal_cdf = job.thermal_cdf;
+    P.thermal_total = job.thermal_total;
+    P.thermal_guide = job.thermal_guide;
+    P.n_guide = job.n_guide;
+    P.S = job.S;
+    P.absorbed = job.absorbed;
+    const long long total = desc_total(d);
+    const long long pb = d->pid_begin, pe = d->pid_end <= 0 ? total : d->pid_end;
+    if (pb < 0 || pe > total || pb > pe) return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad packet id range");
     P.pid_begin = pb;
     P.pid_end = pe;
-    P.roulette_thr = d->roulette_threshold;
-    P.roulette_surv = d->roulette_survival > 0.0 ? d->roulette_survival : 1.0;
-    P.max_events = d->max_events > 0 ? (d->max_events < 2147483647ll ? d->max_events : 2147483647ll) : 100000;
-    P.max_trials = d->max_trials > 0 ? d->max_trials : 1000;
-    P.time_budget_ns = d->time_budget_s > 0.0 ? d->time_budget_s * 1e9 : 0.0;
     P.counter = reinterpret_cast<unsigned long long*>(ctx->d_work);
     P.stats = reinterpret_cast<double*>(ctx->d_work + 8);
     P.status = reinterpret_cast<unsigned*>(ctx->d_work + 8 + 16 * 8);
@@ -455,7 +544,7 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t
     if (block % 32 != 0 || block > 128)
         return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: block_size must be a multiple of 32, <= 128");
     const size_t smem = transport_smem_bytes(P, d->precision, block);
-    int bps = transport_max_blocks_per_sm(d->precision, P.t.model, block, smem);
+    int bps = transport_max_blocks_per_sm(d->precision, P.t.model, false, block, smem);
     if (d->blocks_per_sm > 0 && d->blocks_per_sm < bps) bps = d->blocks_per_sm;
     const long long work = pe - pb;
     long long grid = (long long)ctx->n_sm * bps;
@@ -478,31 +567,8 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint32_t
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     float ms = 0.f;
     CK(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-    if (st_out) {
-        const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(raw + 6);
-        st_out->emitted_energy += raw[0];
-        st_out->escaped_energy += raw[1];
-        st_out->absorbed_energy += raw[2];
-        st_out->roulette_lost += raw[3];
-        st_out->roulette_gain += raw[4];
-        st_out->cap_lost += raw[5];
-        st_out->events += (double)cnt[0];
-        st_out->segments += (double)cnt[1];
-        st_out->scatterings += (double)cnt[2];
-        st_out->emitted += (double)cnt[3];
-        st_out->escaped += (double)cnt[4];
-        st_out->roulette_killed += (double)cnt[5];
-        st_out->cap_hits += (double)cnt[6];
-        st_out->trials += (double)cnt[7];
-        st_out->tally_segments += (double)cnt[8];
-        st_out->absorb_segments += (double)cnt[9];
-        st_out->kernel_ms += ms;
-        st_out->status_bits = (double)((unsigned)st_out->status_bits | status);
-    }
-    if (status & MCRT_STATUS_TIMEOUT) return fail(ctx, MCRT_E_TIMEOUT, "mcrt_launch_packets: time budget exhausted");
-    if (status & (MCRT_STATUS_EVENT_CAP | MCRT_STATUS_TRIAL_CAP))
-        return fail(ctx, MCRT_E_EVENT_CAP, "mcrt_launch_packets: packets reached the event or trial cap");
-    return MCRT_OK;
+    if (st_out) add_stats(st_out, raw, status, ms);
+    return status_of(ctx, status);
 }
 
 mcrt_status mcrt_launch_packets(mcrt_ctx* const* models, int32_t n_models, const mcrt_launch_desc* desc,
@@ -511,19 +577,8 @@ mcrt_status mcrt_launch_packets(mcrt_ctx* const* models, int32_t n_models, const
     for (int m = 0; m < n_models; ++m)
         if (!models[m]) return fail(nullptr, MCRT_E_INVAL, "mcrt_launch_packets: model %d is NULL", m);
     if (out_stats) std::memset(out_stats, 0, sizeof(*out_stats));
-    mcrt_status worst = MCRT_OK;
-    for (int m = 0; m < n_models; ++m) {
-        mcrt_status s = launch_one(models[m], desc, desc->stream + (uint32_t)m, out_stats, out_stats != nullptr);
-        if (s == MCRT_E_EVENT_CAP || s == MCRT_E_TIMEOUT) {
-            worst = s;
-            continue;
-        }
-        if (s != MCRT_OK) {
-            std::snprintf(g_err, sizeof g_err, "model %d: %s", m, models[m]->err);
-            return s;
-        }
-    }
-    return worst;
+    if (n_models == 1) return launch_one(models[0], desc, out_stats, out_stats != nullptr);
+    return launch_batched(models, n_models, desc, out_stats);
 }
 
 mcrt_status mcrt_image_stokes(mcrt_ctx* ctx, int32_t camera, double* out) {
@@ -610,3 +665,363 @@ mcrt_status mcrt_unit_eval(int32_t fn, int32_t precision, int64_t n, const doubl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Batched launches: many models (e.g. one per wavelength) in one persistent launch
+// ---------------------------------------------------------------------------------
+struct mcrt_batch {
+    std::vector<mcrt_ctx*> models;
+    mcrt_launch_desc desc{};
+    std::vector<mcrt_source> sources;
+    std::vector<mcrt_camera> cameras;
+    cudaStream_t stream = nullptr;  // private stream: the launch sequence is captured on it
+    std::vector<JobDev> jobs;
+    JobDev* d_jobs = nullptr;
+    JobDev* d_trial = nullptr;
+    unsigned char* d_work = nullptr;
+    TransportParams P{};
+    long long per_job = 0;
+    int n_sm = 0, block = 128, bps = 0, interleave = 0;
+    double* d_images = nullptr;
+    std::vector<size_t> img_off;  // [job][camera] offsets into d_images
+    size_t img_elems = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t kernel_node = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+#define BK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            (void)cudaGetLastError();                                                             \
+            return fail(nullptr, MCRT_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_));          \
+        }                                                                                         \
+    } while (0)
+
+void batch_free(mcrt_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_trial);
+    cudaFree(b->d_work);
+    cudaFree(b->d_images);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+// Job table, work area and launch parameters for the models; tallies of every model
+// are sized and zeroed (prepare_model).
+mcrt_status batch_build(mcrt_batch** out, mcrt_ctx* const* models, int32_t n_models, const mcrt_launch_desc* desc,
+                        bool images) {
+    *out = nullptr;
+    if (!models || n_models < 1 || !desc) return fail(nullptr, MCRT_E_INVAL, "batch: no models or desc");
+    mcrt_status st = check_desc(nullptr, desc);
+    if (st != MCRT_OK) return st;
+    if (desc->n_trace > 0 || desc->accumulate || desc->pid_begin != 0 || desc->pid_end > 0)
+        return fail(nullptr, MCRT_E_INVAL, "batch: traces, accumulation and packet id ranges are single-model options");
+    for (int m = 0; m < n_models; ++m) {
+        if (!models[m]) return fail(nullptr, MCRT_E_INVAL, "batch: model %d is NULL", m);
+        if (!models[m]->tables_set) return fail(nullptr, MCRT_E_STATE, "batch: model %d has no optics", m);
+        if (models[m]->t.model != models[0]->t.model)
+            return fail(nullptr, MCRT_E_INVAL, "batch: all models need the same scattering model");
+    }
+    mcrt_batch* b = new (std::nothrow) mcrt_batch();
+    if (!b) return fail(nullptr, MCRT_E_NOMEM, "batch: host allocation failed");
+    b->models.assign(models, models + n_models);
+    b->desc = *desc;
+    b->sources.assign(desc->sources, desc->sources + desc->n_sources);
+    b->cameras.assign(desc->cameras, desc->cameras + desc->n_cameras);
+    b->desc.sources = b->sources.data();
+    b->desc.cameras = b->cameras.data();
+    b->per_job = desc_total(desc);
+    b->jobs.resize(n_models);
+    for (int m = 0; m < n_models; ++m) {
+        st = prepare_model(models[m], &b->desc, desc->stream + (uint32_t)m, b->jobs[m]);
+        if (st != MCRT_OK) {
+            std::snprintf(g_err, sizeof g_err, "batch: model %d: %s", m, models[m]->err);
+            batch_free(b);
+            return st;
+        }
+        b->jobs[m].pid_start = (long long)m * b->per_job;
+        b->jobs[m].index = (unsigned)m;
+        if (cudaStreamSynchronize(models[m]->stream) != cudaSuccess) {
+            batch_free(b);
+            return fail(nullptr, MCRT_E_CUDA, "batch: model %d stream failed", m);
+        }
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_jobs, sizeof(JobDev) * n_models);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_trial, sizeof(JobDev) * n_models);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_work, kWorkBytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_jobs, b->jobs.data(), sizeof(JobDev) * n_models, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && images) {
+        for (int m = 0; m < n_models; ++m)
+            for (int k = 0; k < desc->n_cameras; ++k) {
+                b->img_off.push_back(b->img_elems);
+                b->img_elems += (size_t)4 * desc->cameras[k].npix[0] * desc->cameras[k].npix[1];
+            }
+        if (b->img_elems) e = cudaMalloc(&b->d_images, b->img_elems * sizeof(double));
+    }
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? MCRT_E_NOMEM : MCRT_E_CUDA, "batch: %s",
+                    cudaGetErrorString(e));
+    }
+    TransportParams& P = b->P;
+    fill_common(&b->desc, P);
+    P.t = models[0]->t;  // selects the kernel; the tables themselves come from the jobs
+    P.jobs = b->d_jobs;
+    P.n_jobs = n_models;
+    P.pid_begin = 0;
+    P.pid_end = (long long)n_models * b->per_job;
+    P.counter = reinterpret_cast<unsigned long long*>(b->d_work);
+    P.stats = reinterpret_cast<double*>(b->d_work + 8);
+    P.status = reinterpret_cast<unsigned*>(b->d_work + 8 + 16 * 8);
+    b->block = desc->block_size > 0 ? desc->block_size : 128;
+    if (b->block % 32 != 0 || b->block > 128) {
+        batch_free(b);
+        return fail(nullptr, MCRT_E_INVAL, "batch: block_size must be a multiple of 32, <= 128");
+    }
+    b->bps = desc->blocks_per_sm;
+    *out = b;
+    return MCRT_OK;
+}
+
+int batch_grid(const mcrt_batch* b, const TransportParams& P, int block, int bps_req) {
+    const size_t smem = transport_smem_bytes(P, b->desc.precision, block);
+    int bps = transport_max_blocks_per_sm(b->desc.precision, P.t.model, true, block, smem);
+    if (bps_req > 0 && bps_req < bps) bps = bps_req;
+    long long grid = (long long)b->n_sm * bps;
+    const long long work = P.pid_end - P.pid_begin;
+    const long long need = (work + block - 1) / block;
+    if (need < grid) grid = need > 0 ? need : 1;
+    return (int)grid;
+}
+
+// Queues one batched transport launch (and optionally the images) on b->stream.
+mcrt_status batch_enqueue(mcrt_batch* b, const TransportParams& P, int block, int bps, bool zero_tallies,
+                          bool images, bool capturing = false) {
+    // inside a stream capture the timing events must become event-record nodes
+    const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    BK(cudaMemsetAsync(b->d_work, 0, kWorkBytes, b->stream));
+    if (zero_tallies)
+        for (mcrt_ctx* c : b->models) {
+            BK(cudaMemsetAsync(c->d_S, 0, c->S_elems * sizeof(double), b->stream));
+            BK(cudaMemsetAsync(c->d_absorbed, 0, (size_t)c->g.ncell * sizeof(double), b->stream));
+        }
+    BK(cudaEventRecordWithFlags(b->ev0, b->stream, ev_flags));
+    if (P.pid_end > P.pid_begin) BK(launch_transport(P, b->desc.precision, block, batch_grid(b, P, block, bps), b->stream));
+    BK(cudaEventRecordWithFlags(b->ev1, b->stream, ev_flags));
+    if (images && b->d_images) {
+        size_t i = 0;
+        for (size_t m = 0; m < b->models.size(); ++m) {
+            const mcrt_ctx* c = b->models[m];
+            for (int k = 0; k < b->desc.n_cameras; ++k, ++i) {
+                const mcrt_camera& cm = b->cameras[k];
+                ImageParams ip{};
+                ip.g = c->g;
+                ip.t = c->t;
+                const double nn = std::sqrt(cm.dir[0] * cm.dir[0] + cm.dir[1] * cm.dir[1] + cm.dir[2] * cm.dir[2]);
+                for (int a = 0; a < 3; ++a) ip.cam.dir[a] = cm.dir[a] / nn;
+                host_basis(ip.cam.dir, ip.cam.th, ip.cam.ph);
+                for (int a = 0; a < 3; ++a) ip.center[a] = cm.center[a];
+                ip.fov[0] = cm.fov[0];
+                ip.fov[1] = cm.fov[1];
+                ip.npix[0] = cm.npix[0];
+                ip.npix[1] = cm.npix[1];
+                ip.cam_index = k;
+                ip.n_cam = b->desc.n_cameras;
+                ip.S = c->d_S;
+                ip.out = b->d_images + b->img_off[i];
+                BK(launch_image(ip, b->desc.precision, b->stream));
+            }
+        }
+    }
+    return MCRT_OK;
+}
+
+mcrt_status batch_read_stats(mcrt_batch* b, mcrt_stats* out) {
+    double raw[16];
+    unsigned status = 0;
+    BK(cudaMemcpyAsync(raw, b->d_work + 8, sizeof raw, cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaMemcpyAsync(&status, b->d_work + 8 + 16 * 8, sizeof status, cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    float ms = 0.f;
+    BK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        add_stats(out, raw, status, ms);
+    }
+    return status_of(nullptr, status);
+}
+
+// Captures memsets + transport + images into a CUDA graph and finds the transport node.
+mcrt_status batch_capture(mcrt_batch* b) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    // dynamic shared memory attributes are set outside the capture
+    batch_grid(b, b->P, b->block, b->bps);
+    BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    mcrt_status st = batch_enqueue(b, b->P, b->block, b->bps, true, true, true);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (st != MCRT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(nullptr, MCRT_E_CUDA, "batch: capture: %s", cudaGetErrorString(e));
+    b->graph = g;
+    BK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    size_t n = 0;
+    BK(cudaGraphGetNodes(b->graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    BK(cudaGraphGetNodes(b->graph, nodes.data(), &n));
+    const void* kfn = transport_kernel(b->desc.precision, b->P.t.model, true);
+    b->kernel_node = nullptr;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        BK(cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        BK(cudaGraphKernelNodeGetParams(nd, &kp));
+        if (kp.func == kfn) b->kernel_node = nd;
+    }
+    if (!b->kernel_node && b->P.pid_end > b->P.pid_begin)
+        return fail(nullptr, MCRT_E_CUDA, "batch: transport node not found in the captured graph");
+    return MCRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mcrt_status mcrt_batch_create(mcrt_batch** out, mcrt_ctx* const* models, int32_t n_models,
+                              const mcrt_launch_desc* desc) {
+    if (!out) return fail(nullptr, MCRT_E_INVAL, "mcrt_batch_create: out is NULL");
+    mcrt_batch* b = nullptr;
+    mcrt_status st = batch_build(&b, models, n_models, desc, true);
+    if (st != MCRT_OK) return st;
+    st = batch_capture(b);
+    if (st != MCRT_OK) {
+        batch_free(b);
+        return st;
+    }
+    *out = b;
+    return MCRT_OK;
+}
+
+mcrt_status mcrt_batch_run(mcrt_batch* b, uint32_t seed, mcrt_stats* out_stats) {
+    if (!b || !b->exec) return fail(nullptr, MCRT_E_INVAL, "mcrt_batch_run: no batch");
+    if (b->kernel_node) {
+        TransportParams Pr = b->P;
+        Pr.seed = seed;
+        cudaKernelNodeParams kp;
+        BK(cudaGraphKernelNodeGetParams(b->kernel_node, &kp));
+        void* args[] = {&Pr};
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        BK(cudaGraphExecKernelNodeSetParams(b->exec, b->kernel_node, &kp));
+    }
+    BK(cudaGraphLaunch(b->exec, b->stream));
+    for (mcrt_ctx* c : b->models) c->launched = true;
+    if (!out_stats) return MCRT_OK;
+    return batch_read_stats(b, out_stats);
+}
+
+mcrt_status mcrt_batch_tune(mcrt_batch* b, int64_t packets_per_job, mcrt_tune_report* report) {
+    if (!b) return fail(nullptr, MCRT_E_INVAL, "mcrt_batch_tune: no batch");
+    if (packets_per_job < 1) return fail(nullptr, MCRT_E_INVAL, "mcrt_batch_tune: packets_per_job < 1");
+    const long long trial = packets_per_job < b->per_job ? packets_per_job : b->per_job;
+    std::vector<JobDev> tj = b->jobs;
+    for (size_t m = 0; m < tj.size(); ++m) tj[m].pid_start = (long long)m * trial;
+    BK(cudaMemcpy(b->d_trial, tj.data(), sizeof(JobDev) * tj.size(), cudaMemcpyHostToDevice));
+    mcrt_tune_report rep{};
+    double best = -1.0;
+    const int blocks[3] = {64, 96, 128};
+    for (int bi = 0; bi < 3; ++bi)
+        for (int occ = 0; occ < 2; ++occ)
+            for (int il = 0; il < 2; ++il) {
+                TransportParams Pt = b->P;
+                Pt.jobs = b->d_trial;
+                Pt.pid_end = (long long)tj.size() * trial;
+                Pt.job_interleave = il;
+                const size_t smem = transport_smem_bytes(Pt, b->desc.precision, blocks[bi]);
+                const int bmax = transport_max_blocks_per_sm(b->desc.precision, Pt.t.model, true, blocks[bi], smem);
+                const int bps = occ == 0 ? bmax : (bmax > 1 ? bmax - 1 : 1);
+                if (occ == 1 && bmax <= 1) continue;
+                mcrt_status st = batch_enqueue(b, Pt, blocks[bi], bps, false, false);
+                if (st != MCRT_OK) return st;
+                mcrt_stats s{};
+                st = batch_read_stats(b, &s);
+                if (st != MCRT_OK && st != MCRT_E_EVENT_CAP) return st;
+                const double rate = s.kernel_ms > 0 ? s.events / (s.kernel_ms * 1e-3) : 0.0;
+                if (rep.n < 16) {
+                    rep.block_size[rep.n] = blocks[bi];
+                    rep.blocks_per_sm[rep.n] = bps;
+                    rep.interleave[rep.n] = il;
+                    rep.events_per_s[rep.n] = rate;
+                    if (rate > best) {
+                        best = rate;
+                        rep.best = rep.n;
+                    }
+                    rep.n++;
+                }
+            }
+    b->block = rep.block_size[rep.best];
+    b->bps = rep.blocks_per_sm[rep.best];
+    b->interleave = rep.interleave[rep.best];
+    b->P.job_interleave = b->interleave;
+    if (report) *report = rep;
+    return batch_capture(b);
+}
+
+mcrt_status mcrt_batch_images(mcrt_batch* b, double* out) {
+    if (!b || !out) return fail(nullptr, MCRT_E_INVAL, "mcrt_batch_images: no batch or out");
+    if (!b->d_images) return MCRT_OK;
+    BK(cudaMemcpyAsync(out, b->d_images, b->img_elems * sizeof(double), cudaMemcpyDefault, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    return MCRT_OK;
+}
+
+mcrt_status mcrt_batch_destroy(mcrt_batch* b) {
+    if (b) cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    return MCRT_OK;
+}
+
+}  // extern "C"
+
+// n_models > 1: one persistent launch over the job table of all models (no graph).
+static mcrt_status launch_batched(mcrt_ctx* const* models, int32_t n_models, const mcrt_launch_desc* desc,
+                                  mcrt_stats* out_stats) {
+    mcrt_batch* b = nullptr;
+    mcrt_status st = batch_build(&b, models, n_models, desc, false);
+    if (st != MCRT_OK) return st;
+    st = batch_enqueue(b, b->P, b->block, b->bps, false, false);
+    if (st == MCRT_OK) {
+        for (mcrt_ctx* c : b->models) c->launched = true;
+        mcrt_stats tmp{};
+        st = batch_read_stats(b, out_stats ? out_stats : &tmp);
+    }
+    batch_free(b);
+    return st;
+}

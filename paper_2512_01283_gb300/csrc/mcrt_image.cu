@@ -361,6 +361,7 @@ cudaError_t launch_image(const ImageParams& p, int precision, cudaStream_t s) {
     const long long npix = (long long)p.npix[0] * p.npix[1];
     const int block = 128;
     const unsigned grid = (unsigned)((npix + block - 1) / block);
+    (void)cudaGetLastError();  // report this launch's error only
     if (precision == MCRT_FP64)
         k_image<double><<<grid, block, 0, s>>>(p);
     else
@@ -375,6 +376,7 @@ cudaError_t launch_setup_cells(const float* ka, const float* ks, const float* bf
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const long long want = (ncell + 255) / 256;
     const unsigned grid = (unsigned)(want < (long long)nsm * 8 ? (want > 0 ? want : 1) : (long long)nsm * 8);
+    (void)cudaGetLastError();  // report this launch's error only
     k_setup_cells<<<grid, 256, 0, s>>>(ka, ks, bf, em, ncell, cells, bad);
     return cudaGetLastError();
 }
@@ -383,6 +385,7 @@ cudaError_t launch_prepare_tables(int model, int n_bins, int n_theta, int n_kthe
                                   const float* bin_weight, const float* kext, float4* mix, float4* bins,
                                   double* env_cdf, float* env, double* bin_cdf, float4* kext4, double* alpha1_mean,
                                   cudaStream_t s) {
+    (void)cudaGetLastError();  // report this launch's error only
     k_prepare_tables<<<1, 256, 0, s>>>(model, n_bins, n_theta, n_ktheta, mueller, bin_weight, kext, mix, bins,
                                        env_cdf, env, bin_cdf, kext4, alpha1_mean);
     return cudaGetLastError();
@@ -391,8 +394,13 @@ cudaError_t launch_prepare_tables(int model, int n_bins, int n_theta, int n_kthe
 cudaError_t launch_thermal_cdf(const GridDev& g, double alpha1_mean, double* cdf, double* block_sums, int n_blocks,
                                cudaStream_t s) {
     const double vol = g.d[0] * g.d[1] * g.d[2];
+    (void)cudaGetLastError();  // report these launches' errors only
     k_scan_local<<<n_blocks, kScanBlock, 0, s>>>(g.cells, g.ncell, alpha1_mean, vol, cdf, block_sums);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     k_scan_sums<<<1, 32, 0, s>>>(block_sums, n_blocks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     k_scan_add<<<n_blocks, kScanBlock, 0, s>>>(cdf, g.ncell, block_sums);
     return cudaGetLastError();
 }
@@ -421,6 +429,7 @@ cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* 
                                  cudaStream_t s) {
     const long long n = n_guide + 1;
     const unsigned grid = (unsigned)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
+    (void)cudaGetLastError();  // report this launch's error only
     k_thermal_guide<<<grid, 256, 0, s>>>(cdf, ncell, guide, n_guide);
     return cudaGetLastError();
 }
@@ -430,6 +439,7 @@ int thermal_cdf_blocks(long long ncell) { return (int)((ncell + (long long)kScan
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s) {
     const int block = 128;
     const unsigned grid = (unsigned)((n + block - 1) / block);
+    (void)cudaGetLastError();  // report this launch's error only
     if (precision == MCRT_FP64)
         k_unit<double><<<grid, block, 0, s>>>(fn, n, in, out);
     else

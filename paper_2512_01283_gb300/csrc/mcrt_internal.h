@@ -47,6 +47,27 @@ struct CameraDev {
     double dir[3], th[3], ph[3];
 };
 
+// One job of a batched launch (a model, e.g. at one wavelength): its grid, tallies,
+// tables, thermal-emission CDF and the energy per packet of each source.
+struct JobDev {
+    int n[3];
+    float lo_f[3], d_f[3];
+    double lo[3], hi[3], d[3];
+    long long ncell;
+    const float4* cells;
+    double* S;
+    double* absorbed;
+    TablesDev t;
+    const double* thermal_cdf;
+    double thermal_total;
+    const long long* thermal_guide;
+    long long n_guide;
+    double src_eps[kMaxSources];
+    long long pid_start;  // first index of the job in the batch's packet index space
+    unsigned stream;      // Philox key word 1
+    unsigned index;
+};
+
 struct TransportParams {
     GridDev g;
     float lo_f[3], d_f[3];  // FP32 copies of g.lo, g.d
@@ -72,6 +93,11 @@ struct TransportParams {
     unsigned* status;
     double* trace;
     long long n_trace;
+    // batched launch: job table (nullptr for a single model); packet indices
+    // [0, total) are split over the jobs by JobDev::pid_start
+    const JobDev* jobs;
+    int n_jobs;
+    int job_interleave;  // 1: packet index i belongs to job i % n_jobs (equal packet counts)
 };
 
 struct ImageParams {
@@ -87,7 +113,8 @@ struct ImageParams {
 
 // launchers (defined in the .cu files)
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s);
-int transport_max_blocks_per_sm(int precision, int model, int block, size_t smem);
+const void* transport_kernel(int precision, int model, bool batch);
+int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem);
 size_t transport_smem_bytes(const TransportParams& p, int precision, int block);
 cudaError_t launch_image(const ImageParams& p, int precision, cudaStream_t s);
 cudaError_t launch_setup_cells(const float* ka, const float* ks, const float* bf, const float* em, long long ncell,

@@ -99,9 +99,11 @@ void basis(const double n[3], double th[3], double ph[3]) {
 #define NA_CK(call)                                                                          \
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess)                                                               \
+        if (e_ != cudaSuccess) {                                                             \
+            (void)cudaGetLastError();                                                        \
             return mcrt_fail_noctx(MCRT_E_CUDA, "mcrt_launch_packets_noalloc: %s: %s", #call, \
                                    cudaGetErrorString(e_));                                  \
+        }                                                                                    \
     } while (0)
 
 }  // namespace
@@ -269,7 +271,7 @@ extern "C" mcrt_status mcrt_launch_packets_noalloc(const mcrt_noalloc_problem* p
     NA_CK(cudaGetDevice(&dev));
     NA_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const size_t smem = transport_smem_bytes(P, d->precision, block);
-    int bps = transport_max_blocks_per_sm(d->precision, P.t.model, block, smem);
+    int bps = transport_max_blocks_per_sm(d->precision, P.t.model, false, block, smem);
     if (d->blocks_per_sm > 0 && d->blocks_per_sm < bps) bps = d->blocks_per_sm;
     const long long nwork = pe - pb;
     long long grid = (long long)nsm * bps;

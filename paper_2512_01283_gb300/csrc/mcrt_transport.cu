@@ -151,6 +151,7 @@ template <typename T> struct Packet {
     T I_birth, e_abs, e_gain;
     double tau;  // remaining scattering optical depth (FP64 running sum)
     long long pid;
+    const JobDev* job;  // batched launches: the packet's job
     unsigned events, n_seg, n_sca, n_tally, n_abs, trials;
     int ix, iy, iz, src;
     float4 cq, cr;  // record of the current cell: q_B and (kappa_abs, kappa_sca, B, 0)
@@ -164,12 +165,70 @@ struct BlockTotals {
     unsigned status;
 };
 
-template <typename T> __device__ __forceinline__ T g_lo(const TransportParams& P, int a);
-template <> __device__ __forceinline__ float g_lo<float>(const TransportParams& P, int a) { return P.lo_f[a]; }
-template <> __device__ __forceinline__ double g_lo<double>(const TransportParams& P, int a) { return P.g.lo[a]; }
-template <typename T> __device__ __forceinline__ T g_d(const TransportParams& P, int a);
-template <> __device__ __forceinline__ float g_d<float>(const TransportParams& P, int a) { return P.d_f[a]; }
-template <> __device__ __forceinline__ double g_d<double>(const TransportParams& P, int a) { return P.g.d[a]; }
+template <typename T> __device__ __forceinline__ T pick(float f, double d);
+template <> __device__ __forceinline__ float pick<float>(float f, double) { return f; }
+template <> __device__ __forceinline__ double pick<double>(float, double d) { return d; }
+
+// Model-dependent data a packet reads: for a single-model launch the kernel
+// parameters and the tables staged in shared memory; for a batched launch the
+// packet's record in the job table (tables read through L1).
+template <typename T, bool B> struct JobRef;
+
+template <typename T> struct JobRef<T, false> {
+    const TransportParams& P;
+    const float4* kx;
+    const float4* mx;
+    __device__ __forceinline__ int n(int a) const { return P.g.n[a]; }
+    __device__ __forceinline__ T lo(int a) const { return pick<T>(P.lo_f[a], P.g.lo[a]); }
+    __device__ __forceinline__ T d(int a) const { return pick<T>(P.d_f[a], P.g.d[a]); }
+    __device__ __forceinline__ double lo_d(int a) const { return P.g.lo[a]; }
+    __device__ __forceinline__ double hi_d(int a) const { return P.g.hi[a]; }
+    __device__ __forceinline__ long long ncell() const { return P.g.ncell; }
+    __device__ __forceinline__ const float4* cells() const { return P.g.cells; }
+    __device__ __forceinline__ double* S() const { return P.S; }
+    __device__ __forceinline__ double* absorbed() const { return P.absorbed; }
+    __device__ __forceinline__ const TablesDev& t() const { return P.t; }
+    __device__ __forceinline__ const float4* kext() const { return kx; }
+    __device__ __forceinline__ const float4* mix() const { return mx; }
+    __device__ __forceinline__ unsigned stream() const { return P.stream; }
+    __device__ __forceinline__ double eps(int s) const { return P.src[s].eps; }
+    __device__ __forceinline__ const double* cdf() const { return P.thermal_cdf; }
+    __device__ __forceinline__ double cdf_total() const { return P.thermal_total; }
+    __device__ __forceinline__ const long long* guide() const { return P.thermal_guide; }
+    __device__ __forceinline__ long long n_guide() const { return P.n_guide; }
+    __device__ __forceinline__ unsigned index() const { return 0u; }
+};
+
+template <typename T> struct JobRef<T, true> {
+    const JobDev* j;
+    __device__ __forceinline__ int n(int a) const { return j->n[a]; }
+    __device__ __forceinline__ T lo(int a) const { return pick<T>(j->lo_f[a], j->lo[a]); }
+    __device__ __forceinline__ T d(int a) const { return pick<T>(j->d_f[a], j->d[a]); }
+    __device__ __forceinline__ double lo_d(int a) const { return j->lo[a]; }
+    __device__ __forceinline__ double hi_d(int a) const { return j->hi[a]; }
+    __device__ __forceinline__ long long ncell() const { return j->ncell; }
+    __device__ __forceinline__ const float4* cells() const { return j->cells; }
+    __device__ __forceinline__ double* S() const { return j->S; }
+    __device__ __forceinline__ double* absorbed() const { return j->absorbed; }
+    __device__ __forceinline__ const TablesDev& t() const { return j->t; }
+    __device__ __forceinline__ const float4* kext() const { return j->t.kext; }
+    __device__ __forceinline__ const float4* mix() const { return j->t.mix; }
+    __device__ __forceinline__ unsigned stream() const { return j->stream; }
+    __device__ __forceinline__ double eps(int s) const { return j->src_eps[s]; }
+    __device__ __forceinline__ const double* cdf() const { return j->thermal_cdf; }
+    __device__ __forceinline__ double cdf_total() const { return j->thermal_total; }
+    __device__ __forceinline__ const long long* guide() const { return j->thermal_guide; }
+    __device__ __forceinline__ long long n_guide() const { return j->n_guide; }
+    __device__ __forceinline__ unsigned index() const { return j->index; }
+};
+
+template <typename T, bool B>
+__device__ __forceinline__ JobRef<T, B> job_of(const TransportParams& P, const Smem<T>& sm, const Packet<T>& pk) {
+    if constexpr (B)
+        return JobRef<T, true>{pk.job};
+    else
+        return JobRef<T, false>{P, sm.kext, sm.mix};
+}
 
 // Widening of an FP32 value to FP64 with integer operations only (the FP64 pipe of
 // GB300 is narrow): exact for normal numbers, infinities and NaN; FP32 subnormals
@@ -187,11 +246,11 @@ __device__ __forceinline__ double widen(float f) {
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
-template <typename T>
-__device__ __forceinline__ void load_cell(const TransportParams& P, int ix, int iy, int iz, float4& q, float4& r) {
-    const long long c = ((long long)iz * P.g.n[1] + iy) * P.g.n[0] + ix;
-    q = __ldg(&P.g.cells[2 * c]);
-    r = __ldg(&P.g.cells[2 * c + 1]);
+template <typename J>
+__device__ __forceinline__ void load_cell(const J& job, int ix, int iy, int iz, float4& q, float4& r) {
+    const long long c = ((long long)iz * job.n(1) + iy) * job.n(0) + ix;
+    q = __ldg(&job.cells()[2 * c]);
+    r = __ldg(&job.cells()[2 * c + 1]);
 }
 
 // Packet end: optional trace record, then the packet's totals into the block's.
@@ -242,31 +301,34 @@ __device__ void finish(const TransportParams& P, const Packet<T>& pk, int flag, 
 // First cell whose cumulative emission weight exceeds `target`: a guide table over
 // equal steps of the total narrows the search, and the answer is checked against
 // the definition (full binary search when the check fails).
-__device__ __forceinline__ long long thermal_cell(const TransportParams& P, double u) {
-    const double target = u * P.thermal_total;
-    const long long last = P.g.ncell - 1;
+template <typename J> __device__ __forceinline__ long long thermal_cell(const J& job, double u) {
+    const double* cdf = job.cdf();
+    const double target = u * job.cdf_total();
+    const long long last = job.ncell() - 1;
     long long lo = 0, hi = last;
-    if (P.thermal_guide) {
-        long long k = (long long)(u * (double)P.n_guide);
-        k = k < 0 ? 0 : (k >= P.n_guide ? P.n_guide - 1 : k);
-        lo = P.thermal_guide[k];
-        hi = P.thermal_guide[k + 1];
+    const long long* guide = job.guide();
+    if (guide) {
+        const long long ng = job.n_guide();
+        long long k = (long long)(u * (double)ng);
+        k = k < 0 ? 0 : (k >= ng ? ng - 1 : k);
+        lo = guide[k];
+        hi = guide[k + 1];
     }
     while (lo < hi) {
         const long long mid = lo + (hi - lo) / 2;
-        if (P.thermal_cdf[mid] > target)
+        if (cdf[mid] > target)
             hi = mid;
         else
             lo = mid + 1;
     }
-    const bool ok = P.thermal_cdf[lo] > target || lo == last;
-    const bool ok_prev = lo == 0 || !(P.thermal_cdf[lo - 1] > target);
+    const bool ok = cdf[lo] > target || lo == last;
+    const bool ok_prev = lo == 0 || !(cdf[lo - 1] > target);
     if (ok && ok_prev) return lo;
     lo = 0;
     hi = last;
     while (lo < hi) {
         const long long mid = lo + (hi - lo) / 2;
-        if (P.thermal_cdf[mid] > target)
+        if (cdf[mid] > target)
             hi = mid;
         else
             lo = mid + 1;
@@ -275,38 +337,39 @@ __device__ __forceinline__ long long thermal_cell(const TransportParams& P, doub
 }
 
 // Packet birth, event 0: slot 0 = (tau, cos theta, phi, cell), slot 1 = (x, y, z, -).
-// Returns false when the packet starts outside the grid (it is then finished).
-template <typename T>
-__device__ bool emit(const TransportParams& P, const Smem<T>& sm, long long pid, Packet<T>& pk, BlockTotals& bt) {
+// pid is the packet id within its model.  Returns false when the packet starts
+// outside the grid (it is then finished).
+template <typename T, bool B>
+__device__ bool emit(const TransportParams& P, const JobRef<T, B>& job, long long pid, Packet<T>& pk, BlockTotals& bt) {
     int s = 0;
     while (s < P.n_src - 1 && pid >= P.src[s].start + P.src[s].count) ++s;
     const SourceDev& src = P.src[s];
-    const Draw4<T> u0 = draw4<T>(pid, 0u, 0u, P.seed, P.stream);
-    const Draw4<T> u1 = draw4<T>(pid, 0u, 1u, P.seed, P.stream);
+    const Draw4<T> u0 = draw4<T>(pid, 0u, 0u, P.seed, job.stream());
+    const Draw4<T> u1 = draw4<T>(pid, 0u, 1u, P.seed, job.stream());
     pk.pid = pid;
     pk.src = s;
     pk.events = 1;
     pk.n_seg = pk.n_sca = pk.n_tally = pk.n_abs = pk.trials = 0;
     pk.e_abs = pk.e_gain = T(0);
-    const T eps = T(src.eps);
+    const T eps = T(job.eps(s));
     pk.X0 = eps;
     pk.X1 = pk.X2 = pk.X3 = T(0);
     bool inside;
     if (src.type == MCRT_SRC_THERMAL) {
-        const long long c = thermal_cell(P, (double)u0.d);
-        pk.ix = (int)(c % P.g.n[0]);
-        pk.iy = (int)((c / P.g.n[0]) % P.g.n[1]);
-        pk.iz = (int)(c / ((long long)P.g.n[0] * P.g.n[1]));
-        pk.px = g_lo<T>(P, 0) + (T(pk.ix) + u1.a) * g_d<T>(P, 0);
-        pk.py = g_lo<T>(P, 1) + (T(pk.iy) + u1.b) * g_d<T>(P, 1);
-        pk.pz = g_lo<T>(P, 2) + (T(pk.iz) + u1.c) * g_d<T>(P, 2);
+        const long long c = thermal_cell(job, (double)u0.d);
+        pk.ix = (int)(c % job.n(0));
+        pk.iy = (int)((c / job.n(0)) % job.n(1));
+        pk.iz = (int)(c / ((long long)job.n(0) * job.n(1)));
+        pk.px = job.lo(0) + (T(pk.ix) + u1.a) * job.d(0);
+        pk.py = job.lo(1) + (T(pk.iy) + u1.b) * job.d(1);
+        pk.pz = job.lo(2) + (T(pk.iz) + u1.c) * job.d(2);
         T n[3];
         iso_dir(u0.b, u0.c, n);
         pk.nx = n[0];
         pk.ny = n[1];
         pk.nz = n[2];
         inside = true;
-        load_cell<T>(P, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
+        load_cell(job, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
         // emission alpha_abs B (1,0,0,0) in the grain-meridian basis, weight
         // (alpha1(theta') - omega) / (mean alpha1 - omega)
         const T kext = T(pk.cr.x) + T(pk.cr.y);
@@ -316,8 +379,8 @@ __device__ bool emit(const TransportParams& P, const Smem<T>& sm, long long pid,
         stokes_basis(nv, th, ph);
         const GrainFrame<T> f = grain_frame(pk.cq, nv, ph);
         T a1, a2, a3;
-        kext_eval(P.t, sm.kext, f.cos_tp, a1, a2, a3);
-        const T w = (a1 - omega) / (T(P.t.alpha1_mean) - omega);
+        kext_eval(job.t(), job.kext(), f.cos_tp, a1, a2, a3);
+        const T w = (a1 - omega) / (T(job.t().alpha1_mean) - omega);
         pk.X0 = eps * w;
         pk.X1 = eps * w * a2 / (a1 - omega);
         rotate_qu(pk.X1, pk.X2, f.c2, -f.s2);
@@ -329,9 +392,9 @@ __device__ bool emit(const TransportParams& P, const Smem<T>& sm, long long pid,
             p[2] = T(src.pos[2]);
             iso_dir(u0.b, u0.c, n);
         } else {
-            p[0] = T(P.g.lo[0] + (double)u1.a * (P.g.hi[0] - P.g.lo[0]));
-            p[1] = T(P.g.lo[1] + (double)u1.b * (P.g.hi[1] - P.g.lo[1]));
-            p[2] = T(src.beam_dir > 0 ? P.g.lo[2] : P.g.hi[2]);
+            p[0] = T(job.lo_d(0) + (double)u1.a * (job.hi_d(0) - job.lo_d(0)));
+            p[1] = T(job.lo_d(1) + (double)u1.b * (job.hi_d(1) - job.lo_d(1)));
+            p[2] = T(src.beam_dir > 0 ? job.lo_d(2) : job.hi_d(2));
             n[0] = T(0);
             n[1] = T(0);
             n[2] = src.beam_dir > 0 ? T(1) : T(-1);
@@ -339,9 +402,9 @@ __device__ bool emit(const TransportParams& P, const Smem<T>& sm, long long pid,
         GridT<T> g;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            g.n[a] = P.g.n[a];
-            g.lo[a] = g_lo<T>(P, a);
-            g.d[a] = g_d<T>(P, a);
+            g.n[a] = job.n(a);
+            g.lo[a] = job.lo(a);
+            g.d[a] = job.d(a);
         }
         int idx[3];
         inside = locate(g, p, n, idx);
@@ -354,7 +417,7 @@ __device__ bool emit(const TransportParams& P, const Smem<T>& sm, long long pid,
         pk.ix = idx[0];
         pk.iy = idx[1];
         pk.iz = idx[2];
-        if (inside) load_cell<T>(P, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
+        if (inside) load_cell(job, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
     }
     pk.tau = -(double)t_log(u0.a);
     pk.I_birth = pk.X0;
@@ -364,13 +427,13 @@ __device__ bool emit(const TransportParams& P, const Smem<T>& sm, long long pid,
 
 // Exit of the current cell along n: distance, axis (ties to the lowest axis) and the
 // coordinate of the exit face.
-template <typename T>
-__device__ __forceinline__ T exit_face(const TransportParams& P, const Packet<T>& pk, int& axis, T& face) {
+template <typename T, typename J>
+__device__ __forceinline__ T exit_face(const J& job, const Packet<T>& pk, int& axis, T& face) {
     T best = T(INFINITY);
     axis = -1;
     face = T(0);
     if (pk.nx != T(0)) {
-        const T f = g_lo<T>(P, 0) + T(pk.nx > T(0) ? pk.ix + 1 : pk.ix) * g_d<T>(P, 0);
+        const T f = job.lo(0) + T(pk.nx > T(0) ? pk.ix + 1 : pk.ix) * job.d(0);
         T t = (f - pk.px) / pk.nx;
         t = t < T(0) ? T(0) : t;
         if (t < best) {
@@ -380,7 +443,7 @@ __device__ __forceinline__ T exit_face(const TransportParams& P, const Packet<T>
         }
     }
     if (pk.ny != T(0)) {
-        const T f = g_lo<T>(P, 1) + T(pk.ny > T(0) ? pk.iy + 1 : pk.iy) * g_d<T>(P, 1);
+        const T f = job.lo(1) + T(pk.ny > T(0) ? pk.iy + 1 : pk.iy) * job.d(1);
         T t = (f - pk.py) / pk.ny;
         t = t < T(0) ? T(0) : t;
         if (t < best) {
@@ -390,7 +453,7 @@ __device__ __forceinline__ T exit_face(const TransportParams& P, const Packet<T>
         }
     }
     if (pk.nz != T(0)) {
-        const T f = g_lo<T>(P, 2) + T(pk.nz > T(0) ? pk.iz + 1 : pk.iz) * g_d<T>(P, 2);
+        const T f = job.lo(2) + T(pk.nz > T(0) ? pk.iz + 1 : pk.iz) * job.d(2);
         T t = (f - pk.pz) / pk.nz;
         t = t < T(0) ? T(0) : t;
         if (t < best) {
@@ -404,23 +467,26 @@ __device__ __forceinline__ T exit_face(const TransportParams& P, const Packet<T>
 
 // One event of a live packet: a cell segment, then a scattering when the sampled
 // optical depth runs out inside the cell.  `work` = live lanes of the warp.
-template <typename T, int SCAT>
+template <typename T, int SCAT, bool B>
 __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm, Packet<T>& pk, bool& alive,
                                      BlockTotals& bt, unsigned work) {
+    const JobRef<T, B> job = job_of<T, B>(P, sm, pk);
+    const TablesDev& tabs = job.t();
     const T ks = T(pk.cr.y);
     const T kext = T(pk.cr.x) + ks;
     const bool capped = pk.events >= (unsigned)P.max_events;
     int axis;
     T face;
-    const T ell_exit = exit_face(P, pk, axis, face);
+    const T ell_exit = exit_face(job, pk, axis, face);
     // a packet without a finite exit (non-finite direction) ends as escaped
     const bool lost = !capped && axis < 0;
     const bool want_A = !capped && !lost && kext > T(0);
     const bool want_S = want_A && ks > T(0) && P.n_cam > 0;
-    const unsigned c32 = (unsigned)(((long long)pk.iz * P.g.n[1] + pk.iy) * P.g.n[0] + pk.ix);
-    // converged point: same-cell groups for the aggregated tallies; lanes that
-    // leave below are outside actA / actS
-    const unsigned peers = __match_any_sync(work, c32);
+    const unsigned c32 = (unsigned)(((long long)pk.iz * job.n(1) + pk.iy) * job.n(0) + pk.ix);
+    // converged point: same-cell groups (of the same model) for the aggregated
+    // tallies; lanes that leave below are outside actA / actS
+    const unsigned long long key = ((unsigned long long)job.index() << 32) | c32;
+    const unsigned peers = __match_any_sync(work, key);
     const unsigned actA = __ballot_sync(work, want_A);
     const unsigned actS = __ballot_sync(work, want_S);
     if (capped || lost) {
@@ -440,15 +506,15 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     if (!scatter_here) {
         if (axis == 0) {
             nix += pk.nx > T(0) ? 1 : -1;
-            next_in = nix >= 0 && nix < P.g.n[0];
+            next_in = nix >= 0 && nix < job.n(0);
         } else if (axis == 1) {
             niy += pk.ny > T(0) ? 1 : -1;
-            next_in = niy >= 0 && niy < P.g.n[1];
+            next_in = niy >= 0 && niy < job.n(1);
         } else {
             niz += pk.nz > T(0) ? 1 : -1;
-            next_in = niz >= 0 && niz < P.g.n[2];
+            next_in = niz >= 0 && niz < job.n(2);
         }
-        if (next_in) load_cell<T>(P, nix, niy, niz, nq, nr);
+        if (next_in) load_cell(job, nix, niy, niz, nq, nr);
     }
 
     const V3<T> n{pk.nx, pk.ny, pk.nz};
@@ -460,15 +526,15 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
 
     if (want_A) {
         T c2 = T(1), s2 = T(0), a1, a2, a3;
-        if (P.t.k_iso) {
-            a1 = T(sm.kext[0].x);
+        if (tabs.k_iso) {
+            a1 = T(job.kext()[0].x);
             a2 = T(0);
             a3 = T(0);
         } else {
             const GrainFrame<T> f = grain_frame(pk.cq, n, ph);
             c2 = f.c2;
             s2 = f.s2;
-            kext_eval(P.t, sm.kext, f.cos_tp, a1, a2, a3);
+            kext_eval(tabs, job.kext(), f.cos_tp, a1, a2, a3);
         }
         const T a = a1 - omega;
         const T dtau = kext * ell;
@@ -484,13 +550,13 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             pk.e_abs += dI;
             if (dI != T(0)) pk.n_abs++;
             if (gmax > 1u) dI = group_sum(actA, group, dI, gmax);
-            if (lane == leader && dI != T(0)) atomicAdd(&P.absorbed[c32], widen(dI));
+            if (lane == leader && dI != T(0)) atomicAdd(&job.absorbed()[c32], widen(dI));
         }
         if (want_S) {
             rotate_qu(Wg[1], Wg[2], c2, -s2);
             const unsigned gmax = __reduce_max_sync(actS, (unsigned)__popc(group));
             pk.n_tally++;
-            double* Sc = P.S + (size_t)c32 * (size_t)P.n_cam * 4;
+            double* Sc = job.S() + (size_t)c32 * (size_t)P.n_cam * 4;
             double* slot = sm.stage + threadIdx.x * kStageDoubles;
             for (int k0 = 0; k0 < P.n_cam; k0 += kStageCams) {
                 const int kn = P.n_cam - k0 < kStageCams ? P.n_cam - k0 : kStageCams;
@@ -503,7 +569,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
                     if (SCAT == MCRT_SCAT_RAYLEIGH)
                         rayleigh_matrix(mu, Pm);
                     else
-                        table_matrix(sm.mix, P.t.n_theta, mu, Pm);
+                        table_matrix(job.mix(), tabs.n_theta, mu, Pm);
                     const PlaneRot<T> pr = plane_rotation(n, th, ph, Om, thc, phc);
                     T sv[4];
                     apply_plane(pr, Pm, Wg, sv);
@@ -558,7 +624,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     pk.pz += ell * pk.nz;
     pk.n_sca++;
     pk.events++;
-    const Draw4<T> us = draw4<T>(pk.pid, pk.n_sca, 0u, P.seed, P.stream);
+    const Draw4<T> us = draw4<T>(pk.pid, pk.n_sca, 0u, P.seed, job.stream());
     if (P.roulette_thr > 0.0 && (double)pk.X0 < P.roulette_thr * (double)pk.I_birth) {
         if ((double)us.b < P.roulette_surv) {
             const T gmul = T(1.0 / P.roulette_surv);
@@ -576,20 +642,20 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     int bin = 0;
     const float4* tab = nullptr;
     if (SCAT == MCRT_SCAT_TABLE) {
-        bin = P.t.n_bins - 1;
-        for (int k = 0; k < P.t.n_bins; ++k)
-            if (us.c < T(P.t.bin_cdf[k])) {
+        bin = tabs.n_bins - 1;
+        for (int k = 0; k < tabs.n_bins; ++k)
+            if (us.c < T(tabs.bin_cdf[k])) {
                 bin = k;
                 break;
             }
-        tab = P.t.bins + (size_t)bin * P.t.n_theta * 2;
+        tab = tabs.bins + (size_t)bin * tabs.n_theta * 2;
     }
     const T X[4] = {pk.X0, pk.X1, pk.X2, pk.X3};
     V3<T> n2;
     T Pm[6];
     bool accepted = false;
     for (int t = 0; t < P.max_trials; ++t) {
-        const Draw4<T> ut = draw4<T>(pk.pid, pk.n_sca, 1u + (unsigned)t, P.seed, P.stream);
+        const Draw4<T> ut = draw4<T>(pk.pid, pk.n_sca, 1u + (unsigned)t, P.seed, job.stream());
         pk.trials++;
         T bound;
         if (SCAT == MCRT_SCAT_RAYLEIGH) {
@@ -600,8 +666,8 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             bound = ut.c * T(2) * T(0.11936620731892133) * X[0];  // 2 * 3/(8 pi)
         } else {
             // interval j of the piecewise-constant envelope of P11: first j with u < cdf_j
-            const int nint = P.t.n_theta - 1;
-            const double* cdf = P.t.env_cdf + (size_t)bin * nint;
+            const int nint = tabs.n_theta - 1;
+            const double* cdf = tabs.env_cdf + (size_t)bin * nint;
             int lo = 0, hi = nint - 1;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
@@ -621,8 +687,8 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             t_sincospi(T(2) * ut.c, &sa, &ca);
             n2 = V3<T>{mu * n.x + sn * (ca * th.x + sa * ph.x), mu * n.y + sn * (ca * th.y + sa * ph.y),
                        mu * n.z + sn * (ca * th.z + sa * ph.z)};
-            table_matrix(tab, P.t.n_theta, mu, Pm);
-            bound = ut.d * T(2) * T(P.t.env[(size_t)bin * nint + j]) * X[0];
+            table_matrix(tab, tabs.n_theta, mu, Pm);
+            bound = ut.d * T(2) * T(tabs.env[(size_t)bin * nint + j]) * X[0];
         }
         const T Qs = plane_Q(th, ph, n2, X);
         if (bound < Pm[0] * X[0] + Pm[1] * Qs) {
@@ -651,18 +717,34 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     pk.tau = -(double)t_log(us.a);
 }
 
-template <typename T, int SCAT>
-__global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCKS : 1) k_transport(const __grid_constant__ TransportParams P) {
+// Job of a batch packet index: the last job whose first index is <= gpid.
+__device__ __forceinline__ int job_index(const TransportParams& P, long long gpid) {
+    int lo = 0, hi = P.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.jobs[mid].pid_start <= gpid)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int SCAT, bool B>
+__global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCKS : 1)
+    k_transport(const __grid_constant__ TransportParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockTotals bt;
-    // shared layout: kext table, mixture table (TABLE), cameras, tally staging
+    // shared layout: kext table and mixture table (single model, TABLE), cameras,
+    // tally staging
     float4* s_kext = reinterpret_cast<float4*>(smem_raw);
-    float4* s_mix = s_kext + P.t.n_ktheta;
-    const int n_mix = (SCAT == MCRT_SCAT_TABLE) ? 2 * P.t.n_theta : 0;
+    const int n_k = B ? 0 : P.t.n_ktheta;
+    float4* s_mix = s_kext + n_k;
+    const int n_mix = (!B && SCAT == MCRT_SCAT_TABLE) ? 2 * P.t.n_theta : 0;
     T* s_cam = reinterpret_cast<T*>(s_mix + n_mix);
     const int cam_bytes = 12 * P.n_cam * (int)sizeof(T);
     double* s_stage = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(s_cam) + cam_bytes);
-    for (int i = threadIdx.x; i < P.t.n_ktheta; i += blockDim.x) s_kext[i] = P.t.kext[i];
+    for (int i = threadIdx.x; i < n_k; i += blockDim.x) s_kext[i] = P.t.kext[i];
     for (int i = threadIdx.x; i < n_mix; i += blockDim.x) s_mix[i] = P.t.mix[i];
     for (int i = threadIdx.x; i < 12 * P.n_cam; i += blockDim.x) {
         const CameraDev& cd = P.cam[i / 12];
@@ -676,6 +758,7 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
 
     const Smem<T> sm{s_cam, s_mix, s_kext, s_stage};
     Packet<T> pk;
+    pk.job = nullptr;
     bool alive = false, pool_done = false;
     const unsigned long long t0 = global_ns();
 
@@ -690,8 +773,18 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
             if (pid >= P.pid_end || late) {
                 pool_done = true;
                 if (late && pid < P.pid_end) atomicOr(&bt.status, (unsigned)MCRT_STATUS_TIMEOUT);
+            } else if constexpr (B) {
+                long long local;
+                if (P.job_interleave) {
+                    pk.job = &P.jobs[pid % P.n_jobs];
+                    local = pid / P.n_jobs;
+                } else {
+                    pk.job = &P.jobs[job_index(P, pid)];
+                    local = pid - pk.job->pid_start;
+                }
+                alive = emit<T, true>(P, JobRef<T, true>{pk.job}, local, pk, bt);
             } else {
-                alive = emit<T>(P, sm, pid, pk, bt);
+                alive = emit<T, false>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
             }
         }
         const unsigned work = __ballot_sync(kFull, alive);
@@ -699,7 +792,7 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
             if (__all_sync(kFull, pool_done)) break;
             continue;
         }
-        if (alive) step<T, SCAT>(P, sm, pk, alive, bt, work);
+        if (alive) step<T, SCAT, B>(P, sm, pk, alive, bt, work);
     }
 
     bulk_wait_all();  // this thread's reductions have completed before the block ends
@@ -713,26 +806,36 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
         atomicOr(P.status, bt.status);
     }
 }
+
 }  // namespace
 
 size_t transport_smem_bytes(const TransportParams& p, int precision, int block) {
+    const bool batch = p.jobs != nullptr;
     const size_t tsize = precision == MCRT_FP64 ? sizeof(double) : sizeof(float);
-    const size_t mix = p.t.model == MCRT_SCAT_TABLE ? 2 * (size_t)p.t.n_theta * sizeof(float4) : 0;
+    const size_t kx = batch ? 0 : (size_t)p.t.n_ktheta * sizeof(float4);
+    const size_t mix = (!batch && p.t.model == MCRT_SCAT_TABLE) ? 2 * (size_t)p.t.n_theta * sizeof(float4) : 0;
     const size_t cams = 12 * (size_t)p.n_cam * tsize;
-    return (size_t)p.t.n_ktheta * sizeof(float4) + mix + cams + (size_t)block * kStageDoubles * sizeof(double);
+    return kx + mix + cams + (size_t)block * kStageDoubles * sizeof(double);
 }
 
-static const void* kernel_ptr(int precision, int model) {
-    if (precision == MCRT_FP64)
-        return model == MCRT_SCAT_TABLE ? (const void*)k_transport<double, MCRT_SCAT_TABLE>
-                                        : (const void*)k_transport<double, MCRT_SCAT_RAYLEIGH>;
-    return model == MCRT_SCAT_TABLE ? (const void*)k_transport<float, MCRT_SCAT_TABLE>
-                                    : (const void*)k_transport<float, MCRT_SCAT_RAYLEIGH>;
+const void* transport_kernel(int precision, int model, bool batch) {
+    if (precision == MCRT_FP64) {
+        if (model == MCRT_SCAT_TABLE)
+            return batch ? (const void*)k_transport<double, MCRT_SCAT_TABLE, true>
+                         : (const void*)k_transport<double, MCRT_SCAT_TABLE, false>;
+        return batch ? (const void*)k_transport<double, MCRT_SCAT_RAYLEIGH, true>
+                     : (const void*)k_transport<double, MCRT_SCAT_RAYLEIGH, false>;
+    }
+    if (model == MCRT_SCAT_TABLE)
+        return batch ? (const void*)k_transport<float, MCRT_SCAT_TABLE, true>
+                     : (const void*)k_transport<float, MCRT_SCAT_TABLE, false>;
+    return batch ? (const void*)k_transport<float, MCRT_SCAT_RAYLEIGH, true>
+                 : (const void*)k_transport<float, MCRT_SCAT_RAYLEIGH, false>;
 }
 
-int transport_max_blocks_per_sm(int precision, int model, int block, size_t smem) {
+int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem) {
     int nb = 0;
-    const void* k = kernel_ptr(precision, model);
+    const void* k = transport_kernel(precision, model, batch);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
@@ -740,7 +843,7 @@ int transport_max_blocks_per_sm(int precision, int model, int block, size_t smem
 
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s) {
     const size_t smem = transport_smem_bytes(p, precision, block);
-    const void* k = kernel_ptr(precision, p.t.model);
+    const void* k = transport_kernel(precision, p.t.model, p.jobs != nullptr);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

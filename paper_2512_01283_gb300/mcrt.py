@@ -60,6 +60,11 @@ class Stats(C.Structure):
     _fields_ = [(f, C.c_double) for f in STAT_FIELDS]
 
 
+class TuneReport(C.Structure):
+    _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("block_size", C.c_int32 * 16),
+                ("blocks_per_sm", C.c_int32 * 16), ("interleave", C.c_int32 * 16), ("events_per_s", C.c_double * 16)]
+
+
 class NoAllocProblem(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("kappa_abs", C.c_void_p), ("kappa_sca", C.c_void_p),
@@ -73,7 +78,8 @@ _lib = None
 
 # symbols of include/mcrt.h
 SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "mcrt_image_stokes",
-           "mcrt_get_tallies", "mcrt_destroy", "mcrt_last_error", "mcrt_unit_eval", "mcrt_launch_packets_noalloc"]
+           "mcrt_get_tallies", "mcrt_destroy", "mcrt_last_error", "mcrt_unit_eval", "mcrt_launch_packets_noalloc",
+           "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_tune", "mcrt_batch_images", "mcrt_batch_destroy"]
 
 
 def lib():
@@ -96,6 +102,11 @@ def lib():
     L.mcrt_last_error.restype = C.c_char_p
     L.mcrt_unit_eval.argtypes = [i32, i32, i64, vp, vp]
     L.mcrt_launch_packets_noalloc.argtypes = [C.POINTER(NoAllocProblem), C.POINTER(LaunchDesc), C.POINTER(Stats)]
+    L.mcrt_batch_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), i32, C.POINTER(LaunchDesc)]
+    L.mcrt_batch_run.argtypes = [vp, C.c_uint32, C.POINTER(Stats)]
+    L.mcrt_batch_tune.argtypes = [vp, i64, C.POINTER(TuneReport)]
+    L.mcrt_batch_images.argtypes = [vp, vp]
+    L.mcrt_batch_destroy.argtypes = [vp]
     for name in SYMBOLS:
         if name != "mcrt_last_error":
             getattr(L, name).restype = C.c_int
@@ -313,3 +324,64 @@ def launch_noalloc(model_dev: dict, run: dict, source, absorbed, precision="fp32
     out["status"] = status
     del keep
     return out
+
+
+class Batch:
+    """mcrt_batch_*: many models in one persistent launch captured in a CUDA graph."""
+
+    def __init__(self, models, run: dict, precision="fp32", **kw):
+        L = lib()
+        self.models = list(models)
+        self.run = run
+        arr = (C.c_void_p * len(self.models))(*[mm.h for mm in self.models])
+        d, self._keep = make_desc(run, precision, default_center=self.models[0].center, **kw)
+        h = C.c_void_p()
+        _check(L.mcrt_batch_create(C.byref(h), arr, len(self.models), C.byref(d)))
+        self.h = h
+        cams = run.get("cameras", [])
+        self.image_shape = [(4, c["npix"][1], c["npix"][0]) for c in cams]
+
+    def tune(self, packets_per_job):
+        rep = TuneReport()
+        _check(lib().mcrt_batch_tune(self.h, int(packets_per_job), C.byref(rep)))
+        rows = [{"block_size": rep.block_size[i], "blocks_per_sm": rep.blocks_per_sm[i],
+                 "interleave": rep.interleave[i], "events_per_s": rep.events_per_s[i]} for i in range(rep.n)]
+        return {"trials": rows, "best": rep.best}
+
+    def launch(self, seed):
+        st = Stats()
+        status = lib().mcrt_batch_run(self.h, int(seed) & 0xffffffff, C.byref(st))
+        if status not in (MCRT_OK, MCRT_E_EVENT_CAP, MCRT_E_TIMEOUT):
+            _check(status)
+        out = {f: getattr(st, f) for f in STAT_FIELDS}
+        out["status"] = status
+        return out
+
+    def images(self, out=None):
+        """All images, [model][camera] -> array [4][ny][nx]."""
+        n = sum(int(np.prod(s)) for s in self.image_shape) * len(self.models)
+        flat = np.zeros(n) if out is None else out
+        p, keep = _ptr(flat, np.float64)
+        _check(lib().mcrt_batch_images(self.h, p))
+        if out is not None:
+            return out
+        res, off = [], 0
+        for _ in self.models:
+            row = []
+            for s in self.image_shape:
+                k = int(np.prod(s))
+                row.append(flat[off:off + k].reshape(s))
+                off += k
+            res.append(row)
+        return res
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mcrt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

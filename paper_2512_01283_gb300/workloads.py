@@ -19,6 +19,10 @@ Workloads (sizes as stated):
                     (181 angles); star plus thermal emission; 8 cameras at 256^2.
   twisted_slab      slab with a field rotating by 2 pi per unit optical depth (the
                     twisted-field test of Sec. 3.2).
+  sweep             batched sweep: 32 models with edges drawn uniformly in 32..192, clumpy
+                    log-normal density (sigma_ln = 1), mean optical depth log-uniform in
+                    [1, 100], times 8 wavelengths 0.5-3 um (kappa ~ lambda^-1.5); central
+                    star; one camera at 45 deg, 128^2.
 
 The grain tables are synthetic (no measured optical constants are available): per bin
 a Henyey-Greenstein P11, P12/P11 = -p (1-c^2)/(1+c^2), P22 = P11,
@@ -223,3 +227,42 @@ def disk_run(n_packets=100_000_000, seed=2, n_cam=8, npix=256, star_luminosity=1
                         {"type": "thermal", "luminosity": 0.0, "n_packets": n_packets - n_star}],
             "cameras": inclination_cameras(n_cam, npix, 2.0), "seed": seed,
             "roulette_threshold": 1e-4, "roulette_survival": 0.1}
+
+
+def clumpy_density(n, seed, smooth_cells=2.0):
+    """rho = exp(g - 1/2), g a unit-variance Gaussian random field: white noise
+    smoothed with a Gaussian of ``smooth_cells`` cells, rescaled to unit variance
+    (so that <rho> = 1 for a log-normal field with sigma_ln = 1)."""
+    from scipy.ndimage import gaussian_filter
+
+    rng = np.random.default_rng(seed)
+    g = gaussian_filter(rng.standard_normal((n, n, n)), smooth_cells, mode="wrap")
+    g = (g - g.mean()) / g.std()
+    return np.exp(g - 0.5)
+
+
+def sweep_models(n_models=32, n_lambda=8, n_min=32, n_max=192, albedo=0.6, seed0=1000, edges=None):
+    """Model dicts of the batched sweep, ordered model-major: [m][lambda].  Grid
+    [-1,1]^3; the mean extinction optical depth across the box (length 2) is
+    tau_m at 1 um, log-uniform in [1, 100]; kappa scales as (lambda / 1 um)^-1.5."""
+    lams = np.logspace(np.log10(0.5), np.log10(3.0), n_lambda)
+    optics = table_optics()
+    out = []
+    for m in range(n_models):
+        rng = np.random.default_rng(seed0 + m)
+        n = int(rng.integers(n_min, n_max + 1)) if edges is None else int(edges[m])
+        tau = 10 ** rng.uniform(0.0, 2.0)
+        rho = clumpy_density(n, seed0 + m)
+        for lam in lams:
+            kext = (tau / 2.0 * lam ** -1.5 * rho).astype(np.float32)
+            ks = (albedo * kext).astype(np.float32)
+            out.append({"lo": (-1.0, -1.0, -1.0), "hi": (1.0, 1.0, 1.0), "kappa_abs": (kext - ks).astype(np.float32),
+                        "kappa_sca": ks, "bfield": None, "emissivity": None, "optics": optics,
+                        "edge": n, "tau": tau, "lambda_um": float(lam)})
+    return out
+
+
+def sweep_run(n_packets=10_000_000, seed=4, npix=128):
+    return {"sources": [{"type": "point", "pos": (0.0, 0.0, 0.0), "luminosity": 1.0, "n_packets": n_packets}],
+            "cameras": [camera((math.sin(math.pi / 4), 0.0, math.cos(math.pi / 4)), (npix, npix), (2.0, 2.0))],
+            "seed": seed, "roulette_threshold": 1e-4, "roulette_survival": 0.1}

@@ -1,0 +1,119 @@
+"""Batched launches (many models in one persistent launch, CUDA graph, autotuner)
+against single-model launches and the CPU oracle.  Needs a GB300 (``-m gpu``).
+
+Job m of a batch is model m with Philox stream desc.stream + m, so its tallies must
+equal a single launch of that model with that stream (FP64 sums in another order:
+1e-9 relative); one job is also compared with the oracle.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_01283_gb300 import build as B
+from paper_2512_01283_gb300 import mcrt as M
+from paper_2512_01283_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sweep():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for -m gpu tests")
+    B.build()
+    models = W.sweep_models(n_models=3, n_lambda=2, n_min=12, n_max=20)
+    run = W.sweep_run(n_packets=4000, npix=24)
+    return models, run
+
+
+def singles(models, run, precision):
+    out = []
+    for m, model in enumerate(models):
+        mdl = M.Model(model)
+        st = M.launch(mdl, dict(run, stream=m), precision=precision)
+        S, A = mdl.tallies(1)
+        img = np.zeros((4, 24, 24))
+        mdl.image(0, img)
+        mdl.close()
+        out.append((st, S, A, img))
+    return out
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batched_launch_equals_single_launches(sweep, precision):
+    models, run = sweep
+    ref = singles(models, run, precision)
+    mdls = [M.Model(m) for m in models]
+    st = M.launch(mdls, run, precision=precision)
+    assert st["emitted"] == len(models) * 4000
+    assert st["events"] == sum(r[0]["events"] for r in ref)
+    for mdl, (rst, rS, rA, rimg) in zip(mdls, ref):
+        S, A = mdl.tallies(1)
+        # FP32 launches pre-sum same-cell lanes of a warp in FP32, and warps differ
+        tol = 1e-9 if precision == "fp64" else 1e-6
+        assert rel(S, rS) < tol and rel(A, rA) < tol
+        img = np.zeros((4, 24, 24))
+        mdl.image(0, img)
+        # images of FP32 launches are FP32 arithmetic on tallies equal to ~1e-15
+        assert rel(img, rimg) < (1e-9 if precision == "fp64" else 1e-6)
+        mdl.close()
+
+
+def test_graph_batch_runs_tune_and_images(sweep):
+    models, run = sweep
+    ref = singles(models, dict(run, seed=77), "fp32")
+    mdls = [M.Model(m) for m in models]
+    b = M.Batch(mdls, run, precision="fp32")
+    for rep in range(2):  # the graph zeroes the tallies itself
+        st = b.launch(seed=77)
+        assert st["status"] == M.MCRT_OK
+        assert st["events"] == sum(r[0]["events"] for r in ref)
+        imgs = b.images()
+        for m, mdl in enumerate(mdls):
+            S, A = mdl.tallies(1)
+            assert rel(S, ref[m][1]) < 1e-6, (rep, m)  # FP32 same-cell pre-sums
+            assert rel(imgs[m][0], ref[m][3]) < 1e-6, (rep, m)  # FP32 image arithmetic
+    other = b.launch(seed=78)
+    assert other["events"] != st["events"]
+    rep = b.tune(packets_per_job=1000)
+    assert len(rep["trials"]) >= 6 and 0 <= rep["best"] < len(rep["trials"])
+    assert all(t["events_per_s"] > 0 for t in rep["trials"])
+    st = b.launch(seed=77)  # after tuning (possibly interleaved order) the result is unchanged
+    for m, mdl in enumerate(mdls):
+        S, _ = mdl.tallies(1)
+        assert rel(S, ref[m][1]) < 1e-6, m
+    b.close()
+    for mdl in mdls:
+        mdl.close()
+
+
+def test_batch_job_against_oracle(sweep):
+    """One job of an FP64 batch against the oracle run of the same model with the
+    same Philox stream: the source tally and absorbed energy agree to rounding."""
+    models, run = sweep
+    mdls = [M.Model(m) for m in models]
+    M.launch(mdls, run, precision="fp64")
+    m = 2
+    S, A = mdls[m].tallies(1)
+    o = O.transport(models[m], dict(run, stream=m, n_threads=4))
+    assert rel(S, o["S"]) < 1e-6
+    assert rel(A, o["absorbed"]) < 1e-6
+    for mdl in mdls:
+        mdl.close()
+
+
+def test_batch_rejects_mixed_models(sweep):
+    models, run = sweep
+    a = M.Model(models[0])
+    b = M.Model(W.rayleigh_sphere(n=8))
+    with pytest.raises(M.McrtError) as e:
+        M.launch([a, b], run)
+    assert e.value.status == M.MCRT_E_INVAL
+    a.close()
+    b.close()

@@ -511,3 +511,19 @@ def test_thermal_cell_selection_follows_weights():
     assert np.all(np.abs(h - w) < 5 * np.sqrt(w * (1 - w) / 20000) + 1e-12)
     L = O.thermal_luminosity(model, run)
     assert abs(L - 4 * math.pi * em.sum() * f32(1.0) * 0.125) < 1e-9
+
+
+def test_sweep_generator_statistics():
+    """Batched-sweep inputs: ln rho has unit variance (sigma_ln = 1) and <rho> ~ 1;
+    kappa scales as lambda^-1.5 between the wavelengths of one model."""
+    r = W.clumpy_density(48, 3)
+    assert abs(np.log(r).std() - 1.0) < 1e-9
+    assert abs(r.mean() - 1.0) < 0.1
+    ms = W.sweep_models(n_models=2, n_lambda=3, n_min=8, n_max=10)
+    for m in range(2):
+        a, b = ms[3 * m], ms[3 * m + 2]
+        k_a = a["kappa_abs"] + a["kappa_sca"]
+        k_b = b["kappa_abs"] + b["kappa_sca"]
+        ratio = (b["lambda_um"] / a["lambda_um"]) ** -1.5
+        assert np.allclose(k_b, k_a * ratio, rtol=1e-5)
+        assert 1.0 <= a["tau"] <= 100.0
