@@ -268,6 +268,45 @@ MCRT_API mcrt_status mcrt_batch_images(mcrt_batch *batch, double *out);
 MCRT_API mcrt_status mcrt_batch_destroy(mcrt_batch *batch); /* NULL-safe */
 
 /*
+ * Learned surrogate of the grain optics (Sec. 2.2 lets the Mueller matrix come from
+ * analytic forms, tables or neural networks; Sec. 4 proposes networks for
+ * multi-dimensional grain optics).  The network maps u = (n_i[3], n_s[3], s) --
+ * incident and scattered directions in the grain frame and s in [-1, 1], the
+ * position of ln x between the first and last tabulated size parameter -- to 20
+ * outputs: the 4x4 scattering matrix from the grain-frame Stokes basis of n_i to
+ * that of n_s divided by N(s) = max P11 (16, row-major), alpha1..3 at the polar
+ * angle of n_i, and ln N(s).  Layers 16 (7 inputs, zero padded) -> 128 -> 128 -> 128
+ * -> 128 -> 24 (20 used), SiLU; BF16 weights and activations with FP32 accumulation
+ * on the tensor cores; FP32 master weights and Adam.
+ *   create: copies the tables of `optics` (MCRT_SCAT_TABLE) as the label source and
+ *           initialises the weights from `seed`.
+ *   train:  n_steps Adam steps on fresh batches of `batch` samples generated on the
+ *           GPU from the tables (uniform directions, uniform s); learning rate `lr`
+ *           with cosine decay; loss_history (host, nullable) gets the mean squared
+ *           error of each step.
+ *   eval:   outputs [n][20] (host or device) for inputs [n][7].
+ *   labels: the training targets [n][20] of inputs [n][7].
+ *   grad:   loss sum_b sum_o w_o (y - t)^2 / (20 n) and its gradient with respect
+ *           to every parameter (layout of params) for given inputs and targets
+ *           [n][20]; loss_weights [20] nullable (ones).
+ *   params: get (set = 0) or set (set = 1) the FP32 parameters, per layer W[out][in]
+ *           then b[out]; mcrt_surrogate_param_count() of them.
+ * Errors of these calls are read with mcrt_last_error(NULL).
+ */
+typedef struct mcrt_surrogate mcrt_surrogate;
+
+MCRT_API mcrt_status mcrt_surrogate_create(mcrt_surrogate **out, const mcrt_ctx *optics, uint32_t seed);
+MCRT_API mcrt_status mcrt_surrogate_train(mcrt_surrogate *s, int64_t n_steps, int32_t batch, double lr,
+                                          double *loss_history);
+MCRT_API mcrt_status mcrt_surrogate_eval(mcrt_surrogate *s, int64_t n, const float *inputs, float *outputs);
+MCRT_API mcrt_status mcrt_surrogate_labels(mcrt_surrogate *s, int64_t n, const float *inputs, float *labels);
+MCRT_API mcrt_status mcrt_surrogate_grad(mcrt_surrogate *s, int64_t n, const float *inputs, const float *targets,
+                                         const float *loss_weights, float *grads, double *loss);
+MCRT_API mcrt_status mcrt_surrogate_params(mcrt_surrogate *s, float *params, int32_t set);
+MCRT_API int64_t mcrt_surrogate_param_count(void);
+MCRT_API mcrt_status mcrt_surrogate_destroy(mcrt_surrogate *s); /* NULL-safe */
+
+/*
  * Transport without allocation.  The paper has no counterpart to this entry point;
  * it exists for callers that cannot allocate device memory themselves or through
  * this library: code running inside another framework's memory pool or under a

@@ -141,6 +141,12 @@ constexpr size_t kWorkBytes = 8 + 16 * 8 + 8;
 
 }  // namespace
 
+mcrt_status mcrt_ctx_tables(const mcrt_ctx* ctx, TablesDev* out) {
+    if (!ctx || !ctx->tables_set || !out) return MCRT_E_STATE;
+    *out = ctx->t;
+    return MCRT_OK;
+}
+
 mcrt_status mcrt_fail_noctx(mcrt_status st, const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);

@@ -132,6 +132,10 @@ cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* i
 
 }  // namespace mcrt
 
+// Optics tables of a model (device pointers owned by the model); MCRT_E_STATE when
+// none are set.
+mcrt_status mcrt_ctx_tables(const mcrt_ctx* ctx, mcrt::TablesDev* out);
+
 // Records `fmt` as the calling thread's context-less error message (read with
 // mcrt_last_error(NULL)) and returns st.
 mcrt_status mcrt_fail_noctx(mcrt_status st, const char* fmt, ...);

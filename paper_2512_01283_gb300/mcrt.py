@@ -79,7 +79,9 @@ _lib = None
 # symbols of include/mcrt.h
 SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "mcrt_image_stokes",
            "mcrt_get_tallies", "mcrt_destroy", "mcrt_last_error", "mcrt_unit_eval", "mcrt_launch_packets_noalloc",
-           "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_tune", "mcrt_batch_images", "mcrt_batch_destroy"]
+           "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_tune", "mcrt_batch_images", "mcrt_batch_destroy",
+           "mcrt_surrogate_create", "mcrt_surrogate_train", "mcrt_surrogate_eval", "mcrt_surrogate_labels",
+           "mcrt_surrogate_grad", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy"]
 
 
 def lib():
@@ -107,8 +109,17 @@ def lib():
     L.mcrt_batch_tune.argtypes = [vp, i64, C.POINTER(TuneReport)]
     L.mcrt_batch_images.argtypes = [vp, vp]
     L.mcrt_batch_destroy.argtypes = [vp]
+    L.mcrt_surrogate_create.argtypes = [C.POINTER(C.c_void_p), vp, C.c_uint32]
+    L.mcrt_surrogate_train.argtypes = [vp, i64, i32, C.c_double, vp]
+    L.mcrt_surrogate_eval.argtypes = [vp, i64, vp, vp]
+    L.mcrt_surrogate_labels.argtypes = [vp, i64, vp, vp]
+    L.mcrt_surrogate_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.mcrt_surrogate_params.argtypes = [vp, vp, i32]
+    L.mcrt_surrogate_param_count.argtypes = []
+    L.mcrt_surrogate_param_count.restype = C.c_int64
+    L.mcrt_surrogate_destroy.argtypes = [vp]
     for name in SYMBOLS:
-        if name != "mcrt_last_error":
+        if name not in ("mcrt_last_error", "mcrt_surrogate_param_count"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -378,6 +389,83 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lib().mcrt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """mcrt_surrogate_*: the MLP surrogate of the grain optics (GPU training and
+    evaluation; marshalling only)."""
+
+    N_IN, N_OUT = 7, 20
+    LAYERS = [(16, 128), (128, 128), (128, 128), (128, 128), (128, 24)]
+
+    def __init__(self, model: "Model", seed=3):
+        h = C.c_void_p()
+        _check(lib().mcrt_surrogate_create(C.byref(h), model.h, int(seed) & 0xffffffff))
+        self.h = h
+        self.n_params = int(lib().mcrt_surrogate_param_count())
+
+    def train(self, n_steps, batch=8192, lr=2e-3):
+        hist = np.zeros(max(1, int(n_steps)))
+        _check(lib().mcrt_surrogate_train(self.h, int(n_steps), int(batch), float(lr),
+                                          C.c_void_p(hist.ctypes.data)))
+        return hist[:int(n_steps)]
+
+    def eval(self, inputs):
+        x = np.ascontiguousarray(np.asarray(inputs, dtype=np.float32))
+        out = np.zeros((x.shape[0], self.N_OUT), dtype=np.float32)
+        _check(lib().mcrt_surrogate_eval(self.h, x.shape[0], C.c_void_p(x.ctypes.data), C.c_void_p(out.ctypes.data)))
+        return out
+
+    def labels(self, inputs):
+        x = np.ascontiguousarray(np.asarray(inputs, dtype=np.float32))
+        out = np.zeros((x.shape[0], self.N_OUT), dtype=np.float32)
+        _check(lib().mcrt_surrogate_labels(self.h, x.shape[0], C.c_void_p(x.ctypes.data),
+                                           C.c_void_p(out.ctypes.data)))
+        return out
+
+    def grad(self, inputs, targets, loss_weights=None):
+        x = np.ascontiguousarray(np.asarray(inputs, dtype=np.float32))
+        t = np.ascontiguousarray(np.asarray(targets, dtype=np.float32))
+        w = None if loss_weights is None else np.ascontiguousarray(np.asarray(loss_weights, dtype=np.float32))
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = C.c_double()
+        _check(lib().mcrt_surrogate_grad(self.h, x.shape[0], C.c_void_p(x.ctypes.data), C.c_void_p(t.ctypes.data),
+                                         C.c_void_p(w.ctypes.data) if w is not None else None,
+                                         C.c_void_p(g.ctypes.data), C.byref(loss)))
+        return loss.value, self.unflatten(g)
+
+    def get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(lib().mcrt_surrogate_params(self.h, C.c_void_p(p.ctypes.data), 0))
+        return self.unflatten(p)
+
+    def set_params(self, layers):
+        p = np.ascontiguousarray(self.flatten(layers), dtype=np.float32)
+        _check(lib().mcrt_surrogate_params(self.h, C.c_void_p(p.ctypes.data), 1))
+
+    def unflatten(self, p):
+        out, off = [], 0
+        for ni, no in self.LAYERS:
+            W = np.asarray(p[off:off + no * ni]).reshape(no, ni)
+            off += no * ni
+            b = np.asarray(p[off:off + no])
+            off += no
+            out.append((W, b))
+        return out
+
+    def flatten(self, layers):
+        return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in layers])
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mcrt_surrogate_destroy(self.h)
             self.h = None
 
     def __del__(self):

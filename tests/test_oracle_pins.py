@@ -527,3 +527,70 @@ def test_sweep_generator_statistics():
         ratio = (b["lambda_um"] / a["lambda_um"]) ** -1.5
         assert np.allclose(k_b, k_a * ratio, rtol=1e-5)
         assert 1.0 <= a["tau"] <= 100.0
+
+
+# ---------------------------------------------------------------------------------
+# grain-optics surrogate: labels and the FP64 MLP reference
+# ---------------------------------------------------------------------------------
+def test_surrogate_labels_reduce_to_the_tables():
+    """At the tabulated sizes the label matrix, taken back to the scattering-plane
+    basis, is the bin table; between sizes it interpolates in ln x; alpha follows the
+    extinction table; realizable (Z11 >= |row 1|)."""
+    from oracle import mlp_oracle as MO
+
+    opt = W.table_optics(n_bins=8)
+    tabs, kext = opt["mueller"], opt["kext"]
+    rng = np.random.default_rng(5)
+    for trial in range(40):
+        ni, ns = rand_dirs(2, rng)
+        k = trial % 8
+        s = -1.0 + 2.0 * k / 7
+        lab = MO.label(np.r_[ni, ns, s], tabs, kext)
+        N = math.exp(lab[19])
+        Z = lab[:16].reshape(4, 4) * N
+        mu = float(np.dot(ni, ns))
+        P = MO.theta_interp(tabs[k].astype(np.float64), mu)
+        assert abs(N - tabs[k][:, 0].max()) < 1e-6 * N
+        # unpolarized input: the intensity is P11 and the polarization degree is |P12|/P11
+        out = Z @ np.array([1.0, 0, 0, 0])
+        assert abs(out[0] - P[0]) < 1e-6 * P[0]
+        assert abs(math.hypot(out[1], out[2]) - abs(P[1])) < 1e-6 * P[0]
+        assert Z[0, 0] ** 2 >= Z[0, 1] ** 2 + Z[0, 2] ** 2 + Z[0, 3] ** 2 - 1e-12
+        a = MO.kext_interp(kext, ni[2])
+        assert np.allclose(lab[16:19], a)
+    # halfway between bins 2 and 3 in ln x
+    ni, ns = rand_dirs(2, rng)
+    s = -1.0 + 2.0 * 2.5 / 7
+    lab = MO.label(np.r_[ni, ns, s], tabs, kext)
+    mid = 0.5 * (tabs[2].astype(np.float64) + tabs[3].astype(np.float64))
+    P = MO.theta_interp(mid, float(np.dot(ni, ns)))
+    assert abs(lab[0] * math.exp(lab[19]) - (np.array(lab[:16]).reshape(4, 4) * math.exp(lab[19]) @ [1, 0, 0, 0])[0]) < 1e-9
+    assert abs((lab[:16].reshape(4, 4) * math.exp(lab[19]) @ [1, 0, 0, 0])[0] - P[0]) < 1e-6 * P[0]
+
+
+def test_mlp_reference_gradients_by_central_differences():
+    from oracle import mlp_oracle as MO
+
+    rng = np.random.default_rng(9)
+    params = [(rng.normal(scale=1 / math.sqrt(ni), size=(no, ni)), rng.normal(scale=0.1, size=no))
+              for ni, no in MO.LAYERS]
+    x = MO.pad_inputs(rng.uniform(-1, 1, size=(5, MO.N_IN)))
+    t = rng.normal(size=(5, MO.N_OUT))
+    w = rng.uniform(0.5, 2.0, size=MO.N_OUT)
+    loss, grads = MO.loss_and_grads(params, x, t, w)
+    h = 1e-6
+    for li in (0, 2, 4):
+        W, b = params[li]
+        for (i, j) in [(0, 0), (3, 5), (W.shape[0] - 1, W.shape[1] - 1)]:
+            Wp = W.copy(); Wp[i, j] += h
+            Wm = W.copy(); Wm[i, j] -= h
+            pp = list(params); pp[li] = (Wp, b)
+            pm = list(params); pm[li] = (Wm, b)
+            num = (MO.loss_and_grads(pp, x, t, w)[0] - MO.loss_and_grads(pm, x, t, w)[0]) / (2 * h)
+            assert abs(num - grads[li][0][i, j]) < 1e-7 * max(1.0, abs(num)), (li, i, j)
+        bp = b.copy(); bp[1] += h
+        bm = b.copy(); bm[1] -= h
+        pp = list(params); pp[li] = (W, bp)
+        pm = list(params); pm[li] = (W, bm)
+        num = (MO.loss_and_grads(pp, x, t, w)[0] - MO.loss_and_grads(pm, x, t, w)[0]) / (2 * h)
+        assert abs(num - grads[li][1][1]) < 1e-7 * max(1.0, abs(num))
