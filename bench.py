@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-packets", type=float, default=1e6, help="packets per job of the batched sweep")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-steps", type=int, default=1, help="timed launches of the surrogate path")
+    ap.add_argument("--sur-train-samples", type=float, default=2e7, help="training samples of the network")
+    ap.add_argument("--sur-bound", type=float, default=0.05, help="error-map bound of the table fallback")
     return ap.parse_args()
 
 
@@ -175,6 +179,78 @@ def run_sweep(args, M, W, torch):
     batch.close()
     for m in mdls:
         m.close()
+    return out
+
+
+def image_diff(a, b):
+    """Relative L2 differences of Stokes image stacks [cam][4][ny][nx]: I, and
+    (Q, U) against I; plus the largest relative difference of integrated I."""
+    a, b = np.asarray(a), np.asarray(b)
+    dI = np.sqrt(np.sum((a[:, 0] - b[:, 0]) ** 2, axis=(1, 2)) / np.sum(b[:, 0] ** 2, axis=(1, 2)))
+    dP = np.sqrt(np.sum((a[:, 1:3] - b[:, 1:3]) ** 2, axis=(1, 2, 3)) / np.sum(b[:, 0] ** 2, axis=(1, 2)))
+    tot = np.abs(a[:, 0].sum(axis=(1, 2)) - b[:, 0].sum(axis=(1, 2))) / b[:, 0].sum(axis=(1, 2))
+    return {"I_rel_l2": float(dI.mean()), "QU_rel_l2": float(dP.mean()), "I_total_rel_max": float(tot.max())}
+
+
+def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_value):
+    """The same disk with the grain optics from the MLP surrogate: trained here on the
+    tables (2e7 samples), table fallback above the error-map bound; throughput and
+    the images' difference from the table path's, next to the table path's own
+    Monte-Carlo difference between two seeds."""
+    mdl = M.Model(model)
+    t0 = time.perf_counter()
+    sur = M.Surrogate(mdl, seed=5)
+    n_train = int(round(args.sur_train_samples / 2048))
+    hist = sur.train(n_steps=n_train, batch=2048, lr=3e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    emap = sur.error_map(1 << 22)
+    mdl.set_surrogate(sur, args.sur_bound)
+    setup_s = time.perf_counter() - t1
+    n_cam = len(run["cameras"])
+    npix = run["cameras"][0]["npix"]
+    imgs = np.zeros((n_cam, 4, npix[1], npix[0]))
+    # warm-up on the first 2^21 packets (kernels loaded, round buffers at full size)
+    M.launch(mdl, dict(run, seed=77, pid_end=1 << 21), precision="fp32", optics="surrogate")
+    torch.cuda.synchronize()
+    sts = []
+    t2 = time.perf_counter()
+    for k in range(args.sur_steps):
+        # a seed of its own: compared with the table images like a second table seed is
+        sts.append(M.launch(mdl, dict(run, seed=5000 + k), precision="fp32", optics="surrogate"))
+        for c in range(n_cam):
+            mdl.image(c, imgs[c])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t2
+    ev = sum(st["events"] for st in sts)
+    value = ev / wall
+    st = sts[-1]
+    rows = st["mlp_tally_rows"] + st["mlp_scatter_rows"]
+    fb = st["mlp_fallback_map"] + st["mlp_fallback_realizability"]
+    flop_row = 2.0 * (16 * 128 + 3 * 128 * 128 + 128 * 24)
+    other = np.zeros_like(imgs)
+    table_step(2000 + args.steps, other)
+    out = {"workload": "flared disk %d^3 as the table line, grain optics from the MLP surrogate (7 -> 128 x 4 -> 20, "
+                       "SiLU, BF16 weights, FP32 accumulation, mma.sync m16n8k16), trained on %.0e samples from the "
+                       "tables, table fallback above error bound %g; %.0e packets"
+                       % (args.grid, n_train * 2048, args.sur_bound, args.packets),
+           "value": value, "unit": UNIT, "ms_per_step": 1e3 * wall / args.sur_steps,
+           "vs_table_path": value / table_value,
+           "train": {"samples": n_train * 2048, "steps": n_train, "batch": 2048, "seconds": train_s,
+                     "loss_first": float(hist[0]), "loss_last": float(np.mean(hist[-20:]))},
+           "error_map": {"median": float(np.median(emap)), "p90": float(np.quantile(emap, 0.9)),
+                         "max": float(emap.max()), "cells_above_bound": int(np.sum(emap > args.sur_bound)),
+                         "setup_s": setup_s},
+           "mlp_rows_per_step": rows, "fallback_fraction": fb / max(rows, 1.0),
+           "envelope_miss_fraction": st["envelope_miss"] / max(st["mlp_scatter_rows"], 1.0),
+           "tally_overflow": st["tally_overflow"], "rounds": st["wave_iterations"],
+           "mlp_tflops_over_launch": rows * flop_row / (wall / args.sur_steps) / 1e12,
+           "image_error": {"surrogate_vs_table": image_diff(imgs, table_imgs),
+                           "table_vs_table_other_seed": image_diff(other, table_imgs)},
+           "gpu_launches_per_step": int(st["wave_iterations"]) * 4 + n_cam}
+    sur.close()
+    mdl.close()
     return out
 
 
@@ -332,6 +408,16 @@ def main():
 
     if not args.no_sweep:
         line["batched_sweep"] = run_sweep(args, M, W, torch)
+
+    if not args.no_surrogate and world == 1:
+        table_imgs = imgs.cpu().numpy()
+
+        def table_step(seed, out):
+            M.launch(mdl, dict(run, seed=seed), precision="fp32")
+            for k in range(n_cam):
+                mdl.image(k, out[k])
+
+        line["surrogate"] = run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, value)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1

@@ -59,6 +59,7 @@ enum { MCRT_BOUNDARY_OUTFLOW = 0 };
 enum { MCRT_SRC_POINT = 0, MCRT_SRC_BEAM = 1, MCRT_SRC_THERMAL = 2 };
 enum { MCRT_SCAT_RAYLEIGH = 0, MCRT_SCAT_TABLE = 1 };
 enum { MCRT_FP32 = 0, MCRT_FP64 = 1 };
+enum { MCRT_OPTICS_TABLES = 0, MCRT_OPTICS_SURROGATE = 1 };
 enum { MCRT_MAX_SOURCES = 8, MCRT_MAX_CAMERAS = 16 };
 
 /* Status bits reported in mcrt_stats.status_bits. */
@@ -118,6 +119,10 @@ typedef struct {
                                      segments, flag (1 escaped, 2 roulette, 3 event cap,
                                      4 trial cap), I_birth, source, events; host or device;
                                      nullable */
+    int32_t optics;               /* MCRT_OPTICS_TABLES: the optics set with
+                                     mcrt_set_dust_tables; MCRT_OPTICS_SURROGATE: the
+                                     network attached with mcrt_set_surrogate (FP32, one
+                                     model, no time budget) */
 } mcrt_launch_desc;
 
 /* Totals of a launch (FP64 sums over packets). */
@@ -129,6 +134,14 @@ typedef struct {
     double status_bits;           /* MCRT_STATUS_* bits, as a number */
     double tally_segments;        /* segments that added to the source tally */
     double absorb_segments;       /* segments that added to the absorbed-energy tally */
+    /* surrogate launches only (zero otherwise) */
+    double mlp_tally_rows;        /* network evaluations for the source tally (segment x camera) */
+    double mlp_scatter_rows;      /* network evaluations for rejection trials */
+    double mlp_fallback_map;      /* evaluations replaced by the tables: error-map cell above bound */
+    double mlp_fallback_realizability; /* ... network matrix not physically realizable */
+    double tally_overflow;        /* tally segments done with the tables for want of queue space */
+    double envelope_miss;         /* accepted-or-not trials whose target exceeded the envelope */
+    double wave_iterations;       /* transport / network rounds of the launch */
 } mcrt_stats;
 
 /*
@@ -273,9 +286,11 @@ MCRT_API mcrt_status mcrt_batch_destroy(mcrt_batch *batch); /* NULL-safe */
  * multi-dimensional grain optics).  The network maps u = (n_i[3], n_s[3], s) --
  * incident and scattered directions in the grain frame and s in [-1, 1], the
  * position of ln x between the first and last tabulated size parameter -- to 20
- * outputs: the 4x4 scattering matrix from the grain-frame Stokes basis of n_i to
- * that of n_s divided by N(s) = max P11 (16, row-major), alpha1..3 at the polar
- * angle of n_i, and ln N(s).  Layers 16 (7 inputs, zero padded) -> 128 -> 128 -> 128
+ * outputs for the 4x4 scattering matrix M in the scattering-plane basis (Sec. 2.1;
+ * the rotations into and out of the plane are applied exactly by the kernels): ln M11
+ * (M in 1/sr) and the other 15 entries divided by M11 (row-major, (0,0) left out);
+ * then alpha1..3 at the polar angle of n_i and ln N(s), N(s) = max P11 over the
+ * scattering angle.  Layers 16 (7 inputs, zero padded) -> 128 -> 128 -> 128
  * -> 128 -> 24 (20 used), SiLU; BF16 weights and activations with FP32 accumulation
  * on the tensor cores; FP32 master weights and Adam.
  *   create: copies the tables of `optics` (MCRT_SCAT_TABLE) as the label source and
@@ -305,6 +320,48 @@ MCRT_API mcrt_status mcrt_surrogate_grad(mcrt_surrogate *s, int64_t n, const flo
 MCRT_API mcrt_status mcrt_surrogate_params(mcrt_surrogate *s, float *params, int32_t set);
 MCRT_API int64_t mcrt_surrogate_param_count(void);
 MCRT_API mcrt_status mcrt_surrogate_destroy(mcrt_surrogate *s); /* NULL-safe */
+
+/*
+ * Error map of the current network: n_samples inputs drawn uniformly (directions on
+ * the sphere, s in [-1, 1]) are evaluated by the network and by the tables; each of
+ * the 8^4 cells of (cos theta_i, cos theta_s, delta phi = phi_s - phi_i in [0, 2 pi),
+ * s), 8 equal bins per coordinate, index ((i*8 + j)*8 + k)*8 + l, gets the largest
+ * error max_e |M_net,e - M_e| / M11 over its samples (relative to the true M11).  map (host or device,
+ * [4096] FP32, nullable) receives it.  Training or setting parameters invalidates it.
+ */
+MCRT_API mcrt_status mcrt_surrogate_error_map(mcrt_surrogate *s, int64_t n_samples, float *map);
+
+/*
+ * Attach the network to a model for launches with desc->optics =
+ * MCRT_OPTICS_SURROGATE.  The model needs MCRT_SCAT_TABLE optics: they remain the
+ * fallback.  Copies the network (BF16 weights, FP32 biases), its error map (computed
+ * with 2^22 samples if not yet done) and the extinction elements alpha1..3 that the
+ * network gives on the model's n_ktheta angles (averaged over 16 scattered
+ * directions and sizes; rows with alpha1 <= 0 or |alpha2| >= alpha1 keep the table's
+ * row).  In surrogate launches
+ *  - each tallying segment and camera evaluates the network at the grain-frame
+ *    directions of the packet and the camera and at the size s of the packet's
+ *    current flight (a grain-size bin drawn with the bin weights at every emission
+ *    and scattering, so that the tally averages to the bin mixture);
+ *  - each rejection trial evaluates it at the proposed direction and the size bin
+ *    drawn for the scattering; the proposals and the envelope are the tables' (the
+ *    envelope widened by 5%);
+ *  - an evaluation uses the tables instead when its error-map cell exceeds `bound`
+ *    (relative to M11) or when the network's matrix fails the realizability check
+ *    M11^2 >= M12^2 + M13^2 + M14^2 and M11^2 >= M21^2 + M31^2 + M41^2 by more than 5%
+ *    in those squared norms (smaller excesses are scaled back onto the boundary);
+ *  - extinction and emission use the distilled alpha1..3; step-2 images of such a
+ *    launch too.
+ * The surrogate may be destroyed afterwards.  bound = 0 means 0.05.  bound < 0 is a
+ * validation mode: the surrogate path's kernels run but every evaluation takes the
+ * tables, the envelope is not widened and extinction uses the tables' alpha, so the
+ * packets follow the table path's trajectories exactly (same random numbers and
+ * decisions, up to rounding); only the tally differs, sampling one size bin per flight
+ * instead of the bin mixture, with the same expectation.
+ * Errors: MCRT_E_INVAL, MCRT_E_STATE (no MCRT_SCAT_TABLE optics), MCRT_E_NOMEM,
+ * MCRT_E_CUDA.
+ */
+MCRT_API mcrt_status mcrt_set_surrogate(mcrt_ctx *ctx, mcrt_surrogate *s, double bound);
 
 /*
  * Transport without allocation.  The paper has no counterpart to this entry point;

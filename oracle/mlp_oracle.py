@@ -9,12 +9,18 @@ Mueller matrix may be supplied analytically, as tables, or by a network):
          last tabulated size parameter;
   P(Theta; s) = the bin tables interpolated linearly in the scattering angle and
          linearly in ln x between neighbouring bins;
-  Z_g  = the 4x4 matrix taking Stokes vectors in the grain-frame Stokes basis of n_i
-         to that of n_s (Sec. 2.1 bases; both basis rotations folded in), built here
-         by applying the oracle's scattering transfer to the unit Stokes vectors;
+  M    = the 4x4 scattering matrix in the scattering-plane basis (Sec. 2.1: the
+         Stokes vector is rotated into the scattering plane, multiplied, rotated out),
+         [[P11, P12, 0, 0], [P12, P22, 0, 0], [0, 0, P33, P34], [0, 0, -P34, P44]] for
+         these tables; a network for aligned grains learns the general 16 entries as
+         functions of both grain-frame directions;
   N(s) = max over the tabulated angles of the interpolated P11;
-  outputs: Z_g / N (16, row-major), alpha1..3 at the polar angle of n_i (the
-         extinction table, linear in theta'), ln N.
+  outputs: ln M11 (= ln P11, 1/sr), the other 15 entries of M divided by M11
+         (row-major, (0,0) left out), alpha1..3 at the polar angle of n_i (the
+         extinction table, linear in theta'), ln N.  The logarithm and the ratios give
+         every direction the same relative accuracy although P11 of a
+         forward-scattering bin spans about three decades; the plane rotations stay
+         exact geometry outside the network.
 MLP: 16 (7 inputs, zero padded) -> 128 -> 128 -> 128 -> 128 -> 24 (20 used), SiLU
 after every hidden layer, weights W_l [n_out][n_in], biases b_l.
 """
@@ -24,7 +30,6 @@ import math
 
 import numpy as np
 
-from oracle import oracle as O
 
 N_IN, N_IN_PAD, HIDDEN, N_OUT, N_OUT_PAD = 7, 16, 128, 20, 24
 LAYERS = [(N_IN_PAD, HIDDEN), (HIDDEN, HIDDEN), (HIDDEN, HIDDEN), (HIDDEN, HIDDEN), (HIDDEN, N_OUT_PAD)]
@@ -36,6 +41,8 @@ LAYERS = [(N_IN_PAD, HIDDEN), (HIDDEN, HIDDEN), (HIDDEN, HIDDEN), (HIDDEN, HIDDE
 def interp_bins(tabs, s):
     """Tables [n_bins][n_theta][6] interpolated linearly in ln x at s in [-1, 1]."""
     nb = tabs.shape[0]
+    if nb == 1:  # a single size bin: nothing to interpolate in ln x
+        return tabs[0].astype(np.float64)
     b = (min(max(s, -1.0), 1.0) + 1.0) * 0.5 * (nb - 1)
     k = min(int(math.floor(b)), nb - 2)
     f = b - k
@@ -63,17 +70,22 @@ def label(u, tabs, kext):
     ni, ns, s = np.asarray(u[0:3], float), np.asarray(u[3:6], float), float(u[6])
     tab = interp_bins(tabs, s)
     N = float(tab[:, 0].max())
-    P = theta_interp(tab, float(np.dot(ni, ns)))
-    Z = np.zeros((4, 4))
-    for j in range(4):
-        e = np.zeros(4)
-        e[j] = 1.0
-        Z[:, j] = O.mueller_apply(e, ni, ns, P)
+    P11, P12, P22, P33, P34, P44 = theta_interp(tab, float(np.dot(ni, ns)))
+    M = np.array([[P11, P12, 0.0, 0.0], [P12, P22, 0.0, 0.0], [0.0, 0.0, P33, P34], [0.0, 0.0, -P34, P44]])
     out = np.zeros(N_OUT)
-    out[:16] = (Z / N).ravel()
+    flat = M.ravel()
+    out[0] = math.log(flat[0])
+    out[1:16] = flat[1:16] / flat[0]
     out[16:19] = kext_interp(kext, ni[2])
     out[19] = math.log(N)
     return out
+
+
+def matrix(out):
+    """The 4x4 scattering-plane matrix encoded by the first 16 outputs."""
+    out = np.asarray(out, dtype=float)
+    r = np.concatenate([[1.0], out[1:16]])
+    return math.exp(out[0]) * r.reshape(4, 4)
 
 
 # ----------------------------------------------------------------------------------

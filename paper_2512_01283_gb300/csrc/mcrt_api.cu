@@ -13,6 +13,7 @@
 
 #include "mcrt.h"
 #include "mcrt_internal.h"
+#include "mcrt_mlp_infer.cuh"
 
 using namespace mcrt;
 
@@ -44,6 +45,20 @@ struct mcrt_ctx {
     mcrt_camera cams[kMaxCams];
     bool launched = false;
     int precision = MCRT_FP32;  // arithmetic of the last launch, reused by its images
+    // attached surrogate: network image, error map, distilled extinction table
+    bool sur_set = false;
+    unsigned char* d_sur_image = nullptr;
+    float* d_sur_map = nullptr;
+    float4* d_sur_kext = nullptr;
+    float sur_bound = 0.05f;
+    int sur_kext_fixed = 0;
+    int last_optics = MCRT_OPTICS_TABLES;
+    // surrogate launches: control block, tally records, waiting packets
+    WaveCtl* d_wave = nullptr;
+    float4* d_records = nullptr;
+    unsigned long long rec_cap = 0;
+    float4 *d_susp = nullptr, *d_res = nullptr;
+    unsigned long long wave_cap = 0;
     // work area: counter (8 B), stats (16 x 8 B), status (8 B)
     unsigned char* d_work = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -123,7 +138,29 @@ void host_basis(const double n[3], double th[3], double ph[3]) {
     th[2] = ph[0] * n[1] - ph[1] * n[0];
 }
 
+void free_surrogate(mcrt_ctx* c) {
+    cudaFree(c->d_sur_image);
+    cudaFree(c->d_sur_map);
+    cudaFree(c->d_sur_kext);
+    c->d_sur_image = nullptr;
+    c->d_sur_map = nullptr;
+    c->d_sur_kext = nullptr;
+    c->sur_set = false;
+}
+
+void free_wave(mcrt_ctx* c) {
+    cudaFree(c->d_wave);
+    cudaFree(c->d_records);
+    cudaFree(c->d_susp);
+    cudaFree(c->d_res);
+    c->d_wave = nullptr;
+    c->d_records = nullptr;
+    c->d_susp = c->d_res = nullptr;
+    c->rec_cap = c->wave_cap = 0;
+}
+
 void free_tables(mcrt_ctx* c) {
+    free_surrogate(c);  // the network was attached for these tables
     cudaFree(c->d_mix);
     cudaFree(c->d_bins);
     cudaFree(c->d_kext);
@@ -331,6 +368,10 @@ static mcrt_status check_desc(mcrt_ctx* ctx, const mcrt_launch_desc* d) {
     if (d->roulette_threshold < 0.0 || (d->roulette_threshold > 0.0 && !(d->roulette_survival > 0.0 && d->roulette_survival <= 1.0)))
         return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad roulette parameters");
     if (d->n_trace < 0 || (d->n_trace > 0 && !d->trace)) return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad trace");
+    if (d->optics != MCRT_OPTICS_TABLES && d->optics != MCRT_OPTICS_SURROGATE)
+        return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: bad optics %d", d->optics);
+    if (d->optics == MCRT_OPTICS_SURROGATE && (d->precision != MCRT_FP32 || d->time_budget_s > 0.0))
+        return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: surrogate launches are FP32 without a time budget");
     for (int s = 0; s < d->n_sources; ++s) {
         const mcrt_source& src = d->sources[s];
         if (src.type < MCRT_SRC_POINT || src.type > MCRT_SRC_THERMAL)
@@ -466,6 +507,16 @@ static mcrt_status prepare_model(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint3
     return MCRT_OK;
 }
 
+static void add_wave_stats(mcrt_stats* st, const WaveCtl& w) {
+    st->mlp_tally_rows += (double)w.cnt[kCntTallyRows];
+    st->mlp_scatter_rows += (double)w.cnt[kCntScatRows];
+    st->mlp_fallback_map += (double)w.cnt[kCntFallbackMap];
+    st->mlp_fallback_realizability += (double)w.cnt[kCntFallbackReal];
+    st->tally_overflow += (double)w.cnt[kCntOverflow];
+    st->envelope_miss += (double)w.cnt[kCntEnvelopeMiss];
+    st->wave_iterations += (double)w.cnt[kCntIterations];
+}
+
 static void add_stats(mcrt_stats* st, const double raw[16], unsigned status, float ms) {
     const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(raw + 6);
     st->emitted_energy += raw[0];
@@ -504,10 +555,18 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
     JobDev job;
     st = prepare_model(ctx, d, d->stream, job);
     if (st != MCRT_OK) return st;
+    const bool sur = d->optics == MCRT_OPTICS_SURROGATE;
+    if (sur && !ctx->sur_set) return fail(ctx, MCRT_E_STATE, "mcrt_launch_packets: no surrogate attached (mcrt_set_surrogate)");
     TransportParams P{};
     fill_common(d, P);
     P.g = ctx->g;
     P.t = ctx->t;
+    const bool validate = sur && ctx->sur_bound < 0.f;  // every evaluation from the tables
+    if (sur && !validate) {  // extinction and emission from the network's alpha table
+        P.t.kext = ctx->d_sur_kext;
+        P.t.k_iso = 0;
+        P.t.k_const = 0;
+    }
     for (int a = 0; a < 3; ++a) {
         P.lo_f[a] = job.lo_f[a];
         P.d_f[a] = job.d_f[a];
@@ -557,10 +616,71 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
     const long long need = (work + block - 1) / block;
     if (need < grid) grid = need > 0 ? need : 1;
 
+    if (sur) {
+        // capacity of a round: up to 2^21 packets in flight, 32 tally records each
+        unsigned long long cap = work < (1ll << 21) ? (unsigned long long)(work > 0 ? work : 1) : (1ull << 21);
+        const unsigned long long rec_cap = cap * 32ull > 65536ull ? cap * 32ull : 65536ull;
+        if (!ctx->d_wave) CK(ctx, cudaMalloc(&ctx->d_wave, sizeof(WaveCtl)));
+        if (ctx->wave_cap < cap) {
+            cudaFree(ctx->d_susp);
+            cudaFree(ctx->d_res);
+            ctx->d_susp = ctx->d_res = nullptr;
+            ctx->wave_cap = 0;
+            cudaError_t e = cudaMalloc(&ctx->d_susp, (size_t)cap * kStateF4 * sizeof(float4));
+            if (e == cudaSuccess) e = cudaMalloc(&ctx->d_res, (size_t)cap * kStateF4 * sizeof(float4));
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                return fail(ctx, MCRT_E_NOMEM, "mcrt_launch_packets: surrogate packet buffers: %s", cudaGetErrorString(e));
+            }
+            ctx->wave_cap = cap;
+        }
+        if (ctx->rec_cap < rec_cap) {
+            cudaFree(ctx->d_records);
+            ctx->d_records = nullptr;
+            ctx->rec_cap = 0;
+            cudaError_t e = cudaMalloc(&ctx->d_records, (size_t)rec_cap * kRecordF4 * sizeof(float4));
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                return fail(ctx, MCRT_E_NOMEM, "mcrt_launch_packets: surrogate tally queue: %s", cudaGetErrorString(e));
+            }
+            ctx->rec_cap = rec_cap;
+        }
+        P.sur.image = ctx->d_sur_image;
+        P.sur.err_map = ctx->d_sur_map;
+        P.sur.bound = ctx->sur_bound;
+        P.sur.env_margin = validate ? 0.f : 0.05f;
+        P.sur.ctl = ctx->d_wave;
+        P.sur.records = ctx->d_records;
+        P.sur.rec_cap = ctx->rec_cap;
+        P.sur.suspend = ctx->d_susp;
+        P.sur.resume = ctx->d_res;
+        int rounds = 0;
+        float ms = 0.f;
+        if (work > 0) CK(ctx, run_surrogate_transport(P, ctx->n_sm, cap, &rounds, &ms, ctx->stream));
+        ctx->launched = true;
+        ctx->last_optics = MCRT_OPTICS_SURROGATE;
+        if (trace_host)
+            CK(ctx, cudaMemcpyAsync(trace_host, P.trace, (size_t)d->n_trace * 16 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+        double raw[16];
+        unsigned status = 0;
+        WaveCtl w{};
+        CK(ctx, cudaMemcpyAsync(raw, ctx->d_work + 8, 16 * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(&status, ctx->d_work + 8 + 16 * 8, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+        if (work > 0) CK(ctx, cudaMemcpyAsync(&w, ctx->d_wave, sizeof(WaveCtl), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        if (st_out) {
+            add_stats(st_out, raw, status, ms);
+            add_wave_stats(st_out, w);
+        }
+        return status_of(ctx, status);
+    }
+
     CK(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
     if (work > 0) CK(ctx, launch_transport(P, d->precision, block, (int)grid, ctx->stream));
     CK(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
     ctx->launched = true;
+    ctx->last_optics = MCRT_OPTICS_TABLES;
 
     if (trace_host)
         CK(ctx, cudaMemcpyAsync(trace_host, P.trace, (size_t)d->n_trace * 16 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -596,6 +716,11 @@ mcrt_status mcrt_image_stokes(mcrt_ctx* ctx, int32_t camera, double* out) {
     ImageParams p{};
     p.g = ctx->g;
     p.t = ctx->t;
+    if (ctx->last_optics == MCRT_OPTICS_SURROGATE && ctx->sur_set && ctx->sur_bound >= 0.f) {
+        p.t.kext = ctx->d_sur_kext;
+        p.t.k_iso = 0;
+        p.t.k_const = 0;
+    }
     const double nn = std::sqrt(cm.dir[0] * cm.dir[0] + cm.dir[1] * cm.dir[1] + cm.dir[2] * cm.dir[2]);
     for (int a = 0; a < 3; ++a) p.cam.dir[a] = cm.dir[a] / nn;
     host_basis(p.cam.dir, p.cam.th, p.cam.ph);
@@ -637,6 +762,35 @@ mcrt_status mcrt_get_tallies(mcrt_ctx* ctx, double* source, double* absorbed) {
     return MCRT_OK;
 }
 
+mcrt_status mcrt_set_surrogate(mcrt_ctx* ctx, mcrt_surrogate* s, double bound) {
+    if (!ctx || !s) return fail(ctx, MCRT_E_INVAL, "mcrt_set_surrogate: ctx or surrogate is NULL");
+    if (!ctx->tables_set || ctx->t.model != MCRT_SCAT_TABLE)
+        return fail(ctx, MCRT_E_STATE, "mcrt_set_surrogate: the model needs MCRT_SCAT_TABLE optics as the fallback");
+    if (!(bound == bound)) return fail(ctx, MCRT_E_INVAL, "mcrt_set_surrogate: bound is NaN");
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!ctx->d_sur_image) {
+        cudaError_t e = cudaMalloc(&ctx->d_sur_image, mlp::kImgBytes);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_sur_map, sizeof(float) * kErrMapCells);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            free_surrogate(ctx);
+            return fail(ctx, MCRT_E_NOMEM, "mcrt_set_surrogate: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaFree(ctx->d_sur_kext);
+    ctx->d_sur_kext = nullptr;
+    CK(ctx, cudaMalloc(&ctx->d_sur_kext, (size_t)ctx->t.n_ktheta * sizeof(float4)));
+    ctx->sur_set = false;
+    int fixed = 0;
+    const mcrt_status st = mcrt_surrogate_export(s, ctx->t.n_ktheta, ctx->d_kext, ctx->d_sur_image, ctx->d_sur_map,
+                                                 ctx->d_sur_kext, &fixed);
+    if (st != MCRT_OK) return fail(ctx, st, "mcrt_set_surrogate: %s", mcrt_last_error(nullptr));
+    ctx->sur_bound = bound > 0.0 ? (float)bound : (bound < 0.0 ? -1.f : 0.05f);
+    ctx->sur_kext_fixed = fixed;
+    ctx->sur_set = true;
+    return MCRT_OK;
+}
+
 mcrt_status mcrt_destroy(mcrt_ctx* ctx) {
     if (!ctx) return MCRT_OK;
     free_tables(ctx);
@@ -647,6 +801,7 @@ mcrt_status mcrt_destroy(mcrt_ctx* ctx) {
     cudaFree(ctx->d_S);
     cudaFree(ctx->d_absorbed);
     cudaFree(ctx->d_work);
+    free_wave(ctx);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -732,6 +887,8 @@ mcrt_status batch_build(mcrt_batch** out, mcrt_ctx* const* models, int32_t n_mod
     if (st != MCRT_OK) return st;
     if (desc->n_trace > 0 || desc->accumulate || desc->pid_begin != 0 || desc->pid_end > 0)
         return fail(nullptr, MCRT_E_INVAL, "batch: traces, accumulation and packet id ranges are single-model options");
+    if (desc->optics != MCRT_OPTICS_TABLES)
+        return fail(nullptr, MCRT_E_INVAL, "batch: surrogate optics are a single-model option");
     for (int m = 0; m < n_models; ++m) {
         if (!models[m]) return fail(nullptr, MCRT_E_INVAL, "batch: model %d is NULL", m);
         if (!models[m]->tables_set) return fail(nullptr, MCRT_E_STATE, "batch: model %d has no optics", m);

@@ -12,6 +12,12 @@ namespace mcrt {
 
 constexpr int kMaxCams = MCRT_MAX_CAMERAS;
 constexpr int kMaxSources = MCRT_MAX_SOURCES;
+// scattering-model id of the transport instantiation that defers the optics to the
+// network (internal; the tables stay MCRT_SCAT_TABLE)
+constexpr int kScatSurrogate = 2;
+constexpr int kErrMapCells = 4096;  // 8^4 cells of (cos theta_i, cos theta_s, delta phi, s)
+constexpr int kStateF4 = 8;         // suspended packet: 8 float4 (128 bytes)
+constexpr int kRecordF4 = 4;        // tally record: 4 float4 (64 bytes)
 
 // Cell record, 32 bytes = one DRAM sector: q_B (float4) then
 // (kappa_abs, kappa_sca, emissivity, 0).
@@ -68,6 +74,36 @@ struct JobDev {
     unsigned index;
 };
 
+// Control block of the surrogate path (device memory, rewritten by its kernels):
+// packets in flight wait in two buffers between the transport launch, which moves
+// them to their next scattering and queues the tally segments of the way, and the
+// kernels that evaluate the network for the tallies and for the scattering.
+struct WaveCtl {
+    unsigned long long next_pid;       // new packets taken so far (relative to pid_begin)
+    unsigned long long n_new;          // new packets of the current transport launch
+    unsigned long long claim;          // work items claimed in the current transport launch
+    unsigned long long n_resume;       // packets to resume in the current transport launch
+    unsigned long long n_resume_next;  // packets written to the resume buffer by the scattering kernel
+    unsigned long long n_suspend;      // packets suspended at a scattering by the current launch
+    unsigned long long n_records;      // tally records requested by the current launch
+    // totals: network rows (tally, scattering), fallbacks (error map, realizability),
+    // tally segments tallied in place for want of record space, envelope misses
+    unsigned long long cnt[8];
+};
+enum { kCntTallyRows = 0, kCntScatRows, kCntFallbackMap, kCntFallbackReal, kCntOverflow, kCntEnvelopeMiss, kCntIterations };
+
+struct SurrogateDev {
+    const unsigned char* image;  // inference image (mcrt_mlp_infer.cuh layout)
+    const float* err_map;        // [kErrMapCells] largest error per cell, units of N(s)
+    float bound;                 // cells with a larger error use the tables
+    float env_margin;            // rejection envelope factor (1 + margin)
+    WaveCtl* ctl;
+    float4* records;             // [rec_cap][kRecordF4]
+    unsigned long long rec_cap;
+    float4* suspend;             // [cap][kStateF4]
+    float4* resume;              // [cap][kStateF4]
+};
+
 struct TransportParams {
     GridDev g;
     float lo_f[3], d_f[3];  // FP32 copies of g.lo, g.d
@@ -98,6 +134,7 @@ struct TransportParams {
     const JobDev* jobs;
     int n_jobs;
     int job_interleave;  // 1: packet index i belongs to job i % n_jobs (equal packet counts)
+    SurrogateDev sur;    // surrogate path only
 };
 
 struct ImageParams {
@@ -129,6 +166,10 @@ int thermal_cdf_blocks(long long ncell);
 cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* guide, long long n_guide,
                                  cudaStream_t s);
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s);
+// surrogate path (mcrt_wave.cu): the transport loop of one launch; ms_out: device
+// time of all its kernels
+cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned long long cap, int* iterations,
+                                    float* ms_out, cudaStream_t s);
 
 }  // namespace mcrt
 
@@ -139,3 +180,8 @@ mcrt_status mcrt_ctx_tables(const mcrt_ctx* ctx, mcrt::TablesDev* out);
 // Records `fmt` as the calling thread's context-less error message (read with
 // mcrt_last_error(NULL)) and returns st.
 mcrt_status mcrt_fail_noctx(mcrt_status st, const char* fmt, ...);
+
+// Inference data of a trained surrogate (mcrt_mlp.cu) for a model: inference image,
+// error map and the extinction table distilled on n_ktheta angles.
+mcrt_status mcrt_surrogate_export(mcrt_surrogate* s, int n_ktheta, const float4* table, unsigned char* d_image,
+                                  float* d_map, float4* d_kext, int* n_fixed);

@@ -4,9 +4,11 @@
 //
 // The network maps (n_i, n_s, s) -- incident and scattered directions in the grain
 // frame and the position s in [-1, 1] of ln x between the first and last tabulated
-// size parameter -- to 20 numbers: the 4x4 grain-basis scattering matrix divided by
-// its normaliser N(s) = max P11, the extinction elements alpha1..3 at the incident
-// polar angle, and ln N(s).  Architecture 16 (7 inputs, zero padded) -> 128 -> 128 ->
+// size parameter -- to 20 numbers: ln M11 of the 4x4 scattering matrix in the
+// scattering-plane basis and its other 15 entries relative to M11 (the rotations into
+// and out of the plane stay exact geometry in the kernels that use the network), the
+// extinction elements alpha1..3 at the incident polar angle, and ln N(s), N(s) = max
+// P11.  Architecture 16 (7 inputs, zero padded) -> 128 -> 128 ->
 // 128 -> 128 -> 24 (20 used), SiLU; BF16 weights and activations, FP32 accumulation on
 // the tensor cores (mma.sync m16n8k16), FP32 master weights and Adam.
 //
@@ -24,14 +26,19 @@
 #include "mcrt.h"
 #include "mcrt_device.cuh"
 #include "mcrt_internal.h"
+#include "mcrt_mlp_infer.cuh"
 
 namespace mcrt {
 namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int kLayers = 5;
-constexpr int kIn = 7, kInPad = 16, kHid = 128, kOut = 20, kOutPad = 24;
+using mlp::kHid;
+using mlp::kIn;
+using mlp::kInPad;
+using mlp::kLayers;
+using mlp::kOut;
+using mlp::kOutPad;
 __host__ __device__ constexpr int layer_in(int l) { return l == 0 ? kInPad : kHid; }
 __host__ __device__ constexpr int layer_out(int l) { return l == kLayers - 1 ? kOutPad : kHid; }
 // parameter layout: per layer W [out][in] then b [out], layers in order
@@ -70,18 +77,24 @@ __device__ void interp_row(const LabelTables& T, int k, int j, float f, float w,
 }
 
 // 20 targets for (n_i, n_s, s): tables interpolated linearly in the scattering angle
-// and in ln x between bins; grain-basis matrix from the scattering-plane transfer of
-// the four unit Stokes vectors; normalised by the maximum interpolated P11.
+// and in ln x between bins; the scattering-plane matrix M as ln M11 and M_rc / M11;
+// alpha1..3; ln of the maximum interpolated P11.
 __device__ void surrogate_label(const LabelTables& T, const V3<float>& ni, const V3<float>& ns, float s,
                                 float out[kOut]) {
-    const float b = (fminf(fmaxf(s, -1.f), 1.f) + 1.f) * 0.5f * (float)(T.n_bins - 1);
-    int k = (int)floorf(b);
-    k = k > T.n_bins - 2 ? T.n_bins - 2 : (k < 0 ? 0 : k);
-    const float fb = b - (float)k;
+    // bins k and k1 = k + 1 around s (one bin: k = k1 = 0)
+    int k = 0, k1 = 0;
+    float fb = 0.f;
+    if (T.n_bins > 1) {
+        const float b = (fminf(fmaxf(s, -1.f), 1.f) + 1.f) * 0.5f * (float)(T.n_bins - 1);
+        k = (int)floorf(b);
+        k = k > T.n_bins - 2 ? T.n_bins - 2 : (k < 0 ? 0 : k);
+        k1 = k + 1;
+        fb = b - (float)k;
+    }
     float N = 0.f;
     for (int j = 0; j < T.n_theta; ++j) {
         const float v = (1.f - fb) * T.bins[((size_t)k * T.n_theta + j) * 2].x +
-                        fb * T.bins[((size_t)(k + 1) * T.n_theta + j) * 2].x;
+                        fb * T.bins[((size_t)k1 * T.n_theta + j) * 2].x;
         N = fmaxf(N, v);
     }
     const float mu = fminf(fmaxf(dot(ni, ns), -1.f), 1.f);
@@ -91,26 +104,22 @@ __device__ void surrogate_label(const LabelTables& T, const V3<float>& ni, const
     const float ft = x - (float)j;
     float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     interp_row(T, k, j, ft, 1.f - fb, P);
-    interp_row(T, k + 1, j, ft, fb, P);
-    V3<float> thi, phi, ths, phs;
-    stokes_basis(ni, thi, phi);
-    stokes_basis(ns, ths, phs);
-    const PlaneRot<float> r = plane_rotation(ni, thi, phi, ns, ths, phs);
-    const float invN = 1.f / N;
-    for (int c = 0; c < 4; ++c) {
-        float e[4] = {0.f, 0.f, 0.f, 0.f}, y[4];
-        e[c] = 1.f;
-        apply_plane(r, P, e, y);
-        for (int rr = 0; rr < 4; ++rr) out[rr * 4 + c] = y[rr] * invN;
-    }
+    interp_row(T, k1, j, ft, fb, P);
+    // scattering-plane matrix [[P11,P12,0,0],[P12,P22,0,0],[0,0,P33,P34],[0,0,-P34,P44]]
+    // as ln M11 and the entries relative to M11 (equal relative accuracy over the
+    // decades that P11 spans)
+    const float inv = 1.f / P[0];
+    const float Z[16] = {P[0], P[1], 0.f, 0.f, P[1], P[2], 0.f, 0.f, 0.f, 0.f, P[3], P[4], 0.f, 0.f, -P[4], P[5]};
+    out[0] = logf(P[0]);
+    for (int k = 1; k < 16; ++k) out[k] = Z[k] * inv;
     const float xk = acosf(fminf(fmaxf(ni.z, -1.f), 1.f)) * 0.31830988618379067f * (float)(T.n_ktheta - 1);
     int jk = (int)floorf(xk);
     jk = jk > T.n_ktheta - 2 ? T.n_ktheta - 2 : (jk < 0 ? 0 : jk);
     const float fk = xk - (float)jk;
-    const float4 k0 = T.kext[jk], k1 = T.kext[jk + 1];
-    out[16] = (1.f - fk) * k0.x + fk * k1.x;
-    out[17] = (1.f - fk) * k0.y + fk * k1.y;
-    out[18] = (1.f - fk) * k0.z + fk * k1.z;
+    const float4 ka = T.kext[jk], kb = T.kext[jk + 1];
+    out[16] = (1.f - fk) * ka.x + fk * kb.x;
+    out[17] = (1.f - fk) * ka.y + fk * kb.y;
+    out[18] = (1.f - fk) * ka.z + fk * kb.z;
     out[19] = logf(N);
 }
 
@@ -133,7 +142,7 @@ __global__ void k_gen_batch(LabelTables T, unsigned seed, unsigned step, int B, 
     const V3<float> ni = iso_unit(u0.a, u0.b), ns = iso_unit(u0.c, u0.d);
     const float s = 2.f * u1.a - 1.f;
     const float in[kIn] = {ni.x, ni.y, ni.z, ns.x, ns.y, ns.z, s};
-    for (int c = 0; c < kInPad; ++c) X[(size_t)i * kInPad + c] = __float2bfloat16(c < kIn ? in[c] : 0.f);
+    mlp::store_input_row(X + (size_t)i * kInPad, in);
     float out[kOut];
     surrogate_label(T, ni, ns, s, out);
     for (int c = 0; c < kOut; ++c) Y[(size_t)i * kOut + c] = out[c];
@@ -152,7 +161,9 @@ __global__ void k_labels(LabelTables T, int n, const float* __restrict__ in, flo
 __global__ void k_pack_inputs(int n, const float* __restrict__ in, bf16* __restrict__ X) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int c = 0; c < kInPad; ++c) X[(size_t)i * kInPad + c] = __float2bfloat16(c < kIn ? in[(size_t)i * kIn + c] : 0.f);
+    float u[kIn];
+    for (int c = 0; c < kIn; ++c) u[c] = in[(size_t)i * kIn + c];
+    mlp::store_input_row(X + (size_t)i * kInPad, u);
 }
 
 // ---------------------------------------------------------------------------------
@@ -188,11 +199,8 @@ __device__ __forceinline__ void mma_bf16(float c[4], unsigned a0, unsigned a1, u
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
-__device__ __forceinline__ float silu_grad_f(float z) {
-    const float sg = 1.f / (1.f + __expf(-z));
-    return sg * (1.f + z * (1.f - sg));
-}
+__device__ __forceinline__ float silu_f(float z) { return mlp::silu(z); }
+__device__ __forceinline__ float silu_grad_f(float z) { return mlp::silu_grad(z); }
 
 template <int EPI> __global__ void __launch_bounds__(128) k_gemm(const GemmArgs g) {
     __shared__ __align__(16) bf16 As[kTM][kPadK];
@@ -316,11 +324,55 @@ __global__ void k_adam(int P, float* __restrict__ p, const float* __restrict__ g
     }
 }
 
+// BF16 copies of the weights for the training GEMMs.  Layer 0 columns 7-13 repeat
+// columns 0-6 (they multiply the low parts of the split inputs).
 __global__ void k_pack_weights(const float* __restrict__ p, bf16* __restrict__ wbf) {
     for (int l = 0; l < kLayers; ++l) {
         const int n = layer_out(l) * layer_in(l);
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-            wbf[wbf_offset(l) + i] = __float2bfloat16(p[layer_offset(l) + i]);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            int src = i;
+            float v;
+            if (l == 0) {
+                const int o = i / kInPad, c = i % kInPad;
+                src = o * kInPad + (c < kIn ? c : c - kIn);
+                v = c < 2 * kIn ? p[layer_offset(0) + src] : 0.f;
+            } else {
+                v = p[layer_offset(l) + src];
+            }
+            wbf[wbf_offset(l) + i] = __float2bfloat16(v);
+        }
+    }
+}
+
+// Layer-0 weight gradient: a master weight feeds both the hi and the lo column, so
+// its gradient is the sum of the two; the unused columns get zero.
+__global__ void k_fold_l0(float* __restrict__ g) {
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= kHid) return;
+    float* row = g + (size_t)o * kInPad;
+    for (int c = 0; c < kIn; ++c) row[c] += row[c + kIn];
+    for (int c = kIn; c < kInPad; ++c) row[c] = 0.f;
+}
+
+// Inference image (layout in mcrt_mlp_infer.cuh) from the FP32 parameters.
+__global__ void k_pack_image(const float* __restrict__ p, unsigned char* __restrict__ img) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int l = 0; l < kLayers; ++l) {
+        const int ld = l == 0 ? mlp::kLd0 : mlp::kLdH;
+        bf16* w = reinterpret_cast<bf16*>(img + mlp::img_w(l));
+        const int rows = layer_out(l), n = rows * ld;
+        for (int i = tid; i < n; i += nth) {
+            const int o = i / ld, c = i % ld;
+            float v = 0.f;
+            if (l == 0) {
+                if (c < 2 * kIn) v = p[layer_offset(0) + o * kInPad + (c < kIn ? c : c - kIn)];
+            } else if (c < layer_in(l)) {
+                v = p[layer_offset(l) + o * layer_in(l) + c];
+            }
+            w[i] = __float2bfloat16(v);
+        }
+        float* b = reinterpret_cast<float*>(img + mlp::kImgBias) + mlp::bias_off(l);
+        for (int i = tid; i < rows; i += nth) b[i] = p[layer_offset(l) + rows * layer_in(l) + i];
     }
 }
 
@@ -342,6 +394,129 @@ __global__ void k_init_params(float* __restrict__ p, unsigned seed) {
             }
             p[layer_offset(l) + i] = v;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// fused inference (mcrt_mlp_infer.cuh): evaluation, error map, extinction table
+// ---------------------------------------------------------------------------------
+constexpr int kInferBlock = 256;
+struct WarpTile {
+    bf16 in[16 * mlp::kLd0];
+    float out[16 * mlp::kOutLd];
+};
+static_assert(sizeof(WarpTile) % 16 == 0, "tiles stay 16-byte aligned");
+constexpr size_t kInferSmem = mlp::kImgBytes + (kInferBlock / 32) * sizeof(WarpTile);
+
+__device__ __forceinline__ WarpTile& warp_tile(unsigned char* sm) {
+    return reinterpret_cast<WarpTile*>(sm + mlp::kImgBytes)[threadIdx.x >> 5];
+}
+
+// outputs [n][20] of inputs [n][7]
+__global__ void __launch_bounds__(kInferBlock) k_infer(const unsigned char* __restrict__ img, long long n,
+                                                       const float* __restrict__ in, float* __restrict__ out) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    mlp::load_image(sm, img);
+    __syncthreads();
+    WarpTile& wt = warp_tile(sm);
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const long long ntile = (n + 15) / 16;
+    for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntile; tile += (long long)gridDim.x * wpb) {
+        const long long row = tile * 16 + lane;
+        if (lane < 16) {
+            float u[kIn];
+            for (int c = 0; c < kIn; ++c) u[c] = row < n ? in[row * kIn + c] : 0.f;
+            mlp::store_input_row(wt.in + lane * mlp::kLd0, u);
+        }
+        __syncwarp();
+        mlp::warp_mlp16(sm, wt.in, wt.out, lane);
+        __syncwarp();
+        if (lane < 16 && row < n)
+            for (int o = 0; o < kOut; ++o) out[row * kOut + o] = wt.out[lane * mlp::kOutLd + o];
+        __syncwarp();
+    }
+}
+
+// Error map: for n samples (uniform directions, uniform s) the largest error of the
+// network's scattering matrix against the tables relative to the true M11, per cell
+// of (cos theta_i, cos theta_s, delta phi, s).  map: 4096 floats, zeroed by the
+// caller (non-negative floats compare like their bit patterns).
+__global__ void __launch_bounds__(kInferBlock) k_errmap(const unsigned char* __restrict__ img, LabelTables T,
+                                                        long long n, unsigned seed, float* __restrict__ map) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    mlp::load_image(sm, img);
+    __syncthreads();
+    WarpTile& wt = warp_tile(sm);
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const long long ntile = (n + 15) / 16;
+    for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntile; tile += (long long)gridDim.x * wpb) {
+        const long long i = tile * 16 + lane;
+        float lab[kOut];
+        V3<float> ni{0.f, 0.f, 1.f}, ns{0.f, 0.f, 1.f};
+        float s = 0.f;
+        if (lane < 16) {
+            const Draw4<float> u0 = draw4<float>(i, 0u, 0x61u, seed, 0xE77u);
+            const Draw4<float> u1 = draw4<float>(i, 0u, 0x62u, seed, 0xE77u);
+            ni = iso_unit(u0.a, u0.b);
+            ns = iso_unit(u0.c, u0.d);
+            s = 2.f * u1.a - 1.f;
+            surrogate_label(T, ni, ns, s, lab);
+            const float u[kIn] = {ni.x, ni.y, ni.z, ns.x, ns.y, ns.z, s};
+            mlp::store_input_row(wt.in + lane * mlp::kLd0, u);
+        }
+        __syncwarp();
+        mlp::warp_mlp16(sm, wt.in, wt.out, lane);
+        __syncwarp();
+        if (lane < 16 && i < n) {
+            const float* y = wt.out + lane * mlp::kOutLd;
+            const float r = __expf(y[0] - lab[0]);  // M11 of the network / true M11
+            float e = fabsf(r - 1.f);
+            for (int o = 1; o < 16; ++o) e = fmaxf(e, fabsf(r * y[o] - lab[o]));
+            if (!(e <= 3.0e38f)) e = 3.0e38f;  // NaN or inf: always falls back
+            const int idx = mlp::errmap_index(ni.z, ns.z, atan2f(ns.y, ns.x) - atan2f(ni.y, ni.x), s);
+            atomicMax(reinterpret_cast<int*>(map) + idx, __float_as_int(e));
+        }
+        __syncwarp();
+    }
+}
+
+// Extinction elements alpha1..3 of the network on the grid theta'_j = pi j / (n_k - 1):
+// the mean over 16 scattered directions and sizes of outputs 16..18 at
+// n_i = (sin theta', 0, cos theta').  Rows that are not realizable (alpha1 <= 0 or
+// |alpha2| >= alpha1) keep the table's row and are counted.
+__global__ void __launch_bounds__(kInferBlock) k_distill_kext(const unsigned char* __restrict__ img, int n_k,
+                                                              const float4* __restrict__ table,
+                                                              float4* __restrict__ out, unsigned* __restrict__ n_fixed) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    mlp::load_image(sm, img);
+    __syncthreads();
+    WarpTile& wt = warp_tile(sm);
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < n_k; j += gridDim.x * wpb) {
+        if (lane < 16) {
+            float st, ct, sp, cp;
+            sincospif((float)j / (float)(n_k - 1), &st, &ct);
+            const float z = 1.f - (2.f * lane + 1.f) / 16.f, rho = sqrtf(fmaxf(0.f, 1.f - z * z));
+            sincosf(2.39996323f * (float)lane, &sp, &cp);
+            const float u[kIn] = {st, 0.f, ct, rho * cp, rho * sp, z, -1.f + (2.f * lane + 1.f) / 16.f};
+            mlp::store_input_row(wt.in + lane * mlp::kLd0, u);
+        }
+        __syncwarp();
+        mlp::warp_mlp16(sm, wt.in, wt.out, lane);
+        __syncwarp();
+        if (lane == 0) {
+            float a[3] = {0.f, 0.f, 0.f};
+            for (int r = 0; r < 16; ++r)
+                for (int e = 0; e < 3; ++e) a[e] += wt.out[r * mlp::kOutLd + 16 + e] * (1.f / 16.f);
+            const bool ok = a[0] > 0.f && fabsf(a[1]) < a[0] && fabsf(a[2]) < 3.0e38f;
+            if (ok) {
+                out[j] = make_float4(a[0], a[1], a[2], 0.f);
+            } else {
+                out[j] = table[j];
+                atomicAdd(n_fixed, 1u);
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -382,6 +557,10 @@ struct mcrt_surrogate {
     SurrogateBuffers buf;
     unsigned seed = 0;
     long long step = 0;
+    unsigned char* d_image = nullptr;  // inference image of the current parameters
+    float* d_map = nullptr;            // error map [4096]
+    bool map_valid = false;
+    int n_sm = 0;
 };
 
 namespace {
@@ -495,7 +674,11 @@ mcrt_status backward(mcrt_surrogate* s, int B) {
             k_colsum<<<grid, 128, 0, s->stream>>>(B, no, dZ, s->d_grads + layer_offset(l) + no * ni);
             SK(cudaGetLastError());
         }
-        if (l == 0) break;
+        if (l == 0) {
+            k_fold_l0<<<1, kHid, 0, s->stream>>>(s->d_grads + layer_offset(0));
+            SK(cudaGetLastError());
+            break;
+        }
         // dZ_{l-1} = (dZ W) * SiLU'(Z_{l-1}) : M = B, N = ni, K = no
         GemmArgs gx{};
         gx.M = B;
@@ -531,7 +714,77 @@ mcrt_status stage_inputs(mcrt_surrogate* s, const float* in, long long n) {
     return MCRT_OK;
 }
 
+// Inference image of the current parameters (on the surrogate's stream).
+mcrt_status pack_image(mcrt_surrogate* s) {
+    (void)cudaGetLastError();
+    k_pack_image<<<64, 256, 0, s->stream>>>(s->d_params, s->d_image);
+    SK(cudaGetLastError());
+    return MCRT_OK;
+}
+
+template <typename K> mcrt_status infer_attr(K kernel) {
+    SK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem));
+    return MCRT_OK;
+}
+
+int infer_grid(const mcrt_surrogate* s, long long tiles) {
+    const long long per_block = kInferBlock / 32;
+    long long g = (tiles + per_block - 1) / per_block;
+    const long long cap = (long long)(s->n_sm > 0 ? s->n_sm : 1) * 1;
+    return (int)(g < cap ? (g > 0 ? g : 1) : cap);
+}
+
+mcrt_status compute_error_map(mcrt_surrogate* s, long long n_samples) {
+    mcrt_status st = pack_image(s);
+    if (st != MCRT_OK) return st;
+    st = infer_attr(k_errmap);
+    if (st != MCRT_OK) return st;
+    SK(cudaMemsetAsync(s->d_map, 0, sizeof(float) * kErrMapCells, s->stream));
+    k_errmap<<<infer_grid(s, (n_samples + 15) / 16), kInferBlock, kInferSmem, s->stream>>>(
+        s->d_image, tables_of(s), n_samples, s->seed ^ 0x9E3779B9u, s->d_map);
+    SK(cudaGetLastError());
+    SK(cudaStreamSynchronize(s->stream));
+    s->map_valid = true;
+    return MCRT_OK;
+}
+
 }  // namespace
+
+// Inference data of the surrogate for a model's transport: the inference image, the
+// error map (computed with 2^22 samples if not yet done) and the distilled extinction
+// table on n_ktheta angles (rows that are not realizable come from `table`).
+mcrt_status mcrt_surrogate_export(mcrt_surrogate* s, int n_ktheta, const float4* table, unsigned char* d_image,
+                                  float* d_map, float4* d_kext, int* n_fixed) {
+    if (!s->map_valid) {
+        mcrt_status st = compute_error_map(s, 1ll << 22);
+        if (st != MCRT_OK) return st;
+    }
+    mcrt_status st = pack_image(s);
+    if (st != MCRT_OK) return st;
+    st = infer_attr(k_distill_kext);
+    if (st != MCRT_OK) return st;
+    unsigned* d_fixed = nullptr;
+    SK(cudaMalloc(&d_fixed, sizeof(unsigned)));
+    cudaError_t e = cudaMemsetAsync(d_fixed, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) {
+        (void)cudaGetLastError();
+        k_distill_kext<<<infer_grid(s, n_ktheta), kInferBlock, kInferSmem, s->stream>>>(s->d_image, n_ktheta, table,
+                                                                                      d_kext, d_fixed);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_image, s->d_image, mlp::kImgBytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_map, s->d_map, sizeof(float) * kErrMapCells, cudaMemcpyDeviceToDevice, s->stream);
+    unsigned fixed = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&fixed, d_fixed, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(d_fixed);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return mcrt_fail_noctx(MCRT_E_CUDA, "surrogate export: %s", cudaGetErrorString(e));
+    }
+    if (n_fixed) *n_fixed = (int)fixed;
+    return MCRT_OK;
+}
 
 extern "C" {
 
@@ -558,6 +811,13 @@ mcrt_status mcrt_surrogate_create(mcrt_surrogate** out, const mcrt_ctx* optics, 
     if (e == cudaSuccess) e = cudaMalloc(&s->d_w, sizeof(float) * kOut);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_wbf, sizeof(bf16) * kWeights);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_loss, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_image, mlp::kImgBytes);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_map, sizeof(float) * kErrMapCells);
+    if (e == cudaSuccess) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_bins, t.bins, nbins * sizeof(float4), cudaMemcpyDeviceToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->d_kext, t.kext, (size_t)t.n_ktheta * sizeof(float4), cudaMemcpyDeviceToDevice, s->stream);
@@ -587,6 +847,7 @@ mcrt_status mcrt_surrogate_train(mcrt_surrogate* s, int64_t n_steps, int32_t bat
     if (!s || n_steps < 0 || batch < 64 || batch > (1 << 20))
         return mcrt_fail_noctx(MCRT_E_INVAL, "mcrt_surrogate_train: bad arguments");
     SK(ensure_buffers(s->buf, batch));
+    s->map_valid = false;
     const LabelTables T = tables_of(s);
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     for (long long it = 0; it < n_steps; ++it) {
@@ -619,20 +880,30 @@ mcrt_status mcrt_surrogate_eval(mcrt_surrogate* s, int64_t n, const float* input
     if (n == 0) return MCRT_OK;
     mcrt_status st = stage_inputs(s, inputs, n);
     if (st != MCRT_OK) return st;
-    const int chunk = 1 << 16;
-    SK(ensure_buffers(s->buf, chunk > s->buf.B ? chunk : s->buf.B));
-    std::vector<float> y((size_t)chunk * kOutPad);
-    for (long long i0 = 0; i0 < n; i0 += chunk) {
-        const int m = (int)(n - i0 < chunk ? n - i0 : chunk);
-        (void)cudaGetLastError();
-        k_pack_inputs<<<(m + 127) / 128, 128, 0, s->stream>>>(m, s->d_in + (size_t)i0 * kIn, s->buf.x0);
-        SK(cudaGetLastError());
-        st = forward(s, m);
-        if (st != MCRT_OK) return st;
-        SK(cudaMemcpyAsync(y.data(), s->buf.y, (size_t)m * kOutPad * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    st = pack_image(s);
+    if (st != MCRT_OK) return st;
+    st = infer_attr(k_infer);
+    if (st != MCRT_OK) return st;
+    float* d_out = nullptr;
+    SK(cudaMalloc(&d_out, (size_t)n * kOut * sizeof(float)));
+    (void)cudaGetLastError();
+    k_infer<<<infer_grid(s, (n + 15) / 16), kInferBlock, kInferSmem, s->stream>>>(s->d_image, n, s->d_in, d_out);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(outputs, d_out, (size_t)n * kOut * sizeof(float), cudaMemcpyDefault, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return mcrt_fail_noctx(MCRT_E_CUDA, "mcrt_surrogate_eval: %s", cudaGetErrorString(e));
+    return MCRT_OK;
+}
+
+mcrt_status mcrt_surrogate_error_map(mcrt_surrogate* s, int64_t n_samples, float* map) {
+    if (!s || n_samples < 16 || n_samples > (1ll << 34))
+        return mcrt_fail_noctx(MCRT_E_INVAL, "mcrt_surrogate_error_map: bad arguments");
+    mcrt_status st = compute_error_map(s, n_samples);
+    if (st != MCRT_OK) return st;
+    if (map) {
+        SK(cudaMemcpyAsync(map, s->d_map, sizeof(float) * kErrMapCells, cudaMemcpyDefault, s->stream));
         SK(cudaStreamSynchronize(s->stream));
-        for (int i = 0; i < m; ++i)
-            for (int o = 0; o < kOut; ++o) outputs[((size_t)i0 + i) * kOut + o] = y[(size_t)i * kOutPad + o];
     }
     return MCRT_OK;
 }
@@ -688,6 +959,7 @@ mcrt_status mcrt_surrogate_grad(mcrt_surrogate* s, int64_t n, const float* input
 mcrt_status mcrt_surrogate_params(mcrt_surrogate* s, float* params, int32_t set) {
     if (!s || !params) return mcrt_fail_noctx(MCRT_E_INVAL, "mcrt_surrogate_params: bad arguments");
     if (set) {
+        s->map_valid = false;
         SK(cudaMemcpyAsync(s->d_params, params, sizeof(float) * kParams, cudaMemcpyDefault, s->stream));
         (void)cudaGetLastError();
         k_pack_weights<<<64, 256, 0, s->stream>>>(s->d_params, s->d_wbf);
@@ -715,6 +987,8 @@ mcrt_status mcrt_surrogate_destroy(mcrt_surrogate* s) {
     cudaFree(s->d_wbf);
     cudaFree(s->d_loss);
     cudaFree(s->d_in);
+    cudaFree(s->d_image);
+    cudaFree(s->d_map);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return MCRT_OK;

@@ -143,6 +143,7 @@ extern "C" mcrt_status mcrt_launch_packets_noalloc(const mcrt_noalloc_problem* p
         return mcrt_fail_noctx(MCRT_E_INVAL, "%s: bad roulette parameters", me);
     if (d->n_trace < 0 || (d->n_trace > 0 && !on_device(d->trace)))
         return mcrt_fail_noctx(MCRT_E_INVAL, "%s: the trace buffer must be device memory", me);
+    if (d->optics != MCRT_OPTICS_TABLES) return mcrt_fail_noctx(MCRT_E_INVAL, "%s: tables only", me);
 
     cudaStream_t s = (cudaStream_t)pr->cuda_stream;
     unsigned char* base = nullptr;

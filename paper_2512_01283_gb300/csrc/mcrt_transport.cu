@@ -19,6 +19,7 @@
 
 #include "mcrt_device.cuh"
 #include "mcrt_internal.h"
+#include "mcrt_packet.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -39,39 +40,12 @@ constexpr int kDefaultBlock = 128;
 constexpr int kStageCams = 8;
 constexpr int kStageDoubles = 34;
 
-// camera record in shared memory: Omega, theta-hat, phi-hat, each padded to 4
-__device__ __forceinline__ void load_camera(const float* cm, V3<float>& Om, V3<float>& th, V3<float>& ph) {
-    const float4 a = reinterpret_cast<const float4*>(cm)[0], b = reinterpret_cast<const float4*>(cm)[1],
-                 c = reinterpret_cast<const float4*>(cm)[2];
-    Om = V3<float>{a.x, a.y, a.z};
-    th = V3<float>{b.x, b.y, b.z};
-    ph = V3<float>{c.x, c.y, c.z};
-}
-__device__ __forceinline__ void load_camera(const double* cm, V3<double>& Om, V3<double>& th, V3<double>& ph) {
-    Om = V3<double>{cm[0], cm[1], cm[2]};
-    th = V3<double>{cm[4], cm[5], cm[6]};
-    ph = V3<double>{cm[8], cm[9], cm[10]};
-}
-
 template <typename T> struct Smem {
     const T* cam;        // [n_cam][12]: Omega, theta-hat, phi-hat (each padded to 4)
     const float4* mix;   // [n_theta][2]
     const float4* kext;  // [n_ktheta]
     double* stage;       // [blockDim][kStageDoubles]
 };
-
-// TMA bulk reduction (global += shared, FP64) of one thread's staging slot, and the
-// waits on this thread's bulk groups.
-__device__ __forceinline__ void bulk_reduce_add_f64(double* gdst, const double* ssrc, unsigned bytes) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(gdst), "r"(s),
-                 "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -90,42 +64,7 @@ template <typename T> __device__ __forceinline__ void iso_dir(T u_cos, T u_phi, 
     n[2] = ct;
 }
 
-// alpha1..3 at cos(theta'), linear in theta' on the table grid
-template <typename T>
-__device__ __forceinline__ void kext_eval(const TablesDev& t, const float4* kx, T cos_tp, T& a1, T& a2, T& a3) {
-    if (t.k_const) {
-        const float4 k = kx[0];
-        a1 = k.x;
-        a2 = k.y;
-        a3 = k.z;
-        return;
-    }
-    const T c = cos_tp > T(1) ? T(1) : (cos_tp < T(-1) ? T(-1) : cos_tp);
-    const T x = t_acos(c) * T(0.31830988618379067) * T(t.n_ktheta - 1);
-    int j = (int)floor(x);
-    j = j > t.n_ktheta - 2 ? t.n_ktheta - 2 : (j < 0 ? 0 : j);
-    const T f = x - T(j);
-    const float4 k0 = kx[j], k1 = kx[j + 1];
-    a1 = (T(1) - f) * T(k0.x) + f * T(k1.x);
-    a2 = (T(1) - f) * T(k0.y) + f * T(k1.y);
-    a3 = (T(1) - f) * T(k0.z) + f * T(k1.z);
-}
 
-// scattering matrix of a table (rows of two float4) at mu, linear in the angle
-template <typename T> __device__ __forceinline__ void table_matrix(const float4* tab, int n_theta, T mu, T P[6]) {
-    const T c = mu > T(1) ? T(1) : (mu < T(-1) ? T(-1) : mu);
-    const T x = t_acos(c) * T(0.31830988618379067) * T(n_theta - 1);
-    int j = (int)floor(x);
-    j = j > n_theta - 2 ? n_theta - 2 : (j < 0 ? 0 : j);
-    const T f = x - T(j), g = T(1) - f;
-    const float4 a0 = tab[2 * j], a1 = tab[2 * j + 1], b0 = tab[2 * j + 2], b1 = tab[2 * j + 3];
-    P[0] = g * T(a0.x) + f * T(b0.x);
-    P[1] = g * T(a0.y) + f * T(b0.y);
-    P[2] = g * T(a0.z) + f * T(b0.z);
-    P[3] = g * T(a0.w) + f * T(b0.w);
-    P[4] = g * T(a1.x) + f * T(b1.x);
-    P[5] = g * T(a1.y) + f * T(b1.y);
-}
 
 template <typename T>
 __device__ __forceinline__ T group_sum(unsigned mask, unsigned peers, T v, unsigned gmax) {
@@ -143,31 +82,6 @@ __device__ __forceinline__ T group_sum(unsigned mask, unsigned peers, T v, unsig
     return acc;
 }
 
-// Packet state, held in registers for the packet's lifetime (scalar fields only,
-// so that nothing is indexed at run time and nothing lands in local memory).
-template <typename T> struct Packet {
-    T px, py, pz, nx, ny, nz;
-    T X0, X1, X2, X3;
-    T I_birth, e_abs, e_gain;
-    double tau;  // remaining scattering optical depth (FP64 running sum)
-    long long pid;
-    const JobDev* job;  // batched launches: the packet's job
-    unsigned events, n_seg, n_sca, n_tally, n_abs, trials;
-    int ix, iy, iz, src;
-    float4 cq, cr;  // record of the current cell: q_B and (kappa_abs, kappa_sca, B, 0)
-};
-
-// Launch totals of one block (shared memory), folded in once per packet.
-struct BlockTotals {
-    double e[6];               // emitted, escaped, absorbed, roulette lost, roulette gain, capped
-    unsigned long long n[10];  // events, segments, scatterings, emitted, escaped, killed, capped,
-                               // trials, tally segments, absorbing segments
-    unsigned status;
-};
-
-template <typename T> __device__ __forceinline__ T pick(float f, double d);
-template <> __device__ __forceinline__ float pick<float>(float f, double) { return f; }
-template <> __device__ __forceinline__ double pick<double>(float, double d) { return d; }
 
 // Model-dependent data a packet reads: for a single-model launch the kernel
 // parameters and the tables staged in shared memory; for a batched launch the
@@ -230,21 +144,6 @@ __device__ __forceinline__ JobRef<T, B> job_of(const TransportParams& P, const S
         return JobRef<T, false>{P, sm.kext, sm.mix};
 }
 
-// Widening of an FP32 value to FP64 with integer operations only (the FP64 pipe of
-// GB300 is narrow): exact for normal numbers, infinities and NaN; FP32 subnormals
-// (|x| < 1.2e-38) become signed zero.
-__device__ __forceinline__ double widen(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = u & 0x7f800000u;
-    const unsigned sign = u & 0x80000000u;
-    // exponent and mantissa moved into the double's fields, exponent rebased by 1023 - 127
-    unsigned hi = sign | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
-    hi = e == 0x7f800000u ? (sign | 0x7ff00000u | ((u & 0x007fffffu) >> 3)) : hi;
-    hi = e == 0u ? sign : hi;
-    const unsigned lo = e == 0u ? 0u : (u << 29);
-    return __hiloint2double((int)hi, (int)lo);
-}
-__device__ __forceinline__ double widen(double d) { return d; }
 
 template <typename J>
 __device__ __forceinline__ void load_cell(const J& job, int ix, int iy, int iz, float4& q, float4& r) {
@@ -253,50 +152,6 @@ __device__ __forceinline__ void load_cell(const J& job, int ix, int iy, int iz, 
     r = __ldg(&job.cells()[2 * c + 1]);
 }
 
-// Packet end: optional trace record, then the packet's totals into the block's.
-template <typename T>
-__device__ void finish(const TransportParams& P, const Packet<T>& pk, int flag, BlockTotals& bt) {
-    atomicAdd(&bt.e[0], (double)pk.I_birth);
-    atomicAdd(&bt.e[2], (double)pk.e_abs);
-    if (pk.e_gain != T(0)) atomicAdd(&bt.e[4], (double)pk.e_gain);
-    if (flag == 1) {
-        atomicAdd(&bt.e[1], (double)pk.X0);
-        atomicAdd(&bt.n[4], 1ull);
-    } else if (flag == 2) {
-        atomicAdd(&bt.e[3], (double)pk.X0);
-        atomicAdd(&bt.n[5], 1ull);
-    } else {
-        atomicAdd(&bt.e[5], (double)pk.X0);
-        atomicAdd(&bt.n[6], 1ull);
-        atomicOr(&bt.status, flag == 3 ? (unsigned)MCRT_STATUS_EVENT_CAP : (unsigned)MCRT_STATUS_TRIAL_CAP);
-    }
-    atomicAdd(&bt.n[0], (unsigned long long)pk.events);
-    atomicAdd(&bt.n[1], (unsigned long long)pk.n_seg);
-    atomicAdd(&bt.n[2], (unsigned long long)pk.n_sca);
-    atomicAdd(&bt.n[3], 1ull);
-    atomicAdd(&bt.n[7], (unsigned long long)pk.trials);
-    atomicAdd(&bt.n[8], (unsigned long long)pk.n_tally);
-    atomicAdd(&bt.n[9], (unsigned long long)pk.n_abs);
-    if (P.trace && pk.pid < P.n_trace) {
-        double* tr = P.trace + pk.pid * 16;
-        tr[0] = pk.X0;
-        tr[1] = pk.X1;
-        tr[2] = pk.X2;
-        tr[3] = pk.X3;
-        tr[4] = pk.px;
-        tr[5] = pk.py;
-        tr[6] = pk.pz;
-        tr[7] = pk.nx;
-        tr[8] = pk.ny;
-        tr[9] = pk.nz;
-        tr[10] = (double)pk.n_sca;
-        tr[11] = (double)pk.n_seg;
-        tr[12] = (double)flag;
-        tr[13] = (double)pk.I_birth;
-        tr[14] = (double)pk.src;
-        tr[15] = (double)pk.events;
-    }
-}
 
 // First cell whose cumulative emission weight exceeds `target`: a guide table over
 // equal steps of the total narrows the search, and the answer is checked against
@@ -348,6 +203,7 @@ __device__ bool emit(const TransportParams& P, const JobRef<T, B>& job, long lon
     const Draw4<T> u1 = draw4<T>(pid, 0u, 1u, P.seed, job.stream());
     pk.pid = pid;
     pk.src = s;
+    pk.s_flight = flight_size(job.t(), u1.d);
     pk.events = 1;
     pk.n_seg = pk.n_sca = pk.n_tally = pk.n_abs = pk.trials = 0;
     pk.e_abs = pk.e_gain = T(0);
@@ -552,7 +408,37 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             if (gmax > 1u) dI = group_sum(actA, group, dI, gmax);
             if (lane == leader && dI != T(0)) atomicAdd(&job.absorbed()[c32], widen(dI));
         }
-        if (want_S) {
+        bool queued = false;
+        if constexpr (SCAT == kScatSurrogate) {
+            if (want_S) {
+                // the segment waits for the network: one 64-byte record per lane, the
+                // warp's records in consecutive slots; a warp that would run past the
+                // queue's end writes empty records and tallies with the tables below
+                T Wl1 = Wg[1], Wl2 = Wg[2];  // path integral in the packet's basis
+                rotate_qu(Wl1, Wl2, c2, -s2);
+                const int lead = __ffs(actS) - 1;
+                const unsigned cnt = (unsigned)__popc(actS);
+                unsigned long long base = 0;
+                if (lane == lead) base = atomicAdd(&P.sur.ctl->n_records, (unsigned long long)cnt);
+                base = __shfl_sync(actS, base, lead);
+                const unsigned long long idx = base + (unsigned)__popc(actS & ((1u << lane) - 1u));
+                queued = base + cnt <= P.sur.rec_cap;
+                if (idx < P.sur.rec_cap) {
+                    float4* r = P.sur.records + idx * kRecordF4;
+                    if (queued) {
+                        r[0] = make_float4((float)n.x, (float)n.y, (float)n.z, (float)pk.s_flight);
+                        r[1] = make_float4((float)Wg[0], (float)Wl1, (float)Wl2, (float)Wg[3]);
+                        r[2] = pk.cq;
+                        r[3] = make_float4(__uint_as_float(c32), 0.f, 0.f, 0.f);
+                        pk.n_tally++;
+                    } else {
+                        r[3] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, 0.f);
+                    }
+                }
+                if (!queued && lane == lead) atomicAdd(&P.sur.ctl->cnt[kCntOverflow], (unsigned long long)cnt);
+            }
+        }
+        if (want_S && !queued) {
             rotate_qu(Wg[1], Wg[2], c2, -s2);
             const unsigned gmax = __reduce_max_sync(actS, (unsigned)__popc(group));
             pk.n_tally++;
@@ -624,6 +510,17 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     pk.pz += ell * pk.nz;
     pk.n_sca++;
     pk.events++;
+    if constexpr (SCAT == kScatSurrogate) {
+        // the scattering is done by the network's kernel; the packet waits in the
+        // suspend buffer, whose capacity is the launch's number of work items
+        cg::coalesced_group grp = cg::coalesced_threads();
+        unsigned long long base = 0;
+        if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->n_suspend, (unsigned long long)grp.size());
+        base = grp.shfl(base, 0);
+        store_state(P.sur.suspend + (base + grp.thread_rank()) * kStateF4, pk);
+        alive = false;
+        return;
+    }
     const Draw4<T> us = draw4<T>(pk.pid, pk.n_sca, 0u, P.seed, job.stream());
     if (P.roulette_thr > 0.0 && (double)pk.X0 < P.roulette_thr * (double)pk.I_birth) {
         if ((double)us.b < P.roulette_surv) {
@@ -740,7 +637,7 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
     float4* s_kext = reinterpret_cast<float4*>(smem_raw);
     const int n_k = B ? 0 : P.t.n_ktheta;
     float4* s_mix = s_kext + n_k;
-    const int n_mix = (!B && SCAT == MCRT_SCAT_TABLE) ? 2 * P.t.n_theta : 0;
+    const int n_mix = (!B && SCAT != MCRT_SCAT_RAYLEIGH) ? 2 * P.t.n_theta : 0;
     T* s_cam = reinterpret_cast<T*>(s_mix + n_mix);
     const int cam_bytes = 12 * P.n_cam * (int)sizeof(T);
     double* s_stage = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(s_cam) + cam_bytes);
@@ -761,9 +658,36 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
     pk.job = nullptr;
     bool alive = false, pool_done = false;
     const unsigned long long t0 = global_ns();
+    // surrogate path: packets resumed after their scattering, then new packets
+    unsigned long long w_resume = 0, w_new = 0, w_next = 0;
+    if constexpr (SCAT == kScatSurrogate) {
+        w_resume = P.sur.ctl->n_resume;
+        w_new = P.sur.ctl->n_new;
+        w_next = P.sur.ctl->next_pid;
+    }
 
     for (;;) {
-        if (!alive && !pool_done) {
+        if constexpr (SCAT == kScatSurrogate) {
+            if (!alive && !pool_done) {
+                cg::coalesced_group grp = cg::coalesced_threads();
+                unsigned long long base = 0;
+                if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->claim, (unsigned long long)grp.size());
+                base = grp.shfl(base, 0);
+                const unsigned long long idx = base + grp.thread_rank();
+                if (idx < w_resume) {
+                    if constexpr (sizeof(T) == 4) {
+                        load_state(P.sur.resume + idx * kStateF4, pk);
+                        load_cell(JobRef<T, false>{P, sm.kext, sm.mix}, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
+                        alive = true;
+                    }
+                } else if (idx - w_resume < w_new) {
+                    const long long pid = P.pid_begin + (long long)(w_next + (idx - w_resume));
+                    alive = emit<T, false>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
+                } else {
+                    pool_done = true;
+                }
+            }
+        } else if (!alive && !pool_done) {
             cg::coalesced_group grp = cg::coalesced_threads();
             unsigned long long base = 0;
             if (grp.thread_rank() == 0) base = atomicAdd(P.counter, (unsigned long long)grp.size());
@@ -833,9 +757,11 @@ const void* transport_kernel(int precision, int model, bool batch) {
                  : (const void*)k_transport<float, MCRT_SCAT_RAYLEIGH, false>;
 }
 
+const void* transport_kernel_surrogate() { return (const void*)k_transport<float, kScatSurrogate, false>; }
+
 int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem) {
     int nb = 0;
-    const void* k = transport_kernel(precision, model, batch);
+    const void* k = model == kScatSurrogate ? transport_kernel_surrogate() : transport_kernel(precision, model, batch);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
@@ -843,7 +769,7 @@ int transport_max_blocks_per_sm(int precision, int model, bool batch, int block,
 
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s) {
     const size_t smem = transport_smem_bytes(p, precision, block);
-    const void* k = transport_kernel(precision, p.t.model, p.jobs != nullptr);
+    const void* k = p.sur.ctl ? transport_kernel_surrogate() : transport_kernel(precision, p.t.model, p.jobs != nullptr);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

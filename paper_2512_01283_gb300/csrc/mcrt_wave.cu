@@ -1,0 +1,529 @@
+// mcrt_wave.cu -- the surrogate path: step 1 of the two-step scheme (Sec. 2.2-2.3)
+// with the grain optics of Sec. 2.2 taken from the network of mcrt_mlp.cu instead of
+// the tables.
+//
+// The network is a dense contraction, so it runs where the rows are dense: the
+// transport kernel (k_transport, surrogate instantiation) moves every packet in
+// flight to its next scattering, applies extinction, and leaves one 64-byte record
+// per tallying segment (direction, flight size, path integral, grain quaternion,
+// cell); at the scattering the packet itself waits in a 128-byte slot.  Then
+//  - k_sur_tally evaluates the network for every (record, camera) row, 16 rows per
+//    warp through mcrt_mlp_infer.cuh, and adds Z W to the FP64 source tally with
+//    TMA bulk reductions;
+//  - k_sur_scatter runs the rejection sampling of the waiting packets, each warp
+//    evaluating up to 16 trials at once (trials of the same packet in order, the
+//    first accepted one wins, which is exactly the sequential rule);
+// and the survivors resume in the next transport launch, with new packets filling
+// the rest of the round's capacity.  Rounds repeat until no packet is left.
+#include <cooperative_groups.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "mcrt_device.cuh"
+#include "mcrt_internal.h"
+#include "mcrt_mlp_infer.cuh"
+#include "mcrt_packet.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace mcrt {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWaveBlock = 384;  // 12 warps per SM share one copy of the network
+
+struct TallyWarp {
+    __nv_bfloat16 in[16 * mlp::kLd0];
+    float out[16 * mlp::kOutLd];
+    double stage[16 * 4];  // Stokes rows of the tile's records, source of the bulk reductions
+};
+struct ScatWarp {
+    __nv_bfloat16 in[16 * mlp::kLd0];
+    float out[16 * mlp::kOutLd];
+};
+static_assert(sizeof(TallyWarp) % 16 == 0 && sizeof(ScatWarp) % 16 == 0, "16-byte aligned tiles");
+constexpr size_t kCamBytes = kMaxCams * 12 * sizeof(float);
+constexpr size_t kTallySmem = mlp::kImgBytes + kCamBytes + (kWaveBlock / 32) * sizeof(TallyWarp);
+constexpr size_t kScatSmem = mlp::kImgBytes + (kWaveBlock / 32) * sizeof(ScatWarp);
+
+// Realizability of a network matrix (outputs: ln M11, then M_rc / M11 row-major
+// without (0,0)): M11 = e^{y0} > 0, and neither a polarized input nor an unpolarized
+// one may give more polarization than intensity, |row 1| <= M11 and |column 1| <=
+// M11.  Matrices within 5% of that boundary (in the squared norms) are scaled back
+// onto it -- fully polarizing directions sit exactly there and the network lands on
+// either side -- and the rest fail.  m receives the 16 ratios (m[0] = 1).
+__device__ __forceinline__ bool realizable(const float* y, float m[16]) {
+    m[0] = 1.f;
+#pragma unroll
+    for (int k = 1; k < 16; ++k) m[k] = y[k];
+    const float r = m[1] * m[1] + m[2] * m[2] + m[3] * m[3];
+    const float c = m[4] * m[4] + m[8] * m[8] + m[12] * m[12];
+    if (!(fabsf(y[0]) < 80.f) || !(r <= 1.05f) || !(c <= 1.05f)) return false;
+    if (r > 1.f) {
+        const float f = rsqrtf(r);
+        m[1] *= f;
+        m[2] *= f;
+        m[3] *= f;
+    }
+    if (c > 1.f) {
+        const float f = rsqrtf(c);
+        m[4] *= f;
+        m[8] *= f;
+        m[12] *= f;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool map_says_fallback(const SurrogateDev& s, const V3<float>& a, const V3<float>& b,
+                                                  float size) {
+    const int idx = mlp::errmap_index(a.z, b.z, atan2f(b.y, b.x) - atan2f(a.y, a.x), size);
+    return !(__ldg(&s.err_map[idx]) <= s.bound);
+}
+
+// Round set-up: new packets taken by the previous round are counted, the packets
+// resumed by the scattering kernel become this round's resume list, and new packets
+// fill the capacity left.
+__global__ void k_wave_begin(WaveCtl* c, unsigned long long total, unsigned long long cap) {
+    c->next_pid += c->n_new;
+    c->n_resume = c->n_resume_next;
+    c->n_resume_next = 0;
+    const unsigned long long left = total > c->next_pid ? total - c->next_pid : 0;
+    const unsigned long long room = cap > c->n_resume ? cap - c->n_resume : 0;
+    c->n_new = left < room ? left : room;
+    c->claim = 0;
+    c->n_suspend = 0;
+    c->n_records = 0;
+    c->cnt[kCntIterations] += 1;
+}
+
+__device__ __forceinline__ void flush_counters(WaveCtl* ctl, unsigned long long* s_cnt, const unsigned long long* v,
+                                               int n, const int* which) {
+    for (int k = 0; k < n; ++k)
+        if (v[k]) atomicAdd(&s_cnt[k], v[k]);
+    __syncthreads();
+    if (threadIdx.x < n && s_cnt[threadIdx.x]) atomicAdd(&ctl->cnt[which[threadIdx.x]], s_cnt[threadIdx.x]);
+}
+
+// Source tally of the queued segments: row (record, camera) -> the network at
+// (n_GF, Omega_c,GF, s) gives the scattering-plane matrix M -> rotate W into the
+// plane of n -> Omega_c, apply M, rotate into the camera basis -> S[cell][camera].
+// The rows of one record are consecutive (cameras padded to 1, 2, 4, 8 or 16), so
+// a record's cameras are one contiguous FP64 bulk reduction.
+__global__ void __launch_bounds__(kWaveBlock, 1) k_sur_tally(const __grid_constant__ TransportParams P) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ unsigned long long s_cnt[3];
+    mlp::load_image(sm, P.sur.image);
+    float* s_cam = reinterpret_cast<float*>(sm + mlp::kImgBytes);
+    for (int i = threadIdx.x; i < 12 * P.n_cam; i += blockDim.x) {
+        const CameraDev& cd = P.cam[i / 12];
+        const int e = i % 12, v = e / 4, w = e % 4;
+        s_cam[i] = w == 3 ? 0.f : (float)(v == 0 ? cd.dir[w] : (v == 1 ? cd.th[w] : cd.ph[w]));
+    }
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    TallyWarp& tw = reinterpret_cast<TallyWarp*>(sm + mlp::kImgBytes + kCamBytes)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const unsigned long long nreq = P.sur.ctl->n_records;
+    const unsigned long long nrec = nreq < P.sur.rec_cap ? nreq : P.sur.rec_cap;
+    const int ncam = P.n_cam;
+    const int ncp = ncam <= 1 ? 1 : (ncam <= 2 ? 2 : (ncam <= 4 ? 4 : (ncam <= 8 ? 8 : 16)));
+    const int per_tile = 16 / ncp;
+    const unsigned long long ntile = (nrec + per_tile - 1) / per_tile;
+    unsigned long long c_rows = 0, c_map = 0, c_real = 0;
+    for (unsigned long long tile = (unsigned long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntile;
+         tile += (unsigned long long)gridDim.x * wpb) {
+        bulk_wait_read();  // this lane's reductions of the previous tile have read the staging rows
+        __syncwarp();
+        const int cam = lane % ncp;
+        bool valid = false, fb = false;
+        unsigned cell = 0;
+        float s = 0.f, W[4] = {0.f, 0.f, 0.f, 0.f}, mu = 1.f;
+        PlaneRot<float> pr{1.f, 0.f, 1.f, 0.f};
+        if (lane < 16) {
+            float u[mlp::kIn] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const unsigned long long rec = tile * per_tile + (unsigned)(lane / ncp);
+            if (rec < nrec) {
+                const float4* r = P.sur.records + rec * kRecordF4;
+                cell = __float_as_uint(r[3].x);
+                valid = cam < ncam && cell != 0xffffffffu;
+                if (valid) {
+                    const float4 r0 = r[0], r1 = r[1], q = r[2];
+                    const V3<float> n{r0.x, r0.y, r0.z};
+                    s = r0.w;
+                    W[0] = r1.x;
+                    W[1] = r1.y;
+                    W[2] = r1.z;
+                    W[3] = r1.w;
+                    V3<float> th, ph, Om, thc, phc;
+                    stokes_basis(n, th, ph);
+                    load_camera(s_cam + 12 * cam, Om, thc, phc);
+                    // scattering plane of n -> Omega_c, in the lab frame (as the table path)
+                    pr = plane_rotation(n, th, ph, Om, thc, phc);
+                    mu = dot(n, Om);
+                    // the network sees both directions in the grain frame
+                    const V3<float> nGF = quat_to_grain(q, n), cGF = quat_to_grain(q, Om);
+                    u[0] = nGF.x;
+                    u[1] = nGF.y;
+                    u[2] = nGF.z;
+                    u[3] = cGF.x;
+                    u[4] = cGF.y;
+                    u[5] = cGF.z;
+                    u[6] = s;
+                    fb = map_says_fallback(P.sur, nGF, cGF, s);
+                }
+            }
+            mlp::store_input_row(tw.in + lane * mlp::kLd0, u);
+        }
+        __syncwarp();
+        mlp::warp_mlp16(sm, tw.in, tw.out, lane);
+        __syncwarp();
+        if (valid) {
+            const float* y = tw.out + lane * mlp::kOutLd;
+            float Y[4], m[16];
+            const bool real = realizable(y, m);
+            if (!fb && real) {
+                apply_plane_full(pr, __expf(y[0]), m, W, Y);
+            } else {
+                float Pm[6];
+                table_at(P.t, s, mu, Pm);
+                apply_plane(pr, Pm, W, Y);
+                if (fb)
+                    ++c_map;
+                else
+                    ++c_real;
+            }
+            ++c_rows;
+            double2* d2 = reinterpret_cast<double2*>(tw.stage + lane * 4);
+            d2[0] = make_double2((double)Y[0], (double)Y[1]);
+            d2[1] = make_double2((double)Y[2], (double)Y[3]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncwarp();
+        if (valid && cam == 0)
+            bulk_reduce_add_f64(P.S + (size_t)cell * (size_t)ncam * 4, tw.stage + lane * 4, (unsigned)ncam * 32u);
+    }
+    bulk_wait_all();
+    const unsigned long long v[3] = {c_rows, c_map, c_real};
+    const int which[3] = {kCntTallyRows, kCntFallbackMap, kCntFallbackReal};
+    flush_counters(P.sur.ctl, s_cnt, v, 3, which);
+}
+
+// Scattering of the waiting packets (Sec. 2.2 rejection sampling): lanes 0-15 own
+// one packet each; every round the unresolved packets share the warp's 16 rows,
+// packet k taking trials t_k .. t_k + T - 1 (T = 16 / unresolved) with the same
+// Philox counters, proposals and envelope as the table path; the network gives
+// the target (Z X)_0 of each trial.
+__global__ void __launch_bounds__(kWaveBlock, 1) k_sur_scatter(const __grid_constant__ TransportParams P) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ BlockTotals bt;
+    __shared__ unsigned long long s_cnt[4];
+    mlp::load_image(sm, P.sur.image);
+    if (threadIdx.x < 6) bt.e[threadIdx.x] = 0.0;
+    if (threadIdx.x < 10) bt.n[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) bt.status = 0u;
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    ScatWarp& sw = reinterpret_cast<ScatWarp*>(sm + mlp::kImgBytes)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const TablesDev& tabs = P.t;
+    const int nint = tabs.n_theta - 1;
+    const float widen_env = 1.f + P.sur.env_margin;
+    const unsigned long long nsus = P.sur.ctl->n_suspend;
+    const unsigned long long nbatch = (nsus + 15) / 16;
+    unsigned long long c_rows = 0, c_map = 0, c_real = 0, c_miss = 0;
+    for (unsigned long long batch = (unsigned long long)blockIdx.x * wpb + (threadIdx.x >> 5); batch < nbatch;
+         batch += (unsigned long long)gridDim.x * wpb) {
+        Packet<float> pk;
+        pk.X0 = pk.X1 = pk.X2 = pk.X3 = 0.f;
+        pk.pid = 0;
+        pk.n_sca = 0;
+        bool live = false;
+        float us_a = 0.5f, us_d = 0.5f, sk = 0.f;
+        int bin = 0;
+        float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+        V3<float> n{0.f, 0.f, 1.f}, th{1.f, 0.f, 0.f}, ph{0.f, 1.f, 0.f}, nGF{0.f, 0.f, 1.f};
+        const unsigned long long i = batch * 16 + (unsigned)lane;
+        if (lane < 16 && i < nsus) {
+            load_state(P.sur.suspend + i * kStateF4, pk);
+            const Draw4<float> us = draw4<float>(pk.pid, pk.n_sca, 0u, P.seed, P.stream);
+            us_a = us.a;
+            us_d = us.d;
+            live = true;
+            if (P.roulette_thr > 0.0 && (double)pk.X0 < P.roulette_thr * (double)pk.I_birth) {
+                if ((double)us.b < P.roulette_surv) {
+                    const float gmul = (float)(1.0 / P.roulette_surv);
+                    pk.e_gain += pk.X0 * (gmul - 1.f);
+                    pk.X0 *= gmul;
+                    pk.X1 *= gmul;
+                    pk.X2 *= gmul;
+                    pk.X3 *= gmul;
+                } else {
+                    finish(P, pk, 2, bt);
+                    live = false;
+                }
+            }
+            if (live) {
+                bin = tabs.n_bins - 1;
+                for (int k = 0; k < tabs.n_bins; ++k)
+                    if (us.c < (float)tabs.bin_cdf[k]) {
+                        bin = k;
+                        break;
+                    }
+                sk = tabs.n_bins > 1 ? -1.f + 2.f * (float)bin / (float)(tabs.n_bins - 1) : 0.f;
+                const long long c = ((long long)pk.iz * P.g.n[1] + pk.iy) * P.g.n[0] + pk.ix;
+                q = __ldg(&P.g.cells[2 * c]);
+                n = V3<float>{pk.nx, pk.ny, pk.nz};
+                stokes_basis(n, th, ph);
+                nGF = quat_to_grain(q, n);
+            }
+        }
+        const unsigned pid_lo = (unsigned)((unsigned long long)pk.pid & 0xffffffffull);
+        const unsigned pid_hi = (unsigned)((unsigned long long)pk.pid >> 32);
+        unsigned U = __ballot_sync(kFull, live);
+        int t_next = 0;
+        bool resolved = false;
+        V3<float> n2s{0.f, 0.f, 1.f};
+        float Ys[4] = {0.f, 0.f, 0.f, 0.f};
+        while (U) {
+            const int nu = __popc(U), T = 16 / nu;
+            int owner = 0, j = 0;
+            bool rowv = false;
+            if (lane < 16) {
+                const int slot = lane / T;
+                if (slot < nu) {
+                    owner = (int)__fns(U, 0u, slot + 1);
+                    j = lane % T;
+                    rowv = true;
+                }
+            }
+            // the owning packet's data
+            const float onx = __shfl_sync(kFull, n.x, owner), ony = __shfl_sync(kFull, n.y, owner),
+                        onz = __shfl_sync(kFull, n.z, owner);
+            const float otx = __shfl_sync(kFull, th.x, owner), oty = __shfl_sync(kFull, th.y, owner),
+                        otz = __shfl_sync(kFull, th.z, owner);
+            const float opx = __shfl_sync(kFull, ph.x, owner), opy = __shfl_sync(kFull, ph.y, owner),
+                        opz = __shfl_sync(kFull, ph.z, owner);
+            const float4 oq = make_float4(__shfl_sync(kFull, q.x, owner), __shfl_sync(kFull, q.y, owner),
+                                          __shfl_sync(kFull, q.z, owner), __shfl_sync(kFull, q.w, owner));
+            const V3<float> og{__shfl_sync(kFull, nGF.x, owner), __shfl_sync(kFull, nGF.y, owner),
+                               __shfl_sync(kFull, nGF.z, owner)};
+            const float oX[4] = {__shfl_sync(kFull, pk.X0, owner), __shfl_sync(kFull, pk.X1, owner),
+                                 __shfl_sync(kFull, pk.X2, owner), __shfl_sync(kFull, pk.X3, owner)};
+            const float oX0 = oX[0];
+            const int obin = __shfl_sync(kFull, bin, owner);
+            const float osk = __shfl_sync(kFull, sk, owner);
+            const unsigned opl = __shfl_sync(kFull, pid_lo, owner), oph = __shfl_sync(kFull, pid_hi, owner);
+            const unsigned onsca = __shfl_sync(kFull, pk.n_sca, owner);
+            const int ot = __shfl_sync(kFull, t_next, owner) + j;
+            rowv = rowv && ot < P.max_trials;
+            float bound = 0.f, bmax = 0.f, mu = 1.f;
+            V3<float> n2{0.f, 0.f, 1.f};
+            PlaneRot<float> pr{1.f, 0.f, 1.f, 0.f};
+            bool fb = false;
+            if (lane < 16) {
+                float u[mlp::kIn] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (rowv) {
+                    const long long opid = (long long)(((unsigned long long)oph << 32) | (unsigned long long)opl);
+                    const Draw4<float> ut = draw4<float>(opid, onsca, 1u + (unsigned)ot, P.seed, P.stream);
+                    // interval of the piecewise-constant envelope of bin obin, then the
+                    // angle inside it and the azimuth (as the table path)
+                    const double* cdf = tabs.env_cdf + (size_t)obin * nint;
+                    int lo = 0, hi = nint - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (ut.a < (float)cdf[mid])
+                            hi = mid;
+                        else
+                            lo = mid + 1;
+                    }
+                    float s0, c0, s1, c1;
+                    sincospif((float)lo / (float)nint, &s0, &c0);
+                    sincospif((float)(lo + 1) / (float)nint, &s1, &c1);
+                    mu = c0 - ut.b * (c0 - c1);
+                    float sn = (1.f - mu) * (1.f + mu);
+                    sn = sn > 0.f ? sqrtf(sn) : 0.f;
+                    float sa, ca;
+                    sincospif(2.f * ut.c, &sa, &ca);
+                    n2 = V3<float>{mu * onx + sn * (ca * otx + sa * opx), mu * ony + sn * (ca * oty + sa * opy),
+                                   mu * onz + sn * (ca * otz + sa * opz)};
+                    bmax = 2.f * tabs.env[(size_t)obin * nint + lo] * oX0 * widen_env;
+                    bound = ut.d * bmax;
+                    V3<float> th2, ph2;
+                    stokes_basis(n2, th2, ph2);
+                    pr = plane_rotation(V3<float>{onx, ony, onz}, V3<float>{otx, oty, otz}, V3<float>{opx, opy, opz},
+                                        n2, th2, ph2);
+                    const V3<float> n2GF = quat_to_grain(oq, n2);
+                    u[0] = og.x;
+                    u[1] = og.y;
+                    u[2] = og.z;
+                    u[3] = n2GF.x;
+                    u[4] = n2GF.y;
+                    u[5] = n2GF.z;
+                    u[6] = osk;
+                    fb = map_says_fallback(P.sur, og, n2GF, osk);
+                }
+                mlp::store_input_row(sw.in + lane * mlp::kLd0, u);
+            }
+            __syncwarp();
+            mlp::warp_mlp16(sm, sw.in, sw.out, lane);
+            __syncwarp();
+            bool acc = false;
+            float Yr[4] = {0.f, 0.f, 0.f, 0.f};
+            if (rowv) {
+                const float* y = sw.out + lane * mlp::kOutLd;
+                float m[16];
+                const bool real = realizable(y, m);
+                if (!fb && real) {
+                    apply_plane_full(pr, __expf(y[0]), m, oX, Yr);
+                } else {
+                    float Pm[6];
+                    table_at(tabs, osk, mu, Pm);
+                    apply_plane(pr, Pm, oX, Yr);
+                    if (fb)
+                        ++c_map;
+                    else
+                        ++c_real;
+                }
+                ++c_rows;
+                if (Yr[0] > bmax) ++c_miss;
+                acc = bound < Yr[0];
+            }
+            __syncwarp();
+            // each owner takes its first accepted row, in trial order
+            const unsigned A = __ballot_sync(kFull, rowv && acc);
+            const unsigned V = __ballot_sync(kFull, rowv);
+            const bool mine = lane < 16 && ((U >> lane) & 1u);
+            int src = lane, examined = 0;
+            bool got = false;
+            if (mine) {
+                const int sp = __popc(U & ((1u << lane) - 1u));
+                const unsigned m = ((1u << T) - 1u) << (sp * T);
+                const unsigned a = A & m;
+                if (a) {
+                    src = __ffs(a) - 1;
+                    got = true;
+                    examined = src - sp * T + 1;
+                } else {
+                    examined = __popc(V & m);
+                }
+            }
+            float g[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) g[e] = __shfl_sync(kFull, Yr[e], src);
+            const float gx = __shfl_sync(kFull, n2.x, src), gy = __shfl_sync(kFull, n2.y, src),
+                        gz = __shfl_sync(kFull, n2.z, src);
+            if (mine) {
+                pk.trials += (unsigned)examined;
+                t_next += T;
+                if (got) {
+                    resolved = true;
+                    for (int e = 0; e < 4; ++e) Ys[e] = g[e];
+                    n2s = V3<float>{gx, gy, gz};
+                } else if (t_next >= P.max_trials) {
+                    finish(P, pk, 4, bt);
+                    live = false;
+                }
+            }
+            U = __ballot_sync(kFull, live && !resolved);
+        }
+        if (resolved) {
+            // Ys is in the lab basis of the new direction; the intensity is kept
+            const float norm = pk.X0 / Ys[0];
+            pk.X0 = Ys[0] * norm;
+            pk.X1 = Ys[1] * norm;
+            pk.X2 = Ys[2] * norm;
+            pk.X3 = Ys[3] * norm;
+            pk.nx = n2s.x;
+            pk.ny = n2s.y;
+            pk.nz = n2s.z;
+            pk.tau = -(double)logf(us_a);
+            pk.s_flight = flight_size(tabs, us_d);
+            cg::coalesced_group grp = cg::coalesced_threads();
+            unsigned long long base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->n_resume_next, (unsigned long long)grp.size());
+            base = grp.shfl(base, 0);
+            store_state(P.sur.resume + (base + grp.thread_rank()) * kStateF4, pk);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        if (bt.e[threadIdx.x] != 0.0) atomicAdd(&P.stats[threadIdx.x], bt.e[threadIdx.x]);
+    } else if (threadIdx.x < 16) {
+        unsigned long long* c = reinterpret_cast<unsigned long long*>(P.stats + 6);
+        if (bt.n[threadIdx.x - 6]) atomicAdd(&c[threadIdx.x - 6], bt.n[threadIdx.x - 6]);
+    } else if (threadIdx.x == 16 && bt.status) {
+        atomicOr(P.status, bt.status);
+    }
+    const unsigned long long v[4] = {c_rows, c_map, c_real, c_miss};
+    const int which[4] = {kCntScatRows, kCntFallbackMap, kCntFallbackReal, kCntEnvelopeMiss};
+    flush_counters(P.sur.ctl, s_cnt, v, 4, which);
+}
+
+}  // namespace
+
+cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned long long cap, int* iterations,
+                                    float* ms_out, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_sur_tally, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallySmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sur_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatSmem);
+    if (e != cudaSuccess) return e;
+    const unsigned long long total = (unsigned long long)(p.pid_end - p.pid_begin);
+    const int block = 128;
+    const size_t tsmem = transport_smem_bytes(p, MCRT_FP32, block);
+    const int bps = transport_max_blocks_per_sm(MCRT_FP32, kScatSurrogate, false, block, tsmem);
+    const int tgrid = n_sm * bps;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.sur.ctl, 0, sizeof(WaveCtl), s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    unsigned long long C = cap;
+    // a packet advances by at least one event per round
+    const long long max_rounds = p.max_events + (long long)(total / 256) + 1000;
+    WaveCtl h{};
+    int it = 0;
+    for (; e == cudaSuccess; ++it) {
+        if (it >= max_rounds) {
+            e = cudaErrorUnknown;
+            break;
+        }
+        k_wave_begin<<<1, 1, 0, s>>>(p.sur.ctl, total, C);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_transport(p, MCRT_FP32, block, tgrid, s);
+        if (e == cudaSuccess) {
+            k_sur_tally<<<n_sm, kWaveBlock, kTallySmem, s>>>(p);
+            k_sur_scatter<<<n_sm, kWaveBlock, kScatSmem, s>>>(p);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, p.sur.ctl, sizeof(WaveCtl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        if (h.n_resume_next == 0 && h.next_pid + h.n_new >= total) {
+            ++it;
+            break;
+        }
+        // keep the next round's records within the queue: capacity from this
+        // round's records per work item, with a factor 2 of headroom
+        const unsigned long long items = h.n_resume + h.n_new;
+        if (items > 0 && h.n_records > 0) {
+            const double per = (double)h.n_records / (double)items;
+            double want = 0.5 * (double)p.sur.rec_cap / per;
+            if (want > (double)cap) want = (double)cap;
+            if (want < 1024.0) want = 1024.0;
+            C = (unsigned long long)want;
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (iterations) *iterations = it;
+    if (ms_out) *ms_out = ms;
+    return e;
+}
+
+}  // namespace mcrt

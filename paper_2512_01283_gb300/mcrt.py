@@ -48,12 +48,16 @@ class LaunchDesc(C.Structure):
                 ("roulette_threshold", C.c_double), ("roulette_survival", C.c_double),
                 ("max_events", C.c_int64), ("max_trials", C.c_int32), ("block_size", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("time_budget_s", C.c_double),
-                ("n_trace", C.c_int64), ("trace", C.c_void_p)]
+                ("n_trace", C.c_int64), ("trace", C.c_void_p), ("optics", C.c_int32)]
+
+OPTICS = {"tables": 0, "surrogate": 1}
 
 
 STAT_FIELDS = ["emitted_energy", "escaped_energy", "absorbed_energy", "roulette_lost", "roulette_gain", "cap_lost",
                "events", "segments", "scatterings", "emitted", "escaped", "roulette_killed", "cap_hits", "trials",
-               "kernel_ms", "status_bits", "tally_segments", "absorb_segments"]
+               "kernel_ms", "status_bits", "tally_segments", "absorb_segments",
+               "mlp_tally_rows", "mlp_scatter_rows", "mlp_fallback_map", "mlp_fallback_realizability",
+               "tally_overflow", "envelope_miss", "wave_iterations"]
 
 
 class Stats(C.Structure):
@@ -81,7 +85,8 @@ SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "m
            "mcrt_get_tallies", "mcrt_destroy", "mcrt_last_error", "mcrt_unit_eval", "mcrt_launch_packets_noalloc",
            "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_tune", "mcrt_batch_images", "mcrt_batch_destroy",
            "mcrt_surrogate_create", "mcrt_surrogate_train", "mcrt_surrogate_eval", "mcrt_surrogate_labels",
-           "mcrt_surrogate_grad", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy"]
+           "mcrt_surrogate_grad", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy",
+           "mcrt_surrogate_error_map", "mcrt_set_surrogate"]
 
 
 def lib():
@@ -118,6 +123,8 @@ def lib():
     L.mcrt_surrogate_param_count.argtypes = []
     L.mcrt_surrogate_param_count.restype = C.c_int64
     L.mcrt_surrogate_destroy.argtypes = [vp]
+    L.mcrt_surrogate_error_map.argtypes = [vp, i64, vp]
+    L.mcrt_set_surrogate.argtypes = [vp, vp, C.c_double]
     for name in SYMBOLS:
         if name not in ("mcrt_last_error", "mcrt_surrogate_param_count"):
             getattr(L, name).restype = C.c_int
@@ -201,6 +208,10 @@ class Model:
         _check(L.mcrt_image_stokes(self.h, int(camera), p), self.h)
         return out
 
+    def set_surrogate(self, sur: "Surrogate", bound=0.05):
+        """mcrt_set_surrogate: attach a trained network (launch with optics="surrogate")."""
+        _check(lib().mcrt_set_surrogate(self.h, sur.h, float(bound)), self.h)
+
     def tallies(self, n_cam: int):
         L = lib()
         S = np.zeros((self.ncell, max(1, n_cam), 4))
@@ -260,6 +271,7 @@ def make_desc(run: dict, precision="fp32", trace=None, n_trace=0, default_center
     d.block_size = int(kw.get("block_size", 0))
     d.blocks_per_sm = int(kw.get("blocks_per_sm", 0))
     d.time_budget_s = float(kw.get("time_budget_s", 0.0))
+    d.optics = OPTICS[kw.get("optics", "tables")]
     if trace is not None:
         p, k = _ptr(trace, np.float64)
         keep.append(k)
@@ -440,6 +452,13 @@ class Surrogate:
                                          C.c_void_p(w.ctypes.data) if w is not None else None,
                                          C.c_void_p(g.ctypes.data), C.byref(loss)))
         return loss.value, self.unflatten(g)
+
+    def error_map(self, n_samples=1 << 22):
+        """mcrt_surrogate_error_map: largest error per (cos theta_i, cos theta_s,
+        delta phi, s) cell, shape (8, 8, 8, 8)."""
+        m = np.zeros(4096, dtype=np.float32)
+        _check(lib().mcrt_surrogate_error_map(self.h, int(n_samples), C.c_void_p(m.ctypes.data)))
+        return m.reshape(8, 8, 8, 8)
 
     def get_params(self):
         p = np.zeros(self.n_params, dtype=np.float32)

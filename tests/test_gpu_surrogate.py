@@ -1,16 +1,21 @@
 """The MLP surrogate of the grain optics on the GPU: its labels, forward pass and
-gradients against the FP64 CPU reference (oracle/mlp_oracle.py), and training.
-Needs a GB300 (``-m gpu``).
+gradients against the FP64 CPU reference (oracle/mlp_oracle.py), training, the error
+map, the surrogate transport path, and what the network gains over a table of the
+same memory.  Needs a GB300 (``-m gpu``).
 
 Tolerances: labels are FP32 arithmetic on the same tables (1e-5 of the output
 scale); the forward pass runs BF16 activations with FP32 accumulation (2e-2 of the
-output scale against FP64 with the same BF16-rounded weights); gradients 5e-2
-relative in norm per layer (BF16 backward).
+output scale against FP64 with the same BF16-rounded weights and exact inputs: the
+network takes its inputs as BF16 high + low parts); gradients 5e-2 relative in norm
+per layer (BF16 backward).  Transport: the validation mode (every evaluation from
+the tables) follows the oracle's trajectories like the table path (99% of traces to
+1e-4); image totals are Monte-Carlo estimates compared within a few per cent.
 """
 import numpy as np
 import pytest
 
 from oracle import mlp_oracle as MO
+from oracle import oracle as O
 from paper_2512_01283_gb300 import build as B
 from paper_2512_01283_gb300 import mcrt as M
 from paper_2512_01283_gb300 import workloads as W
@@ -65,7 +70,7 @@ def test_forward_matches_reference(sur):
     layers = s.get_params()
     ref_params = [(bf16(W_), b_.astype(np.float64)) for W_, b_ in layers]
     u = inputs(512)
-    x = bf16(MO.pad_inputs(u))
+    x = MO.pad_inputs(u.astype(np.float64))
     # reference with BF16 rounding of the activations between layers, as on the GPU
     h = x
     for i, (W_, b_) in enumerate(ref_params):
@@ -86,7 +91,8 @@ def test_gradients_match_reference(sur):
     w = RNG.uniform(0.5, 2.0, size=20).astype(np.float32)
     loss, grads = s.grad(u, t, w)
     ref_params = [(bf16(W_), b_.astype(np.float64)) for W_, b_ in layers]
-    rloss, rgrads = MO.loss_and_grads(ref_params, bf16(MO.pad_inputs(u)), t.astype(np.float64), w.astype(np.float64))
+    rloss, rgrads = MO.loss_and_grads(ref_params, MO.pad_inputs(u.astype(np.float64)), t.astype(np.float64),
+                                      w.astype(np.float64))
     assert abs(loss - rloss) < 2e-2 * rloss
     for li, ((gW, gb), (rW, rb)) in enumerate(zip(grads, rgrads)):
         if li == 0:
@@ -107,3 +113,171 @@ def test_training_reduces_the_error(sur):
     assert hist[-20:].mean() < 0.2 * hist[:20].mean()
     after = np.sqrt(np.mean((s.eval(u) - lab) ** 2))
     assert after < 0.3 * before
+
+
+def test_error_map_bounds_fresh_samples(sur):
+    """The map holds the largest error per cell over 2^20 samples; errors of fresh
+    samples rarely exceed their cell's value."""
+    s, _ = sur
+    emap = s.error_map(1 << 20)
+    assert emap.shape == (8, 8, 8, 8) and np.all(np.isfinite(emap)) and np.all(emap >= 0)
+    u = inputs(4000)
+    y = s.eval(u).astype(np.float64)
+    lab = s.labels(u).astype(np.float64)
+    r = np.exp(y[:, 0:1] - lab[:, 0:1])
+    err = np.maximum(np.abs(r[:, 0] - 1), np.max(np.abs(r * y[:, 1:16] - lab[:, 1:16]), axis=1))
+    ni, ns, sz = u[:, 0:3], u[:, 3:6], u[:, 6]
+    dphi = np.mod(np.arctan2(ns[:, 1], ns[:, 0]) - np.arctan2(ni[:, 1], ni[:, 0]), 2 * np.pi)
+    b = lambda x, lo, w: np.clip(np.floor((x - lo) * w).astype(int), 0, 7)
+    cell = emap[b(ni[:, 2], -1, 4), b(ns[:, 2], -1, 4), b(dphi, 0, 4 / np.pi), b(sz, -1, 4)]
+    assert np.mean(err > cell * 1.0001 + 1e-6) < 0.05
+
+
+# ---------------------------------------------------------------------------------
+# the surrogate transport path
+# ---------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def disk_net():
+    """A network trained on the disk's tables (the same optics as W.disk) with 2e7
+    samples."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for -m gpu tests")
+    B.build()
+    model = W.disk(n=24)
+    m = M.Model(model)
+    s = M.Surrogate(m, seed=11)
+    hist = s.train(n_steps=9765, batch=2048, lr=3e-3)  # 2e7 samples
+    assert np.isfinite(hist).all()
+    yield model, s
+    s.close()
+    m.close()
+
+
+def run_model(model, run, optics="tables", sur=None, bound=0.05, n_trace=0):
+    m = M.Model(model)
+    if sur is not None:
+        m.set_surrogate(sur, bound)
+    tr = np.zeros((max(1, n_trace), 16))
+    st = M.launch(m, run, precision="fp32", trace=tr if n_trace else None, n_trace=n_trace, optics=optics)
+    imgs = []
+    for k, c in enumerate(run["cameras"]):
+        out = np.zeros((4, c["npix"][1], c["npix"][0]))
+        m.image(k, out)
+        imgs.append(out)
+    m.close()
+    return st, imgs, tr[:n_trace]
+
+
+def balance(st):
+    return (st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"]
+            + st["cap_lost"]) / st["emitted_energy"]
+
+
+def test_validation_mode_follows_the_oracle(disk_net):
+    """bound < 0: the surrogate path's kernels with every evaluation from the tables
+    (suspend / resume rounds, 16-row trial batches, tally records) reproduce the
+    oracle's packet trajectories; the tally samples one size bin per flight, so the
+    images agree with the oracle's within Monte-Carlo noise."""
+    model, s = disk_net
+    run = W.disk_run(n_packets=20_000, n_cam=4, npix=32)
+    st, imgs, tr = run_model(model, run, optics="surrogate", sur=s, bound=-1.0, n_trace=20_000)
+    o = O.transport(model, dict(run, n_trace=20_000, n_threads=8))
+    I = np.abs(o["trace"][:, 0:1]) + 1e-300
+    err = np.max(np.abs(tr[:, 0:4] - o["trace"][:, 0:4]) / I, axis=1)
+    same = (tr[:, 12] == o["trace"][:, 12]) & (tr[:, 10] == o["trace"][:, 10])
+    assert np.mean((err < 1e-4) & same) >= 0.99
+    assert st["mlp_fallback_map"] == st["mlp_tally_rows"] + st["mlp_scatter_rows"]
+    assert st["wave_iterations"] > 1 and st["tally_overflow"] == 0
+    assert abs(balance(st) - 1.0) < 1e-5
+    assert abs(st["events"] - o["stats"]["events"]) <= 1e-3 * o["stats"]["events"]
+    for k in range(4):
+        ref = O.image(model, dict(run, n_threads=8), o["S"], k)
+        assert abs(imgs[k][0].sum() - ref[0].sum()) < 0.05 * ref[0].sum(), k
+
+
+def test_surrogate_path_against_table_path(disk_net):
+    """Trained network, bound 0.05: energy is conserved exactly, the network serves
+    most evaluations, and the Stokes images agree with the table path's within the
+    network's error and Monte-Carlo noise."""
+    model, s = disk_net
+    run = W.disk_run(n_packets=40_000, n_cam=4, npix=32)
+    st_t, img_t, _ = run_model(model, run)
+    st_s, img_s, _ = run_model(model, run, optics="surrogate", sur=s, bound=0.05)
+    assert abs(balance(st_s) - 1.0) < 1e-5
+    rows = st_s["mlp_tally_rows"] + st_s["mlp_scatter_rows"]
+    assert rows > 0
+    assert (st_s["mlp_fallback_map"] + st_s["mlp_fallback_realizability"]) < 0.5 * rows
+    assert st_s["envelope_miss"] < 0.01 * st_s["mlp_scatter_rows"]
+    assert abs(st_s["events"] - st_t["events"]) < 0.05 * st_t["events"]
+    for k in range(4):
+        It = img_t[k][0].sum()
+        assert abs(img_s[k][0].sum() - It) < 0.05 * It, k
+        for e in (1, 2):
+            assert abs(img_s[k][e].sum() - img_t[k][e].sum()) < 0.02 * It, (k, e)
+
+
+def test_surrogate_launch_options_rejected(disk_net):
+    model, s = disk_net
+    run = W.disk_run(n_packets=1000, n_cam=1, npix=8)
+    m = M.Model(model)
+    with pytest.raises(M.McrtError) as e:
+        M.launch(m, run, optics="surrogate")
+    assert e.value.status == M.MCRT_E_STATE  # nothing attached
+    m.set_surrogate(s, 0.05)
+    with pytest.raises(M.McrtError) as e:
+        M.launch(m, run, precision="fp64", optics="surrogate")
+    assert e.value.status == M.MCRT_E_INVAL
+    with pytest.raises(M.McrtError) as e:
+        M.launch([m, m], run, optics="surrogate")
+    assert e.value.status == M.MCRT_E_INVAL
+    m.close()
+
+
+def test_network_beats_a_table_of_equal_memory(disk_net):
+    """What the network gains: for grain optics that depend on both directions in
+    the grain frame and on the size (five coordinates), a table of the network's
+    size (4 x 6 x 4 x 6 x 2 nodes of the same 20 FP32 outputs, 92 KB, multilinear)
+    is far less accurate than the network (117 KB), judged on fresh inputs against
+    the FP64 labels of the oracle."""
+    from scipy.interpolate import RegularGridInterpolator
+
+    model, s = disk_net
+    tabs = np.asarray(model["optics"]["mueller"], dtype=np.float64)
+    kext = np.asarray(model["optics"]["kext"], dtype=np.float64)
+    axes = [np.linspace(-1, 1, 4), np.linspace(0, 2 * np.pi, 7), np.linspace(-1, 1, 4),
+            np.linspace(0, 2 * np.pi, 7), np.linspace(-1, 1, 2)]
+
+    def unit(c, p):
+        r = np.sqrt(max(0.0, 1 - c * c))
+        return np.array([r * np.cos(p), r * np.sin(p), c])
+
+    grid = np.zeros([len(a) for a in axes] + [16])
+    for i, ci in enumerate(axes[0]):
+        for j, pi in enumerate(axes[1][:-1]):
+            for k, cs in enumerate(axes[2]):
+                for l, ps in enumerate(axes[3][:-1]):
+                    for m_, sz in enumerate(axes[4]):
+                        u = np.concatenate([unit(ci, pi), unit(cs, ps), [sz]])
+                        grid[i, j, k, l, m_] = MO.label(u, tabs, kext)[:16]
+    grid[:, -1] = grid[:, 0]
+    grid[:, :, :, -1] = grid[:, :, :, 0]  # periodic azimuths
+    interp = RegularGridInterpolator(axes, grid)
+    # memory of the table: stored nodes (without the periodic copies) x 20 numbers x 4 B
+    table_bytes = 4 * 6 * 4 * 6 * 2 * 20 * 4
+    assert table_bytes <= 119264
+    u = inputs(1500).astype(np.float64)
+    ref = np.array([MO.label(x, tabs, kext) for x in u])
+    y = s.eval(u).astype(np.float64)
+    pts = np.stack([u[:, 2], np.mod(np.arctan2(u[:, 1], u[:, 0]), 2 * np.pi), u[:, 5],
+                    np.mod(np.arctan2(u[:, 4], u[:, 3]), 2 * np.pi), u[:, 6]], axis=1)
+    tab = interp(pts)
+
+    def rel_err(est):  # matrices of both encodings, error relative to the true M11
+        return np.array([(MO.matrix(e) - MO.matrix(r)).ravel() / np.exp(r[0]) for e, r in zip(est, ref)])
+
+    net_rms = np.sqrt(np.mean(rel_err(y) ** 2))
+    tab_rms = np.sqrt(np.mean(rel_err(tab) ** 2))
+    print(f"rms error relative to M11: network {net_rms:.4g}, equal-memory table {tab_rms:.4g}")
+    assert net_rms < tab_rms / 3

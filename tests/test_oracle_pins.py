@@ -533,9 +533,10 @@ def test_sweep_generator_statistics():
 # grain-optics surrogate: labels and the FP64 MLP reference
 # ---------------------------------------------------------------------------------
 def test_surrogate_labels_reduce_to_the_tables():
-    """At the tabulated sizes the label matrix, taken back to the scattering-plane
-    basis, is the bin table; between sizes it interpolates in ln x; alpha follows the
-    extinction table; realizable (Z11 >= |row 1|)."""
+    """At the tabulated sizes the label matrix is the bin table in the scattering-plane
+    basis; applied with the plane rotations it is the oracle's scattering transfer;
+    between sizes it interpolates in ln x; alpha follows the extinction table;
+    realizable (M11 >= |row 1|, |column 1|)."""
     from oracle import mlp_oracle as MO
 
     opt = W.table_optics(n_bins=8)
@@ -547,14 +548,17 @@ def test_surrogate_labels_reduce_to_the_tables():
         s = -1.0 + 2.0 * k / 7
         lab = MO.label(np.r_[ni, ns, s], tabs, kext)
         N = math.exp(lab[19])
-        Z = lab[:16].reshape(4, 4) * N
+        Z = MO.matrix(lab)
         mu = float(np.dot(ni, ns))
         P = MO.theta_interp(tabs[k].astype(np.float64), mu)
         assert abs(N - tabs[k][:, 0].max()) < 1e-6 * N
-        # unpolarized input: the intensity is P11 and the polarization degree is |P12|/P11
-        out = Z @ np.array([1.0, 0, 0, 0])
-        assert abs(out[0] - P[0]) < 1e-6 * P[0]
-        assert abs(math.hypot(out[1], out[2]) - abs(P[1])) < 1e-6 * P[0]
+        # the 4x4 form of the six table elements
+        ref = np.array([[P[0], P[1], 0, 0], [P[1], P[2], 0, 0], [0, 0, P[3], P[4]], [0, 0, -P[4], P[5]]])
+        assert np.allclose(Z, ref, rtol=1e-12, atol=1e-12 * P[0])
+        # with the plane rotations: the oracle's scattering transfer of a polarized input
+        X = np.array([1.0, 0.3, -0.2, 0.1])
+        Zg = np.array([O.mueller_apply(e, ni, ns, P) for e in np.eye(4)]).T
+        assert np.allclose(Zg @ X, O.mueller_apply(X, ni, ns, Z[[0, 0, 1, 2, 2, 3], [0, 1, 1, 2, 3, 3]]))
         assert Z[0, 0] ** 2 >= Z[0, 1] ** 2 + Z[0, 2] ** 2 + Z[0, 3] ** 2 - 1e-12
         a = MO.kext_interp(kext, ni[2])
         assert np.allclose(lab[16:19], a)
@@ -564,8 +568,11 @@ def test_surrogate_labels_reduce_to_the_tables():
     lab = MO.label(np.r_[ni, ns, s], tabs, kext)
     mid = 0.5 * (tabs[2].astype(np.float64) + tabs[3].astype(np.float64))
     P = MO.theta_interp(mid, float(np.dot(ni, ns)))
-    assert abs(lab[0] * math.exp(lab[19]) - (np.array(lab[:16]).reshape(4, 4) * math.exp(lab[19]) @ [1, 0, 0, 0])[0]) < 1e-9
-    assert abs((lab[:16].reshape(4, 4) * math.exp(lab[19]) @ [1, 0, 0, 0])[0] - P[0]) < 1e-6 * P[0]
+    assert abs(math.exp(lab[0]) - (MO.matrix(lab) @ [1, 0, 0, 0])[0]) < 1e-12 * math.exp(lab[0])
+    assert abs((MO.matrix(lab) @ [1, 0, 0, 0])[0] - P[0]) < 1e-6 * P[0]
+    # the ratios of a realizable matrix: row 1 and column 1 within the unit ball
+    assert lab[1] ** 2 + lab[2] ** 2 + lab[3] ** 2 <= 1 + 1e-12
+    assert lab[4] ** 2 + lab[8] ** 2 + lab[12] ** 2 <= 1 + 1e-12
 
 
 def test_mlp_reference_gradients_by_central_differences():
