@@ -619,7 +619,10 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
     if (sur) {
         // capacity of a round: up to 2^21 packets in flight, 32 tally records each
         unsigned long long cap = work < (1ll << 21) ? (unsigned long long)(work > 0 ? work : 1) : (1ull << 21);
-        const unsigned long long rec_cap = cap * 32ull > 65536ull ? cap * 32ull : 65536ull;
+        // soft limit: room for one more record per thread of the transport grid
+        const unsigned long long margin = (unsigned long long)ctx->n_sm * 16ull * 128ull;
+        unsigned long long rec_cap = cap * 32ull;
+        if (rec_cap < 4 * margin) rec_cap = 4 * margin;
         if (!ctx->d_wave) CK(ctx, cudaMalloc(&ctx->d_wave, sizeof(WaveCtl)));
         if (ctx->wave_cap < cap) {
             cudaFree(ctx->d_susp);
@@ -652,6 +655,7 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
         P.sur.ctl = ctx->d_wave;
         P.sur.records = ctx->d_records;
         P.sur.rec_cap = ctx->rec_cap;
+        P.sur.rec_soft = ctx->rec_cap - margin;
         P.sur.suspend = ctx->d_susp;
         P.sur.resume = ctx->d_res;
         int rounds = 0;

@@ -86,6 +86,7 @@ struct WaveCtl {
     unsigned long long n_resume_next;  // packets written to the resume buffer by the scattering kernel
     unsigned long long n_suspend;      // packets suspended at a scattering by the current launch
     unsigned long long n_records;      // tally records requested by the current launch
+    unsigned long long full;           // the record queue passed its soft limit: packets park
     // totals: network rows (tally, scattering), fallbacks (error map, realizability),
     // tally segments tallied in place for want of record space, envelope misses
     unsigned long long cnt[8];
@@ -100,6 +101,8 @@ struct SurrogateDev {
     WaveCtl* ctl;
     float4* records;             // [rec_cap][kRecordF4]
     unsigned long long rec_cap;
+    unsigned long long rec_soft;  // rec_cap minus the threads of the transport grid (one
+                                  // more record each at most once the soft limit is passed)
     float4* suspend;             // [cap][kStateF4]
     float4* resume;              // [cap][kStateF4]
 };

@@ -82,6 +82,7 @@ template <typename T> struct Packet {
     T X0, X1, X2, X3;
     T I_birth, e_abs, e_gain;
     T s_flight;  // surrogate path: grain-size coordinate of the current flight's tally
+    bool park;   // surrogate path: stop after this segment (record queue near its end)
     double tau;  // remaining scattering optical depth (FP64 running sum)
     long long pid;
     const JobDev* job;  // batched launches: the packet's job
@@ -214,8 +215,9 @@ __device__ __forceinline__ void apply_plane_full(const PlaneRot<float>& r, float
 }
 
 // A packet waiting between kernels: 8 float4 (128 bytes); its cell record is
-// reloaded from (ix, iy, iz) when it resumes.
-__device__ __forceinline__ void store_state(float4* d, const Packet<float>& pk) {
+// reloaded from (ix, iy, iz) when it resumes.  parked = 1: stopped inside its flight
+// (nothing to do before it resumes), 0: waiting for its scattering.
+__device__ __forceinline__ void store_state(float4* d, const Packet<float>& pk, unsigned parked = 0u) {
     const unsigned long long pid = (unsigned long long)pk.pid;
     d[0] = make_float4(pk.px, pk.py, pk.pz, pk.X0);
     d[1] = make_float4(pk.nx, pk.ny, pk.nz, pk.X1);
@@ -227,7 +229,7 @@ __device__ __forceinline__ void store_state(float4* d, const Packet<float>& pk) 
                        __uint_as_float(pk.n_tally));
     d[6] = make_float4(__uint_as_float(pk.n_abs), __uint_as_float(pk.trials), __int_as_float(pk.ix),
                        __int_as_float(pk.iy));
-    d[7] = make_float4(__int_as_float(pk.iz), 0.f, 0.f, 0.f);
+    d[7] = make_float4(__int_as_float(pk.iz), __uint_as_float(parked), 0.f, 0.f);
 }
 
 __device__ __forceinline__ void load_state(const float4* d, Packet<float>& pk) {
@@ -259,6 +261,7 @@ __device__ __forceinline__ void load_state(const float4* d, Packet<float>& pk) {
     pk.iy = __float_as_int(h.w);
     pk.iz = __float_as_int(k.x);
     pk.job = nullptr;
+    pk.park = false;
 }
 
 }  // namespace

@@ -321,6 +321,25 @@ __device__ __forceinline__ T exit_face(const J& job, const Packet<T>& pk, int& a
     return best;
 }
 
+// Surrogate path: the packet leaves this launch for the suspend buffer (one slot per
+// work item of the launch, so it cannot run over), waiting for its scattering
+// (parked = 0) or stopped inside its flight (parked = 1).
+template <typename T>
+__device__ __forceinline__ void suspend_packet(const TransportParams& P, const Packet<T>& pk, unsigned parked) {
+    if constexpr (sizeof(T) == 4) {
+        cg::coalesced_group grp = cg::coalesced_threads();
+        unsigned long long base = 0;
+        if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->n_suspend, (unsigned long long)grp.size());
+        base = grp.shfl(base, 0);
+        store_state(P.sur.suspend + (base + grp.thread_rank()) * kStateF4, pk, parked);
+    }
+}
+template <typename T> __device__ __forceinline__ void park_packet(const TransportParams& P, Packet<T>& pk, bool& alive) {
+    pk.park = false;
+    suspend_packet(P, pk, 1u);
+    alive = false;
+}
+
 // One event of a live packet: a cell segment, then a scattering when the sampled
 // optical depth runs out inside the cell.  `work` = live lanes of the warp.
 template <typename T, int SCAT, bool B>
@@ -435,6 +454,11 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
                         r[3] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, 0.f);
                     }
                 }
+                // past the soft limit every lane stops after this segment and takes no new
+                // work, so at most one record per thread lands beyond it: the queue never
+                // runs over (the table tally below is a guard that should stay unused)
+                if (idx >= P.sur.rec_soft) pk.park = true;
+                if (lane == lead && base + cnt > P.sur.rec_soft) atomicExch(&P.sur.ctl->full, 1ull);
                 if (!queued && lane == lead) atomicAdd(&P.sur.ctl->cnt[kCntOverflow], (unsigned long long)cnt);
             }
         }
@@ -501,6 +525,9 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         }
         pk.cq = nq;
         pk.cr = nr;
+        if constexpr (SCAT == kScatSurrogate) {
+            if (pk.park) park_packet(P, pk, alive);
+        }
         return;
     }
 
@@ -513,11 +540,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     if constexpr (SCAT == kScatSurrogate) {
         // the scattering is done by the network's kernel; the packet waits in the
         // suspend buffer, whose capacity is the launch's number of work items
-        cg::coalesced_group grp = cg::coalesced_threads();
-        unsigned long long base = 0;
-        if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->n_suspend, (unsigned long long)grp.size());
-        base = grp.shfl(base, 0);
-        store_state(P.sur.suspend + (base + grp.thread_rank()) * kStateF4, pk);
+        suspend_packet(P, pk, 0u);
         alive = false;
         return;
     }
@@ -674,6 +697,10 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
                 if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->claim, (unsigned long long)grp.size());
                 base = grp.shfl(base, 0);
                 const unsigned long long idx = base + grp.thread_rank();
+                // the record queue is near its end: work items taken now wait for the
+                // next round without a segment
+                const bool full = *reinterpret_cast<volatile unsigned long long*>(&P.sur.ctl->full) != 0ull;
+                pk.park = false;
                 if (idx < w_resume) {
                     if constexpr (sizeof(T) == 4) {
                         load_state(P.sur.resume + idx * kStateF4, pk);
@@ -683,9 +710,11 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
                 } else if (idx - w_resume < w_new) {
                     const long long pid = P.pid_begin + (long long)(w_next + (idx - w_resume));
                     alive = emit<T, false>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
+                    pk.park = false;
                 } else {
                     pool_done = true;
                 }
+                if (alive && full) park_packet(P, pk, alive);
             }
         } else if (!alive && !pool_done) {
             cg::coalesced_group grp = cg::coalesced_threads();

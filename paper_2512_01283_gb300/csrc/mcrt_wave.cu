@@ -94,6 +94,7 @@ __global__ void k_wave_begin(WaveCtl* c, unsigned long long total, unsigned long
     c->claim = 0;
     c->n_suspend = 0;
     c->n_records = 0;
+    c->full = 0;
     c->cnt[kCntIterations] += 1;
 }
 
@@ -244,7 +245,20 @@ __global__ void __launch_bounds__(kWaveBlock, 1) k_sur_scatter(const __grid_cons
         float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
         V3<float> n{0.f, 0.f, 1.f}, th{1.f, 0.f, 0.f}, ph{0.f, 1.f, 0.f}, nGF{0.f, 0.f, 1.f};
         const unsigned long long i = batch * 16 + (unsigned)lane;
-        if (lane < 16 && i < nsus) {
+        bool parked = false;
+        if (lane < 16 && i < nsus) parked = __float_as_uint(P.sur.suspend[i * kStateF4 + 7].y) != 0u;
+        if (parked) {
+            // stopped inside its flight: straight to the resume buffer
+            cg::coalesced_group grp = cg::coalesced_threads();
+            unsigned long long base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->n_resume_next, (unsigned long long)grp.size());
+            base = grp.shfl(base, 0);
+            const float4* src = P.sur.suspend + i * kStateF4;
+            float4* dst = P.sur.resume + (base + grp.thread_rank()) * kStateF4;
+#pragma unroll
+            for (int e = 0; e < kStateF4; ++e) dst[e] = src[e];
+        }
+        if (lane < 16 && i < nsus && !parked) {
             load_state(P.sur.suspend + i * kStateF4, pk);
             const Draw4<float> us = draw4<float>(pk.pid, pk.n_sca, 0u, P.seed, P.stream);
             us_a = us.a;
