@@ -140,8 +140,10 @@ typedef struct {
     double mlp_fallback_map;      /* evaluations replaced by the tables: error-map cell above bound */
     double mlp_fallback_realizability; /* ... network matrix not physically realizable */
     double tally_overflow;        /* tally segments done with the tables for want of queue space */
-    double envelope_miss;         /* accepted-or-not trials whose target exceeded the envelope */
+    double envelope_miss;         /* trials whose target exceeded the (widened) envelope */
     double wave_iterations;       /* transport / network rounds of the launch */
+    double ms_transport, ms_tally, ms_scatter; /* device time of the rounds' transport,
+                                     network-tally and network-scattering kernels */
 } mcrt_stats;
 
 /*

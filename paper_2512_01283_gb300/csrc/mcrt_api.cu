@@ -659,8 +659,8 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
         P.sur.suspend = ctx->d_susp;
         P.sur.resume = ctx->d_res;
         int rounds = 0;
-        float ms = 0.f;
-        if (work > 0) CK(ctx, run_surrogate_transport(P, ctx->n_sm, cap, &rounds, &ms, ctx->stream));
+        float ms = 0.f, kms[3] = {0.f, 0.f, 0.f};
+        if (work > 0) CK(ctx, run_surrogate_transport(P, ctx->n_sm, cap, &rounds, &ms, kms, ctx->stream));
         ctx->launched = true;
         ctx->last_optics = MCRT_OPTICS_SURROGATE;
         if (trace_host)
@@ -676,6 +676,9 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
         if (st_out) {
             add_stats(st_out, raw, status, ms);
             add_wave_stats(st_out, w);
+            st_out->ms_transport += kms[0];
+            st_out->ms_tally += kms[1];
+            st_out->ms_scatter += kms[2];
         }
         return status_of(ctx, status);
     }

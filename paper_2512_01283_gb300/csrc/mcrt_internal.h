@@ -170,9 +170,10 @@ cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* 
                                  cudaStream_t s);
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s);
 // surrogate path (mcrt_wave.cu): the transport loop of one launch; ms_out: device
-// time of all its kernels
+// time of the whole loop; ms_kernels[3]: summed times of the transport, tally and
+// scattering kernels
 cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned long long cap, int* iterations,
-                                    float* ms_out, cudaStream_t s);
+                                    float* ms_out, float* ms_kernels, cudaStream_t s);
 
 }  // namespace mcrt
 

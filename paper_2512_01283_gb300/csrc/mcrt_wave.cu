@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(kWaveBlock, 1) k_sur_scatter(const __grid_cons
 }  // namespace
 
 cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned long long cap, int* iterations,
-                                    float* ms_out, cudaStream_t s) {
+                                    float* ms_out, float* ms_kernels, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k_sur_tally, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallySmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sur_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatSmem);
@@ -488,9 +488,11 @@ cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned
     const size_t tsmem = transport_smem_bytes(p, MCRT_FP32, block);
     const int bps = transport_max_blocks_per_sm(MCRT_FP32, kScatSurrogate, false, block, tsmem);
     const int tgrid = n_sm * bps;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, ek[4] = {nullptr, nullptr, nullptr, nullptr};
     e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ek[k]);
+    float kms[3] = {0.f, 0.f, 0.f};  // transport, tally, scattering kernels
     if (e == cudaSuccess) e = cudaMemsetAsync(p.sur.ctl, 0, sizeof(WaveCtl), s);
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     unsigned long long C = cap;
@@ -505,14 +507,26 @@ cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned
         }
         k_wave_begin<<<1, 1, 0, s>>>(p.sur.ctl, total, C);
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(ek[0], s);
         if (e == cudaSuccess) e = launch_transport(p, MCRT_FP32, block, tgrid, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ek[1], s);
         if (e == cudaSuccess) {
             k_sur_tally<<<n_sm, kWaveBlock, kTallySmem, s>>>(p);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ek[2], s);
+        if (e == cudaSuccess) {
             k_sur_scatter<<<n_sm, kWaveBlock, kScatSmem, s>>>(p);
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) e = cudaEventRecord(ek[3], s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&h, p.sur.ctl, sizeof(WaveCtl), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ek[k], ek[k + 1]);
+            kms[k] += t;
+        }
         if (e != cudaSuccess) break;
         if (h.n_resume_next == 0 && h.next_pid + h.n_new >= total) {
             ++it;
@@ -535,8 +549,12 @@ cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    for (int k = 0; k < 4; ++k)
+        if (ek[k]) cudaEventDestroy(ek[k]);
     if (iterations) *iterations = it;
     if (ms_out) *ms_out = ms;
+    if (ms_kernels)
+        for (int k = 0; k < 3; ++k) ms_kernels[k] = kms[k];
     return e;
 }
 

@@ -57,7 +57,7 @@ STAT_FIELDS = ["emitted_energy", "escaped_energy", "absorbed_energy", "roulette_
                "events", "segments", "scatterings", "emitted", "escaped", "roulette_killed", "cap_hits", "trials",
                "kernel_ms", "status_bits", "tally_segments", "absorb_segments",
                "mlp_tally_rows", "mlp_scatter_rows", "mlp_fallback_map", "mlp_fallback_realizability",
-               "tally_overflow", "envelope_miss", "wave_iterations"]
+               "tally_overflow", "envelope_miss", "wave_iterations", "ms_transport", "ms_tally", "ms_scatter"]
 
 
 class Stats(C.Structure):
