@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-packets", type=float, default=1e6, help="packets per job of the batched sweep")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--inline-tally", action="store_true",
+                    help="table path: tally inside the transport kernel instead of a tally kernel per round")
     ap.add_argument("--sur-steps", type=int, default=1, help="timed launches of the surrogate path")
     ap.add_argument("--sur-train-samples", type=float, default=2e7, help="training samples of the network")
     ap.add_argument("--sur-bound", type=float, default=0.05, help="error-map bound of the table fallback")
@@ -334,7 +336,7 @@ def main():
     imgs = torch.empty((n_cam, 4, npix[1], npix[0]), dtype=torch.float64, device="cuda")
 
     def step(seed):
-        st = M.launch(mdl, dict(run, seed=seed), precision="fp32")
+        st = M.launch(mdl, dict(run, seed=seed), precision="fp32", inline_tally=args.inline_tally)
         for k in range(n_cam):
             mdl.image(k, imgs[k])
         return st
@@ -395,8 +397,12 @@ def main():
             "clocks": cs.summary(),
             "detail": {"events_per_step": events / args.steps, "segments_per_step": seg / args.steps,
                        "scatterings_per_step": sum(s["scatterings"] for s in stats) / args.steps,
+                       "tally_segments_per_step": tal / args.steps,
                        "transport_ms_per_step": kms / args.steps,
-                       "imaging_ms_per_step": ms / args.steps - kms / args.steps}}
+                       "imaging_ms_per_step": ms / args.steps - kms / args.steps,
+                       "rounds_per_step": sum(s["wave_iterations"] for s in stats) / args.steps,
+                       "round_kernels_ms_per_step": {"transport": sum(s["ms_transport"] for s in stats) / args.steps,
+                                                     "tally": sum(s["ms_tally"] for s in stats) / args.steps}}}
 
     # end to end through the public API with host buffers: H2D of the model, both
     # steps, D2H of the images, every step

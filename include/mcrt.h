@@ -60,6 +60,11 @@ enum { MCRT_SRC_POINT = 0, MCRT_SRC_BEAM = 1, MCRT_SRC_THERMAL = 2 };
 enum { MCRT_SCAT_RAYLEIGH = 0, MCRT_SCAT_TABLE = 1 };
 enum { MCRT_FP32 = 0, MCRT_FP64 = 1 };
 enum { MCRT_OPTICS_TABLES = 0, MCRT_OPTICS_SURROGATE = 1 };
+/* Launch flags (mcrt_launch_desc.flags). */
+enum {
+    MCRT_FLAG_INLINE_TALLY = 1 /* FP32 table launches: tally inside the transport kernel instead of the
+                                  default rounds (transport, then a tally kernel over the queued segments) */
+};
 enum { MCRT_MAX_SOURCES = 8, MCRT_MAX_CAMERAS = 16 };
 
 /* Status bits reported in mcrt_stats.status_bits. */
@@ -123,6 +128,7 @@ typedef struct {
                                      mcrt_set_dust_tables; MCRT_OPTICS_SURROGATE: the
                                      network attached with mcrt_set_surrogate (FP32, one
                                      model, no time budget) */
+    int32_t flags;                /* MCRT_FLAG_* */
 } mcrt_launch_desc;
 
 /* Totals of a launch (FP64 sums over packets). */

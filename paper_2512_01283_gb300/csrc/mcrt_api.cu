@@ -557,6 +557,10 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
     if (st != MCRT_OK) return st;
     const bool sur = d->optics == MCRT_OPTICS_SURROGATE;
     if (sur && !ctx->sur_set) return fail(ctx, MCRT_E_STATE, "mcrt_launch_packets: no surrogate attached (mcrt_set_surrogate)");
+    // FP32 table launches tally in a kernel of their own unless asked not to
+    const bool deferred_table = !sur && ctx->t.model == MCRT_SCAT_TABLE && d->precision == MCRT_FP32 &&
+                                d->n_cameras > 0 && !(d->time_budget_s > 0.0) && !(d->flags & MCRT_FLAG_INLINE_TALLY);
+    const bool rounds = sur || deferred_table;
     TransportParams P{};
     fill_common(d, P);
     P.g = ctx->g;
@@ -616,7 +620,7 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
     const long long need = (work + block - 1) / block;
     if (need < grid) grid = need > 0 ? need : 1;
 
-    if (sur) {
+    if (rounds) {
         // capacity of a round: up to 2^21 packets in flight, 32 tally records each
         unsigned long long cap = work < (1ll << 21) ? (unsigned long long)(work > 0 ? work : 1) : (1ull << 21);
         // soft limit: room for one more record per thread of the transport grid
@@ -658,11 +662,13 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
         P.sur.rec_soft = ctx->rec_cap - margin;
         P.sur.suspend = ctx->d_susp;
         P.sur.resume = ctx->d_res;
-        int rounds = 0;
+        int n_rounds = 0;
         float ms = 0.f, kms[3] = {0.f, 0.f, 0.f};
-        if (work > 0) CK(ctx, run_surrogate_transport(P, ctx->n_sm, cap, &rounds, &ms, kms, ctx->stream));
+        if (work > 0)
+            CK(ctx, run_round_transport(P, sur ? kScatSurrogate : kScatTableDeferred, ctx->n_sm, cap, &n_rounds, &ms,
+                                        kms, ctx->stream));
         ctx->launched = true;
-        ctx->last_optics = MCRT_OPTICS_SURROGATE;
+        ctx->last_optics = sur ? MCRT_OPTICS_SURROGATE : MCRT_OPTICS_TABLES;
         if (trace_host)
             CK(ctx, cudaMemcpyAsync(trace_host, P.trace, (size_t)d->n_trace * 16 * sizeof(double),
                                     cudaMemcpyDeviceToHost, ctx->stream));
@@ -680,6 +686,8 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
             st_out->ms_tally += kms[1];
             st_out->ms_scatter += kms[2];
         }
+        if (!sur && w.cnt[kCntOverflow] > 0)
+            return fail(ctx, MCRT_E_CUDA, "mcrt_launch_packets: internal error, tally queue overflow");
         return status_of(ctx, status);
     }
 

@@ -15,6 +15,10 @@ constexpr int kMaxSources = MCRT_MAX_SOURCES;
 // scattering-model id of the transport instantiation that defers the optics to the
 // network (internal; the tables stay MCRT_SCAT_TABLE)
 constexpr int kScatSurrogate = 2;
+// table optics with the source tally deferred to a separate coherent kernel (FP32,
+// one model): the transport kernel leaves 32-byte records instead of the camera loop
+constexpr int kScatTableDeferred = 3;
+constexpr int kTableRecordF4 = 2;  // table tally record: 2 float4 (32 bytes)
 constexpr int kErrMapCells = 4096;  // 8^4 cells of (cos theta_i, cos theta_s, delta phi, s)
 constexpr int kStateF4 = 8;         // suspended packet: 8 float4 (128 bytes)
 constexpr int kRecordF4 = 4;        // tally record: 4 float4 (64 bytes)
@@ -105,6 +109,7 @@ struct SurrogateDev {
                                   // more record each at most once the soft limit is passed)
     float4* suspend;             // [cap][kStateF4]
     float4* resume;              // [cap][kStateF4]
+    int deferred;                // which round-based instantiation runs (kScat* id), 0: none
 };
 
 struct TransportParams {
@@ -169,11 +174,12 @@ int thermal_cdf_blocks(long long ncell);
 cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* guide, long long n_guide,
                                  cudaStream_t s);
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s);
-// surrogate path (mcrt_wave.cu): the transport loop of one launch; ms_out: device
-// time of the whole loop; ms_kernels[3]: summed times of the transport, tally and
-// scattering kernels
-cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned long long cap, int* iterations,
-                                    float* ms_out, float* ms_kernels, cudaStream_t s);
+// round-based paths (mcrt_wave.cu): the transport loop of one launch with the tally
+// (and, for the surrogate, the scattering) in kernels of their own; model is
+// kScatSurrogate or kScatTableDeferred; ms_out: device time of the whole loop;
+// ms_kernels[3]: summed times of the transport, tally and scattering kernels
+cudaError_t run_round_transport(const TransportParams& p, int model, int n_sm, unsigned long long cap,
+                                int* iterations, float* ms_out, float* ms_kernels, cudaStream_t s);
 
 }  // namespace mcrt
 

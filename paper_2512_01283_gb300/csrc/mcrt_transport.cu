@@ -321,7 +321,10 @@ __device__ __forceinline__ T exit_face(const J& job, const Packet<T>& pk, int& a
     return best;
 }
 
-// Surrogate path: the packet leaves this launch for the suspend buffer (one slot per
+__host__ __device__ constexpr bool table_optics(int scat) { return scat == MCRT_SCAT_TABLE || scat == kScatTableDeferred; }
+__host__ __device__ constexpr bool round_based(int scat) { return scat == kScatSurrogate || scat == kScatTableDeferred; }
+
+// Round-based paths: the packet leaves this launch for the suspend buffer (one slot per
 // work item of the launch, so it cannot run over), waiting for its scattering
 // (parked = 0) or stopped inside its flight (parked = 1).
 template <typename T>
@@ -428,11 +431,12 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             if (lane == leader && dI != T(0)) atomicAdd(&job.absorbed()[c32], widen(dI));
         }
         bool queued = false;
-        if constexpr (SCAT == kScatSurrogate) {
+        if constexpr (round_based(SCAT)) {
             if (want_S) {
-                // the segment waits for the network: one 64-byte record per lane, the
-                // warp's records in consecutive slots; a warp that would run past the
-                // queue's end writes empty records and tallies with the tables below
+                // the segment's tally waits for its own kernel: one record per lane (64 B
+                // with the network's inputs, 32 B for the tables), the warp's records in
+                // consecutive slots; a warp that would run past the queue's end writes
+                // empty records and tallies in place below
                 T Wl1 = Wg[1], Wl2 = Wg[2];  // path integral in the packet's basis
                 rotate_qu(Wl1, Wl2, c2, -s2);
                 const int lead = __ffs(actS) - 1;
@@ -443,26 +447,39 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
                 const unsigned long long idx = base + (unsigned)__popc(actS & ((1u << lane) - 1u));
                 queued = base + cnt <= P.sur.rec_cap;
                 if (idx < P.sur.rec_cap) {
-                    float4* r = P.sur.records + idx * kRecordF4;
-                    if (queued) {
-                        r[0] = make_float4((float)n.x, (float)n.y, (float)n.z, (float)pk.s_flight);
-                        r[1] = make_float4((float)Wg[0], (float)Wl1, (float)Wl2, (float)Wg[3]);
-                        r[2] = pk.cq;
-                        r[3] = make_float4(__uint_as_float(c32), 0.f, 0.f, 0.f);
-                        pk.n_tally++;
+                    if constexpr (SCAT == kScatSurrogate) {
+                        float4* r = P.sur.records + idx * kRecordF4;
+                        if (queued) {
+                            r[0] = make_float4((float)n.x, (float)n.y, (float)n.z, (float)pk.s_flight);
+                            r[1] = make_float4((float)Wg[0], (float)Wl1, (float)Wl2, (float)Wg[3]);
+                            r[2] = pk.cq;
+                            r[3] = make_float4(__uint_as_float(c32), 0.f, 0.f, 0.f);
+                        } else {
+                            r[3] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, 0.f);
+                        }
                     } else {
-                        r[3] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, 0.f);
+                        float4* r = P.sur.records + idx * kTableRecordF4;
+                        if (queued) {
+                            r[0] = make_float4((float)n.x, (float)n.y, (float)n.z, (float)Wg[0]);
+                            r[1] = make_float4((float)Wl1, (float)Wl2, (float)Wg[3], __uint_as_float(c32));
+                        } else {
+                            r[1] = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
+                        }
                     }
+                    if (queued) pk.n_tally++;
                 }
-                // past the soft limit every lane stops after this segment and takes no new
-                // work, so at most one record per thread lands beyond it: the queue never
-                // runs over (the table tally below is a guard that should stay unused)
+                // a lane whose record lands past the soft limit parks its packet before its
+                // next segment and parks all work it takes afterwards, so each thread adds
+                // at most one record beyond it and the queue cannot run over (the in-place
+                // tally below is a guard that stays unused)
                 if (idx >= P.sur.rec_soft) pk.park = true;
                 if (lane == lead && base + cnt > P.sur.rec_soft) atomicExch(&P.sur.ctl->full, 1ull);
                 if (!queued && lane == lead) atomicAdd(&P.sur.ctl->cnt[kCntOverflow], (unsigned long long)cnt);
             }
         }
-        if (want_S && !queued) {
+        // the table rounds keep no in-place tally (smaller kernel): a segment that finds
+        // no queue space is counted and fails the launch, which the soft limit rules out
+        if (SCAT != kScatTableDeferred && want_S && !queued) {
             rotate_qu(Wg[1], Wg[2], c2, -s2);
             const unsigned gmax = __reduce_max_sync(actS, (unsigned)__popc(group));
             pk.n_tally++;
@@ -525,9 +542,6 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         }
         pk.cq = nq;
         pk.cr = nr;
-        if constexpr (SCAT == kScatSurrogate) {
-            if (pk.park) park_packet(P, pk, alive);
-        }
         return;
     }
 
@@ -561,7 +575,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     }
     int bin = 0;
     const float4* tab = nullptr;
-    if (SCAT == MCRT_SCAT_TABLE) {
+    if (table_optics(SCAT)) {
         bin = tabs.n_bins - 1;
         for (int k = 0; k < tabs.n_bins; ++k)
             if (us.c < T(tabs.bin_cdf[k])) {
@@ -650,8 +664,18 @@ __device__ __forceinline__ int job_index(const TransportParams& P, long long gpi
     return lo;
 }
 
+// resident blocks per SM of the table-round instantiation: without the camera loop
+// and its staging slots it fits more warps per SM
+#ifndef MCRT_ROUND_MIN_BLOCKS
+#define MCRT_ROUND_MIN_BLOCKS 7
+#endif
+template <typename T, int SCAT>
+constexpr int min_blocks() {
+    return sizeof(T) != 4 ? 1 : (SCAT == kScatTableDeferred ? MCRT_ROUND_MIN_BLOCKS : MCRT_MIN_BLOCKS);
+}
+
 template <typename T, int SCAT, bool B>
-__global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCKS : 1)
+__global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
     k_transport(const __grid_constant__ TransportParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockTotals bt;
@@ -680,17 +704,18 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
     Packet<T> pk;
     pk.job = nullptr;
     bool alive = false, pool_done = false;
+    bool stop = false;  // round-based paths: this lane's record went past the soft limit
     const unsigned long long t0 = global_ns();
     // surrogate path: packets resumed after their scattering, then new packets
     unsigned long long w_resume = 0, w_new = 0, w_next = 0;
-    if constexpr (SCAT == kScatSurrogate) {
+    if constexpr (round_based(SCAT)) {
         w_resume = P.sur.ctl->n_resume;
         w_new = P.sur.ctl->n_new;
         w_next = P.sur.ctl->next_pid;
     }
 
     for (;;) {
-        if constexpr (SCAT == kScatSurrogate) {
+        if constexpr (round_based(SCAT)) {
             if (!alive && !pool_done) {
                 cg::coalesced_group grp = cg::coalesced_threads();
                 unsigned long long base = 0;
@@ -714,7 +739,11 @@ __global__ void __launch_bounds__(kDefaultBlock, sizeof(T) == 4 ? MCRT_MIN_BLOCK
                 } else {
                     pool_done = true;
                 }
-                if (alive && full) park_packet(P, pk, alive);
+                if (alive && (full || stop)) park_packet(P, pk, alive);
+            }
+            if (alive && pk.park) {  // before the next segment, outside the warp's collective steps
+                stop = true;
+                park_packet(P, pk, alive);
             }
         } else if (!alive && !pool_done) {
             cg::coalesced_group grp = cg::coalesced_threads();
@@ -768,7 +797,9 @@ size_t transport_smem_bytes(const TransportParams& p, int precision, int block) 
     const size_t kx = batch ? 0 : (size_t)p.t.n_ktheta * sizeof(float4);
     const size_t mix = (!batch && p.t.model == MCRT_SCAT_TABLE) ? 2 * (size_t)p.t.n_theta * sizeof(float4) : 0;
     const size_t cams = 12 * (size_t)p.n_cam * tsize;
-    return kx + mix + cams + (size_t)block * kStageDoubles * sizeof(double);
+    // the table rounds tally in their own kernel: no staging slots
+    const size_t stage = p.sur.deferred == kScatTableDeferred ? 0 : (size_t)block * kStageDoubles * sizeof(double);
+    return kx + mix + cams + stage;
 }
 
 const void* transport_kernel(int precision, int model, bool batch) {
@@ -786,11 +817,14 @@ const void* transport_kernel(int precision, int model, bool batch) {
                  : (const void*)k_transport<float, MCRT_SCAT_RAYLEIGH, false>;
 }
 
-const void* transport_kernel_surrogate() { return (const void*)k_transport<float, kScatSurrogate, false>; }
+const void* transport_kernel_rounds(int model) {
+    return model == kScatSurrogate ? (const void*)k_transport<float, kScatSurrogate, false>
+                                   : (const void*)k_transport<float, kScatTableDeferred, false>;
+}
 
 int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem) {
     int nb = 0;
-    const void* k = model == kScatSurrogate ? transport_kernel_surrogate() : transport_kernel(precision, model, batch);
+    const void* k = round_based(model) ? transport_kernel_rounds(model) : transport_kernel(precision, model, batch);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
@@ -798,7 +832,8 @@ int transport_max_blocks_per_sm(int precision, int model, bool batch, int block,
 
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s) {
     const size_t smem = transport_smem_bytes(p, precision, block);
-    const void* k = p.sur.ctl ? transport_kernel_surrogate() : transport_kernel(precision, p.t.model, p.jobs != nullptr);
+    const void* k = p.sur.deferred ? transport_kernel_rounds(p.sur.deferred)
+                                   : transport_kernel(precision, p.t.model, p.jobs != nullptr);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -82,11 +82,12 @@ __device__ __forceinline__ bool map_says_fallback(const SurrogateDev& s, const V
 }
 
 // Round set-up: new packets taken by the previous round are counted, the packets
-// resumed by the scattering kernel become this round's resume list, and new packets
-// fill the capacity left.
-__global__ void k_wave_begin(WaveCtl* c, unsigned long long total, unsigned long long cap) {
+// waiting from the previous round become this round's resume list (written by the
+// scattering kernel, or, with swap, the previous transport's suspend buffer itself),
+// and new packets fill the capacity left.
+__global__ void k_wave_begin(WaveCtl* c, unsigned long long total, unsigned long long cap, int swap) {
     c->next_pid += c->n_new;
-    c->n_resume = c->n_resume_next;
+    c->n_resume = swap ? c->n_suspend : c->n_resume_next;
     c->n_resume_next = 0;
     const unsigned long long left = total > c->next_pid ? total - c->next_pid : 0;
     const unsigned long long room = cap > c->n_resume ? cap - c->n_resume : 0;
@@ -475,19 +476,102 @@ __global__ void __launch_bounds__(kWaveBlock, 1) k_sur_scatter(const __grid_cons
     flush_counters(P.sur.ctl, s_cnt, v, 4, which);
 }
 
+// Source tally of queued table-path segments: one (record, camera) row per lane,
+// the mixture table and the cameras in shared memory; a record's cameras are one
+// contiguous FP64 bulk reduction into S[cell].  Same arithmetic as the in-place
+// tally of k_transport (table_matrix, plane_rotation, apply_plane), with every
+// lane of the warp busy.
+constexpr int kTabBlock = 256;
+__global__ void __launch_bounds__(kTabBlock) k_tab_tally(const __grid_constant__ TransportParams P) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    float4* s_mix = reinterpret_cast<float4*>(sm);
+    const int n_mix = 2 * P.t.n_theta;
+    float* s_cam = reinterpret_cast<float*>(s_mix + n_mix);
+    double* s_stage = reinterpret_cast<double*>(s_cam + 12 * kMaxCams);
+    for (int i = threadIdx.x; i < n_mix; i += blockDim.x) s_mix[i] = P.t.mix[i];
+    for (int i = threadIdx.x; i < 12 * P.n_cam; i += blockDim.x) {
+        const CameraDev& cd = P.cam[i / 12];
+        const int e = i % 12, v = e / 4, w = e % 4;
+        s_cam[i] = w == 3 ? 0.f : (float)(v == 0 ? cd.dir[w] : (v == 1 ? cd.th[w] : cd.ph[w]));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    double* stage = s_stage + (threadIdx.x >> 5) * 32 * 4;
+    const unsigned long long nreq = P.sur.ctl->n_records;
+    const unsigned long long nrec = nreq < P.sur.rec_cap ? nreq : P.sur.rec_cap;
+    const int ncam = P.n_cam;
+    const int ncp = ncam <= 1 ? 1 : (ncam <= 2 ? 2 : (ncam <= 4 ? 4 : (ncam <= 8 ? 8 : 16)));
+    const int per_tile = 32 / ncp;
+    const unsigned long long ntile = (nrec + per_tile - 1) / per_tile;
+    for (unsigned long long tile = (unsigned long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntile;
+         tile += (unsigned long long)gridDim.x * wpb) {
+        bulk_wait_read();  // this lane's reductions of the previous tile have read the staging rows
+        __syncwarp();
+        const int cam = lane % ncp;
+        const unsigned long long rec = tile * per_tile + (unsigned)(lane / ncp);
+        bool valid = false;
+        unsigned cell = 0;
+        if (rec < nrec) {
+            const float4* r = P.sur.records + rec * kTableRecordF4;
+            const float4 r0 = r[0], r1 = r[1];
+            cell = __float_as_uint(r1.w);
+            valid = cam < ncam && cell != 0xffffffffu;
+            if (valid) {
+                const V3<float> n{r0.x, r0.y, r0.z};
+                const float W[4] = {r0.w, r1.x, r1.y, r1.z};
+                V3<float> th, ph, Om, thc, phc;
+                stokes_basis(n, th, ph);
+                load_camera(s_cam + 12 * cam, Om, thc, phc);
+                float Pm[6], Y[4];
+                table_matrix(s_mix, P.t.n_theta, dot(n, Om), Pm);
+                const PlaneRot<float> pr = plane_rotation(n, th, ph, Om, thc, phc);
+                apply_plane(pr, Pm, W, Y);
+                double2* d2 = reinterpret_cast<double2*>(stage + lane * 4);
+                d2[0] = make_double2(widen(Y[0]), widen(Y[1]));
+                d2[1] = make_double2(widen(Y[2]), widen(Y[3]));
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+        }
+        __syncwarp();
+        if (valid && cam == 0)
+            bulk_reduce_add_f64(P.S + (size_t)cell * (size_t)ncam * 4, stage + lane * 4, (unsigned)ncam * 32u);
+    }
+    bulk_wait_all();
+}
+
+size_t tab_tally_smem(const TransportParams& p) {
+    return (size_t)2 * p.t.n_theta * sizeof(float4) + 12 * kMaxCams * sizeof(float) +
+           (size_t)(kTabBlock / 32) * 32 * 4 * sizeof(double);
+}
+
 }  // namespace
 
-cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned long long cap, int* iterations,
-                                    float* ms_out, float* ms_kernels, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_sur_tally, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallySmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sur_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatSmem);
+cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm, unsigned long long cap,
+                                int* iterations, float* ms_out, float* ms_kernels, cudaStream_t s) {
+    const bool sur = model == kScatSurrogate;
+    TransportParams p = p_in;
+    p.sur.deferred = model;
+    cudaError_t e = cudaSuccess;
+    int tab_grid = n_sm;
+    const size_t tab_smem = tab_tally_smem(p);
+    if (sur) {
+        e = cudaFuncSetAttribute(k_sur_tally, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallySmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sur_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatSmem);
+    } else {
+        if (tab_smem > 48 * 1024)
+            e = cudaFuncSetAttribute(k_tab_tally, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_smem);
+        int nb = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tab_tally, kTabBlock, tab_smem);
+        tab_grid = n_sm * (nb > 0 ? nb : 1);
+    }
     if (e != cudaSuccess) return e;
     const unsigned long long total = (unsigned long long)(p.pid_end - p.pid_begin);
     const int block = 128;
     const size_t tsmem = transport_smem_bytes(p, MCRT_FP32, block);
-    const int bps = transport_max_blocks_per_sm(MCRT_FP32, kScatSurrogate, false, block, tsmem);
+    const int bps = transport_max_blocks_per_sm(MCRT_FP32, model, false, block, tsmem);
     const int tgrid = n_sm * bps;
+    float4* const bufs[2] = {p_in.sur.resume, p_in.sur.suspend};
     cudaEvent_t e0 = nullptr, e1 = nullptr, ek[4] = {nullptr, nullptr, nullptr, nullptr};
     e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -505,17 +589,24 @@ cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned
             e = cudaErrorUnknown;
             break;
         }
-        k_wave_begin<<<1, 1, 0, s>>>(p.sur.ctl, total, C);
+        if (!sur) {  // parked packets wait in the other buffer: the two swap roles every round
+            p.sur.resume = bufs[it & 1];
+            p.sur.suspend = bufs[(it + 1) & 1];
+        }
+        k_wave_begin<<<1, 1, 0, s>>>(p.sur.ctl, total, C, sur ? 0 : 1);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ek[0], s);
         if (e == cudaSuccess) e = launch_transport(p, MCRT_FP32, block, tgrid, s);
         if (e == cudaSuccess) e = cudaEventRecord(ek[1], s);
         if (e == cudaSuccess) {
-            k_sur_tally<<<n_sm, kWaveBlock, kTallySmem, s>>>(p);
+            if (sur)
+                k_sur_tally<<<n_sm, kWaveBlock, kTallySmem, s>>>(p);
+            else
+                k_tab_tally<<<tab_grid, kTabBlock, tab_smem, s>>>(p);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(ek[2], s);
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && sur) {
             k_sur_scatter<<<n_sm, kWaveBlock, kScatSmem, s>>>(p);
             e = cudaGetLastError();
         }
@@ -528,14 +619,17 @@ cudaError_t run_surrogate_transport(const TransportParams& p, int n_sm, unsigned
             kms[k] += t;
         }
         if (e != cudaSuccess) break;
-        if (h.n_resume_next == 0 && h.next_pid + h.n_new >= total) {
+        const unsigned long long waiting = sur ? h.n_resume_next : h.n_suspend;
+        if (waiting == 0 && h.next_pid + h.n_new >= total) {
             ++it;
             break;
         }
-        // keep the next round's records within the queue: capacity from this
-        // round's records per work item, with a factor 2 of headroom
+        // surrogate rounds end at each packet's scattering: keep their records within
+        // the queue (capacity from this round's records per work item, factor 2 of
+        // headroom).  Table rounds run packets to their end and are meant to stop on a
+        // full queue, which parks what is left: they keep the full capacity.
         const unsigned long long items = h.n_resume + h.n_new;
-        if (items > 0 && h.n_records > 0) {
+        if (sur && items > 0 && h.n_records > 0) {
             const double per = (double)h.n_records / (double)items;
             double want = 0.5 * (double)p.sur.rec_cap / per;
             if (want > (double)cap) want = (double)cap;
