@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--inline-tally", action="store_true",
                     help="table path: tally inside the transport kernel instead of a tally kernel per round")
+    ap.add_argument("--tally-bps", type=int, default=0,
+                    help="table rounds: > 0 overlaps each tally (this many blocks per SM) with the next transport")
+    ap.add_argument("--transport-bps", type=int, default=0, help="table rounds: transport blocks per SM (0: auto)")
     ap.add_argument("--sur-steps", type=int, default=1, help="timed launches of the surrogate path")
     ap.add_argument("--sur-train-samples", type=float, default=2e7, help="training samples of the network")
     ap.add_argument("--sur-bound", type=float, default=0.05, help="error-map bound of the table fallback")
@@ -336,7 +339,8 @@ def main():
     imgs = torch.empty((n_cam, 4, npix[1], npix[0]), dtype=torch.float64, device="cuda")
 
     def step(seed):
-        st = M.launch(mdl, dict(run, seed=seed), precision="fp32", inline_tally=args.inline_tally)
+        st = M.launch(mdl, dict(run, seed=seed), precision="fp32", inline_tally=args.inline_tally,
+                      tally_blocks_per_sm=args.tally_bps, blocks_per_sm=args.transport_bps)
         for k in range(n_cam):
             mdl.image(k, imgs[k])
         return st

@@ -129,6 +129,11 @@ typedef struct {
                                      network attached with mcrt_set_surrogate (FP32, one
                                      model, no time budget) */
     int32_t flags;                /* MCRT_FLAG_* */
+    int32_t tally_blocks_per_sm;  /* FP32 table rounds: 0 runs each round's transport and tally
+                                     kernels one after the other (default); > 0 runs a round's
+                                     tally, with this many blocks per SM, beside the next round's
+                                     transport, whose blocks per SM are then blocks_per_sm (0 = its
+                                     maximum minus 2).  Measured slower on the disk workload. */
 } mcrt_launch_desc;
 
 /* Totals of a launch (FP64 sums over packets). */

@@ -55,6 +55,7 @@ struct mcrt_ctx {
     int last_optics = MCRT_OPTICS_TABLES;
     // surrogate launches: control block, tally records, waiting packets
     WaveCtl* d_wave = nullptr;
+    cudaStream_t tally_stream = nullptr;  // table rounds: tally kernels beside the next transport
     float4* d_records = nullptr;
     unsigned long long rec_cap = 0;
     float4 *d_susp = nullptr, *d_res = nullptr;
@@ -664,9 +665,28 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
         P.sur.resume = ctx->d_res;
         int n_rounds = 0;
         float ms = 0.f, kms[3] = {0.f, 0.f, 0.f};
-        if (work > 0)
+        // overlap of a round's tally with the next transport is opt-in: measured slower on the
+        // disk (the latency-bound transport slows down under the tally's DRAM traffic)
+        const bool overlap = !sur && d->tally_blocks_per_sm > 0;
+        if (overlap && !ctx->tally_stream) {
+            int lo = 0, hi = 0;
+            CK(ctx, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            CK(ctx, cudaStreamCreateWithPriority(&ctx->tally_stream, cudaStreamNonBlocking, hi));
+        }
+        if (work > 0 && overlap) {
+            // the transport leaves room on every SM for the tally kernels of the round before
+            P.sur.deferred = kScatTableDeferred;
+            const size_t tsm = transport_smem_bytes(P, MCRT_FP32, 128);
+            const int bmax = transport_max_blocks_per_sm(MCRT_FP32, kScatTableDeferred, false, 128, tsm);
+            int tbps = d->blocks_per_sm > 0 ? d->blocks_per_sm : (bmax > 2 ? bmax - 2 : 1);
+            if (tbps > bmax) tbps = bmax;
+            const int abps = d->tally_blocks_per_sm;
+            CK(ctx, run_table_rounds_overlapped(P, ctx->n_sm, cap, tbps, abps, &n_rounds, &ms, kms, ctx->stream,
+                                                ctx->tally_stream));
+        } else if (work > 0) {
             CK(ctx, run_round_transport(P, sur ? kScatSurrogate : kScatTableDeferred, ctx->n_sm, cap, &n_rounds, &ms,
                                         kms, ctx->stream));
+        }
         ctx->launched = true;
         ctx->last_optics = sur ? MCRT_OPTICS_SURROGATE : MCRT_OPTICS_TABLES;
         if (trace_host)
@@ -817,6 +837,7 @@ mcrt_status mcrt_destroy(mcrt_ctx* ctx) {
     cudaFree(ctx->d_absorbed);
     cudaFree(ctx->d_work);
     free_wave(ctx);
+    if (ctx->tally_stream) cudaStreamDestroy(ctx->tally_stream);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;

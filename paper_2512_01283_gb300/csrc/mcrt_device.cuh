@@ -143,6 +143,9 @@ template <typename T> __device__ __forceinline__ void stokes_basis(const V3<T>& 
 
 __device__ __forceinline__ float t_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double t_rcp(double x) { return 1.0 / x; }
+// quotient: the fast reciprocal-based form in FP32 (about 2 ulp), exact in FP64
+__device__ __forceinline__ float t_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double t_div(double a, double b) { return a / b; }
 
 // (cos 2psi, sin 2psi) from any (A, B) proportional to (cos psi, sin psi); (1, 0)
 // for A = B = 0.  Tiny inputs are rescaled first so that 1/r cannot overflow.
@@ -202,7 +205,7 @@ __device__ __forceinline__ GrainFrame<T> grain_frame(const float4& q, const V3<T
 // E(x) = (1 - e^{-x}) / x
 template <typename T> __device__ __forceinline__ T e1(T x) {
     if (fabs(x) < T(1e-4)) return T(1) - x * (T(0.5) - x * T(1.0 / 6.0));
-    return -t_expm1(-x) / x;
+    return t_div(-t_expm1(-x), x);
 }
 
 // int_0^1 e^{-(x - i y) s} ds = (re, im)
@@ -223,7 +226,7 @@ template <typename T> __device__ __forceinline__ void e1_complex(T x, T y, T& re
     const T ex = t_exp(-x);
     const T nr = -t_expm1(-x) + T(2) * ex * sh * sh;  // 1 - e^{-x} cos y
     const T ni = ex * sy;                               // e^{-x} sin y
-    const T den = T(1) / (x * x + y * y);
+    const T den = t_rcp(x * x + y * y);
     re = (nr * x + ni * y) * den;
     im = (nr * y - ni * x) * den;
     (void)cy;

@@ -89,7 +89,8 @@ struct WaveCtl {
     unsigned long long n_resume;       // packets to resume in the current transport launch
     unsigned long long n_resume_next;  // packets written to the resume buffer by the scattering kernel
     unsigned long long n_suspend;      // packets suspended at a scattering by the current launch
-    unsigned long long n_records;      // tally records requested by the current launch
+    unsigned long long n_rec[2];       // tally records requested per record buffer (the table
+                                       // rounds alternate two buffers; the surrogate uses [0])
     unsigned long long full;           // the record queue passed its soft limit: packets park
     // totals: network rows (tally, scattering), fallbacks (error map, realizability),
     // tally segments tallied in place for want of record space, envelope misses
@@ -110,6 +111,7 @@ struct SurrogateDev {
     float4* suspend;             // [cap][kStateF4]
     float4* resume;              // [cap][kStateF4]
     int deferred;                // which round-based instantiation runs (kScat* id), 0: none
+    int rec_slot;                // record buffer (and counter n_rec[rec_slot]) of this launch
 };
 
 struct TransportParams {
@@ -180,6 +182,12 @@ cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* i
 // ms_kernels[3]: summed times of the transport, tally and scattering kernels
 cudaError_t run_round_transport(const TransportParams& p, int model, int n_sm, unsigned long long cap,
                                 int* iterations, float* ms_out, float* ms_kernels, cudaStream_t s);
+// table rounds with the tally of round r on stream s2 overlapping the transport of
+// round r+1 on s: tbps transport blocks and tally_bps tally blocks per SM; the record
+// queue (p.sur.records, capacity p.sur.rec_cap each) is two buffers back to back
+cudaError_t run_table_rounds_overlapped(const TransportParams& p, int n_sm, unsigned long long cap, int tbps,
+                                        int tally_bps, int* iterations, float* ms_out, float* ms_kernels,
+                                        cudaStream_t s, cudaStream_t s2);
 
 }  // namespace mcrt
 

@@ -82,7 +82,8 @@ template <typename T> struct Packet {
     T X0, X1, X2, X3;
     T I_birth, e_abs, e_gain;
     T s_flight;  // surrogate path: grain-size coordinate of the current flight's tally
-    bool park;   // surrogate path: stop after this segment (record queue near its end)
+    bool park;     // round-based paths: stop before the next segment (record queue near its end)
+    bool pending;  // a scattering waits for the warp's next scattering phase
     double tau;  // remaining scattering optical depth (FP64 running sum)
     long long pid;
     const JobDev* job;  // batched launches: the packet's job
@@ -262,6 +263,7 @@ __device__ __forceinline__ void load_state(const float4* d, Packet<float>& pk) {
     pk.iz = __float_as_int(k.x);
     pk.job = nullptr;
     pk.park = false;
+    pk.pending = false;
 }
 
 }  // namespace

@@ -34,6 +34,14 @@ constexpr int kDefaultBlock = 128;
 #ifndef MCRT_MIN_BLOCKS
 #define MCRT_MIN_BLOCKS 5
 #endif
+// lanes of a warp that wait before the warp runs the scattering code (or takes new
+// packets) for all of them at once
+#ifndef MCRT_SCATTER_BATCH
+#define MCRT_SCATTER_BATCH 8
+#endif
+#ifndef MCRT_REFILL_BATCH
+#define MCRT_REFILL_BATCH 4
+#endif
 // per-thread staging slot for the TMA bulk reduction of one segment's source
 // contributions: up to 8 cameras x 4 Stokes FP64 (256 B), padded to 272 B so that
 // the 16-byte stores of a warp spread over all shared-memory banks
@@ -204,6 +212,7 @@ __device__ bool emit(const TransportParams& P, const JobRef<T, B>& job, long lon
     pk.pid = pid;
     pk.src = s;
     pk.s_flight = flight_size(job.t(), u1.d);
+    pk.pending = false;
     pk.events = 1;
     pk.n_seg = pk.n_sca = pk.n_tally = pk.n_abs = pk.trials = 0;
     pk.e_abs = pk.e_gain = T(0);
@@ -290,7 +299,7 @@ __device__ __forceinline__ T exit_face(const J& job, const Packet<T>& pk, int& a
     face = T(0);
     if (pk.nx != T(0)) {
         const T f = job.lo(0) + T(pk.nx > T(0) ? pk.ix + 1 : pk.ix) * job.d(0);
-        T t = (f - pk.px) / pk.nx;
+        T t = t_div(f - pk.px, pk.nx);
         t = t < T(0) ? T(0) : t;
         if (t < best) {
             best = t;
@@ -300,7 +309,7 @@ __device__ __forceinline__ T exit_face(const J& job, const Packet<T>& pk, int& a
     }
     if (pk.ny != T(0)) {
         const T f = job.lo(1) + T(pk.ny > T(0) ? pk.iy + 1 : pk.iy) * job.d(1);
-        T t = (f - pk.py) / pk.ny;
+        T t = t_div(f - pk.py, pk.ny);
         t = t < T(0) ? T(0) : t;
         if (t < best) {
             best = t;
@@ -310,7 +319,7 @@ __device__ __forceinline__ T exit_face(const J& job, const Packet<T>& pk, int& a
     }
     if (pk.nz != T(0)) {
         const T f = job.lo(2) + T(pk.nz > T(0) ? pk.iz + 1 : pk.iz) * job.d(2);
-        T t = (f - pk.pz) / pk.nz;
+        T t = t_div(f - pk.pz, pk.nz);
         t = t < T(0) ? T(0) : t;
         if (t < best) {
             best = t;
@@ -372,7 +381,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         alive = false;
         return;
     }
-    const T omega = kext > T(0) ? ks / kext : T(0);
+    const T omega = kext > T(0) ? t_div(ks, kext) : T(0);
     const T dsca_exit = ks * ell_exit;
     const bool scatter_here = (ks > T(0)) && (pk.tau < widen(dsca_exit));
     const T ell = scatter_here ? T(pk.tau) / ks : ell_exit;
@@ -442,7 +451,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
                 const int lead = __ffs(actS) - 1;
                 const unsigned cnt = (unsigned)__popc(actS);
                 unsigned long long base = 0;
-                if (lane == lead) base = atomicAdd(&P.sur.ctl->n_records, (unsigned long long)cnt);
+                if (lane == lead) base = atomicAdd(&P.sur.ctl->n_rec[P.sur.rec_slot], (unsigned long long)cnt);
                 base = __shfl_sync(actS, base, lead);
                 const unsigned long long idx = base + (unsigned)__popc(actS & ((1u << lane) - 1u));
                 queued = base + cnt <= P.sur.rec_cap;
@@ -558,6 +567,20 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         alive = false;
         return;
     }
+    // the rejection sampling waits until enough lanes of the warp need it (scatter_event)
+    pk.pending = true;
+}
+
+// Scattering of a packet at its current position (Sec. 2.2): roulette, size bin, then
+// rejection sampling of the new direction; run for the warp's waiting lanes together.
+template <typename T, int SCAT, bool B>
+__device__ __forceinline__ void scatter_event(const TransportParams& P, const Smem<T>& sm, Packet<T>& pk, bool& alive,
+                                              BlockTotals& bt) {
+    const JobRef<T, B> job = job_of<T, B>(P, sm, pk);
+    const TablesDev& tabs = job.t();
+    const V3<T> n{pk.nx, pk.ny, pk.nz};
+    V3<T> th, ph;
+    stokes_basis(n, th, ph);
     const Draw4<T> us = draw4<T>(pk.pid, pk.n_sca, 0u, P.seed, job.stream());
     if (P.roulette_thr > 0.0 && (double)pk.X0 < P.roulette_thr * (double)pk.I_birth) {
         if ((double)us.b < P.roulette_surv) {
@@ -715,8 +738,13 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
     }
 
     for (;;) {
+        // dead lanes take new work in groups, so that the birth code runs for several
+        // lanes at once (or when no lane can move otherwise)
+        const unsigned need = __ballot_sync(kFull, !alive && !pool_done);
+        const unsigned busy = __ballot_sync(kFull, alive && !pk.pending);
+        const bool refill = need != 0u && (__popc(need) >= MCRT_REFILL_BATCH || busy == 0u);
         if constexpr (round_based(SCAT)) {
-            if (!alive && !pool_done) {
+            if (refill && !alive && !pool_done) {
                 cg::coalesced_group grp = cg::coalesced_threads();
                 unsigned long long base = 0;
                 if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->claim, (unsigned long long)grp.size());
@@ -741,11 +769,11 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
                 }
                 if (alive && (full || stop)) park_packet(P, pk, alive);
             }
-            if (alive && pk.park) {  // before the next segment, outside the warp's collective steps
+            if (alive && pk.park && !pk.pending) {  // before the next segment, outside collective steps
                 stop = true;
                 park_packet(P, pk, alive);
             }
-        } else if (!alive && !pool_done) {
+        } else if (refill && !alive && !pool_done) {
             cg::coalesced_group grp = cg::coalesced_threads();
             unsigned long long base = 0;
             if (grp.thread_rank() == 0) base = atomicAdd(P.counter, (unsigned long long)grp.size());
@@ -769,12 +797,23 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
                 alive = emit<T, false>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
             }
         }
-        const unsigned work = __ballot_sync(kFull, alive);
-        if (work == 0u) {
+        const unsigned pend = __ballot_sync(kFull, alive && pk.pending);
+        const unsigned work = __ballot_sync(kFull, alive && !pk.pending);
+        if (work == 0u && pend == 0u) {
             if (__all_sync(kFull, pool_done)) break;
             continue;
         }
-        if (alive) step<T, SCAT, B>(P, sm, pk, alive, bt, work);
+        // scatterings of the warp run together once enough lanes wait for one
+        if (pend != 0u && (__popc(pend) >= MCRT_SCATTER_BATCH || work == 0u)) {
+            if constexpr (SCAT != kScatSurrogate) {  // the surrogate scatters in its own kernel
+                if (alive && pk.pending) {
+                    pk.pending = false;
+                    scatter_event<T, SCAT, B>(P, sm, pk, alive, bt);
+                }
+            }
+            continue;
+        }
+        if (alive && !pk.pending) step<T, SCAT, B>(P, sm, pk, alive, bt, work);
     }
 
     bulk_wait_all();  // this thread's reductions have completed before the block ends

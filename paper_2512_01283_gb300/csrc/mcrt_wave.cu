@@ -85,7 +85,7 @@ __device__ __forceinline__ bool map_says_fallback(const SurrogateDev& s, const V
 // waiting from the previous round become this round's resume list (written by the
 // scattering kernel, or, with swap, the previous transport's suspend buffer itself),
 // and new packets fill the capacity left.
-__global__ void k_wave_begin(WaveCtl* c, unsigned long long total, unsigned long long cap, int swap) {
+__global__ void k_wave_begin(WaveCtl* c, unsigned long long total, unsigned long long cap, int swap, int slot) {
     c->next_pid += c->n_new;
     c->n_resume = swap ? c->n_suspend : c->n_resume_next;
     c->n_resume_next = 0;
@@ -94,7 +94,7 @@ __global__ void k_wave_begin(WaveCtl* c, unsigned long long total, unsigned long
     c->n_new = left < room ? left : room;
     c->claim = 0;
     c->n_suspend = 0;
-    c->n_records = 0;
+    c->n_rec[slot] = 0;
     c->full = 0;
     c->cnt[kCntIterations] += 1;
 }
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kWaveBlock, 1) k_sur_tally(const __grid_consta
     __syncthreads();
     TallyWarp& tw = reinterpret_cast<TallyWarp*>(sm + mlp::kImgBytes + kCamBytes)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    const unsigned long long nreq = P.sur.ctl->n_records;
+    const unsigned long long nreq = P.sur.ctl->n_rec[P.sur.rec_slot];
     const unsigned long long nrec = nreq < P.sur.rec_cap ? nreq : P.sur.rec_cap;
     const int ncam = P.n_cam;
     const int ncp = ncam <= 1 ? 1 : (ncam <= 2 ? 2 : (ncam <= 4 ? 4 : (ncam <= 8 ? 8 : 16)));
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(kTabBlock) k_tab_tally(const __grid_constant__
     __syncthreads();
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     double* stage = s_stage + (threadIdx.x >> 5) * 32 * 4;
-    const unsigned long long nreq = P.sur.ctl->n_records;
+    const unsigned long long nreq = P.sur.ctl->n_rec[P.sur.rec_slot];
     const unsigned long long nrec = nreq < P.sur.rec_cap ? nreq : P.sur.rec_cap;
     const int ncam = P.n_cam;
     const int ncp = ncam <= 1 ? 1 : (ncam <= 2 ? 2 : (ncam <= 4 ? 4 : (ncam <= 8 ? 8 : 16)));
@@ -551,6 +551,7 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
     const bool sur = model == kScatSurrogate;
     TransportParams p = p_in;
     p.sur.deferred = model;
+    p.sur.rec_slot = 0;
     cudaError_t e = cudaSuccess;
     int tab_grid = n_sm;
     const size_t tab_smem = tab_tally_smem(p);
@@ -593,7 +594,7 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
             p.sur.resume = bufs[it & 1];
             p.sur.suspend = bufs[(it + 1) & 1];
         }
-        k_wave_begin<<<1, 1, 0, s>>>(p.sur.ctl, total, C, sur ? 0 : 1);
+        k_wave_begin<<<1, 1, 0, s>>>(p.sur.ctl, total, C, sur ? 0 : 1, 0);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ek[0], s);
         if (e == cudaSuccess) e = launch_transport(p, MCRT_FP32, block, tgrid, s);
@@ -629,8 +630,8 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
         // headroom).  Table rounds run packets to their end and are meant to stop on a
         // full queue, which parks what is left: they keep the full capacity.
         const unsigned long long items = h.n_resume + h.n_new;
-        if (sur && items > 0 && h.n_records > 0) {
-            const double per = (double)h.n_records / (double)items;
+        if (sur && items > 0 && h.n_rec[0] > 0) {
+            const double per = (double)h.n_rec[0] / (double)items;
             double want = 0.5 * (double)p.sur.rec_cap / per;
             if (want > (double)cap) want = (double)cap;
             if (want < 1024.0) want = 1024.0;
@@ -645,6 +646,105 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
     if (e1) cudaEventDestroy(e1);
     for (int k = 0; k < 4; ++k)
         if (ek[k]) cudaEventDestroy(ek[k]);
+    if (iterations) *iterations = it;
+    if (ms_out) *ms_out = ms;
+    if (ms_kernels)
+        for (int k = 0; k < 3; ++k) ms_kernels[k] = kms[k];
+    return e;
+}
+
+cudaError_t run_table_rounds_overlapped(const TransportParams& p_in, int n_sm, unsigned long long cap, int tbps,
+                                        int tally_bps, int* iterations, float* ms_out, float* ms_kernels,
+                                        cudaStream_t s, cudaStream_t s2) {
+    TransportParams p = p_in;
+    p.sur.deferred = kScatTableDeferred;
+    const size_t tab_smem = tab_tally_smem(p);
+    cudaError_t e = cudaSuccess;
+    if (tab_smem > 48 * 1024)
+        e = cudaFuncSetAttribute(k_tab_tally, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_smem);
+    if (e != cudaSuccess) return e;
+    const unsigned long long total = (unsigned long long)(p.pid_end - p.pid_begin);
+    const int tgrid = n_sm * (tbps > 0 ? tbps : 1), tab_grid = n_sm * (tally_bps > 0 ? tally_bps : 1);
+    float4* const bufs[2] = {p_in.sur.resume, p_in.sur.suspend};
+    float4* const recs[2] = {p_in.sur.records, p_in.sur.records + p_in.sur.rec_cap * kTableRecordF4};
+    cudaEvent_t e0 = nullptr, e1 = nullptr, tb = nullptr, te = nullptr, join = nullptr;
+    cudaEvent_t ab[2] = {nullptr, nullptr}, ae[2] = {nullptr, nullptr};
+    e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventCreate(&tb);
+    if (e == cudaSuccess) e = cudaEventCreate(&te);
+    if (e == cudaSuccess) e = cudaEventCreate(&join);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        e = cudaEventCreate(&ab[k]);
+        if (e == cudaSuccess) e = cudaEventCreate(&ae[k]);
+    }
+    float kms[3] = {0.f, 0.f, 0.f};
+    bool pending[2] = {false, false};  // a tally kernel of this slot has not been accounted yet
+    auto account = [&](int slot) -> cudaError_t {
+        if (!pending[slot]) return cudaSuccess;
+        cudaError_t r = cudaEventSynchronize(ae[slot]);
+        float t = 0.f;
+        if (r == cudaSuccess) r = cudaEventElapsedTime(&t, ab[slot], ae[slot]);
+        kms[1] += t;
+        pending[slot] = false;
+        return r;
+    };
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.sur.ctl, 0, sizeof(WaveCtl), s);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    const long long max_rounds = p.max_events + (long long)(total / 256) + 1000;
+    WaveCtl h{};
+    int it = 0;
+    for (; e == cudaSuccess; ++it) {
+        if (it >= max_rounds) {
+            e = cudaErrorUnknown;
+            break;
+        }
+        const int slot = it & 1;
+        // the tally of round it-2 read this slot's records and counter
+        if (pending[slot]) e = cudaStreamWaitEvent(s, ae[slot], 0);
+        if (e == cudaSuccess) e = account(slot);
+        p.sur.resume = bufs[it & 1];
+        p.sur.suspend = bufs[(it + 1) & 1];
+        p.sur.records = recs[slot];
+        p.sur.rec_slot = slot;
+        if (e == cudaSuccess) {
+            k_wave_begin<<<1, 1, 0, s>>>(p.sur.ctl, total, cap, 1, slot);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(tb, s);
+        if (e == cudaSuccess) e = launch_transport(p, MCRT_FP32, 128, tgrid, s);
+        if (e == cudaSuccess) e = cudaEventRecord(te, s);
+        // this round's tally runs beside the next round's transport
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, te, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(ab[slot], s2);
+        if (e == cudaSuccess) {
+            k_tab_tally<<<tab_grid, kTabBlock, tab_smem, s2>>>(p);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ae[slot], s2);
+        if (e == cudaSuccess) pending[slot] = true;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, p.sur.ctl, sizeof(WaveCtl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, tb, te);
+        kms[0] += t;
+        if (e != cudaSuccess) break;
+        if (h.n_suspend == 0 && h.next_pid + h.n_new >= total) {
+            ++it;
+            break;
+        }
+    }
+    // the last tallies join the main stream before the end of the launch
+    if (e == cudaSuccess) e = cudaEventRecord(join, s2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = account(k);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEvent_t all[] = {e0, e1, tb, te, join, ab[0], ab[1], ae[0], ae[1]};
+    for (cudaEvent_t x : all)
+        if (x) cudaEventDestroy(x);
     if (iterations) *iterations = it;
     if (ms_out) *ms_out = ms;
     if (ms_kernels)

@@ -48,7 +48,8 @@ class LaunchDesc(C.Structure):
                 ("roulette_threshold", C.c_double), ("roulette_survival", C.c_double),
                 ("max_events", C.c_int64), ("max_trials", C.c_int32), ("block_size", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("time_budget_s", C.c_double),
-                ("n_trace", C.c_int64), ("trace", C.c_void_p), ("optics", C.c_int32), ("flags", C.c_int32)]
+                ("n_trace", C.c_int64), ("trace", C.c_void_p), ("optics", C.c_int32), ("flags", C.c_int32),
+                ("tally_blocks_per_sm", C.c_int32)]
 
 FLAG_INLINE_TALLY = 1
 
@@ -275,6 +276,7 @@ def make_desc(run: dict, precision="fp32", trace=None, n_trace=0, default_center
     d.time_budget_s = float(kw.get("time_budget_s", 0.0))
     d.optics = OPTICS[kw.get("optics", "tables")]
     d.flags = FLAG_INLINE_TALLY if kw.get("inline_tally", False) else 0
+    d.tally_blocks_per_sm = int(kw.get("tally_blocks_per_sm", 0))
     if trace is not None:
         p, k = _ptr(trace, np.float64)
         keep.append(k)
