@@ -244,7 +244,8 @@ def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_v
     other = np.zeros_like(imgs)
     table_step(2000 + args.steps, other)
     out = {"workload": "flared disk %d^3 as the table line, grain optics from the MLP surrogate (7 -> 128 x 4 -> 20, "
-                       "SiLU, BF16 weights, FP32 accumulation, mma.sync m16n8k16), trained on %.0e samples from the "
+                       "SiLU, BF16 weights, FP32 accumulation; tally on tcgen05, rejection trials on mma.sync), "
+                       "trained on %.0e samples from the "
                        "tables, table fallback above error bound %g; %.0e packets"
                        % (args.grid, n_train * 2048, args.sur_bound, args.packets),
            "value": value, "unit": UNIT, "ms_per_step": 1e3 * wall / args.sur_steps,
@@ -260,7 +261,8 @@ def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_v
            "mlp_tflops_over_launch": rows * flop_row / (wall / args.sur_steps) / 1e12,
            "kernel_ms": {"transport": st["ms_transport"], "tally": st["ms_tally"], "scatter": st["ms_scatter"],
                          "rounds_total": st["kernel_ms"]},
-           "roofline": {"bound": "tensor", "kernel": "k_sur_tally (mma.sync m16n8k16 BF16, FP32 accumulate)",
+           "roofline": {"bound": "tensor", "kernel": "k_sur_tally_tc (tcgen05.mma kind::f16, BF16 x BF16 -> FP32 in "
+                                                     "tensor memory, 3 tiles of 128 rows in flight per SM)",
                         "achieved": st["mlp_tally_rows"] * flop_row / (st["ms_tally"] * 1e-3) / 1e12,
                         "peak": peak_bf16, "unit": "TFLOP/s",
                         "frac": st["mlp_tally_rows"] * flop_row / (st["ms_tally"] * 1e-3) / 1e12 / peak_bf16,

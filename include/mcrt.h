@@ -62,8 +62,10 @@ enum { MCRT_FP32 = 0, MCRT_FP64 = 1 };
 enum { MCRT_OPTICS_TABLES = 0, MCRT_OPTICS_SURROGATE = 1 };
 /* Launch flags (mcrt_launch_desc.flags). */
 enum {
-    MCRT_FLAG_INLINE_TALLY = 1 /* FP32 table launches: tally inside the transport kernel instead of the
-                                  default rounds (transport, then a tally kernel over the queued segments) */
+    MCRT_FLAG_INLINE_TALLY = 1,  /* FP32 table launches: tally inside the transport kernel instead of the
+                                    default rounds (transport, then a tally kernel over the queued segments) */
+    MCRT_FLAG_MMA_SYNC_TALLY = 2 /* surrogate launches: the network of the tally on warp-level mma.sync
+                                    instead of the default 5th-generation tensor cores (tcgen05) */
 };
 enum { MCRT_MAX_SOURCES = 8, MCRT_MAX_CAMERAS = 16 };
 
@@ -71,7 +73,9 @@ enum { MCRT_MAX_SOURCES = 8, MCRT_MAX_CAMERAS = 16 };
 enum {
     MCRT_STATUS_EVENT_CAP = 1u, /* a packet reached max_events */
     MCRT_STATUS_TRIAL_CAP = 2u, /* a scattering found no accepted proposal in max_trials */
-    MCRT_STATUS_TIMEOUT = 4u    /* time budget exhausted before the packet pool */
+    MCRT_STATUS_TIMEOUT = 4u,   /* time budget exhausted before the packet pool */
+    MCRT_STATUS_DEVICE_TIMEOUT = 8u /* a tensor-core operation did not complete in time; the kernel
+                                       stopped and the tallies are incomplete */
 };
 
 /* A packet source (paper Sec. 2.2: packets are emitted, then transported). */
@@ -343,6 +347,18 @@ MCRT_API mcrt_status mcrt_surrogate_destroy(mcrt_surrogate *s); /* NULL-safe */
  * [4096] FP32, nullable) receives it.  Training or setting parameters invalidates it.
  */
 MCRT_API mcrt_status mcrt_surrogate_error_map(mcrt_surrogate *s, int64_t n_samples, float *map);
+
+/*
+ * Evaluation on a chosen tensor-core engine: MCRT_ENGINE_MMA_SYNC (warp-level
+ * mma.sync m16n8k16, the engine of mcrt_surrogate_eval) or MCRT_ENGINE_TCGEN05 (5th-
+ * generation tensor cores: tcgen05.mma with the accumulator in tensor memory, 128
+ * rows per CTA).  Same network, inputs and outputs as mcrt_surrogate_eval; the two
+ * engines differ only in the order of FP32 additions.  MCRT_E_TIMEOUT if a
+ * tensor-core operation did not complete within 2 s (the kernel then stops).
+ */
+enum { MCRT_ENGINE_MMA_SYNC = 0, MCRT_ENGINE_TCGEN05 = 1 };
+MCRT_API mcrt_status mcrt_surrogate_eval_engine(mcrt_surrogate *s, int32_t engine, int64_t n, const float *inputs,
+                                                float *outputs);
 
 /*
  * Attach the network to a model for launches with desc->optics =

@@ -14,6 +14,7 @@
 #include "mcrt.h"
 #include "mcrt_internal.h"
 #include "mcrt_mlp_infer.cuh"
+#include "mcrt_mlp_tc.cuh"
 
 using namespace mcrt;
 
@@ -48,6 +49,7 @@ struct mcrt_ctx {
     // attached surrogate: network image, error map, distilled extinction table
     bool sur_set = false;
     unsigned char* d_sur_image = nullptr;
+    unsigned char* d_sur_image_tc = nullptr;
     float* d_sur_map = nullptr;
     float4* d_sur_kext = nullptr;
     float sur_bound = 0.05f;
@@ -141,9 +143,11 @@ void host_basis(const double n[3], double th[3], double ph[3]) {
 
 void free_surrogate(mcrt_ctx* c) {
     cudaFree(c->d_sur_image);
+    cudaFree(c->d_sur_image_tc);
     cudaFree(c->d_sur_map);
     cudaFree(c->d_sur_kext);
     c->d_sur_image = nullptr;
+    c->d_sur_image_tc = nullptr;
     c->d_sur_map = nullptr;
     c->d_sur_kext = nullptr;
     c->sur_set = false;
@@ -541,6 +545,8 @@ static void add_stats(mcrt_stats* st, const double raw[16], unsigned status, flo
 }
 
 static mcrt_status status_of(mcrt_ctx* ctx, unsigned status) {
+    if (status & MCRT_STATUS_DEVICE_TIMEOUT)
+        return fail(ctx, MCRT_E_TIMEOUT, "mcrt_launch_packets: a tensor-core wait timed out; tallies incomplete");
     if (status & MCRT_STATUS_TIMEOUT) return fail(ctx, MCRT_E_TIMEOUT, "mcrt_launch_packets: time budget exhausted");
     if (status & (MCRT_STATUS_EVENT_CAP | MCRT_STATUS_TRIAL_CAP))
         return fail(ctx, MCRT_E_EVENT_CAP, "mcrt_launch_packets: packets reached the event or trial cap");
@@ -654,6 +660,8 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
             ctx->rec_cap = rec_cap;
         }
         P.sur.image = ctx->d_sur_image;
+        P.sur.image_tc = ctx->d_sur_image_tc;
+        P.sur.tally_engine = (d->flags & MCRT_FLAG_MMA_SYNC_TALLY) ? MCRT_ENGINE_MMA_SYNC : MCRT_ENGINE_TCGEN05;
         P.sur.err_map = ctx->d_sur_map;
         P.sur.bound = ctx->sur_bound;
         P.sur.env_margin = validate ? 0.f : 0.05f;
@@ -805,6 +813,7 @@ mcrt_status mcrt_set_surrogate(mcrt_ctx* ctx, mcrt_surrogate* s, double bound) {
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     if (!ctx->d_sur_image) {
         cudaError_t e = cudaMalloc(&ctx->d_sur_image, mlp::kImgBytes);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->d_sur_image_tc, tc::kImgBytes);
         if (e == cudaSuccess) e = cudaMalloc(&ctx->d_sur_map, sizeof(float) * kErrMapCells);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
@@ -817,8 +826,8 @@ mcrt_status mcrt_set_surrogate(mcrt_ctx* ctx, mcrt_surrogate* s, double bound) {
     CK(ctx, cudaMalloc(&ctx->d_sur_kext, (size_t)ctx->t.n_ktheta * sizeof(float4)));
     ctx->sur_set = false;
     int fixed = 0;
-    const mcrt_status st = mcrt_surrogate_export(s, ctx->t.n_ktheta, ctx->d_kext, ctx->d_sur_image, ctx->d_sur_map,
-                                                 ctx->d_sur_kext, &fixed);
+    const mcrt_status st = mcrt_surrogate_export(s, ctx->t.n_ktheta, ctx->d_kext, ctx->d_sur_image,
+                                                 ctx->d_sur_image_tc, ctx->d_sur_map, ctx->d_sur_kext, &fixed);
     if (st != MCRT_OK) return fail(ctx, st, "mcrt_set_surrogate: %s", mcrt_last_error(nullptr));
     ctx->sur_bound = bound > 0.0 ? (float)bound : (bound < 0.0 ? -1.f : 0.05f);
     ctx->sur_kext_fixed = fixed;

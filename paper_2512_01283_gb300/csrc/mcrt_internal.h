@@ -100,6 +100,8 @@ enum { kCntTallyRows = 0, kCntScatRows, kCntFallbackMap, kCntFallbackReal, kCntO
 
 struct SurrogateDev {
     const unsigned char* image;  // inference image (mcrt_mlp_infer.cuh layout)
+    const unsigned char* image_tc;  // the same network for the tcgen05 engine (mcrt_mlp_tc.cuh)
+    int tally_engine;            // MCRT_ENGINE_* of the tally kernel
     const float* err_map;        // [kErrMapCells] largest error per cell, units of N(s)
     float bound;                 // cells with a larger error use the tables
     float env_margin;            // rejection envelope factor (1 + margin)
@@ -202,4 +204,4 @@ mcrt_status mcrt_fail_noctx(mcrt_status st, const char* fmt, ...);
 // Inference data of a trained surrogate (mcrt_mlp.cu) for a model: inference image,
 // error map and the extinction table distilled on n_ktheta angles.
 mcrt_status mcrt_surrogate_export(mcrt_surrogate* s, int n_ktheta, const float4* table, unsigned char* d_image,
-                                  float* d_map, float4* d_kext, int* n_fixed);
+                                  unsigned char* d_image_tc, float* d_map, float4* d_kext, int* n_fixed);

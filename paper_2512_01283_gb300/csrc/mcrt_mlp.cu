@@ -27,6 +27,7 @@
 #include "mcrt_device.cuh"
 #include "mcrt_internal.h"
 #include "mcrt_mlp_infer.cuh"
+#include "mcrt_mlp_tc.cuh"
 
 namespace mcrt {
 namespace {
@@ -397,6 +398,65 @@ __global__ void k_init_params(float* __restrict__ p, unsigned seed) {
     }
 }
 
+// Inference image for the tcgen05 engine (mcrt_mlp_tc.cuh layout) from the FP32
+// parameters: weights in 8x16-byte core matrices, layer 0 columns 7-13 repeating
+// columns 0-6, output rows 24-31 zero; biases, output ones padded with zeros.  The
+// hidden layers hold W / 2 and b / 2 (exact), so their epilogue gets z / 2 directly.
+__global__ void k_pack_image_tc(const float* __restrict__ p, unsigned char* __restrict__ img) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int l = 0; l < kLayers; ++l) {
+        const int K = l == 0 ? 16 : 128, N = l == kLayers - 1 ? tc::kN4 : 128;
+        __nv_bfloat16* w = reinterpret_cast<__nv_bfloat16*>(img + tc::w_off(l));
+        for (int i = tid; i < N * K; i += nth) {
+            const int r = i / K, k = i % K;
+            float v = 0.f;
+            if (l == 0) {
+                if (k < 2 * kIn) v = p[layer_offset(0) + r * kInPad + (k < kIn ? k : k - kIn)];
+            } else if (r < layer_out(l)) {
+                v = p[layer_offset(l) + r * layer_in(l) + k];
+            }
+            const float half = l < kLayers - 1 ? 0.5f : 1.f;
+            w[tc::core_off(r, k, K) / 2] = __float2bfloat16(v * half);
+        }
+        float* b = reinterpret_cast<float*>(img + tc::kBias) + 128 * l;
+        const float half = l < kLayers - 1 ? 0.5f : 1.f;
+        for (int i = tid; i < N; i += nth)
+            b[i] = i < layer_out(l) ? half * p[layer_offset(l) + layer_out(l) * layer_in(l) + i] : 0.f;
+    }
+}
+
+// outputs [n][20] of inputs [n][7] on the tcgen05 engine: 128 rows per tile, kTcGroups
+// tiles in flight per CTA
+constexpr int kTcGroups = 3;
+__global__ void __launch_bounds__(tc::kRows * kTcGroups, 1)
+    k_infer_tc(const unsigned char* __restrict__ img, long long n, const float* __restrict__ in,
+               float* __restrict__ out, unsigned* __restrict__ error) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) unsigned long long mbar[kTcGroups];
+    __shared__ unsigned tmem_slot;
+    const tc::Group g = tc::setup(kTcGroups, sm, img, mbar, &tmem_slot);
+    unsigned phase = 0;
+    bool failed = false;
+    const long long ntile = (n + tc::kRows - 1) / tc::kRows;
+    const int gi = threadIdx.x / tc::kRows;
+    for (long long tile = (long long)blockIdx.x * kTcGroups + gi; tile < ntile; tile += (long long)gridDim.x * kTcGroups) {
+        const long long row = tile * tc::kRows + g.t;
+        float u[kIn];
+        for (int c = 0; c < kIn; ++c) u[c] = row < n ? in[row * kIn + c] : 0.f;
+        tc::store_input(g, u);
+        float y[24];
+        if (!tc::forward(g, y, phase, 2000000000ull)) {
+            failed = true;
+            if (g.t == 0) atomicOr(error, 1u);
+            break;
+        }
+        if (row < n)
+            for (int o = 0; o < kOut; ++o) out[row * kOut + o] = y[o];
+        tc::group_sync(g);  // every row has read its outputs before the next tile's layer 0
+    }
+    tc::teardown(kTcGroups, g, failed, phase, 2000000000ull);
+}
+
 // ---------------------------------------------------------------------------------
 // fused inference (mcrt_mlp_infer.cuh): evaluation, error map, extinction table
 // ---------------------------------------------------------------------------------
@@ -754,7 +814,7 @@ mcrt_status compute_error_map(mcrt_surrogate* s, long long n_samples) {
 // error map (computed with 2^22 samples if not yet done) and the distilled extinction
 // table on n_ktheta angles (rows that are not realizable come from `table`).
 mcrt_status mcrt_surrogate_export(mcrt_surrogate* s, int n_ktheta, const float4* table, unsigned char* d_image,
-                                  float* d_map, float4* d_kext, int* n_fixed) {
+                                  unsigned char* d_image_tc, float* d_map, float4* d_kext, int* n_fixed) {
     if (!s->map_valid) {
         mcrt_status st = compute_error_map(s, 1ll << 22);
         if (st != MCRT_OK) return st;
@@ -773,6 +833,10 @@ mcrt_status mcrt_surrogate_export(mcrt_surrogate* s, int n_ktheta, const float4*
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_image, s->d_image, mlp::kImgBytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) {
+        k_pack_image_tc<<<64, 256, 0, s->stream>>>(s->d_params, d_image_tc);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_map, s->d_map, sizeof(float) * kErrMapCells, cudaMemcpyDeviceToDevice, s->stream);
     unsigned fixed = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&fixed, d_fixed, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream);
@@ -893,6 +957,49 @@ mcrt_status mcrt_surrogate_eval(mcrt_surrogate* s, int64_t n, const float* input
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     cudaFree(d_out);
     if (e != cudaSuccess) return mcrt_fail_noctx(MCRT_E_CUDA, "mcrt_surrogate_eval: %s", cudaGetErrorString(e));
+    return MCRT_OK;
+}
+
+mcrt_status mcrt_surrogate_eval_engine(mcrt_surrogate* s, int32_t engine, int64_t n, const float* inputs,
+                                       float* outputs) {
+    if (engine == MCRT_ENGINE_MMA_SYNC) return mcrt_surrogate_eval(s, n, inputs, outputs);
+    if (!s || engine != MCRT_ENGINE_TCGEN05 || n < 0 || (n > 0 && (!inputs || !outputs)))
+        return mcrt_fail_noctx(MCRT_E_INVAL, "mcrt_surrogate_eval_engine: bad arguments");
+    if (n == 0) return MCRT_OK;
+    mcrt_status st = stage_inputs(s, inputs, n);
+    if (st != MCRT_OK) return st;
+    unsigned char* d_img = nullptr;
+    float* d_out = nullptr;
+    unsigned* d_err = nullptr;
+    unsigned err = 0;
+    cudaError_t e = cudaMalloc(&d_img, tc::kImgBytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)n * kOut * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) {
+        (void)cudaGetLastError();
+        k_pack_image_tc<<<64, 256, 0, s->stream>>>(s->d_params, d_img);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::smem_bytes(kTcGroups));
+    if (e == cudaSuccess) {
+        const long long tiles = (n + tc::kRows * kTcGroups - 1) / (tc::kRows * kTcGroups);
+        const int grid = (int)(tiles < s->n_sm ? tiles : s->n_sm);
+        k_infer_tc<<<grid, tc::kRows * kTcGroups, tc::smem_bytes(kTcGroups), s->stream>>>(d_img, n, s->d_in, d_out, d_err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(outputs, d_out, (size_t)n * kOut * sizeof(float), cudaMemcpyDefault, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(d_img);
+    cudaFree(d_out);
+    cudaFree(d_err);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return mcrt_fail_noctx(MCRT_E_CUDA, "mcrt_surrogate_eval_engine: %s", cudaGetErrorString(e));
+    }
+    if (err) return mcrt_fail_noctx(MCRT_E_TIMEOUT, "mcrt_surrogate_eval_engine: a tensor-core wait timed out");
     return MCRT_OK;
 }
 

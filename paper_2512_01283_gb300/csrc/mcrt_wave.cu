@@ -23,6 +23,7 @@
 #include "mcrt_device.cuh"
 #include "mcrt_internal.h"
 #include "mcrt_mlp_infer.cuh"
+#include "mcrt_mlp_tc.cuh"
 #include "mcrt_packet.cuh"
 
 namespace cg = cooperative_groups;
@@ -209,6 +210,120 @@ __global__ void __launch_bounds__(kWaveBlock, 1) k_sur_tally(const __grid_consta
     const unsigned long long v[3] = {c_rows, c_map, c_real};
     const int which[3] = {kCntTallyRows, kCntFallbackMap, kCntFallbackReal};
     flush_counters(P.sur.ctl, s_cnt, v, 3, which);
+}
+
+// The same tally on the 5th-generation tensor cores: a CTA of kTcGroups groups of
+// 128 threads, each group taking tiles of 128 rows, thread t building row t's inputs,
+// reading row t of the network's output from tensor memory (mcrt_mlp_tc.cuh) and
+// finishing row t; while one group works on the CUDA cores another's MMAs run.  A
+// record's rows (at most 16 cameras) lie in one warp, whose first-camera lane issues
+// the bulk reduction from the group's staging rows (they reuse its input tile).
+constexpr int kTcGroups = 3;
+constexpr size_t kTallyTcSmem = tc::smem_bytes(kTcGroups) + kCamBytes;
+constexpr unsigned long long kTensorWaitNs = 2000000000ull;
+static_assert(tc::kA0Bytes >= tc::kRows * 4 * (int)sizeof(double), "staging rows fit the input tile");
+
+__global__ void __launch_bounds__(tc::kRows * kTcGroups, 1) k_sur_tally_tc(const __grid_constant__ TransportParams P) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) unsigned long long mbar[kTcGroups];
+    __shared__ unsigned tmem_slot;
+    __shared__ unsigned long long s_cnt[3];
+    if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0ull;
+    float* s_cam = reinterpret_cast<float*>(sm + tc::smem_bytes(kTcGroups));
+    for (int i = threadIdx.x; i < 12 * P.n_cam; i += blockDim.x) {
+        const CameraDev& cd = P.cam[i / 12];
+        const int e = i % 12, v = e / 4, w = e % 4;
+        s_cam[i] = w == 3 ? 0.f : (float)(v == 0 ? cd.dir[w] : (v == 1 ? cd.th[w] : cd.ph[w]));
+    }
+    const tc::Group g = tc::setup(kTcGroups, sm, P.sur.image_tc, mbar, &tmem_slot);  // ends with a barrier
+    double* stage = reinterpret_cast<double*>(g.a0);
+    const int t = g.t, gi = threadIdx.x / tc::kRows;
+    const unsigned long long nreq = P.sur.ctl->n_rec[P.sur.rec_slot];
+    const unsigned long long nrec = nreq < P.sur.rec_cap ? nreq : P.sur.rec_cap;
+    const int ncam = P.n_cam;
+    const int ncp = ncam <= 1 ? 1 : (ncam <= 2 ? 2 : (ncam <= 4 ? 4 : (ncam <= 8 ? 8 : 16)));
+    const int per_tile = tc::kRows / ncp;
+    const unsigned long long ntile = (nrec + per_tile - 1) / per_tile;
+    unsigned long long c_rows = 0, c_map = 0, c_real = 0;
+    unsigned phase = 0;
+    bool failed = false;
+    for (unsigned long long tile = (unsigned long long)blockIdx.x * kTcGroups + gi; tile < ntile;
+         tile += (unsigned long long)gridDim.x * kTcGroups) {
+        // the staging rows share the input tile: every reduction of the previous tile
+        // has read them before any row is overwritten
+        bulk_wait_read();
+        tc::group_sync(g);
+        const int cam = t % ncp;
+        const unsigned long long rec = tile * per_tile + (unsigned)(t / ncp);
+        bool valid = false, fb = false;
+        unsigned cell = 0;
+        float s = 0.f, W[4] = {0.f, 0.f, 0.f, 0.f}, mu = 1.f;
+        PlaneRot<float> pr{1.f, 0.f, 1.f, 0.f};
+        float u[mlp::kIn] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (rec < nrec) {
+            const float4* r = P.sur.records + rec * kRecordF4;
+            cell = __float_as_uint(r[3].x);
+            valid = cam < ncam && cell != 0xffffffffu;
+            if (valid) {
+                const float4 r0 = r[0], r1 = r[1], q = r[2];
+                const V3<float> n{r0.x, r0.y, r0.z};
+                s = r0.w;
+                W[0] = r1.x;
+                W[1] = r1.y;
+                W[2] = r1.z;
+                W[3] = r1.w;
+                V3<float> th, ph, Om, thc, phc;
+                stokes_basis(n, th, ph);
+                load_camera(s_cam + 12 * cam, Om, thc, phc);
+                pr = plane_rotation(n, th, ph, Om, thc, phc);
+                mu = dot(n, Om);
+                const V3<float> nGF = quat_to_grain(q, n), cGF = quat_to_grain(q, Om);
+                u[0] = nGF.x;
+                u[1] = nGF.y;
+                u[2] = nGF.z;
+                u[3] = cGF.x;
+                u[4] = cGF.y;
+                u[5] = cGF.z;
+                u[6] = s;
+                fb = map_says_fallback(P.sur, nGF, cGF, s);
+            }
+        }
+        tc::store_input(g, u);
+        float y[24];
+        if (!tc::forward(g, y, phase, kTensorWaitNs)) {
+            failed = true;
+            break;
+        }
+        if (valid) {
+            float Y[4], m[16];
+            const bool real = realizable(y, m);
+            if (!fb && real) {
+                apply_plane_full(pr, __expf(y[0]), m, W, Y);
+            } else {
+                float Pm[6];
+                table_at(P.t, s, mu, Pm);
+                apply_plane(pr, Pm, W, Y);
+                if (fb)
+                    ++c_map;
+                else
+                    ++c_real;
+            }
+            ++c_rows;
+            double2* d2 = reinterpret_cast<double2*>(stage + t * 4);
+            d2[0] = make_double2((double)Y[0], (double)Y[1]);
+            d2[1] = make_double2((double)Y[2], (double)Y[3]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+        __syncwarp();
+        if (valid && cam == 0)
+            bulk_reduce_add_f64(P.S + (size_t)cell * (size_t)ncam * 4, stage + t * 4, (unsigned)ncam * 32u);
+    }
+    bulk_wait_all();
+    if (failed && t == 0) atomicOr(P.status, (unsigned)MCRT_STATUS_DEVICE_TIMEOUT);
+    const unsigned long long v[3] = {c_rows, c_map, c_real};
+    const int which[3] = {kCntTallyRows, kCntFallbackMap, kCntFallbackReal};
+    flush_counters(P.sur.ctl, s_cnt, v, 3, which);
+    tc::teardown(kTcGroups, g, failed, phase, kTensorWaitNs);
 }
 
 // Scattering of the waiting packets (Sec. 2.2 rejection sampling): lanes 0-15 own
@@ -558,6 +673,8 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
     if (sur) {
         e = cudaFuncSetAttribute(k_sur_tally, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallySmem);
         if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sur_tally_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallyTcSmem);
+        if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_sur_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatSmem);
     } else {
         if (tab_smem > 48 * 1024)
@@ -600,7 +717,9 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
         if (e == cudaSuccess) e = launch_transport(p, MCRT_FP32, block, tgrid, s);
         if (e == cudaSuccess) e = cudaEventRecord(ek[1], s);
         if (e == cudaSuccess) {
-            if (sur)
+            if (sur && p.sur.tally_engine == MCRT_ENGINE_TCGEN05)
+                k_sur_tally_tc<<<n_sm, tc::kRows * kTcGroups, kTallyTcSmem, s>>>(p);
+            else if (sur)
                 k_sur_tally<<<n_sm, kWaveBlock, kTallySmem, s>>>(p);
             else
                 k_tab_tally<<<tab_grid, kTabBlock, tab_smem, s>>>(p);

@@ -52,6 +52,7 @@ class LaunchDesc(C.Structure):
                 ("tally_blocks_per_sm", C.c_int32)]
 
 FLAG_INLINE_TALLY = 1
+FLAG_MMA_SYNC_TALLY = 2
 
 OPTICS = {"tables": 0, "surrogate": 1}
 
@@ -89,7 +90,7 @@ SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "m
            "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_tune", "mcrt_batch_images", "mcrt_batch_destroy",
            "mcrt_surrogate_create", "mcrt_surrogate_train", "mcrt_surrogate_eval", "mcrt_surrogate_labels",
            "mcrt_surrogate_grad", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy",
-           "mcrt_surrogate_error_map", "mcrt_set_surrogate"]
+           "mcrt_surrogate_error_map", "mcrt_set_surrogate", "mcrt_surrogate_eval_engine"]
 
 
 def lib():
@@ -128,6 +129,7 @@ def lib():
     L.mcrt_surrogate_destroy.argtypes = [vp]
     L.mcrt_surrogate_error_map.argtypes = [vp, i64, vp]
     L.mcrt_set_surrogate.argtypes = [vp, vp, C.c_double]
+    L.mcrt_surrogate_eval_engine.argtypes = [vp, i32, i64, vp, vp]
     for name in SYMBOLS:
         if name not in ("mcrt_last_error", "mcrt_surrogate_param_count"):
             getattr(L, name).restype = C.c_int
@@ -275,7 +277,8 @@ def make_desc(run: dict, precision="fp32", trace=None, n_trace=0, default_center
     d.blocks_per_sm = int(kw.get("blocks_per_sm", 0))
     d.time_budget_s = float(kw.get("time_budget_s", 0.0))
     d.optics = OPTICS[kw.get("optics", "tables")]
-    d.flags = FLAG_INLINE_TALLY if kw.get("inline_tally", False) else 0
+    d.flags = (FLAG_INLINE_TALLY if kw.get("inline_tally", False) else 0) | \
+        (FLAG_MMA_SYNC_TALLY if kw.get("tally_engine", "tcgen05") == "mma" else 0)
     d.tally_blocks_per_sm = int(kw.get("tally_blocks_per_sm", 0))
     if trace is not None:
         p, k = _ptr(trace, np.float64)
@@ -434,10 +437,14 @@ class Surrogate:
                                           C.c_void_p(hist.ctypes.data)))
         return hist[:int(n_steps)]
 
-    def eval(self, inputs):
+    ENGINES = {"mma": 0, "tcgen05": 1}
+
+    def eval(self, inputs, engine="mma"):
+        """Network outputs [n][20]; engine "mma" (mma.sync) or "tcgen05"."""
         x = np.ascontiguousarray(np.asarray(inputs, dtype=np.float32))
         out = np.zeros((x.shape[0], self.N_OUT), dtype=np.float32)
-        _check(lib().mcrt_surrogate_eval(self.h, x.shape[0], C.c_void_p(x.ctypes.data), C.c_void_p(out.ctypes.data)))
+        _check(lib().mcrt_surrogate_eval_engine(self.h, self.ENGINES[engine], x.shape[0], C.c_void_p(x.ctypes.data),
+                                                C.c_void_p(out.ctypes.data)))
         return out
 
     def labels(self, inputs):

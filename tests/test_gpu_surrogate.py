@@ -81,6 +81,21 @@ def test_forward_matches_reference(sur):
     assert np.abs(y - h[:, :20]).max() < 2e-2 * scale
 
 
+def test_tcgen05_engine_matches_mma_engine(sur):
+    """The 5th-generation tensor-core engine (tcgen05.mma, TMEM accumulators, 128-row
+    tiles) against the mma.sync engine on the same BF16 network: equal up to FP32
+    summation order and the BF16 rounding of activations it can flip; a ragged last
+    tile (1000 = 7 x 128 + 104 rows)."""
+    s, _ = sur
+    u = inputs(1000)
+    a = s.eval(u, engine="mma").astype(np.float64)
+    b = s.eval(u, engine="tcgen05").astype(np.float64)
+    scale = np.abs(a).max()
+    assert np.all(np.isfinite(b))
+    assert np.abs(a - b).max() < 1e-2 * scale
+    assert np.abs(a - b).mean() < 1e-3 * scale
+
+
 def test_gradients_match_reference(sur):
     """GPU backward (BF16 operands, FP32 accumulation) against the FP64 reference
     backward with the same BF16-rounded weights and inputs."""
@@ -216,6 +231,26 @@ def test_surrogate_path_against_table_path(disk_net):
         assert abs(img_s[k][0].sum() - It) < 0.05 * It, k
         for e in (1, 2):
             assert abs(img_s[k][e].sum() - img_t[k][e].sum()) < 0.02 * It, (k, e)
+
+
+def test_tally_engines_agree(disk_net):
+    """The source tally of a surrogate launch on tcgen05 (default) and on mma.sync:
+    same records, same network, so the tallies and images agree up to FP32 rounding
+    (and rare BF16 activation flips); trajectories are identical."""
+    model, s = disk_net
+    run = W.disk_run(n_packets=20_000, n_cam=4, npix=32)
+    out = {}
+    for eng in ("tcgen05", "mma"):
+        m = M.Model(model)
+        m.set_surrogate(s, 0.05)
+        st = M.launch(m, run, precision="fp32", optics="surrogate", tally_engine=eng)
+        S, A = m.tallies(4)
+        out[eng] = (st, S, A)
+        m.close()
+    (st_t, S_t, A_t), (st_m, S_m, A_m) = out["tcgen05"], out["mma"]
+    assert st_t["events"] == st_m["events"] and st_t["mlp_tally_rows"] == st_m["mlp_tally_rows"]
+    assert np.linalg.norm(A_t - A_m) < 1e-9 * np.linalg.norm(A_m)  # FP64 atomics in another order
+    assert np.linalg.norm(S_t - S_m) < 2e-3 * np.linalg.norm(S_m)
 
 
 def test_surrogate_launch_options_rejected(disk_net):
