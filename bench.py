@@ -87,16 +87,18 @@ def kernel_source_sha():
 
     h = hashlib.sha256()
     for f in ("paper_2512_01283_gb300/csrc/mcrt_transport.cu", "paper_2512_01283_gb300/csrc/mcrt_device.cuh",
-              "paper_2512_01283_gb300/csrc/mcrt_internal.h", "paper_2512_01283_gb300/csrc/mcrt_packet.cuh"):
+              "paper_2512_01283_gb300/csrc/mcrt_internal.h", "paper_2512_01283_gb300/csrc/mcrt_packet.cuh",
+              "paper_2512_01283_gb300/csrc/mcrt_wave.cu"):
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(segments_per_launch):
-    """DRAM bytes (read + write) per transport launch from the committed ncu summary:
-    bytes per segment of the captured small launch times this launch's segments;
-    None when the kernel sources changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "k_transport_disk192.md")
+def profiled_traffic(kernel, units_per_launch):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu summary of
+    the disk workload: bytes per unit (segment of the transport kernel, record of the
+    tally kernel) of the captured small launch times this launch's units; None when
+    the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "rounds_disk192.md")
     if not os.path.exists(path):
         return None
     fields = {}
@@ -104,9 +106,10 @@ def profiled_traffic(segments_per_launch):
         if ":" in line and not line.startswith(("|", "#", "`")):
             k, v = line.split(":", 1)
             fields[k.strip()] = v.strip()
-    if fields.get("kernel_source_sha") != kernel_source_sha() or "traffic_bytes_per_segment" not in fields:
+    key = "%s_traffic_bytes_per_unit" % kernel
+    if fields.get("kernel_source_sha") != kernel_source_sha() or key not in fields:
         return None
-    return float(fields["traffic_bytes_per_segment"]) * segments_per_launch
+    return float(fields[key]) * units_per_launch
 
 
 class ClockSampler:
@@ -376,30 +379,57 @@ def main():
     ms_max, ev_all = float(ms_t.item()), float(ev_t.item())
     value = ev_all / (ms_max * 1e-3)
 
-    # roofline of the dominant kernel (transport): algorithmic bytes per launch /
-    # its CUDA-event duration measured inside the library on the launching stream
+    # rooflines: algorithmic bytes of each kernel over its CUDA-event time measured
+    # inside the library on the launching stream.  FP32 table launches run in rounds:
+    # the transport kernel (32 B cell + 16 B absorbed RMW per absorbing segment + 32 B
+    # record per tallying segment) and the tally kernel (32 B record + 64 B source RMW
+    # per camera and record); the dominant one (longer time) is `roofline`.
     seg = sum(s["segments"] for s in stats)
     tal = sum(s["tally_segments"] for s in stats)
     ab = sum(s["absorb_segments"] for s in stats)
     kms = sum(s["kernel_ms"] for s in stats)
-    alg_bytes = 32.0 * seg + 16.0 * ab + 64.0 * n_cam * tal
+    t_ms = sum(s["ms_transport"] for s in stats)
+    a_ms = sum(s["ms_tally"] for s in stats)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = alg_bytes / (kms * 1e-3) / 1e9
-    traffic = profiled_traffic(seg / args.steps)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "kernel": "k_transport<float, table>", "bytes_per_segment": "32 cell + 16 absorbed RMW (if absorbing) "
-                "+ 64 x n_cam source RMW (if scattering)"}
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kernels = {}
+    if t_ms > 0 and a_ms > 0:
+        b_t = 32.0 * seg + 16.0 * ab + 32.0 * tal
+        b_a = (32.0 + 64.0 * n_cam) * tal
+        kernels["transport"] = {"kernel": "k_transport<float, table rounds>", "bound": "hbm",
+                                "achieved": b_t / (t_ms * 1e-3) / 1e9, "ms_per_step": t_ms / args.steps,
+                                "bytes_per_unit": "32 cell + 16 absorbed RMW (absorbing) + 32 record (tallying) per segment",
+                                "traffic": profiled_traffic("transport", seg / args.steps)}
+        kernels["tally"] = {"kernel": "k_tab_tally", "bound": "hbm", "achieved": b_a / (a_ms * 1e-3) / 1e9,
+                            "ms_per_step": a_ms / args.steps,
+                            "bytes_per_unit": "32 record + 64 x n_cam source RMW per tallying segment",
+                            "traffic": profiled_traffic("tally", tal / args.steps)}
+        for k in kernels.values():
+            k.update({"peak": peak, "unit": "GB/s", "frac": k["achieved"] / peak, "peak_source": src})
+        dom = kernels["transport"] if t_ms >= a_ms else kernels["tally"]
+        roofline = dict(dom)
+        alg_step = b_t + b_a
+    else:
+        alg_step = 32.0 * seg + 16.0 * ab + 64.0 * n_cam * tal
+        achieved = alg_step / (kms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "peak_source": src, "kernel": "k_transport<float, table> (tally in place)",
+                    "bytes_per_unit": "32 cell + 16 absorbed RMW (if absorbing) + 64 x n_cam source RMW (if "
+                                      "scattering) per segment"}
+    roofline_step = {"achieved": alg_step / (ms_max * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg_step / (ms_max * 1e-3) / 1e9 / peak,
+                     "note": "all algorithmic bytes of step 1 over the whole step time (images included)"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
-            "roofline": roofline, "gpu_launches": args.steps * (1 + n_cam),
+            "roofline": roofline, "roofline_kernels": kernels, "roofline_step": roofline_step,
+            "gpu_launches": int(sum(3 * s["wave_iterations"] if s["wave_iterations"] else 1 for s in stats) + args.steps * n_cam),
             "clocks": cs.summary(),
             "detail": {"events_per_step": events / args.steps, "segments_per_step": seg / args.steps,
                        "scatterings_per_step": sum(s["scatterings"] for s in stats) / args.steps,
@@ -431,7 +461,7 @@ def main():
             e_ev += st["events"]
         e_val = e_ev / e_t
         line["e2e"] = {"value": e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
-        line["gpu_launches_e2e_per_step"] = 1 + n_cam + 5
+        line["gpu_launches_e2e_per_step"] = int(3 * st["wave_iterations"]) + n_cam + 5
 
     if not args.no_sweep:
         line["batched_sweep"] = run_sweep(args, M, W, torch)
