@@ -321,6 +321,7 @@ def main():
 
     from paper_2512_01283_gb300 import build as B
     from paper_2512_01283_gb300 import mcrt as M
+    from paper_2512_01283_gb300 import multigpu as MG
     from paper_2512_01283_gb300 import workloads as W
 
     torch.cuda.set_device(local_rank)
@@ -336,8 +337,8 @@ def main():
     B.build()
 
     model = W.disk(n=args.grid)
-    run = W.disk_run(n_packets=int(args.packets))
-    run["stream"] = rank  # independent packets per rank (weak scaling), no data-path collective
+    # independent packets per rank (weak scaling, Philox stream = rank), no data-path collective
+    run = MG.rank_run(W.disk_run(n_packets=int(args.packets)), rank)
     n_cam = len(run["cameras"])
     npix = run["cameras"][0]["npix"]
     mdl = M.Model(model)
@@ -371,12 +372,7 @@ def main():
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     events = sum(s["events"] for s in stats)
-    ms_t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    ev_t = torch.tensor([events], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ev_t, op=dist.ReduceOp.SUM)
-    ms_max, ev_all = float(ms_t.item()), float(ev_t.item())
+    ms_max, ev_all = MG.reduce_timing(ms, events, dist, device="cuda")
     value = ev_all / (ms_max * 1e-3)
 
     # rooflines: algorithmic bytes of each kernel over its CUDA-event time measured

@@ -366,3 +366,22 @@ def test_event_cap_and_time_budget_report_status():
     st = M.launch(m, W.rayleigh_sphere_run(1000, npix=8))
     assert st["status"] == M.MCRT_OK and st["emitted"] == 1000
     m.close()
+
+
+def test_table_rounds_equal_the_in_place_tally():
+    """FP32 table launches run in rounds (transport, then a tally kernel over the queued
+    segments) by default; the in-place tally (MCRT_FLAG_INLINE_TALLY) and the rounds
+    with each tally beside the next transport (tally_blocks_per_sm > 0) give the same
+    packets and the same tallies up to FP32 rounding of the per-segment terms."""
+    model = W.disk(n=24)
+    run = W.disk_run(n_packets=20_000, n_cam=4, npix=32)
+    ref = gpu_run(model, run, "fp32", n_trace=20_000, inline_tally=True)
+    for kw in ({}, {"tally_blocks_per_sm": 2}):
+        g = gpu_run(model, run, "fp32", n_trace=20_000, **kw)
+        assert g["stats"]["events"] == ref["stats"]["events"]
+        assert g["stats"]["wave_iterations"] >= 1
+        assert trace_match_fraction(g["trace"], ref["trace"], 1e-6) >= 0.999
+        assert np.linalg.norm(g["S"] - ref["S"]) < 1e-6 * np.linalg.norm(ref["S"])
+        assert np.linalg.norm(g["absorbed"] - ref["absorbed"]) < 1e-9 * np.linalg.norm(ref["absorbed"])
+        for k in range(4):
+            assert np.linalg.norm(g["images"][k] - ref["images"][k]) < 1e-6 * np.linalg.norm(ref["images"][k])
