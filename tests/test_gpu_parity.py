@@ -385,3 +385,35 @@ def test_table_rounds_equal_the_in_place_tally():
         assert np.linalg.norm(g["absorbed"] - ref["absorbed"]) < 1e-9 * np.linalg.norm(ref["absorbed"])
         for k in range(4):
             assert np.linalg.norm(g["images"][k] - ref["images"][k]) < 1e-6 * np.linalg.norm(ref["images"][k])
+
+
+@pytest.mark.parametrize("n_cam", [1, 3, 16])
+def test_table_rounds_camera_counts(n_cam):
+    """The tally kernel pads each record's cameras to 1, 2, 4, 8 or 16 rows: odd and
+    extreme camera counts give the in-place tally's result."""
+    model = W.disk(n=20)
+    run = dict(W.disk_run(n_packets=6_000, n_cam=8, npix=16))
+    run["cameras"] = W.inclination_cameras(n_cam=n_cam, npix=16)
+    ref = gpu_run(model, run, "fp32", inline_tally=True)
+    g = gpu_run(model, run, "fp32")
+    assert g["stats"]["events"] == ref["stats"]["events"]
+    assert g["S"].shape == ref["S"].shape == (20 ** 3, n_cam, 4)
+    assert np.linalg.norm(g["S"] - ref["S"]) < 1e-6 * np.linalg.norm(ref["S"])
+
+
+def test_table_rounds_resume_ranges_and_ragged_counts():
+    """Rounds with packet-id sub-ranges and accumulate (several launches adding to the
+    same tallies), and odd packet counts, equal one launch over all ids."""
+    model = W.disk(n=20)
+    run = W.disk_run(n_packets=12_345, n_cam=2, npix=16)
+    one = gpu_run(model, run, "fp32")
+    m = M.Model(model)
+    M.launch(m, dict(run, pid_end=5_001), precision="fp32")
+    M.launch(m, dict(run, pid_begin=5_001, pid_end=9_999), precision="fp32", accumulate=1)
+    M.launch(m, dict(run, pid_begin=9_999), precision="fp32", accumulate=1)
+    S, A = m.tallies(2)
+    m.close()
+    # FP32 launches pre-sum the absorbed energy of same-cell lanes of a warp in FP32, and
+    # the warps differ between the split and the single launch
+    assert np.linalg.norm(S - one["S"]) < 1e-6 * np.linalg.norm(one["S"])
+    assert np.linalg.norm(A - one["absorbed"]) < 1e-6 * np.linalg.norm(one["absorbed"])

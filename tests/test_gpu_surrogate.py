@@ -253,6 +253,25 @@ def test_tally_engines_agree(disk_net):
     assert np.linalg.norm(S_t - S_m) < 2e-3 * np.linalg.norm(S_m)
 
 
+def test_surrogate_path_odd_camera_count(disk_net):
+    """Three cameras (rows padded to 4 per record) on both tally engines: the same
+    records give the same tallies; energy is conserved."""
+    model, s = disk_net
+    run = dict(W.disk_run(n_packets=8_000, n_cam=4, npix=16))
+    run["cameras"] = W.inclination_cameras(n_cam=3, npix=16)
+    out = {}
+    for eng in ("tcgen05", "mma"):
+        m = M.Model(model)
+        m.set_surrogate(s, 0.05)
+        st = M.launch(m, run, precision="fp32", optics="surrogate", tally_engine=eng)
+        S, _ = m.tallies(3)
+        out[eng] = (st, S)
+        m.close()
+    assert out["tcgen05"][1].shape == (24 ** 3, 3, 4)
+    assert abs(balance(out["tcgen05"][0]) - 1.0) < 1e-5
+    assert np.linalg.norm(out["tcgen05"][1] - out["mma"][1]) < 2e-3 * np.linalg.norm(out["mma"][1])
+
+
 def test_surrogate_launch_options_rejected(disk_net):
     model, s = disk_net
     run = W.disk_run(n_packets=1000, n_cam=1, npix=8)

@@ -41,8 +41,10 @@ def to_device(torch, model):
 
 
 def reference(model, run, precision):
+    # the no-allocation entry point tallies inside the transport kernel: compare with the
+    # allocating entry point on that same path (its FP32 default tallies in rounds)
     m = M.Model(model)
-    st = M.launch(m, run, precision=precision)
+    st = M.launch(m, run, precision=precision, inline_tally=True)
     S, A = m.tallies(len(run["cameras"]))
     m.close()
     return st, S, A
