@@ -215,17 +215,25 @@ template <int EPI> __global__ void __launch_bounds__(128) k_gemm(const GemmArgs 
         for (int j = 0; j < 4; ++j)
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
     const bf16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < g.K; k0 += kTK) {
+    // weight gradients split K (the batch) over gridDim.z blocks, which add their
+    // partial sums to the zeroed gradient; the other epilogues take the whole K
+    int kb = 0, ke = g.K;
+    if (EPI == EPI_DW && gridDim.z > 1) {
+        const int per = ((g.K + gridDim.z - 1) / gridDim.z + kTK - 1) / kTK * kTK;
+        kb = blockIdx.z * per;
+        ke = kb + per < g.K ? kb + per : g.K;
+    }
+    for (int k0 = kb; k0 < ke; k0 += kTK) {
         for (int i = tid; i < kTM * kTK; i += blockDim.x) {
             const int mm = i / kTK, kk = i % kTK, m = m0 + mm, k = k0 + kk;
             bf16 v = zero;
-            if (m < g.M && k < g.K) v = g.a_t ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
+            if (m < g.M && k < ke) v = g.a_t ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
             As[mm][kk] = v;
         }
         for (int i = tid; i < kTN * kTK; i += blockDim.x) {
             const int nn = i / kTK, kk = i % kTK, n = n0 + nn, k = k0 + kk;
             bf16 v = zero;
-            if (n < g.N && k < g.K) v = g.b_kn ? g.B[(size_t)k * g.ldb + n] : g.B[(size_t)n * g.ldb + k];
+            if (n < g.N && k < ke) v = g.b_kn ? g.B[(size_t)k * g.ldb + n] : g.B[(size_t)n * g.ldb + k];
             Bs[nn][kk] = v;
         }
         __syncthreads();
@@ -266,14 +274,25 @@ template <int EPI> __global__ void __launch_bounds__(128) k_gemm(const GemmArgs 
                     } else if (EPI == EPI_DX) {
                         g.Hout[(size_t)m * g.ldh + n] = __float2bfloat16(v * silu_grad_f(g.Zprev[(size_t)m * g.ldz + n]));
                     } else {
-                        g.Zout[(size_t)m * g.ldz + n] = v;
+                        if (gridDim.z > 1)
+                            atomicAdd(&g.Zout[(size_t)m * g.ldz + n], v);
+                        else
+                            g.Zout[(size_t)m * g.ldz + n] = v;
                     }
                 }
 }
 
 template <int EPI> cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
     (void)cudaGetLastError();
-    const dim3 grid((g.N + kTN - 1) / kTN, (g.M + kTM - 1) / kTM);
+    dim3 grid((g.N + kTN - 1) / kTN, (g.M + kTM - 1) / kTM);
+    // weight gradients (small M x N, K = the batch): split K so that the GPU fills;
+    // the output (d_grads) is zeroed before the backward pass
+    if (EPI == EPI_DW) {
+        int z = 256 / (int)(grid.x * grid.y);
+        const int kmax = (g.K + 4 * kTK - 1) / (4 * kTK);  // at least four k-tiles per block
+        z = z < kmax ? z : kmax;
+        grid.z = z > 1 ? z : 1;
+    }
     k_gemm<EPI><<<grid, 128, 0, s>>>(g);
     return cudaGetLastError();
 }
