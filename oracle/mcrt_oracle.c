@@ -95,6 +95,8 @@ typedef struct {
     int32_t max_trials;
     int32_t n_threads;
     int64_t n_trace;
+    int32_t periodic;         /* bit a set: axis a is periodic (a packet leaving the box there re-enters
+                                 on the opposite face), else packets leaving escape */
 } orc_problem;
 
 typedef struct {
@@ -487,9 +489,11 @@ static double exit_distance(const int n3[3], const double lo[3], const double hi
     return best;
 }
 
-/* Move p to the exit face and step the cell index; returns 0 on leaving the grid. */
-static int cross_face(const int n3[3], const double lo[3], const double hi[3], int idx[3], double p[3],
-                      const double n[3], double ell, int axis)
+/* Move p to the exit face and step the cell index; returns 0 on leaving the grid.
+ * Along a periodic axis (bit axis of `periodic`) leaving the grid re-enters it on the
+ * opposite face: index wrapped, coordinate set to that face. */
+static int cross_face_p(const int n3[3], const double lo[3], const double hi[3], int idx[3], double p[3],
+                        const double n[3], double ell, int axis, int periodic)
 {
     double d = (hi[axis] - lo[axis]) / n3[axis];
     for (int a = 0; a < 3; ++a) p[a] += ell * n[a];
@@ -500,7 +504,22 @@ static int cross_face(const int n3[3], const double lo[3], const double hi[3], i
         p[axis] = lo[axis] + idx[axis] * d;
         idx[axis] -= 1;
     }
-    return idx[axis] >= 0 && idx[axis] < n3[axis];
+    if (idx[axis] >= 0 && idx[axis] < n3[axis]) return 1;
+    if (!((periodic >> axis) & 1)) return 0;
+    if (idx[axis] >= n3[axis]) {
+        idx[axis] = 0;
+        p[axis] = lo[axis];
+    } else {
+        idx[axis] = n3[axis] - 1;
+        p[axis] = lo[axis] + n3[axis] * d;
+    }
+    return 1;
+}
+
+static int cross_face(const int n3[3], const double lo[3], const double hi[3], int idx[3], double p[3],
+                      const double n[3], double ell, int axis)
+{
+    return cross_face_p(n3, lo, hi, idx, p, n, ell, axis, 0);
 }
 
 /* Brute list of cells and chord lengths along a ray (for the DDA pins). */
@@ -840,7 +859,7 @@ static void transport_packet(run_ctx *C, int64_t pid)
 
         if (!scatter_here) {
             tau_rem -= dtau_sca_exit;
-            if (!cross_face(P->n, P->lo, P->hi, idx, p, n, ell_exit, axis)) {
+            if (!cross_face_p(P->n, P->lo, P->hi, idx, p, n, ell_exit, axis, P->periodic)) {
                 flag = 1;
                 break;
             }

@@ -57,7 +57,7 @@ class Problem(C.Structure):
                 ("pid_begin", C.c_int64), ("pid_end", C.c_int64),
                 ("roulette_threshold", C.c_double), ("roulette_survival", C.c_double),
                 ("max_events", C.c_int64), ("max_trials", C.c_int32), ("n_threads", C.c_int32),
-                ("n_trace", C.c_int64)]
+                ("n_trace", C.c_int64), ("periodic", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -280,6 +280,7 @@ def make_problem(model: dict, run: dict):
     P.max_trials = int(run.get("max_trials", 1000))
     P.n_threads = int(run.get("n_threads", 1))
     P.n_trace = int(run.get("n_trace", 0))
+    P.periodic = int(model.get("periodic", 0))  # bit a: axis a periodic
     keep.P = P
     return keep
 

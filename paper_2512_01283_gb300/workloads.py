@@ -170,6 +170,32 @@ def dichroic_slab(n=64, tau=1.0, p=0.05, b_angle_deg=45.0, albedo=0.0, emissivit
             "optics": {"model": "rayleigh", "kext": kext_constant(-p, 0.0)}}
 
 
+def plane_parallel_slab(nxy=4, nz=16, tau=1.0, albedo=0.9, periodic=3, b_angle_deg=None, p=0.0):
+    """Plane-parallel slab: z in [0, 1] with uniform kappa_ext = tau (vertical optical
+    depth tau), x, y in [0, 1] periodic (bit a of ``periodic``: axis a), dipole grains;
+    optionally a uniform field in the x-z plane at ``b_angle_deg`` from +z with
+    dichroism alpha2 = -p."""
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    shape = (nz, nxy, nxy)
+    kext = np.full(shape, tau, dtype=np.float32)
+    bf = None
+    if b_angle_deg is not None:
+        a = math.radians(b_angle_deg)
+        bf = np.zeros(shape + (3,), dtype=np.float32)
+        bf[..., 0] = math.sin(a)
+        bf[..., 2] = math.cos(a)
+    return {"lo": lo, "hi": hi, "kappa_abs": (kext * (1 - albedo)).astype(np.float32),
+            "kappa_sca": (kext * albedo).astype(np.float32), "bfield": bf, "emissivity": None,
+            "periodic": int(periodic),
+            "optics": {"model": "rayleigh", "kext": kext_constant(-p, 0.0) if p else kext_isotropic()}}
+
+
+def center_source_run(n_packets, seed=5, cameras=None, pos=(0.5, 0.5, 0.5)):
+    """Isotropic unpolarized point source (luminosity 1) at ``pos``."""
+    return {"sources": [{"type": "point", "pos": tuple(pos), "luminosity": 1.0, "n_packets": int(n_packets)}],
+            "cameras": cameras or [], "seed": seed}
+
+
 def beam_run(n_packets, seed=1, direction=+1, cameras=None, roulette_threshold=0.0):
     return {"sources": [{"type": "beam", "beam_dir": direction, "luminosity": 1.0, "n_packets": n_packets}],
             "cameras": cameras or [], "seed": seed, "roulette_threshold": roulette_threshold,

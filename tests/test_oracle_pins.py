@@ -601,3 +601,50 @@ def test_mlp_reference_gradients_by_central_differences():
         pm = list(params); pm[li] = (W, bm)
         num = (MO.loss_and_grads(pp, x, t, w)[0] - MO.loss_and_grads(pm, x, t, w)[0]) / (2 * h)
         assert abs(num - grads[li][1][1]) < 1e-7 * max(1.0, abs(num))
+
+
+# ---------------------------------------------------------------------------------
+# periodic boundaries (the paper's periodic conditions of its dust-cylinder test)
+# ---------------------------------------------------------------------------------
+def test_periodic_slab_oblique_escape_closed_form():
+    """Absorbing slab z in [0, 1] (kappa = tau), x and y periodic, isotropic point
+    source at the centre: a packet can only leave through z = 0 or z = 1, after the
+    path 0.5 / |n_z| whatever the number of periodic re-entries, so
+    I = (L / N) exp(-tau 0.5 / |n_z|) exactly.  Without the periodic faces packets
+    escape sideways with more intensity."""
+    tau, N = 1.5, 3000
+    model = W.plane_parallel_slab(nxy=4, nz=8, tau=tau, albedo=0.0, periodic=3)
+    run = dict(W.center_source_run(N), n_trace=N, max_events=10_000_000)
+    o = O.transport(model, run)
+    tr = o["trace"]
+    esc = tr[:, 12] == 1
+    assert esc.mean() > 0.999
+    nz = tr[esc, 9]
+    zf = tr[esc, 6]
+    assert np.all(np.isclose(zf, 0.0, atol=1e-12) | np.isclose(zf, 1.0, atol=1e-12))
+    expect = (1.0 / N) * np.exp(-tau * 0.5 / np.abs(nz))
+    assert np.allclose(tr[esc, 0], expect, rtol=1e-10, atol=1e-300)
+    # no dichroism: unpolarized up to the basis rotations' rounding (of the birth intensity)
+    assert np.all(np.abs(tr[esc, 1:4]) <= 1e-14 * tr[esc, 13:14])
+    st = o["stats"]
+    assert abs(st["escaped_energy"] + st["absorbed_energy"] + st["cap_lost"] - st["emitted_energy"]) < 1e-12
+    # the same slab with outflow sides: some packets leave through x or y, brighter
+    model0 = dict(model, periodic=0)
+    o0 = O.transport(model0, run)
+    side = ~(np.isclose(o0["trace"][:, 6], 0.0) | np.isclose(o0["trace"][:, 6], 1.0))
+    assert side.mean() > 0.3
+    assert o0["stats"]["escaped_energy"] > st["escaped_energy"]
+
+
+def test_periodic_scattering_slab_conserves_energy_and_symmetry():
+    """Scattering slab with periodic x, y: energy conservation, and the absorbed energy
+    per z layer is mirror-symmetric about the source's midplane (to Monte-Carlo
+    accuracy)."""
+    model = W.plane_parallel_slab(nxy=4, nz=10, tau=2.0, albedo=0.7, periodic=3)
+    run = dict(W.center_source_run(20_000), n_threads=4)
+    o = O.transport(model, run)
+    st = o["stats"]
+    bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
+    assert abs(bal - st["emitted_energy"]) < 1e-9 * st["emitted_energy"]
+    layers = o["absorbed"].reshape(10, 16).sum(axis=1)
+    assert np.abs(layers - layers[::-1]).max() < 0.05 * layers.max()
