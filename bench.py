@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-packets", type=float, default=1e6, help="packets per job of the batched sweep")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-plane-parallel", action="store_true")
     ap.add_argument("--inline-tally", action="store_true",
                     help="table path: tally inside the transport kernel instead of a tally kernel per round")
     ap.add_argument("--tally-bps", type=int, default=0,
@@ -188,6 +189,28 @@ def run_sweep(args, M, W, torch):
     for m in mdls:
         m.close()
     return out
+
+
+def run_plane_parallel(M, W, torch):
+    """Plane-parallel atmosphere: 64 x 64 x 128 slab, periodic in x and y, vertical
+    optical depth 10, albedo 0.9, aligned dichroic grains (field 30 deg from z, alpha2 =
+    -0.05), central point source, 1e7 packets, FP32."""
+    model = W.plane_parallel_slab(nxy=64, nz=128, tau=10.0, albedo=0.9, periodic=3, b_angle_deg=30.0, p=0.05)
+    run = W.center_source_run(10_000_000, cameras=[W.camera((0.0, 0.0, 1.0), (64, 64), (1.0, 1.0)),
+                                                    W.camera((0.5, 0.0, 0.866), (64, 64), (1.0, 1.0))])
+    m = M.Model(model)
+    M.launch(m, dict(run, seed=90), precision="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = M.launch(m, dict(run, seed=91), precision="fp32")
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    m.close()
+    bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
+    return {"workload": "plane-parallel slab 64x64x128, periodic x and y, tau 10, albedo 0.9, dichroic aligned grains, "
+                        "central point source, 1e7 packets, 2 cameras",
+            "value": st["events"] / wall, "unit": UNIT, "events": st["events"], "seconds": wall,
+            "energy_balance_rel": abs(bal - st["emitted_energy"]) / st["emitted_energy"]}
 
 
 def image_diff(a, b):
@@ -461,6 +484,9 @@ def main():
 
     if not args.no_sweep:
         line["batched_sweep"] = run_sweep(args, M, W, torch)
+
+    if not args.no_plane_parallel and world == 1:
+        line["plane_parallel"] = run_plane_parallel(M, W, torch)
 
     if not args.no_surrogate and world == 1:
         table_imgs = imgs.cpu().numpy()

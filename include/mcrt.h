@@ -55,7 +55,15 @@ typedef enum {
     MCRT_E_STATE = -6      /* call out of order (e.g. image before any launch) */
 } mcrt_status;
 
-enum { MCRT_BOUNDARY_OUTFLOW = 0 };
+/* Boundary of the grid box, per axis: packets leaving through an outflow face escape;
+ * through a face of a periodic axis they re-enter on the opposite face (the paper's
+ * dust-cylinder test, Sec. 3, uses periodic conditions).  Combine the PERIODIC bits. */
+enum {
+    MCRT_BOUNDARY_OUTFLOW = 0,
+    MCRT_BOUNDARY_PERIODIC_X = 1,
+    MCRT_BOUNDARY_PERIODIC_Y = 2,
+    MCRT_BOUNDARY_PERIODIC_Z = 4
+};
 enum { MCRT_SRC_POINT = 0, MCRT_SRC_BEAM = 1, MCRT_SRC_THERMAL = 2 };
 enum { MCRT_SCAT_RAYLEIGH = 0, MCRT_SCAT_TABLE = 1 };
 enum { MCRT_FP32 = 0, MCRT_FP64 = 1 };
@@ -169,7 +177,9 @@ typedef struct {
  *              alignment, q_B = 1) or NULL for none; converted once to the grain
  *              quaternion q_B of eq. (grain-quaternion)
  *   emissivity [nz][ny][nx] FP32 Planck function B per cell, or NULL
- *   boundary   MCRT_BOUNDARY_OUTFLOW (packets leaving the box escape)
+ *   boundary   MCRT_BOUNDARY_OUTFLOW (packets leaving the box escape) or a combination
+ *              of MCRT_BOUNDARY_PERIODIC_X/Y/Z (re-entry on the opposite face along those
+ *              axes; step-2 images still cover the box itself)
  *   cuda_stream  cudaStream_t on which this context queues all its work
  * On success *out owns device copies of the grid (32 bytes per cell).
  * Errors: MCRT_E_INVAL for bad sizes or NULL required pointers, MCRT_E_NOMEM,

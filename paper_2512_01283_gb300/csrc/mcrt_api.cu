@@ -214,8 +214,8 @@ mcrt_status mcrt_create_grid(mcrt_ctx** out, int32_t nx, int32_t ny, int32_t nz,
         if (!(hi[a] > lo[a]) || !std::isfinite(lo[a]) || !std::isfinite(hi[a]))
             return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: empty or non-finite box on axis %d", a);
     if (!kappa_abs || !kappa_sca) return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: kappa_abs/kappa_sca is NULL");
-    if (boundary != MCRT_BOUNDARY_OUTFLOW)
-        return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: only MCRT_BOUNDARY_OUTFLOW is supported");
+    if (boundary < 0 || boundary > (MCRT_BOUNDARY_PERIODIC_X | MCRT_BOUNDARY_PERIODIC_Y | MCRT_BOUNDARY_PERIODIC_Z))
+        return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: boundary must be an MCRT_BOUNDARY_* mask");
 
     mcrt_ctx* c = new (std::nothrow) mcrt_ctx();
     if (!c) return fail(nullptr, MCRT_E_NOMEM, "mcrt_create_grid: host allocation failed");
@@ -229,6 +229,7 @@ mcrt_status mcrt_create_grid(mcrt_ctx** out, int32_t nx, int32_t ny, int32_t nz,
         c->g.d[a] = (hi[a] - lo[a]) / c->g.n[a];
     }
     c->g.ncell = ncell;
+    c->g.periodic = boundary;
     c->has_emissivity = emissivity != nullptr;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
@@ -487,6 +488,7 @@ static mcrt_status prepare_model(mcrt_ctx* ctx, const mcrt_launch_desc* d, uint3
     job = JobDev{};
     for (int a = 0; a < 3; ++a) {
         job.n[a] = ctx->g.n[a];
+        job.periodic = ctx->g.periodic;
         job.lo[a] = ctx->g.lo[a];
         job.hi[a] = ctx->g.hi[a];
         job.d[a] = ctx->g.d[a];

@@ -27,6 +27,7 @@ constexpr int kRecordF4 = 4;        // tally record: 4 float4 (64 bytes)
 // (kappa_abs, kappa_sca, emissivity, 0).
 struct GridDev {
     int n[3];
+    int periodic;  // bit a: axis a periodic (MCRT_BOUNDARY_PERIODIC_*)
     double lo[3], hi[3], d[3];
     long long ncell;
     const float4* cells;  // [ncell][2]
@@ -61,6 +62,7 @@ struct CameraDev {
 // tables, thermal-emission CDF and the energy per packet of each source.
 struct JobDev {
     int n[3];
+    int periodic;
     float lo_f[3], d_f[3];
     double lo[3], hi[3], d[3];
     long long ncell;

@@ -101,6 +101,7 @@ template <typename T> struct JobRef<T, false> {
     const float4* kx;
     const float4* mx;
     __device__ __forceinline__ int n(int a) const { return P.g.n[a]; }
+    __device__ __forceinline__ int periodic() const { return P.g.periodic; }
     __device__ __forceinline__ T lo(int a) const { return pick<T>(P.lo_f[a], P.g.lo[a]); }
     __device__ __forceinline__ T d(int a) const { return pick<T>(P.d_f[a], P.g.d[a]); }
     __device__ __forceinline__ double lo_d(int a) const { return P.g.lo[a]; }
@@ -124,6 +125,7 @@ template <typename T> struct JobRef<T, false> {
 template <typename T> struct JobRef<T, true> {
     const JobDev* j;
     __device__ __forceinline__ int n(int a) const { return j->n[a]; }
+    __device__ __forceinline__ int periodic() const { return j->periodic; }
     __device__ __forceinline__ T lo(int a) const { return pick<T>(j->lo_f[a], j->lo[a]); }
     __device__ __forceinline__ T d(int a) const { return pick<T>(j->d_f[a], j->d[a]); }
     __device__ __forceinline__ double lo_d(int a) const { return j->lo[a]; }
@@ -391,15 +393,16 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     bool next_in = true;
     float4 nq = pk.cq, nr = pk.cr;
     if (!scatter_here) {
-        if (axis == 0) {
-            nix += pk.nx > T(0) ? 1 : -1;
-            next_in = nix >= 0 && nix < job.n(0);
-        } else if (axis == 1) {
-            niy += pk.ny > T(0) ? 1 : -1;
-            next_in = niy >= 0 && niy < job.n(1);
-        } else {
-            niz += pk.nz > T(0) ? 1 : -1;
-            next_in = niz >= 0 && niz < job.n(2);
+        int* ni = axis == 0 ? &nix : (axis == 1 ? &niy : &niz);
+        const T na = axis == 0 ? pk.nx : (axis == 1 ? pk.ny : pk.nz);
+        const int nn = job.n(axis);
+        *ni += na > T(0) ? 1 : -1;
+        next_in = *ni >= 0 && *ni < nn;
+        if (!next_in && ((job.periodic() >> axis) & 1)) {
+            // a periodic axis: the packet re-enters on the opposite face
+            face = na > T(0) ? job.lo(axis) : job.lo(axis) + T(nn) * job.d(axis);
+            *ni = na > T(0) ? 0 : nn - 1;
+            next_in = true;
         }
         if (next_in) load_cell(job, nix, niy, niz, nq, nr);
     }

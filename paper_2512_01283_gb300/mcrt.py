@@ -181,7 +181,8 @@ class Model:
         lo = (C.c_double * 3)(*model["lo"])
         hi = (C.c_double * 3)(*model["hi"])
         h = C.c_void_p()
-        st = L.mcrt_create_grid(C.byref(h), nx, ny, nz, lo, hi, pk, ps, pb, pe, 0, _stream_handle(stream))
+        st = L.mcrt_create_grid(C.byref(h), nx, ny, nz, lo, hi, pk, ps, pb, pe, int(model.get("periodic", 0)),
+                                _stream_handle(stream))
         _check(st)
         self.h = h
         try:

@@ -417,3 +417,38 @@ def test_table_rounds_resume_ranges_and_ragged_counts():
     # the warps differ between the split and the single launch
     assert np.linalg.norm(S - one["S"]) < 1e-6 * np.linalg.norm(one["S"])
     assert np.linalg.norm(A - one["absorbed"]) < 1e-6 * np.linalg.norm(one["absorbed"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_periodic_slab_oblique_escape_on_gpu(prec):
+    """Absorbing slab with periodic x and y: every packet leaves through z = 0 or 1 with
+    I = (L/N) exp(-tau 0.5 / |n_z|) (the oracle's closed-form pin), on both paths."""
+    tau, N = 1.5, 20_000
+    model = W.plane_parallel_slab(nxy=4, nz=8, tau=tau, albedo=0.0, periodic=3)
+    run = dict(W.center_source_run(N), max_events=10_000_000)
+    g = gpu_run(model, run, prec, n_trace=N)
+    tr = g["trace"]
+    esc = tr[:, 12] == 1
+    assert esc.mean() > 0.999
+    zf = tr[esc, 6]
+    assert np.all(np.isclose(zf, 0.0, atol=1e-5) | np.isclose(zf, 1.0, atol=1e-5))
+    expect = (1.0 / N) * np.exp(-tau * 0.5 / np.abs(tr[esc, 9]))
+    rtol = 1e-10 if prec == "fp64" else 2e-4
+    ok = np.isclose(tr[esc, 0], expect, rtol=rtol, atol=1e-30)
+    assert ok.mean() > (0.9999 if prec == "fp64" else 0.995)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_periodic_scattering_slab_parity(prec):
+    """Scattering, dichroic slab with periodic x and y (tables off, dipole grains):
+    packet traces against the oracle, energy conservation."""
+    model = W.plane_parallel_slab(nxy=4, nz=12, tau=3.0, albedo=0.8, periodic=3, b_angle_deg=30.0, p=0.05)
+    run = dict(W.center_source_run(10_000, cameras=[W.camera((0.3, 0.2, 1.0), (8, 8), (1.0, 1.0))]))
+    o = oracle_run(model, run, n_trace=10_000, images=False, n_threads=8)
+    g = gpu_run(model, run, prec, n_trace=10_000)
+    frac = trace_match_fraction(g["trace"], o["trace"], 1e-4)
+    assert frac >= (0.999 if prec == "fp64" else 0.99), frac
+    st = g["stats"]
+    bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
+    assert abs(bal - st["emitted_energy"]) < 1e-6 * st["emitted_energy"]
+    assert np.linalg.norm(g["S"] - o["S"]) < 2e-3 * np.linalg.norm(o["S"])
