@@ -38,6 +38,17 @@
  *   - Rayleigh: isotropic proposal in the grain frame with envelope 2*max Z11.
  *     Tables: proposal from a piecewise-constant envelope of P11 over the
  *     tabulated scattering-angle intervals, azimuth uniform about n.
+ *   - Aligned spheroids (Sec. 2.1 and Sec. 3: dipole approximation, K from the
+ *     optical theorem with no phase lag, so no U-V term): polarizability tensor of
+ *     a spheroid with the radiative-reaction correction; the scattered field is the
+ *     transverse part of the induced dipole (a Jones matrix, applied to the
+ *     coherency matrix).  The cell's kappa_abs and kappa_sca are the orientation-
+ *     averaged opacities; the dichroic parts of K are relative to those averages.
+ *     Scatterings are sampled along n at the unpolarized rate s11 kappa_ext
+ *     (direction-dependent) and the packet is attenuated by K - s11 kappa_ext 1; at a
+ *     scattering the new Stokes vector is Z X (K_sca X)_0 / (s11 (Z X)_0) (the weight
+ *     that keeps the estimator unbiased when the scattering cross section depends on
+ *     direction and polarization).  Isotropic proposal, envelope max(1,|rho|^2) zn.
  *
  * All arithmetic is double precision.  Tallies from several threads are added
  * with compare-and-swap; with one thread the results are deterministic.
@@ -78,7 +89,7 @@ typedef struct {
     const float *kappa_sca;   /* [nz][ny][nx], 1/length */
     const float *bfield;      /* [nz][ny][nx][3] or NULL (no alignment) */
     const float *emissivity;  /* [nz][ny][nx] B_lambda(T) or NULL */
-    int32_t scat_model;       /* 0 Rayleigh (analytic dipole), 1 tables */
+    int32_t scat_model;       /* 0 Rayleigh (analytic dipole), 1 tables, 2 aligned dipole spheroids */
     int32_t n_bins, n_theta;
     const float *mueller;     /* [n_bins][n_theta][6] P11,P12,P22,P33,P34,P44 */
     const float *bin_weight;  /* [n_bins] */
@@ -97,6 +108,9 @@ typedef struct {
     int64_t n_trace;
     int32_t periodic;         /* bit a set: axis a is periodic (a packet leaving the box there re-enters
                                  on the opposite face), else packets leaving escape */
+    double eps_re, eps_im;    /* scat_model 2: dielectric function of the grain material */
+    double aspect;            /* scat_model 2: equatorial over symmetry semi-axis (> 1 oblate) */
+    double size_x;            /* scat_model 2: size parameter 2 pi a_eff / lambda */
 } orc_problem;
 
 typedef struct {
@@ -444,6 +458,156 @@ static double scattered_I(const double X[4], const double n[3], const double n2[
 }
 
 /* ------------------------------------------------------------------------- */
+/* Aligned spheroids in the dipole approximation (Sec. 2.1, Sec. 3: grain     */
+/* optics from the dipole approximation, K from the optical theorem).        */
+/* ------------------------------------------------------------------------- */
+
+/* Depolarization factor L along the symmetry axis of a spheroid whose equatorial
+ * semi-axis is s times its symmetry semi-axis (s > 1 oblate, s < 1 prolate, s = 1 a
+ * sphere).  With g = s^2 - 1 the closed forms for oblate and prolate spheroids
+ * (Bohren & Huffman 1983, eqs. 5.34, 5.35) are both L = s^2 F(g) with
+ * F(g) = sum_k (-g)^k / (2k + 3): for g > 0, F = (1 - atan(sqrt g) / sqrt g) / g;
+ * for g < 0, F = (atanh(sqrt -g) / sqrt -g - 1) / (-g).  The series is summed for
+ * |g| < 0.5, where the closed forms cancel. */
+double orc_spheroid_L(double s)
+{
+    double g = s * s - 1.0, F;
+    if (fabs(g) < 0.5) {
+        F = 0.0;
+        double t = 1.0;
+        for (int k = 0; k < 200; ++k) {
+            F += t / (2 * k + 3);
+            t *= -g;
+        }
+    } else if (g > 0.0) {
+        double f = sqrt(g);
+        F = (1.0 - atan(f) / f) / g;
+    } else {
+        double e = sqrt(-g);
+        F = (atanh(e) / e - 1.0) / (-g);
+    }
+    return s * s * F;
+}
+
+/* Per-grain constants of the aligned dipole spheroid: dielectric function eps,
+ * shape s (as above), size parameter x = 2 pi a_eff / lambda (a_eff the radius of
+ * the sphere of equal volume).  Index 0 is a principal axis perpendicular to the
+ * symmetry axis, index 1 the symmetry axis.
+ *   polarizability per a_eff^3 (Clausius-Mossotti for an ellipsoid):
+ *       alpha_j = (eps - 1) / (3 (1 + L_j (eps - 1))),  L_0 = (1 - L_1) / 2
+ *   with the radiative-reaction correction alpha'_j = alpha_j / (1 - (2i/3) x^3 alpha_j)
+ *   efficiencies (cross section over pi a_eff^2) for the field along axis j:
+ *       Q_ext,j = 4 x Im alpha'_j          (optical theorem)
+ *       Q_sca,j = (8/3) x^4 |alpha'_j|^2   (power radiated by the dipole)
+ *       Q_abs,j = Q_ext,j - Q_sca,j
+ * A field e (unit, transverse) sees C(e) = C_0 (1 - w) + C_1 w with w = (a . e)^2,
+ * a the symmetry axis; over random orientation and polarization <w> = 1/3. */
+typedef struct {
+    double L[2];
+    double complex al[2];     /* alpha'_j per a_eff^3 */
+    double q_ext[2], q_sca[2], q_abs[2];
+    double complex rho;       /* alpha'_1 / alpha'_0 */
+    double zn;                /* 1 / N, N = (8 pi / 3) (2 + |rho|^2) / 3 */
+    double env;               /* max(1, |rho|^2) zn: bound of (Z X)_0 / I */
+} orc_dipole;
+
+static void dipole_setup(double eps_re, double eps_im, double s, double x, orc_dipole *D)
+{
+    double complex eps = eps_re + I * eps_im;
+    D->L[1] = orc_spheroid_L(s);
+    D->L[0] = 0.5 * (1.0 - D->L[1]);
+    for (int j = 0; j < 2; ++j) {
+        double complex a = (eps - 1.0) / (3.0 * (1.0 + D->L[j] * (eps - 1.0)));
+        double complex ap = a / (1.0 - I * (2.0 / 3.0) * x * x * x * a);
+        D->al[j] = ap;
+        D->q_ext[j] = 4.0 * x * cimag(ap);
+        D->q_sca[j] = (8.0 / 3.0) * pow(x, 4) * creal(ap * conj(ap));
+        D->q_abs[j] = D->q_ext[j] - D->q_sca[j];
+    }
+    D->rho = D->al[1] / D->al[0];
+    double r2 = creal(D->rho * conj(D->rho));
+    D->zn = 1.0 / ((8.0 * M_PI / 3.0) * (2.0 + r2) / 3.0);
+    D->env = (r2 > 1.0 ? r2 : 1.0) * D->zn;
+}
+
+/* Test export: [L0, L1, Re a'0, Im a'0, Re a'1, Im a'1, Qext0, Qext1, Qsca0, Qsca1,
+ * Qabs0, Qabs1, Re rho, Im rho, zn, env]. */
+void orc_dipole_constants(double eps_re, double eps_im, double s, double x, double out[16])
+{
+    orc_dipole D;
+    dipole_setup(eps_re, eps_im, s, x, &D);
+    double v[16] = {D.L[0], D.L[1], creal(D.al[0]), cimag(D.al[0]), creal(D.al[1]), cimag(D.al[1]),
+                    D.q_ext[0], D.q_ext[1], D.q_sca[0], D.q_sca[1], D.q_abs[0], D.q_abs[1],
+                    creal(D.rho), cimag(D.rho), D.zn, D.env};
+    memcpy(out, v, sizeof v);
+}
+
+/* Cross section for the transverse field e, relative to its average over random
+ * orientation and polarization: c[0] perpendicular, c[1] along the axis. */
+static double relative_cross_section(const double c[2], double w)
+{
+    double mean = (2.0 * c[0] + c[1]) / 3.0;
+    if (!(mean > 0.0)) return 1.0;  /* no such process: any shape, the cell kappa is 0 */
+    return (c[0] * (1.0 - w) + c[1] * w) / mean;
+}
+
+/* First-row elements (K11, K12) of a dichroic matrix, per unit of its orientation
+ * average, for a packet along n in the basis (e1, e2) transverse to n: K11 and K12 are
+ * the mean and half difference of the cross sections for fields along e1 and e2
+ * (light polarized along e1, Q = I, is removed at K11 + K12). */
+static void dichroic_row(const double c[2], const double axis[3], const double e1[3], const double e2[3],
+                         double K[2])
+{
+    double w1 = dot3(axis, e1), w2 = dot3(axis, e2);
+    double C1 = relative_cross_section(c, w1 * w1), C2 = relative_cross_section(c, w2 * w2);
+    K[0] = 0.5 * (C1 + C2);
+    K[1] = 0.5 * (C1 - C2);
+}
+
+/* Scattered Stokes vector Z X for the scattering n -> n2 by a grain with symmetry
+ * axis `axis` (lab frame); X in the Stokes basis of n, the result in that of n2.  The
+ * induced dipole is p = alpha'_0 (1 + (rho - 1) axis axis^T) E and the far field along
+ * n2 is the part of p transverse to n2, so between the bases (th, ph) of n and (th2,
+ * ph2) of n2 the Jones matrix is J_jk = f2_j . (1 + (rho - 1) axis axis^T) . f_k; the
+ * coherency matrix C = 1/2 [[I+Q, U+iV], [U-iV, I-Q]] goes to J C J^dagger.  Scaled by
+ * zn, so that int Z11 dOmega averaged over orientation is 1 (1/sr). */
+static void dipole_scatter(const orc_dipole *D, const double axis[3], const double X[4], const double n[3],
+                           const double n2[3], double out[4])
+{
+    double th[3], ph[3], th2[3], ph2[3];
+    orc_stokes_basis(n, th, ph);
+    orc_stokes_basis(n2, th2, ph2);
+    const double *f[2] = {th, ph}, *f2[2] = {th2, ph2};
+    double complex J[2][2];
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k)
+            J[j][k] = dot3(f2[j], f[k]) + (D->rho - 1.0) * dot3(f2[j], axis) * dot3(axis, f[k]);
+    double complex Cm[2][2] = {{0.5 * (X[0] + X[1]), 0.5 * (X[2] + I * X[3])},
+                               {0.5 * (X[2] - I * X[3]), 0.5 * (X[0] - X[1])}};
+    double complex Dm[2][2];
+    for (int j = 0; j < 2; ++j)
+        for (int k = 0; k < 2; ++k) {
+            double complex acc = 0.0;
+            for (int l = 0; l < 2; ++l)
+                for (int m = 0; m < 2; ++m) acc += J[j][l] * Cm[l][m] * conj(J[k][m]);
+            Dm[j][k] = acc;
+        }
+    out[0] = D->zn * creal(Dm[0][0] + Dm[1][1]);
+    out[1] = D->zn * creal(Dm[0][0] - Dm[1][1]);
+    out[2] = D->zn * 2.0 * creal(Dm[0][1]);
+    out[3] = D->zn * 2.0 * cimag(Dm[0][1]);
+}
+
+/* Test export of dipole_scatter: grain axis `axis`, out = Z X (1/sr). */
+void orc_dipole_scatter(double eps_re, double eps_im, double s, double x, const double axis[3], const double X[4],
+                        const double n[3], const double n2[3], double out[4])
+{
+    orc_dipole D;
+    dipole_setup(eps_re, eps_im, s, x, &D);
+    dipole_scatter(&D, axis, X, n, n2, out);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Grid and cell-to-cell traversal.                                          */
 /* ------------------------------------------------------------------------- */
 static double cell_size(const orc_problem *P, int a) { return (P->hi[a] - P->lo[a]) / P->n[a]; }
@@ -547,8 +711,14 @@ int64_t orc_dda_walk(const int32_t n3[3], const double lo[3], const double hi[3]
 typedef struct {
     double th[3], ph[3];   /* lab Stokes basis of n */
     double gth[3], gph[3]; /* grain-meridian basis of n, in lab coordinates */
-    double alpha[3];       /* alpha1..3 at theta' */
+    double alpha[3];       /* alpha1..3 at theta' (extinction per unit kappa_ext) */
+    double sca[2];         /* scattering part (s11, s12) of the first row of K per unit
+                              kappa_ext, grain-meridian basis; s11 kappa_ext is the rate
+                              at which scatterings are sampled along n */
+    double gsca;           /* that rate over kappa_sca (1 for Theta-only optics) */
     double thetap;
+    double axis[3];        /* grain symmetry axis in the lab frame */
+    orc_dipole dip;        /* scat_model 2 constants */
 } local_frame;
 
 static void cell_quaternion(const orc_problem *P, int64_t c, double q[4])
@@ -573,7 +743,30 @@ static void make_local_frame(const orc_problem *P, int64_t c, const double n[3],
     if (cz > 1.0) cz = 1.0;
     if (cz < -1.0) cz = -1.0;
     F->thetap = acos(cz);
-    kext_eval(P, F->thetap, F->alpha);
+    const double zg[3] = {0.0, 0.0, 1.0};
+    orc_to_lab(q, zg, F->axis);
+    double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+    double kext = ka + ks;
+    double omega = kext > 0.0 ? ks / kext : 0.0;
+    if (P->scat_model == 2) {
+        /* K = kappa_abs Khat_abs + kappa_sca Khat_sca, each dichroic part relative to its
+         * orientation average; no U-V terms (no phase lag in the optical theorem) */
+        dipole_setup(P->eps_re, P->eps_im, P->aspect, P->size_x, &F->dip);
+        double fa = kext > 0.0 ? ka / kext : 0.0, Ka[2], Ks[2];
+        dichroic_row(F->dip.q_abs, F->axis, F->gth, F->gph, Ka);
+        dichroic_row(F->dip.q_sca, F->axis, F->gth, F->gph, Ks);
+        F->alpha[0] = fa * Ka[0] + omega * Ks[0];
+        F->alpha[1] = fa * Ka[1] + omega * Ks[1];
+        F->alpha[2] = 0.0;
+        F->sca[0] = omega * Ks[0];
+        F->sca[1] = omega * Ks[1];
+        F->gsca = Ks[0];
+    } else {
+        kext_eval(P, F->thetap, F->alpha);
+        F->sca[0] = omega;
+        F->sca[1] = 0.0;
+        F->gsca = 1.0;
+    }
 }
 
 /* Public wrapper for the frame tests: grain-meridian basis and theta'. */
@@ -693,14 +886,17 @@ static int emit_packet(const run_ctx *C, int64_t pid, int s, double eps, double 
         for (int a = 0; a < 3; ++a) p[a] = P->lo[a] + (idx[a] + u1[a]) * cell_size(P, a);
         isotropic(u0[1], u0[2], n);
         inside = 1;
-        /* emission alpha_abs B with alpha_abs = K - omega 1 acting on (1,0,0,0), in the
-         * grain-meridian basis; weight (alpha1(theta') - omega) / (mean alpha1 - omega) */
+        /* emission alpha_abs B with alpha_abs the absorption part of K acting on
+         * (1,0,0,0), in the grain-meridian basis; weight alpha_abs,11(theta') over its
+         * mean over directions (mean alpha1 - omega) */
         local_frame F;
         make_local_frame(P, c, n, &F);
         double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
         double omega = (ka + ks) > 0.0 ? ks / (ka + ks) : 0.0;
-        double w = (F.alpha[0] - omega) / (C->alpha1_mean - omega);
-        double Xg[4] = {eps * w, eps * w * F.alpha[1] / (F.alpha[0] - omega), 0.0, 0.0};
+        /* absorption part of K's first row along n */
+        double kab1 = F.alpha[0] - F.sca[0], kab2 = F.alpha[1] - F.sca[1];
+        double w = kab1 / (C->alpha1_mean - omega);
+        double Xg[4] = {eps * w, kab1 > 0.0 ? eps * w * kab2 / kab1 : 0.0, 0.0, 0.0};
         orc_change_basis(Xg, F.gth, F.gph, F.th, F.ph, X);
     }
     *tau = -log(u0[0]);
@@ -717,6 +913,24 @@ static int scatter_sample(const orc_problem *P, int64_t pid, uint32_t n_sca, int
 {
     const float *tab = NULL;
     double *env_cdf = NULL, env_cdf_total = 0.0;
+    const int dip = P->scat_model == 2;
+    orc_dipole D;
+    double axis[3], I_w = X[0];
+    if (dip) {
+        /* aligned spheroid: the total scattered power (K_sca X)_0 depends on the
+         * polarization; the new Stokes vector is Z X (K_sca X)_0 / (s11 (Z X)_0) with
+         * s11 the sampling rate (Sec. 2.2 weight for direction-dependent cross sections),
+         * i.e. Z X renormalised to I + (s12 / s11) Q in the grain-meridian basis */
+        const double zg[3] = {0.0, 0.0, 1.0};
+        double gth[3], gph[3], th[3], ph[3], tp, Xg[4], Ks[2];
+        dipole_setup(P->eps_re, P->eps_im, P->aspect, P->size_x, &D);
+        orc_to_lab(q, zg, axis);
+        orc_grain_meridian(q, n, gth, gph, &tp);
+        orc_stokes_basis(n, th, ph);
+        orc_change_basis(X, th, ph, gth, gph, Xg);
+        dichroic_row(D.q_sca, axis, gth, gph, Ks);
+        I_w = X[0] + Ks[1] / Ks[0] * Xg[1];
+    }
     if (P->scat_model == 1) {
         tab = P->mueller + (size_t)bin * P->n_theta * 6;
         /* piecewise-constant envelope of P11 over [theta_j, theta_j+1] */
@@ -732,8 +946,15 @@ static int scatter_sample(const orc_problem *P, int64_t pid, uint32_t n_sca, int
     for (int t = 0; t < P->max_trials; ++t) {
         double ut[4];
         draw4(P, pid, n_sca, (uint32_t)(1 + t), ut);
-        double Z[6], bound;
-        if (P->scat_model == 0) {
+        double Z[6], bound, Yd[4];
+        if (dip) {
+            /* isotropic proposal, envelope max(1, |rho|^2) zn I >= (Z X)_0 */
+            double nGF2[3];
+            isotropic(ut[0], ut[1], nGF2);
+            orc_to_lab(q, nGF2, n2);
+            dipole_scatter(&D, axis, X, n, n2, Yd);
+            bound = ut[2] * D.env * X[0];
+        } else if (P->scat_model == 0) {
             /* isotropic proposal in the grain frame, envelope 2 max Z11 */
             double nGF2[3];
             isotropic(ut[0], ut[1], nGF2);
@@ -758,9 +979,12 @@ static int scatter_sample(const orc_problem *P, int64_t pid, uint32_t n_sca, int
             double env = fmax(tab[j * 6], tab[(j + 1) * 6]);
             bound = ut[3] * 2.0 * env * X[0];
         }
-        if (bound < scattered_I(X, n, n2, Z)) {
-            orc_mueller_apply(X, n, n2, Z, Y);
-            double norm = X[0] / Y[0];
+        if (dip ? bound < Yd[0] : bound < scattered_I(X, n, n2, Z)) {
+            if (dip)
+                for (int e = 0; e < 4; ++e) Y[e] = Yd[e];
+            else
+                orc_mueller_apply(X, n, n2, Z, Y);
+            double norm = I_w / Y[0];
             for (int e = 0; e < 4; ++e) Y[e] *= norm;
             result = t + 1;
             break;
@@ -814,19 +1038,21 @@ static void transport_packet(run_ctx *C, int64_t pid)
         int64_t c = ((int64_t)idx[2] * P->n[1] + idx[1]) * P->n[0] + idx[0];
         double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
         double kext = ka + ks;
-        double omega = kext > 0.0 ? ks / kext : 0.0;
         int axis;
         double ell_exit = exit_distance(P->n, P->lo, P->hi, idx, p, n, &axis);
-        double dtau_sca_exit = ks * ell_exit;
-        int scatter_here = (ks > 0.0 && tau_rem < dtau_sca_exit);
-        double ell = scatter_here ? tau_rem / ks : ell_exit;
+        local_frame F;
+        if (kext > 0.0) make_local_frame(P, c, n, &F);
+        /* scattering optical depth sampled along n: kappa_sca for Theta-only optics, the
+         * direction-dependent unpolarized rate s11 kappa_ext for aligned spheroids */
+        double ks_n = (P->scat_model == 2 && kext > 0.0) ? ks * F.gsca : ks;
+        double dtau_sca_exit = ks_n * ell_exit;
+        int scatter_here = (ks_n > 0.0 && tau_rem < dtau_sca_exit);
+        double ell = scatter_here ? tau_rem / ks_n : ell_exit;
 
         /* ---- extinction, absorption and the step-1 tally over the segment ---- */
         if (kext > 0.0) {
-            local_frame F;
-            make_local_frame(P, c, n, &F);
             double dtau = kext * ell;
-            double a = F.alpha[0] - omega;
+            double a = F.alpha[0] - F.sca[0];
             double Xg[4], Yg[4], Wg[4], Y[4];
             orc_change_basis(X, F.th, F.ph, F.gth, F.gph, Xg);
             orc_attenuate(Xg, a, F.alpha[1], F.alpha[2], dtau, Yg);
@@ -839,10 +1065,14 @@ static void transport_packet(run_ctx *C, int64_t pid)
                 orc_change_basis(Wg, F.gth, F.gph, F.th, F.ph, W);
                 for (int k = 0; k < P->n_cam; ++k) {
                     double Z[6], Sc[4];
-                    mixture_mueller(P, dot3(n, P->cams[k].dir), Z);
                     /* eq. (scat-disc-sum): Z(Omega_cam; Omega_pp) applied to the path
                      * integral of I_pp, in the Stokes basis of Omega_cam */
-                    orc_mueller_apply(W, n, P->cams[k].dir, Z, Sc);
+                    if (P->scat_model == 2) {
+                        dipole_scatter(&F.dip, F.axis, W, n, P->cams[k].dir, Sc);
+                    } else {
+                        mixture_mueller(P, dot3(n, P->cams[k].dir), Z);
+                        orc_mueller_apply(W, n, P->cams[k].dir, Z, Sc);
+                    }
                     for (int e = 0; e < 4; ++e) add_double(&R->S[((size_t)c * P->n_cam + k) * 4 + e], Sc[e]);
                 }
             }
@@ -937,7 +1167,8 @@ static int thermal_setup(run_ctx *C)
     int need = 0;
     for (int s = 0; s < P->n_sources; ++s)
         if (P->sources[s].type == 2) need = 1;
-    C->alpha1_mean = kext_alpha1_mean(P);
+    /* the dipole's K is relative to its orientation average: mean alpha1 = 1 */
+    C->alpha1_mean = P->scat_model == 2 ? 1.0 : kext_alpha1_mean(P);
     if (!need) return 0;
     if (!P->emissivity) return -1;
     const int64_t ncell = (int64_t)P->n[0] * P->n[1] * P->n[2];
@@ -1072,7 +1303,7 @@ int orc_image(const orc_problem *P, const double *S, int cam, double scale_S, do
                         local_frame F;
                         make_local_frame(P, c, Om, &F);
                         double Bc = P->emissivity ? P->emissivity[c] : 0.0;
-                        double Sg[4] = {(F.alpha[0] - omega) * Bc, F.alpha[1] * Bc, 0.0, 0.0};
+                        double Sg[4] = {(F.alpha[0] - F.sca[0]) * Bc, (F.alpha[1] - F.sca[1]) * Bc, 0.0, 0.0};
                         if (S && ks > 0.0) {
                             double Sc[4], Sgs[4];
                             for (int e = 0; e < 4; ++e)
@@ -1119,6 +1350,17 @@ int orc_emit(const orc_problem *P, int64_t pid, double out[13])
     out[10] = tau; out[11] = inside; out[12] = s;
     free((void *)C.cdf);
     return 0;
+}
+
+/* Local frame of cell c for direction n: out = [alpha1, alpha2, alpha3, s11, s12, gsca,
+ * theta', gth(3), gph(3)]. */
+void orc_frame(const orc_problem *P, int64_t c, const double n[3], double out[13])
+{
+    local_frame F;
+    make_local_frame(P, c, n, &F);
+    double v[13] = {F.alpha[0], F.alpha[1], F.alpha[2], F.sca[0], F.sca[1], F.gsca, F.thetap,
+                    F.gth[0], F.gth[1], F.gth[2], F.gph[0], F.gph[1], F.gph[2]};
+    memcpy(out, v, sizeof v);
 }
 
 /* One scattering of packet pid at scattering number n_sca with cell quaternion q:

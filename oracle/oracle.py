@@ -57,7 +57,8 @@ class Problem(C.Structure):
                 ("pid_begin", C.c_int64), ("pid_end", C.c_int64),
                 ("roulette_threshold", C.c_double), ("roulette_survival", C.c_double),
                 ("max_events", C.c_int64), ("max_trials", C.c_int32), ("n_threads", C.c_int32),
-                ("n_trace", C.c_int64), ("periodic", C.c_int32)]
+                ("n_trace", C.c_int64), ("periodic", C.c_int32),
+                ("eps_re", C.c_double), ("eps_im", C.c_double), ("aspect", C.c_double), ("size_x", C.c_double)]
 
 
 class Result(C.Structure):
@@ -103,6 +104,11 @@ def lib():
             L.orc_scatter.argtypes = [C.POINTER(Problem), C.c_int64, C.c_uint32, C.c_int, _f64p, _f64p, _f64p,
                                       _f64p]
             L.orc_scatter.restype = C.c_int
+            L.orc_frame.argtypes = [C.POINTER(Problem), C.c_int64, _f64p, _f64p]
+            L.orc_spheroid_L.argtypes = [C.c_double]
+            L.orc_spheroid_L.restype = C.c_double
+            L.orc_dipole_constants.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _f64p]
+            L.orc_dipole_scatter.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double] + [_f64p] * 5
     return _lib
 
 
@@ -200,6 +206,41 @@ def grain_meridian(q, n):
     return gth, gph, float(tp[0])
 
 
+DIPOLE_KEYS = ["L0", "L1", "al0_re", "al0_im", "al1_re", "al1_im", "q_ext0", "q_ext1", "q_sca0", "q_sca1",
+               "q_abs0", "q_abs1", "rho_re", "rho_im", "zn", "env"]
+
+
+def spheroid_L(s):
+    return lib().orc_spheroid_L(float(s))
+
+
+def dipole_constants(eps, aspect, x):
+    """Per-grain constants of the aligned dipole spheroid (index 0: a principal axis
+    perpendicular to the symmetry axis, 1: the symmetry axis)."""
+    o = np.zeros(16)
+    eps = complex(eps)
+    lib().orc_dipole_constants(eps.real, eps.imag, float(aspect), float(x), _pd(o))
+    return dict(zip(DIPOLE_KEYS, o.tolist()))
+
+
+def dipole_scatter(eps, aspect, x, axis, X, n, n2):
+    """Z X (1/sr) for the scattering n -> n2 by a spheroid with symmetry axis `axis`."""
+    eps = complex(eps)
+    axis, X, n, n2, o = _d(axis, 3), _d(X, 4), _d(n, 3), _d(n2, 3), np.zeros(4)
+    lib().orc_dipole_scatter(eps.real, eps.imag, float(aspect), float(x), _pd(axis), _pd(X), _pd(n), _pd(n2), _pd(o))
+    return o
+
+
+def frame(model, cell, n):
+    """Local frame of `cell` (flat index) for direction n: dict with alpha (K per unit
+    kappa_ext, grain-meridian basis), sca (s11, s12), gsca, thetap, gth, gph."""
+    keep = make_problem(model, {"sources": [], "cameras": []})
+    o, n = np.zeros(13), _d(n, 3)
+    lib().orc_frame(C.byref(keep.P), int(cell), _pd(n), _pd(o))
+    return {"alpha": o[0:3].copy(), "sca": o[3:5].copy(), "gsca": float(o[5]), "thetap": float(o[6]),
+            "gth": o[7:10].copy(), "gph": o[10:13].copy()}
+
+
 def dda_walk(shape_xyz, lo, hi, p0, n, max_cells=100000):
     n3 = (C.c_int32 * 3)(*shape_xyz)
     lo, hi, p0, n = _d(lo, 3), _d(hi, 3), _d(p0, 3), _d(n, 3)
@@ -239,15 +280,21 @@ def make_problem(model: dict, run: dict):
     P.bfield = f32("bf", model.get("bfield"))
     P.emissivity = f32("em", model.get("emissivity"))
     optics = model["optics"]
-    P.scat_model = 0 if optics["model"] == "rayleigh" else 1
+    P.scat_model = {"rayleigh": 0, "table": 1, "dipole": 2}[optics["model"]]
+    if P.scat_model == 2:
+        eps = complex(optics["eps"])
+        P.eps_re, P.eps_im = eps.real, eps.imag
+        P.aspect = float(optics["aspect"])
+        P.size_x = float(optics["x"])
     if P.scat_model == 1:
         mu = np.asarray(optics["mueller"], dtype=np.float32)
         P.n_bins, P.n_theta = mu.shape[0], mu.shape[1]
         P.mueller = f32("mu", mu)
         P.bin_weight = f32("bw", optics["bin_weight"])
-    kx = np.asarray(optics["kext"], dtype=np.float32)
-    P.n_ktheta = kx.shape[0]
-    P.kext = f32("kx", kx)
+    if P.scat_model != 2:  # the dipole spheroid computes its own K
+        kx = np.asarray(optics["kext"], dtype=np.float32)
+        P.n_ktheta = kx.shape[0]
+        P.kext = f32("kx", kx)
     srcs = run["sources"]
     arr = (Source * max(1, len(srcs)))()
     for i, s in enumerate(srcs):

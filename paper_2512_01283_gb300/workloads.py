@@ -19,6 +19,14 @@ Workloads (sizes as stated):
                     (181 angles); star plus thermal emission; 8 cameras at 256^2.
   twisted_slab      slab with a field rotating by 2 pi per unit optical depth (the
                     twisted-field test of Sec. 3.2).
+  spheroid_sphere   uniform sphere of aligned oblate dipole spheroids (aspect 2:1,
+                    m = 2.30 + 0.0228 i, as in the circumstellar test of Sec. 3.5) on a
+                    32^3 grid over [-1,1]^3, field along z, radial optical depth 0.01, 1
+                    or 10, central star, camera along x.
+  spheroid_atmosphere  plane-parallel slab of aligned spheroids with aspect 1.03 (the
+                    atmosphere test of Sec. 3.4), periodic in x and y, field along x,
+                    thermal emission, cameras at 45 deg inclination and a range of
+                    azimuths.
   sweep             batched sweep: 32 models with edges drawn uniformly in 32..192, clumpy
                     log-normal density (sigma_ln = 1), mean optical depth log-uniform in
                     [1, 100], times 8 wavelengths 0.5-3 um (kappa ~ lambda^-1.5); central
@@ -102,6 +110,14 @@ def synthetic_bins(n_bins=8, n_theta=N_THETA):
     w = np.sqrt(x)
     w = w / w.sum()
     return tabs.astype(np.float32), w.astype(np.float32), x
+
+
+def dipole_optics(eps=complex(2.30, 0.0228) ** 2, aspect=2.0, x=0.3):
+    """Aligned spheroids in the dipole approximation: complex dielectric function
+    `eps`, equatorial over symmetry semi-axis `aspect` (> 1 oblate, < 1 prolate; the
+    symmetry axis lies along the field), size parameter x = 2 pi a_eff / lambda.  The
+    cells' kappa_abs and kappa_sca are the orientation-averaged opacities."""
+    return {"model": "dipole", "eps": complex(eps), "aspect": float(aspect), "x": float(x)}
 
 
 def rayleigh_optics():
@@ -188,6 +204,43 @@ def plane_parallel_slab(nxy=4, nz=16, tau=1.0, albedo=0.9, periodic=3, b_angle_d
             "kappa_sca": (kext * albedo).astype(np.float32), "bfield": bf, "emissivity": None,
             "periodic": int(periodic),
             "optics": {"model": "rayleigh", "kext": kext_constant(-p, 0.0) if p else kext_isotropic()}}
+
+
+def spheroid_sphere(n=32, tau=1.0, albedo=0.5, radius=1.0, optics=None, b=(0.0, 0.0, 1.0)):
+    """Uniform sphere of aligned dipole spheroids (radial extinction optical depth tau,
+    given albedo) with a uniform field `b`."""
+    lo, hi = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    x, y, z = cell_centres((n, n, n), lo, hi)
+    r = np.sqrt(x * x + y * y + z * z)
+    kext = np.where(r <= radius, tau / radius, 0.0)
+    bf = np.zeros((n, n, n, 3), dtype=np.float32)
+    bf[...] = np.asarray(b, dtype=np.float32)
+    return {"lo": lo, "hi": hi, "kappa_abs": (kext * (1 - albedo)).astype(np.float32),
+            "kappa_sca": (kext * albedo).astype(np.float32), "bfield": bf, "emissivity": None,
+            "optics": optics or dipole_optics()}
+
+
+def spheroid_atmosphere(nxy=4, nz=32, tau=1.0, albedo=0.5, optics=None, emissivity=1.0):
+    """Plane-parallel slab (z in [0, 1], vertical extinction optical depth tau),
+    periodic in x and y, aligned spheroids with the field along x, uniform thermal
+    emission."""
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    shape = (nz, nxy, nxy)
+    kext = np.full(shape, tau, dtype=np.float64)
+    bf = np.zeros(shape + (3,), dtype=np.float32)
+    bf[..., 0] = 1.0
+    return {"lo": lo, "hi": hi, "kappa_abs": (kext * (1 - albedo)).astype(np.float32),
+            "kappa_sca": (kext * albedo).astype(np.float32), "bfield": bf,
+            "emissivity": np.full(shape, emissivity, dtype=np.float32), "periodic": 3,
+            "optics": optics or dipole_optics(aspect=1.03)}
+
+
+def atmosphere_cameras(n_az=8, incl_deg=45.0, npix=8):
+    """Cameras at inclination `incl_deg` from +z and azimuths 0..180 deg."""
+    i = math.radians(incl_deg)
+    return [camera((math.sin(i) * math.cos(a), math.sin(i) * math.sin(a), math.cos(i)), (npix, npix), (1.0, 1.0),
+                   center=(0.5, 0.5, 0.5))
+            for a in np.linspace(0.0, math.pi, n_az)]
 
 
 def center_source_run(n_packets, seed=5, cameras=None, pos=(0.5, 0.5, 0.5)):
