@@ -65,7 +65,9 @@ enum {
     MCRT_BOUNDARY_PERIODIC_Z = 4
 };
 enum { MCRT_SRC_POINT = 0, MCRT_SRC_BEAM = 1, MCRT_SRC_THERMAL = 2 };
-enum { MCRT_SCAT_RAYLEIGH = 0, MCRT_SCAT_TABLE = 1 };
+/* Grain optics: Rayleigh (dipole of a sphere) and tables use mcrt_set_dust_tables;
+ * aligned dipole spheroids use mcrt_set_dust_dipole. */
+enum { MCRT_SCAT_RAYLEIGH = 0, MCRT_SCAT_TABLE = 1, MCRT_SCAT_DIPOLE = 4 };
 enum { MCRT_FP32 = 0, MCRT_FP64 = 1 };
 enum { MCRT_OPTICS_TABLES = 0, MCRT_OPTICS_SURROGATE = 1 };
 /* Launch flags (mcrt_launch_desc.flags). */
@@ -212,6 +214,44 @@ MCRT_API mcrt_status mcrt_set_dust_tables(mcrt_ctx *ctx, int32_t model, int32_t 
                                  const float *kext);
 
 /*
+ * Grain optics of aligned spheroids in the dipole approximation (Sec. 2.1: the dipole
+ * approximation; Sec. 3: K from the optical theorem with no phase lag between the
+ * dipole excitations, so no U-V term).  The grain's symmetry axis lies along the
+ * cell's field (the grain frame of eq. grain-quaternion).
+ *   eps_re, eps_im  dielectric function of the grain material, eps_im >= 0, eps != 1
+ *   aspect          equatorial over symmetry semi-axis: > 1 oblate, < 1 prolate, 1 a
+ *                   sphere (then identical in distribution to MCRT_SCAT_RAYLEIGH)
+ *   size_x          size parameter 2 pi a_eff / lambda >= 0 (a_eff: radius of the sphere
+ *                   of equal volume), entering through the radiative-reaction correction
+ * On the device: depolarization factors L (closed forms of the ellipsoid integral),
+ * polarizabilities alpha_j = (eps-1)/(3(1+L_j(eps-1))) a_eff^3 with the radiative
+ * reaction alpha'_j = alpha_j / (1 - (2i/3) x^3 alpha_j / a_eff^3), and per axis the
+ * cross sections C_ext = 4 pi k Im alpha', C_sca = (8 pi/3) k^4 |alpha'|^2,
+ * C_abs = C_ext - C_sca.  The grid's kappa_abs and kappa_sca are read as the
+ * orientation-averaged opacities; along a direction n the extinction matrix is
+ *   K = kappa_abs Khat_abs(n) + kappa_sca Khat_sca(n)
+ * with each dichroic part relative to its orientation average, the scattering matrix
+ * Z = kappa_sca Zhat with Zhat from the Jones matrix of the induced dipole.  Packets
+ * sample scatterings at the unpolarized rate along n and take the weight
+ * (K_sca X)_0 / (K_sca,11 (Z X)_0) at each scattering.
+ * Replaces any optics set before.  Not accepted by batched launches, the surrogate
+ * (which learns tables) or mcrt_launch_packets_noalloc.
+ * Errors: MCRT_E_INVAL (bad parameters), MCRT_E_NOMEM, MCRT_E_CUDA.
+ */
+MCRT_API mcrt_status mcrt_set_dust_dipole(mcrt_ctx *ctx, double eps_re, double eps_im, double aspect,
+                                          double size_x);
+
+/*
+ * The constants mcrt_set_dust_dipole computes on the device, for checks:
+ *   out [16] host: L_perp, L_par, Re/Im alpha'_perp, Re/Im alpha'_par (per a_eff^3),
+ *        Qext_perp, Qext_par, Qsca_perp, Qsca_par, Qabs_perp, Qabs_par (efficiencies,
+ *        cross section over pi a_eff^2), Re/Im rho = alpha'_par / alpha'_perp,
+ *        zn (Zhat scale, 1/sr), env (rejection envelope of (Zhat X)_0 / I, 1/sr)
+ * Errors: MCRT_E_INVAL, MCRT_E_CUDA.
+ */
+MCRT_API mcrt_status mcrt_dipole_constants(double eps_re, double eps_im, double aspect, double size_x, double *out);
+
+/*
  * Step 1 of the two-step scheme (Sec. 2.2, 2.3): emit and transport packets,
  * accumulating per model the absorbed energy per cell and the source tally
  *   T_c[cell] = sum over path segments of Z(Omega_c; Omega_pp) int I_pp ds
@@ -264,6 +304,13 @@ MCRT_API const char *mcrt_last_error(const mcrt_ctx *ctx);
  *   4 path integral: in [n][8] (I,Q,U,V, a, alpha2, alpha3, dtau) -> out [n][4]
  *   5 scattering-matrix transfer: in [n][16] (I,Q,U,V, n, n2, P11,P12,P22,P33,P34,
  *     P44) -> out [n][4] (Stokes in the basis of n2)
+ *   6 dipole-spheroid scattering: in [n][16] (I,Q,U,V, n, n2, axis, Re rho, Im rho,
+ *     zn) -> out [n][4] (Zhat X in the basis of n2)
+ *   7 dipole-spheroid extinction: in [n][8] (ca_perp, ca_par, cs_perp, cs_par,
+ *     kappa_abs/kappa_ext, kappa_sca/kappa_ext, cos theta', unused) with ca, cs the
+ *     absorption and scattering cross sections over their orientation averages ->
+ *     out [n][4] (alpha1, alpha2, s11, s12: K and its scattering part per unit
+ *     kappa_ext, first row, grain-meridian basis)
  * precision selects the FP32 or FP64 instantiation.
  */
 MCRT_API mcrt_status mcrt_unit_eval(int32_t fn, int32_t precision, int64_t n, const double *in, double *out);

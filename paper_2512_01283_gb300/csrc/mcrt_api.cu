@@ -363,6 +363,64 @@ mcrt_status mcrt_set_dust_tables(mcrt_ctx* ctx, int32_t model, int32_t n_bins, i
     return MCRT_OK;
 }
 
+static mcrt_status dipole_args(mcrt_ctx* ctx, const char* me, double eps_re, double eps_im, double aspect,
+                               double x) {
+    if (!std::isfinite(eps_re) || !std::isfinite(eps_im) || !std::isfinite(aspect) || !std::isfinite(x))
+        return fail(ctx, MCRT_E_INVAL, "%s: non-finite parameter", me);
+    if (eps_im < 0.0) return fail(ctx, MCRT_E_INVAL, "%s: eps_im < 0 (a gain medium)", me);
+    if (eps_re == 1.0 && eps_im == 0.0) return fail(ctx, MCRT_E_INVAL, "%s: eps = 1 (no grain)", me);
+    if (!(aspect > 0.0)) return fail(ctx, MCRT_E_INVAL, "%s: aspect must be > 0", me);
+    if (x < 0.0) return fail(ctx, MCRT_E_INVAL, "%s: size_x must be >= 0", me);
+    return MCRT_OK;
+}
+
+// The 20 constants of k_dipole_setup, on the host.
+static cudaError_t dipole_setup_host(double eps_re, double eps_im, double aspect, double x, double out[20],
+                                     cudaStream_t s) {
+    DevIn d;
+    cudaError_t e = cudaMalloc(&d.owned, 20 * sizeof(double));
+    if (e == cudaSuccess) e = launch_dipole_setup(eps_re, eps_im, aspect, x, (double*)d.owned, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d.owned, 20 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
+mcrt_status mcrt_set_dust_dipole(mcrt_ctx* ctx, double eps_re, double eps_im, double aspect, double size_x) {
+    if (!ctx) return fail(nullptr, MCRT_E_INVAL, "mcrt_set_dust_dipole: ctx is NULL");
+    const mcrt_status st = dipole_args(ctx, "mcrt_set_dust_dipole", eps_re, eps_im, aspect, size_x);
+    if (st != MCRT_OK) return st;
+    double c[20];
+    CK(ctx, dipole_setup_host(eps_re, eps_im, aspect, size_x, c, ctx->stream));
+    for (int k = 0; k < 20; ++k)
+        if (!std::isfinite(c[k])) return fail(ctx, MCRT_E_INVAL, "mcrt_set_dust_dipole: singular polarizability");
+    free_tables(ctx);
+    ctx->cdf_valid = false;
+    TablesDev t{};
+    t.model = MCRT_SCAT_DIPOLE;
+    t.alpha1_mean = 1.0;  // K is relative to its orientation average
+    t.dip.rho_re = c[12];
+    t.dip.rho_im = c[13];
+    t.dip.zn = c[14];
+    t.dip.env = c[15];
+    t.dip.ca[0] = c[16];
+    t.dip.ca[1] = c[17];
+    t.dip.cs[0] = c[18];
+    t.dip.cs[1] = c[19];
+    ctx->t = t;
+    ctx->tables_set = true;
+    return MCRT_OK;
+}
+
+mcrt_status mcrt_dipole_constants(double eps_re, double eps_im, double aspect, double size_x, double* out) {
+    if (!out) return fail(nullptr, MCRT_E_INVAL, "mcrt_dipole_constants: out is NULL");
+    const mcrt_status st = dipole_args(nullptr, "mcrt_dipole_constants", eps_re, eps_im, aspect, size_x);
+    if (st != MCRT_OK) return st;
+    double c[20];
+    CK(nullptr, dipole_setup_host(eps_re, eps_im, aspect, size_x, c, nullptr));
+    std::memcpy(out, c, 16 * sizeof(double));
+    return MCRT_OK;
+}
+
 // Checks of a launch description that do not depend on the model.
 static mcrt_status check_desc(mcrt_ctx* ctx, const mcrt_launch_desc* d) {
     if (d->n_sources < 1 || d->n_sources > kMaxSources || !d->sources)
@@ -856,9 +914,9 @@ mcrt_status mcrt_destroy(mcrt_ctx* ctx) {
 }
 
 mcrt_status mcrt_unit_eval(int32_t fn, int32_t precision, int64_t n, const double* in, double* out) {
-    static const int in_w[6] = {6, 7, 10, 12, 8, 16};
-    static const int out_w[6] = {4, 8, 6, 4, 4, 4};
-    if (fn < 0 || fn > 5) return fail(nullptr, MCRT_E_INVAL, "mcrt_unit_eval: unknown fn %d", fn);
+    static const int in_w[8] = {6, 7, 10, 12, 8, 16, 16, 8};
+    static const int out_w[8] = {4, 8, 6, 4, 4, 4, 4, 4};
+    if (fn < 0 || fn > 7) return fail(nullptr, MCRT_E_INVAL, "mcrt_unit_eval: unknown fn %d", fn);
     if (precision != MCRT_FP32 && precision != MCRT_FP64) return fail(nullptr, MCRT_E_INVAL, "mcrt_unit_eval: precision");
     if (n < 0 || (n > 0 && (!in || !out))) return fail(nullptr, MCRT_E_INVAL, "mcrt_unit_eval: bad buffers");
     if (n == 0) return MCRT_OK;
@@ -941,6 +999,8 @@ mcrt_status batch_build(mcrt_batch** out, mcrt_ctx* const* models, int32_t n_mod
         if (!models[m]->tables_set) return fail(nullptr, MCRT_E_STATE, "batch: model %d has no optics", m);
         if (models[m]->t.model != models[0]->t.model)
             return fail(nullptr, MCRT_E_INVAL, "batch: all models need the same scattering model");
+        if (models[m]->t.model == MCRT_SCAT_DIPOLE)
+            return fail(nullptr, MCRT_E_INVAL, "batch: aligned-spheroid optics are a single-model option");
     }
     mcrt_batch* b = new (std::nothrow) mcrt_batch();
     if (!b) return fail(nullptr, MCRT_E_NOMEM, "batch: host allocation failed");

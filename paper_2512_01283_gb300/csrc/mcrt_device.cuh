@@ -346,6 +346,61 @@ template <typename T> __device__ __forceinline__ void apply_plane(const PlaneRot
 }
 
 // ---------------------------------------------------------------------------------
+// aligned dipole spheroids (Sec. 2.1 dipole approximation, Sec. 3 optical theorem)
+// ---------------------------------------------------------------------------------
+// First row of K per unit kappa_ext in the grain-meridian basis at cos theta' = ct, and
+// its scattering part (s11, s12).  A field along theta-hat' sees the symmetry axis with
+// weight sin^2 theta', one along phi-hat' not at all; each process' cross section is
+// c0 + (c1 - c0) w over its orientation average (ca: absorption, cs: scattering), and
+// fa, fs are kappa_abs / kappa_ext and kappa_sca / kappa_ext.
+template <typename T>
+__device__ __forceinline__ void dipole_K(T ca0, T ca1, T cs0, T cs1, T fa, T fs, T ct, T& a1, T& a2, T& s11, T& s12) {
+    T S2 = (T(1) - ct) * (T(1) + ct);
+    S2 = S2 > T(0) ? S2 : T(0);
+    const T ha = (ca1 - ca0) * T(0.5) * S2;
+    const T hs = (cs1 - cs0) * T(0.5) * S2;
+    s11 = fs * (cs0 + hs);
+    s12 = fs * hs;
+    a1 = fa * (ca0 + ha) + s11;
+    a2 = fa * ha + s12;
+}
+
+// Y = Zhat X for the scattering n -> n2 by a spheroid with symmetry axis ax: X in the
+// Stokes basis (th, ph) of n, Y in the basis (th2, ph2) of n2.  The induced dipole is
+// alpha'_0 (1 + (rho - 1) ax ax^T) E and the far field along n2 its transverse part, so
+// the Jones matrix is J_jk = f2_j . f_k + (rho - 1) (f2_j . ax)(ax . f_k); the coherency
+// matrix C = 1/2 [[I+Q, U+iV], [U-iV, I-Q]] goes to J C J^H, scaled by zn.
+template <typename T>
+__device__ __forceinline__ void dipole_apply(T rho_re, T rho_im, T zn, const V3<T>& ax, const V3<T>& th,
+                                             const V3<T>& ph, const V3<T>& th2, const V3<T>& ph2, const T X[4],
+                                             T Y[4]) {
+    const T rr = rho_re - T(1);
+    const T g0 = dot(th2, ax), g1 = dot(ph2, ax), b0 = dot(ax, th), b1 = dot(ax, ph);
+    // J = (Jr + i Ji)
+    const T Jr00 = dot(th2, th) + rr * g0 * b0, Ji00 = rho_im * g0 * b0;
+    const T Jr01 = dot(th2, ph) + rr * g0 * b1, Ji01 = rho_im * g0 * b1;
+    const T Jr10 = dot(ph2, th) + rr * g1 * b0, Ji10 = rho_im * g1 * b0;
+    const T Jr11 = dot(ph2, ph) + rr * g1 * b1, Ji11 = rho_im * g1 * b1;
+    // C (Hermitian): c00, c11 real, c01 = cr + i ci, c10 = conj(c01)
+    const T c00 = T(0.5) * (X[0] + X[1]), c11 = T(0.5) * (X[0] - X[1]);
+    const T cr = T(0.5) * X[2], ci = T(0.5) * X[3];
+    // M = J C
+    const T Mr00 = Jr00 * c00 + Jr01 * cr + Ji01 * ci, Mi00 = Ji00 * c00 + Ji01 * cr - Jr01 * ci;
+    const T Mr01 = Jr00 * cr - Ji00 * ci + Jr01 * c11, Mi01 = Jr00 * ci + Ji00 * cr + Ji01 * c11;
+    const T Mr10 = Jr10 * c00 + Jr11 * cr + Ji11 * ci, Mi10 = Ji10 * c00 + Ji11 * cr - Jr11 * ci;
+    const T Mr11 = Jr10 * cr - Ji10 * ci + Jr11 * c11, Mi11 = Jr10 * ci + Ji10 * cr + Ji11 * c11;
+    // D = M J^H: D_jk = sum_l M_jl conj(J_kl)
+    const T D00 = Mr00 * Jr00 + Mi00 * Ji00 + Mr01 * Jr01 + Mi01 * Ji01;
+    const T D11 = Mr10 * Jr10 + Mi10 * Ji10 + Mr11 * Jr11 + Mi11 * Ji11;
+    const T Dr01 = Mr00 * Jr10 + Mi00 * Ji10 + Mr01 * Jr11 + Mi01 * Ji11;
+    const T Di01 = Mi00 * Jr10 - Mr00 * Ji10 + Mi01 * Jr11 - Mr01 * Ji11;
+    Y[0] = zn * (D00 + D11);
+    Y[1] = zn * (D00 - D11);
+    Y[2] = zn * T(2) * Dr01;
+    Y[3] = zn * T(2) * Di01;
+}
+
+// ---------------------------------------------------------------------------------
 // uniform grid: exit distance of cell idx along n; ties go to the lowest axis
 // ---------------------------------------------------------------------------------
 template <typename T> struct GridT {

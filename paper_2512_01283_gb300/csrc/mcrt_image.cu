@@ -4,6 +4,8 @@
 // in-cell solution of App. A.  The per-cell source is the emission alpha_abs B plus
 // the step-1 scattering source S = omega / V * T_c, both turned into the
 // grain-meridian basis with the signed eta rotation of Sec. 2.1.
+#include <cuda/std/complex>
+
 #include "mcrt_device.cuh"
 #include "mcrt_internal.h"
 
@@ -92,7 +94,16 @@ template <typename T> __global__ void __launch_bounds__(128) k_image(const __gri
             if (kext > T(0) && ell > T(0)) {
                 const T omega = ks / kext;
                 T c2 = T(1), s2 = T(0), a1, a2, a3;
-                if (P.t.k_iso) {
+                T s11 = omega, s12 = T(0);  // scattering part of K's first row
+                if (P.t.model == MCRT_SCAT_DIPOLE) {
+                    const GrainFrame<T> f = grain_frame(P.g.cells[2 * c], Om, phc);
+                    c2 = f.c2;
+                    s2 = f.s2;
+                    const DipoleDev& dp = P.t.dip;
+                    dipole_K(T(dp.ca[0]), T(dp.ca[1]), T(dp.cs[0]), T(dp.cs[1]), T(r.x) / kext, omega, f.cos_tp, a1,
+                             a2, s11, s12);
+                    a3 = T(0);
+                } else if (P.t.k_iso) {
                     a1 = T(P.t.kext[0].x);
                     a2 = T(0);
                     a3 = T(0);
@@ -104,7 +115,8 @@ template <typename T> __global__ void __launch_bounds__(128) k_image(const __gri
                     kext_lookup(P.t, f.cos_tp, a1, a2, a3);
                 }
                 const T B = T(r.z);
-                T S[4] = {(a1 - omega) * B, a2 * B, T(0), T(0)};
+                // emission: the absorption part of K acting on (B, 0, 0, 0)
+                T S[4] = {(a1 - s11) * B, (a2 - s12) * B, T(0), T(0)};
                 if (P.S && ks > T(0)) {
                     const double* Sc = P.S + ((size_t)c * P.n_cam + P.cam_index) * 4;
                     const T f = omega * inv_vol;
@@ -352,10 +364,93 @@ template <typename T> __global__ void k_unit(int fn, long long n, const double* 
         T Y[4];
         apply_plane(r, P, X, Y);
         for (int e = 0; e < 4; ++e) out[4 * i + e] = Y[e];
+    } else if (fn == 6) {
+        const double* a = in + 16 * i;
+        const T X[4] = {T(a[0]), T(a[1]), T(a[2]), T(a[3])};
+        const V3<T> n{T(a[4]), T(a[5]), T(a[6])}, n2{T(a[7]), T(a[8]), T(a[9])}, ax{T(a[10]), T(a[11]), T(a[12])};
+        V3<T> th, ph, th2, ph2;
+        stokes_basis(n, th, ph);
+        stokes_basis(n2, th2, ph2);
+        T Y[4];
+        dipole_apply(T(a[13]), T(a[14]), T(a[15]), ax, th, ph, th2, ph2, X, Y);
+        for (int e = 0; e < 4; ++e) out[4 * i + e] = Y[e];
+    } else if (fn == 7) {
+        const double* a = in + 8 * i;
+        T a1, a2, s11, s12;
+        dipole_K(T(a[0]), T(a[1]), T(a[2]), T(a[3]), T(a[4]), T(a[5]), T(a[6]), a1, a2, s11, s12);
+        out[4 * i] = a1;
+        out[4 * i + 1] = a2;
+        out[4 * i + 2] = s11;
+        out[4 * i + 3] = s12;
     }
 }
 
+// Depolarization factor along the symmetry axis of a spheroid whose equatorial
+// semi-axis is s times the symmetry one.  With g = s^2 - 1 the oblate and prolate
+// closed forms of the ellipsoid integral are both s^2 F(g), F(g) = sum_k (-g)^k/(2k+3):
+// atan form for g > 0, atanh form for g < 0, and near the sphere (|g| < 0.25) the
+// series, whose terms then fall by 4x each.
+__device__ double spheroid_depolarization(double s) {
+    const double g = s * s - 1.0;
+    double F;
+    if (fabs(g) < 0.25) {
+        F = 0.0;
+        double t = 1.0;
+        for (int k = 0; k < 40; ++k) {
+            F += t / (2.0 * k + 3.0);
+            t *= -g;
+        }
+    } else if (g > 0.0) {
+        const double f = sqrt(g);
+        F = (1.0 - atan(f) / f) / g;
+    } else {
+        const double e = sqrt(-g);
+        F = (atanh(e) / e - 1.0) / (-g);
+    }
+    return s * s * F;
+}
+
+// Constants of aligned dipole spheroids (one thread): out[0..15] as documented for
+// mcrt_dipole_constants, then out[16..19] = ca_perp, ca_par, cs_perp, cs_par (cross
+// sections over their orientation averages (2 c_perp + c_par) / 3).
+__global__ void k_dipole_setup(double eps_re, double eps_im, double aspect, double x, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    using cplx = cuda::std::complex<double>;
+    const cplx eps(eps_re, eps_im);
+    double L[2];
+    L[1] = spheroid_depolarization(aspect);
+    L[0] = 0.5 * (1.0 - L[1]);
+    cplx al[2];
+    double qe[2], qs[2], qa[2];
+    const double x3 = x * x * x;
+    for (int j = 0; j < 2; ++j) {
+        const cplx a = (eps - 1.0) / (3.0 * (1.0 + L[j] * (eps - 1.0)));
+        al[j] = a / (1.0 - cplx(0.0, 2.0 / 3.0 * x3) * a);  // radiative reaction
+        qe[j] = 4.0 * x * al[j].imag();
+        qs[j] = 8.0 / 3.0 * x3 * x * cuda::std::norm(al[j]);
+        qa[j] = qe[j] - qs[j];
+    }
+    const cplx rho = al[1] / al[0];
+    const double r2 = cuda::std::norm(rho);
+    const double zn = 1.0 / (8.0 * 3.14159265358979323846 / 3.0 * (2.0 + r2) / 3.0);
+    const double o[16] = {L[0], L[1], al[0].real(), al[0].imag(), al[1].real(), al[1].imag(), qe[0], qe[1],
+                          qs[0], qs[1], qa[0], qa[1], rho.real(), rho.imag(), zn, (r2 > 1.0 ? r2 : 1.0) * zn};
+    for (int k = 0; k < 16; ++k) out[k] = o[k];
+    const double ma = (2.0 * qa[0] + qa[1]) / 3.0, ms = (2.0 * qs[0] + qs[1]) / 3.0;
+    // a process with zero cross section has no shape (its cell opacity must be 0)
+    out[16] = ma > 0.0 ? qa[0] / ma : 1.0;
+    out[17] = ma > 0.0 ? qa[1] / ma : 1.0;
+    out[18] = ms > 0.0 ? qs[0] / ms : 1.0;
+    out[19] = ms > 0.0 ? qs[1] / ms : 1.0;
+}
+
 }  // namespace
+
+cudaError_t launch_dipole_setup(double eps_re, double eps_im, double aspect, double x, double* out, cudaStream_t s) {
+    (void)cudaGetLastError();  // report this launch's error only
+    k_dipole_setup<<<1, 32, 0, s>>>(eps_re, eps_im, aspect, x, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_image(const ImageParams& p, int precision, cudaStream_t s) {
     const long long npix = (long long)p.npix[0] * p.npix[1];

@@ -33,6 +33,15 @@ struct GridDev {
     const float4* cells;  // [ncell][2]
 };
 
+// Aligned dipole spheroids (MCRT_SCAT_DIPOLE): index 0 a principal axis perpendicular
+// to the symmetry axis, 1 the symmetry axis.
+struct DipoleDev {
+    double rho_re, rho_im;  // alpha'_1 / alpha'_0
+    double ca[2], cs[2];    // absorption and scattering cross sections over their orientation averages
+    double zn;              // Zhat = zn M(J), 1/sr
+    double env;             // bound of (Zhat X)_0 / I
+};
+
 struct TablesDev {
     int model;            // MCRT_SCAT_*
     int n_bins, n_theta, n_ktheta;
@@ -45,6 +54,7 @@ struct TablesDev {
     const double* bin_cdf;  // [n_bins] normalised cumulative bin weights
     const float4* kext;   // [n_ktheta] (alpha1, alpha2, alpha3, 0)
     double alpha1_mean;
+    DipoleDev dip;        // MCRT_SCAT_DIPOLE constants
 };
 
 struct SourceDev {
@@ -180,6 +190,8 @@ int thermal_cdf_blocks(long long ncell);
 cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* guide, long long n_guide,
                                  cudaStream_t s);
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s);
+// one-thread kernel: the 16 constants of mcrt_dipole_constants into out (device)
+cudaError_t launch_dipole_setup(double eps_re, double eps_im, double aspect, double x, double* out, cudaStream_t s);
 // round-based paths (mcrt_wave.cu): the transport loop of one launch with the tally
 // (and, for the surrogate, the scattering) in kernels of their own; model is
 // kScatSurrogate or kScatTableDeferred; ms_out: device time of the whole loop;

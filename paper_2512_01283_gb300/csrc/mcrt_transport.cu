@@ -35,13 +35,20 @@ constexpr int kDefaultBlock = 128;
 #define MCRT_MIN_BLOCKS 5
 #endif
 // lanes of a warp that wait before the warp runs the scattering code (or takes new
-// packets) for all of them at once
+// packets) for all of them at once.  Measured on GB300: the table rounds of the 192^3
+// disk run fastest with 4 and 4 (1.00 s per 1e8-packet step; 1.05 s with 8 and 4, 1.08 s
+// with 1 and 1), the batched launch of the 256-job sweep with 8 and 4 (9.4e9 events/s;
+// 8.7e9 with 4 and 4, 7.5e9 with 1 and 1)
 #ifndef MCRT_SCATTER_BATCH
-#define MCRT_SCATTER_BATCH 8
+#define MCRT_SCATTER_BATCH 4
+#endif
+#ifndef MCRT_SCATTER_BATCH_JOBS
+#define MCRT_SCATTER_BATCH_JOBS 8
 #endif
 #ifndef MCRT_REFILL_BATCH
 #define MCRT_REFILL_BATCH 4
 #endif
+template <bool B> constexpr int scatter_batch() { return B ? MCRT_SCATTER_BATCH_JOBS : MCRT_SCATTER_BATCH; }
 // per-thread staging slot for the TMA bulk reduction of one segment's source
 // contributions: up to 8 cameras x 4 Stokes FP64 (256 B), padded to 272 B so that
 // the 16-byte stores of a warp spread over all shared-memory banks
@@ -237,19 +244,27 @@ __device__ bool emit(const TransportParams& P, const JobRef<T, B>& job, long lon
         pk.nz = n[2];
         inside = true;
         load_cell(job, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
-        // emission alpha_abs B (1,0,0,0) in the grain-meridian basis, weight
-        // (alpha1(theta') - omega) / (mean alpha1 - omega)
+        // emission alpha_abs B (1,0,0,0) in the grain-meridian basis, with alpha_abs the
+        // absorption part of K (K minus its scattering part (s11, s12)); weight
+        // alpha_abs,11(theta') over its mean over directions (mean alpha1 - omega)
         const T kext = T(pk.cr.x) + T(pk.cr.y);
         const T omega = kext > T(0) ? T(pk.cr.y) / kext : T(0);
         const V3<T> nv{pk.nx, pk.ny, pk.nz};
         V3<T> th, ph;
         stokes_basis(nv, th, ph);
         const GrainFrame<T> f = grain_frame(pk.cq, nv, ph);
-        T a1, a2, a3;
-        kext_eval(job.t(), job.kext(), f.cos_tp, a1, a2, a3);
-        const T w = (a1 - omega) / (T(job.t().alpha1_mean) - omega);
+        const TablesDev& tb = job.t();
+        T a1, a2, a3, s11 = omega, s12 = T(0);
+        if (tb.model == MCRT_SCAT_DIPOLE) {
+            dipole_K(T(tb.dip.ca[0]), T(tb.dip.ca[1]), T(tb.dip.cs[0]), T(tb.dip.cs[1]), T(pk.cr.x) / kext, omega,
+                     f.cos_tp, a1, a2, s11, s12);
+            a3 = T(0);
+        } else {
+            kext_eval(tb, job.kext(), f.cos_tp, a1, a2, a3);
+        }
+        const T w = (a1 - s11) / (T(tb.alpha1_mean) - omega);
         pk.X0 = eps * w;
-        pk.X1 = eps * w * a2 / (a1 - omega);
+        pk.X1 = (a1 - s11) > T(0) ? eps * w * (a2 - s12) / (a1 - s11) : T(0);
         rotate_qu(pk.X1, pk.X2, f.c2, -f.s2);
     } else {
         T p[3], n[3];
@@ -383,10 +398,26 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         alive = false;
         return;
     }
-    const T omega = kext > T(0) ? t_div(ks, kext) : T(0);
-    const T dsca_exit = ks * ell_exit;
-    const bool scatter_here = (ks > T(0)) && (pk.tau < widen(dsca_exit));
-    const T ell = scatter_here ? T(pk.tau) / ks : ell_exit;
+    // scattering rate along n: kappa_sca for Theta-only optics; for aligned spheroids the
+    // unpolarized rate kappa_ext s11(theta'), which needs the grain frame first
+    T ks_n = ks;
+    GrainFrame<T> dip_f{T(1), T(0), T(1)};
+    if constexpr (SCAT == MCRT_SCAT_DIPOLE) {
+        if (kext > T(0)) {
+            const V3<T> n0{pk.nx, pk.ny, pk.nz};
+            V3<T> th0, ph0;
+            stokes_basis(n0, th0, ph0);
+            dip_f = grain_frame(pk.cq, n0, ph0);
+            T S2 = (T(1) - dip_f.cos_tp) * (T(1) + dip_f.cos_tp);
+            S2 = S2 > T(0) ? S2 : T(0);
+            const T c0 = T(tabs.dip.cs[0]);
+            ks_n = ks * (c0 + (T(tabs.dip.cs[1]) - c0) * T(0.5) * S2);
+        }
+    }
+    const T omega = kext > T(0) ? t_div(ks_n, kext) : T(0);
+    const T dsca_exit = ks_n * ell_exit;
+    const bool scatter_here = (ks_n > T(0)) && (pk.tau < widen(dsca_exit));
+    const T ell = scatter_here ? T(pk.tau) / ks_n : ell_exit;
 
     // the next cell's record is requested before the segment arithmetic
     int nix = pk.ix, niy = pk.iy, niz = pk.iz;
@@ -416,7 +447,14 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
 
     if (want_A) {
         T c2 = T(1), s2 = T(0), a1, a2, a3;
-        if (tabs.k_iso) {
+        if constexpr (SCAT == MCRT_SCAT_DIPOLE) {
+            c2 = dip_f.c2;
+            s2 = dip_f.s2;
+            T s11, s12;
+            dipole_K(T(tabs.dip.ca[0]), T(tabs.dip.ca[1]), T(tabs.dip.cs[0]), T(tabs.dip.cs[1]),
+                     t_div(T(pk.cr.x), kext), t_div(ks, kext), dip_f.cos_tp, a1, a2, s11, s12);
+            a3 = T(0);
+        } else if (tabs.k_iso) {
             a1 = T(job.kext()[0].x);
             a2 = T(0);
             a3 = T(0);
@@ -497,21 +535,28 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             pk.n_tally++;
             double* Sc = job.S() + (size_t)c32 * (size_t)P.n_cam * 4;
             double* slot = sm.stage + threadIdx.x * kStageDoubles;
+            V3<T> ax{T(0), T(0), T(1)};
+            if constexpr (SCAT == MCRT_SCAT_DIPOLE) ax = quat_to_lab(pk.cq, ax);
             for (int k0 = 0; k0 < P.n_cam; k0 += kStageCams) {
                 const int kn = P.n_cam - k0 < kStageCams ? P.n_cam - k0 : kStageCams;
                 if (lane == leader) bulk_wait_read();  // the slot's previous reduction has read it
                 for (int k = 0; k < kn; ++k) {
                     V3<T> Om, thc, phc;
                     load_camera(sm.cam + 12 * (k0 + k), Om, thc, phc);
-                    const T mu = dot(n, Om);
-                    T Pm[6];
-                    if (SCAT == MCRT_SCAT_RAYLEIGH)
-                        rayleigh_matrix(mu, Pm);
-                    else
-                        table_matrix(job.mix(), tabs.n_theta, mu, Pm);
-                    const PlaneRot<T> pr = plane_rotation(n, th, ph, Om, thc, phc);
                     T sv[4];
-                    apply_plane(pr, Pm, Wg, sv);
+                    if constexpr (SCAT == MCRT_SCAT_DIPOLE) {
+                        dipole_apply(T(tabs.dip.rho_re), T(tabs.dip.rho_im), T(tabs.dip.zn), ax, th, ph, thc, phc, Wg,
+                                     sv);
+                    } else {
+                        const T mu = dot(n, Om);
+                        T Pm[6];
+                        if (SCAT == MCRT_SCAT_RAYLEIGH)
+                            rayleigh_matrix(mu, Pm);
+                        else
+                            table_matrix(job.mix(), tabs.n_theta, mu, Pm);
+                        const PlaneRot<T> pr = plane_rotation(n, th, ph, Om, thc, phc);
+                        apply_plane(pr, Pm, Wg, sv);
+                    }
                     if (gmax > 1u) {
 #pragma unroll
                         for (int e = 0; e < 4; ++e) sv[e] = group_sum(actS, group, sv[e], gmax);
@@ -598,6 +643,54 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
             alive = false;
             return;
         }
+    }
+    if constexpr (SCAT == MCRT_SCAT_DIPOLE) {
+        // aligned spheroid: isotropic proposal, envelope env I >= (Zhat X)_0; the new
+        // Stokes vector is Zhat X (K_sca X)_0 / (s11 (Zhat X)_0), i.e. Zhat X renormalised
+        // to I + (s12 / s11) Q with Q in the grain-meridian basis
+        const DipoleDev& dp = tabs.dip;
+        const V3<T> ax = quat_to_lab(pk.cq, V3<T>{T(0), T(0), T(1)});
+        const GrainFrame<T> f = grain_frame(pk.cq, n, ph);
+        T Qg = pk.X1, Ug = pk.X2;
+        rotate_qu(Qg, Ug, f.c2, f.s2);
+        T S2 = (T(1) - f.cos_tp) * (T(1) + f.cos_tp);
+        S2 = S2 > T(0) ? S2 : T(0);
+        const T hs = (T(dp.cs[1]) - T(dp.cs[0])) * T(0.5) * S2;
+        const T Iw = pk.X0 + t_div(hs, T(dp.cs[0]) + hs) * Qg;
+        const T X[4] = {pk.X0, pk.X1, pk.X2, pk.X3};
+        const T rho_re = T(dp.rho_re), rho_im = T(dp.rho_im), zn = T(dp.zn), env = T(dp.env);
+        V3<T> n2;
+        T Y[4];
+        bool accepted = false;
+        for (int t = 0; t < P.max_trials; ++t) {
+            const Draw4<T> ut = draw4<T>(pk.pid, pk.n_sca, 1u + (unsigned)t, P.seed, job.stream());
+            pk.trials++;
+            T g2[3];
+            iso_dir(ut.a, ut.b, g2);
+            n2 = quat_to_lab(pk.cq, V3<T>{g2[0], g2[1], g2[2]});
+            V3<T> th2, ph2;
+            stokes_basis(n2, th2, ph2);
+            dipole_apply(rho_re, rho_im, zn, ax, th, ph, th2, ph2, X, Y);
+            if (ut.c * env * X[0] < Y[0]) {
+                accepted = true;
+                break;
+            }
+        }
+        if (!accepted) {
+            finish(P, pk, 4, bt);
+            alive = false;
+            return;
+        }
+        const T norm = Iw / Y[0];
+        pk.X0 = Y[0] * norm;
+        pk.X1 = Y[1] * norm;
+        pk.X2 = Y[2] * norm;
+        pk.X3 = Y[3] * norm;
+        pk.nx = n2.x;
+        pk.ny = n2.y;
+        pk.nz = n2.z;
+        pk.tau = -(double)t_log(us.a);
+        return;
     }
     int bin = 0;
     const float4* tab = nullptr;
@@ -710,7 +803,7 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
     float4* s_kext = reinterpret_cast<float4*>(smem_raw);
     const int n_k = B ? 0 : P.t.n_ktheta;
     float4* s_mix = s_kext + n_k;
-    const int n_mix = (!B && SCAT != MCRT_SCAT_RAYLEIGH) ? 2 * P.t.n_theta : 0;
+    const int n_mix = (!B && SCAT != MCRT_SCAT_RAYLEIGH && SCAT != MCRT_SCAT_DIPOLE) ? 2 * P.t.n_theta : 0;
     T* s_cam = reinterpret_cast<T*>(s_mix + n_mix);
     const int cam_bytes = 12 * P.n_cam * (int)sizeof(T);
     double* s_stage = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(s_cam) + cam_bytes);
@@ -807,7 +900,7 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
             continue;
         }
         // scatterings of the warp run together once enough lanes wait for one
-        if (pend != 0u && (__popc(pend) >= MCRT_SCATTER_BATCH || work == 0u)) {
+        if (pend != 0u && (__popc(pend) >= scatter_batch<B>() || work == 0u)) {
             if constexpr (SCAT != kScatSurrogate) {  // the surrogate scatters in its own kernel
                 if (alive && pk.pending) {
                     pk.pending = false;
@@ -845,6 +938,9 @@ size_t transport_smem_bytes(const TransportParams& p, int precision, int block) 
 }
 
 const void* transport_kernel(int precision, int model, bool batch) {
+    if (model == MCRT_SCAT_DIPOLE)  // single-model launches only
+        return precision == MCRT_FP64 ? (const void*)k_transport<double, MCRT_SCAT_DIPOLE, false>
+                                      : (const void*)k_transport<float, MCRT_SCAT_DIPOLE, false>;
     if (precision == MCRT_FP64) {
         if (model == MCRT_SCAT_TABLE)
             return batch ? (const void*)k_transport<double, MCRT_SCAT_TABLE, true>

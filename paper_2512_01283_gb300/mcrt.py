@@ -20,7 +20,7 @@ MCRT_OK, MCRT_E_INVAL, MCRT_E_NOMEM, MCRT_E_CUDA, MCRT_E_EVENT_CAP, MCRT_E_TIMEO
 STATUS_NAMES = {0: "MCRT_OK", -1: "MCRT_E_INVAL", -2: "MCRT_E_NOMEM", -3: "MCRT_E_CUDA", -4: "MCRT_E_EVENT_CAP",
                 -5: "MCRT_E_TIMEOUT", -6: "MCRT_E_STATE"}
 SRC = {"point": 0, "beam": 1, "thermal": 2}
-SCAT = {"rayleigh": 0, "table": 1}
+SCAT = {"rayleigh": 0, "table": 1, "dipole": 4}
 PRECISION = {"fp32": 0, "fp64": 1}
 
 
@@ -90,7 +90,8 @@ SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "m
            "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_tune", "mcrt_batch_images", "mcrt_batch_destroy",
            "mcrt_surrogate_create", "mcrt_surrogate_train", "mcrt_surrogate_eval", "mcrt_surrogate_labels",
            "mcrt_surrogate_grad", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy",
-           "mcrt_surrogate_error_map", "mcrt_set_surrogate", "mcrt_surrogate_eval_engine"]
+           "mcrt_surrogate_error_map", "mcrt_set_surrogate", "mcrt_surrogate_eval_engine", "mcrt_set_dust_dipole",
+           "mcrt_dipole_constants"]
 
 
 def lib():
@@ -130,6 +131,9 @@ def lib():
     L.mcrt_surrogate_error_map.argtypes = [vp, i64, vp]
     L.mcrt_set_surrogate.argtypes = [vp, vp, C.c_double]
     L.mcrt_surrogate_eval_engine.argtypes = [vp, i32, i64, vp, vp]
+    d = C.c_double
+    L.mcrt_set_dust_dipole.argtypes = [vp, d, d, d, d]
+    L.mcrt_dipole_constants.argtypes = [d, d, d, d, C.POINTER(C.c_double)]
     for name in SYMBOLS:
         if name not in ("mcrt_last_error", "mcrt_surrogate_param_count"):
             getattr(L, name).restype = C.c_int
@@ -160,6 +164,19 @@ def _stream_handle(stream):
     if hasattr(stream, "cuda_stream"):
         return C.c_void_p(stream.cuda_stream)
     return C.c_void_p(int(stream))
+
+
+DIPOLE_KEYS = ["L0", "L1", "al0_re", "al0_im", "al1_re", "al1_im", "q_ext0", "q_ext1", "q_sca0", "q_sca1",
+               "q_abs0", "q_abs1", "rho_re", "rho_im", "zn", "env"]
+
+
+def dipole_constants(eps, aspect, x):
+    """Constants of aligned dipole spheroids as the device computes them
+    (mcrt_dipole_constants); index 0 perpendicular to the symmetry axis, 1 along it."""
+    eps = complex(eps)
+    out = (C.c_double * 16)()
+    _check(lib().mcrt_dipole_constants(eps.real, eps.imag, float(aspect), float(x), out))
+    return dict(zip(DIPOLE_KEYS, list(out)))
 
 
 class Model:
@@ -194,6 +211,11 @@ class Model:
     def set_optics(self, optics: dict):
         L = lib()
         m = SCAT[optics["model"]]
+        if m == SCAT["dipole"]:
+            eps = complex(optics["eps"])
+            _check(L.mcrt_set_dust_dipole(self.h, eps.real, eps.imag, float(optics["aspect"]), float(optics["x"])),
+                   self.h)
+            return
         pkx, kx = _ptr(optics["kext"], np.float32)
         n_k = int(np.asarray(optics["kext"]).shape[0]) if not hasattr(optics["kext"], "is_cuda") else optics["kext"].shape[0]
         if m == 1:
@@ -310,7 +332,7 @@ def launch(models, run: dict, precision="fp32", trace=None, n_trace=0, sync=True
 def unit_eval(fn: int, inputs, precision="fp32"):
     """mcrt_unit_eval: evaluate a device building block on host inputs."""
     L = lib()
-    widths_out = [4, 8, 6, 4, 4, 4]
+    widths_out = [4, 8, 6, 4, 4, 4, 4, 4]
     a = np.ascontiguousarray(np.asarray(inputs, dtype=np.float64))
     n = a.shape[0]
     out = np.zeros((n, widths_out[fn]))
