@@ -1058,6 +1058,15 @@ static void transport_packet(run_ctx *C, int64_t pid)
             orc_attenuate(Xg, a, F.alpha[1], F.alpha[2], dtau, Yg);
             orc_change_basis(Yg, F.gth, F.gph, F.th, F.ph, Y);
             double dI = X[0] - Y[0];
+            if (P->scat_model == 2) {
+                /* the decrease of I holds kappa_ext s12 int Q dl, the polarization-dependent
+                 * part of the scattering rate; it is not absorption and returns in
+                 * expectation through the scattering weight, so the absorbed tally is
+                 * int (K_abs X)_0 dl */
+                double Wt[4];
+                orc_segment_integral(Xg, a, F.alpha[1], F.alpha[2], dtau, Wt);
+                dI -= F.sca[1] * Wt[1];
+            }
             if (ks > 0.0 && P->n_cam > 0) {
                 double W[4];
                 orc_segment_integral(Xg, a, F.alpha[1], F.alpha[2], dtau, Wg);
