@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--sweep-packets", type=float, default=1e6, help="packets per job of the batched sweep")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-plane-parallel", action="store_true")
+    ap.add_argument("--no-spheroids", action="store_true", help="skip the aligned-spheroid line")
     ap.add_argument("--inline-tally", action="store_true",
                     help="table path: tally inside the transport kernel instead of a tally kernel per round")
     ap.add_argument("--tally-bps", type=int, default=0,
@@ -213,6 +214,37 @@ def run_plane_parallel(M, W, torch):
             "energy_balance_rel": abs(bal - st["emitted_energy"]) / st["emitted_energy"]}
 
 
+def run_spheroids(M, W, torch):
+    """Aligned oblate dipole spheroids (2:1, m = 2.30 + 0.0228 i, x = 0.3), the
+    circumstellar scene of Sec. 3.5 at a benchmark size: uniform sphere on a 128^3
+    grid, radial optical depth 1, albedo 0.5, field along z, central star, 1e7
+    packets, cameras along x and z at 256^2, FP32."""
+    model = W.spheroid_sphere(n=128, tau=1.0, albedo=0.5)
+    run = {"sources": [{"type": "point", "pos": (0.0, 0.0, 0.0), "luminosity": 1.0, "n_packets": 10_000_000}],
+           "cameras": [W.camera((1.0, 0.0, 0.0), (256, 256), (2.0, 2.0)), W.camera((0.0, 0.0, 1.0), (256, 256), (2.0, 2.0))],
+           "roulette_threshold": 1e-4, "roulette_survival": 0.1}
+    m = M.Model(model)
+    M.launch(m, dict(run, seed=92), precision="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = M.launch(m, dict(run, seed=93), precision="fp32")
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    img = np.zeros((4, 256, 256))
+    m.image(0, img)
+    m.close()
+    bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
+    return {"workload": "aligned oblate dipole spheroids (2:1, m = 2.30+0.0228i, x = 0.3), uniform sphere 128^3, "
+                        "tau 1, albedo 0.5, field along z, central star, 1e7 packets, 2 cameras at 256^2",
+            "value": st["events"] / wall, "unit": UNIT, "events": st["events"], "seconds": wall,
+            "scatterings": st["scatterings"], "trials_per_scattering": st["trials"] / max(1.0, st["scatterings"]),
+            # zero in expectation (Monte-Carlo noise): the polarization-dependent scattering
+            # weights change single packets' energy
+            "energy_balance_rel": (bal - st["emitted_energy"]) / st["emitted_energy"],
+            "image_x": {"I": float(img[0].sum()), "Q_over_I": float(img[1].sum() / img[0].sum()),
+                        "V_over_I": float(img[3].sum() / img[0].sum())}}
+
+
 def image_diff(a, b):
     """Relative L2 differences of Stokes image stacks [cam][4][ny][nx]: I, and
     (Q, U) against I; plus the largest relative difference of integrated I."""
@@ -360,16 +392,33 @@ def main():
     B.build()
 
     model = W.disk(n=args.grid)
-    # independent packets per rank (weak scaling, Philox stream = rank), no data-path collective
-    run = MG.rank_run(W.disk_run(n_packets=int(args.packets)), rank)
+    # weak scaling: the whole job has `world` times the packets, each rank runs its share
+    # of every source's packet ids (all of them on one rank); no collective on the transport
+    run = MG.scaled_run(W.disk_run(n_packets=int(args.packets)), world)
     n_cam = len(run["cameras"])
     npix = run["cameras"][0]["npix"]
     mdl = M.Model(model)
     imgs = torch.empty((n_cam, 4, npix[1], npix[0]), dtype=torch.float64, device="cuda")
+    S_sum = A_sum = None
+    if world > 1:
+        S_sum = torch.empty((mdl.ncell, n_cam, 4), dtype=torch.float64, device="cuda")
+        A_sum = torch.empty((mdl.ncell,), dtype=torch.float64, device="cuda")
+
+    def launch_share(m_, seed, **kw):
+        return MG.rank_launch(lambda r, acc: M.launch(m_, dict(r, seed=seed), precision="fp32", accumulate=acc, **kw),
+                              run, rank, world)
+
+    def exchange(m_):
+        # the one exchange of a sharded run: FP64 tallies summed over ranks before step 2
+        if world > 1:
+            m_.tallies_into(S_sum, A_sum)
+            MG.combine_tallies(S_sum, A_sum, dist)
+            m_.set_tallies(S_sum, A_sum)
 
     def step(seed):
-        st = M.launch(mdl, dict(run, seed=seed), precision="fp32", inline_tally=args.inline_tally,
-                      tally_blocks_per_sm=args.tally_bps, blocks_per_sm=args.transport_bps)
+        st = launch_share(mdl, seed, inline_tally=args.inline_tally, tally_blocks_per_sm=args.tally_bps,
+                          blocks_per_sm=args.transport_bps)
+        exchange(mdl)
         for k in range(n_cam):
             mdl.image(k, imgs[k])
         return st
@@ -471,7 +520,8 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             m2 = M.Model(model)
-            st = M.launch(m2, dict(run, seed=3000 + s), precision="fp32")
+            st = launch_share(m2, 3000 + s)
+            exchange(m2)
             for k in range(n_cam):
                 m2.image(k, host_imgs[k])
             m2.close()
@@ -487,6 +537,9 @@ def main():
 
     if not args.no_plane_parallel and world == 1:
         line["plane_parallel"] = run_plane_parallel(M, W, torch)
+
+    if not args.no_spheroids and world == 1:
+        line["spheroids"] = run_spheroids(M, W, torch)
 
     if not args.no_surrogate and world == 1:
         table_imgs = imgs.cpu().numpy()

@@ -284,6 +284,16 @@ MCRT_API mcrt_status mcrt_image_stokes(mcrt_ctx *ctx, int32_t camera, double *ou
  */
 MCRT_API mcrt_status mcrt_get_tallies(mcrt_ctx *ctx, double *source, double *absorbed);
 
+/*
+ * Replace the step-1 tallies of the last launch (layouts as in mcrt_get_tallies), e.g.
+ * with their sum over ranks that each ran a share of the packet ids: step 2 is linear
+ * in the tallies (Sec. 2.3), so images of the summed tallies are the images of all
+ * packets.  Either pointer may be NULL (that tally is kept).  Host or device; the
+ * caller keeps ownership.
+ * Errors: MCRT_E_INVAL, MCRT_E_STATE (no launch yet), MCRT_E_CUDA.
+ */
+MCRT_API mcrt_status mcrt_set_tallies(mcrt_ctx *ctx, const double *source, const double *absorbed);
+
 /* Release the context and its device memory; NULL is accepted. */
 MCRT_API mcrt_status mcrt_destroy(mcrt_ctx *ctx);
 

@@ -865,6 +865,19 @@ mcrt_status mcrt_get_tallies(mcrt_ctx* ctx, double* source, double* absorbed) {
     return MCRT_OK;
 }
 
+mcrt_status mcrt_set_tallies(mcrt_ctx* ctx, const double* source, const double* absorbed) {
+    if (!ctx) return fail(nullptr, MCRT_E_INVAL, "mcrt_set_tallies: ctx is NULL");
+    if (!ctx->launched) return fail(ctx, MCRT_E_STATE, "mcrt_set_tallies: no launch yet");
+    if (source && ctx->n_cam > 0)
+        CK(ctx, cudaMemcpyAsync(ctx->d_S, source, (size_t)ctx->g.ncell * ctx->n_cam * 4 * sizeof(double),
+                                cudaMemcpyDefault, ctx->stream));
+    if (absorbed)
+        CK(ctx, cudaMemcpyAsync(ctx->d_absorbed, absorbed, (size_t)ctx->g.ncell * sizeof(double), cudaMemcpyDefault,
+                                ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return MCRT_OK;
+}
+
 mcrt_status mcrt_set_surrogate(mcrt_ctx* ctx, mcrt_surrogate* s, double bound) {
     if (!ctx || !s) return fail(ctx, MCRT_E_INVAL, "mcrt_set_surrogate: ctx or surrogate is NULL");
     if (!ctx->tables_set || ctx->t.model != MCRT_SCAT_TABLE)

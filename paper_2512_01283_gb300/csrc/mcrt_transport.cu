@@ -447,10 +447,11 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
 
     if (want_A) {
         T c2 = T(1), s2 = T(0), a1, a2, a3;
+        T s12 = T(0);  // aligned spheroids: polarization-dependent part of the scattering rate
         if constexpr (SCAT == MCRT_SCAT_DIPOLE) {
             c2 = dip_f.c2;
             s2 = dip_f.s2;
-            T s11, s12;
+            T s11;
             dipole_K(T(tabs.dip.ca[0]), T(tabs.dip.ca[1]), T(tabs.dip.cs[0]), T(tabs.dip.cs[1]),
                      t_div(T(pk.cr.x), kext), t_div(ks, kext), dip_f.cos_tp, a1, a2, s11, s12);
             a3 = T(0);
@@ -469,12 +470,15 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         T Xg[4] = {pk.X0, pk.X1, pk.X2, pk.X3};
         rotate_qu(Xg[1], Xg[2], c2, s2);
         T Yg[4], Wg[4];
-        transfer(Xg, a, a2, a3, dtau, Yg, Wg, want_S, ell);
+        transfer(Xg, a, a2, a3, dtau, Yg, Wg, want_S || SCAT == MCRT_SCAT_DIPOLE, ell);
         rotate_qu(Yg[1], Yg[2], c2, -s2);
         // absorbed energy, one FP64 atomic per same-cell group
         {
             const unsigned gmax = __reduce_max_sync(actA, (unsigned)__popc(group));
             T dI = pk.X0 - Yg[0];
+            // aligned spheroids: the decrease of I also holds kappa_ext s12 int Q dl, which the
+            // scattering weight returns in expectation; the absorbed energy is int (K_abs X)_0 dl
+            if constexpr (SCAT == MCRT_SCAT_DIPOLE) dI -= kext * s12 * Wg[1];
             pk.e_abs += dI;
             if (dI != T(0)) pk.n_abs++;
             if (gmax > 1u) dI = group_sum(actA, group, dI, gmax);

@@ -91,7 +91,7 @@ SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "m
            "mcrt_surrogate_create", "mcrt_surrogate_train", "mcrt_surrogate_eval", "mcrt_surrogate_labels",
            "mcrt_surrogate_grad", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy",
            "mcrt_surrogate_error_map", "mcrt_set_surrogate", "mcrt_surrogate_eval_engine", "mcrt_set_dust_dipole",
-           "mcrt_dipole_constants"]
+           "mcrt_dipole_constants", "mcrt_set_tallies"]
 
 
 def lib():
@@ -109,6 +109,7 @@ def lib():
     L.mcrt_launch_packets.argtypes = [C.POINTER(C.c_void_p), i32, C.POINTER(LaunchDesc), C.POINTER(Stats)]
     L.mcrt_image_stokes.argtypes = [vp, i32, vp]
     L.mcrt_get_tallies.argtypes = [vp, vp, vp]
+    L.mcrt_set_tallies.argtypes = [vp, vp, vp]
     L.mcrt_destroy.argtypes = [vp]
     L.mcrt_last_error.argtypes = [vp]
     L.mcrt_last_error.restype = C.c_char_p
@@ -247,6 +248,21 @@ class Model:
         _check(L.mcrt_get_tallies(self.h, C.c_void_p(S.ctypes.data) if n_cam > 0 else None,
                                   C.c_void_p(A.ctypes.data)), self.h)
         return S[:, :n_cam], A
+
+    def tallies_into(self, source=None, absorbed=None):
+        """mcrt_get_tallies into caller buffers (numpy or CUDA tensors, FP64, contiguous)."""
+        for b in (source, absorbed):
+            if isinstance(b, np.ndarray) and (b.dtype != np.float64 or not b.flags.c_contiguous):
+                raise ValueError("tally buffers must be contiguous float64")
+        ps, ks = _ptr(source, np.float64)
+        pa, ka = _ptr(absorbed, np.float64)
+        _check(lib().mcrt_get_tallies(self.h, ps, pa), self.h)
+
+    def set_tallies(self, source=None, absorbed=None):
+        """mcrt_set_tallies: replace the last launch's tallies (e.g. with their sum over ranks)."""
+        ps, ks = _ptr(source, np.float64)
+        pa, ka = _ptr(absorbed, np.float64)
+        _check(lib().mcrt_set_tallies(self.h, ps, pa), self.h)
 
     def close(self):
         if getattr(self, "h", None):

@@ -142,6 +142,9 @@ def test_spheroid_sphere_parity(sphere_oracle, prec):
     assert frac >= (0.999 if prec == "fp64" else 0.99), frac
     dS = np.linalg.norm(g["S"] - o["S"]) / np.linalg.norm(o["S"])
     assert dS < (FP64_AXIS_TOL if prec == "fp64" else 2e-3), dS
+    # absorbed tally: the integral of (K_abs X)_0 on both sides
+    dA = np.linalg.norm(g["absorbed"] - o["absorbed"]) / np.linalg.norm(o["absorbed"])
+    assert dA < (FP64_AXIS_TOL if prec == "fp64" else 2e-3), dA
     for k in range(2):
         Itot = o["images"][k][0].sum()
         for e in range(4):
@@ -150,6 +153,7 @@ def test_spheroid_sphere_parity(sphere_oracle, prec):
         assert abs(g["stats"][key] - o["stats"][key]) <= 2e-3 * o["stats"][key] + 2, key
     st = g["stats"]
     assert st["scatterings"] > 5000 and st["trials"] > st["scatterings"]
+    assert st["absorbed_energy"] == pytest.approx(o["stats"]["absorbed_energy"], rel=1e-6 if prec == "fp64" else 2e-3)
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", FP64_AXIS_TOL), ("fp32", 2e-5)])

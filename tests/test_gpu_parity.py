@@ -452,3 +452,39 @@ def test_periodic_scattering_slab_parity(prec):
     bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
     assert abs(bal - st["emitted_energy"]) < 1e-6 * st["emitted_energy"]
     assert np.linalg.norm(g["S"] - o["S"]) < 2e-3 * np.linalg.norm(o["S"])
+
+
+def test_rank_shares_and_the_tally_exchange():
+    """Two ranks' shares of the packet ids run on two models (as two GPUs would), the
+    tallies summed through CUDA tensors with get/set_tallies: tallies and images equal a
+    single launch over all ids, up to the order of the FP64 additions."""
+    import torch
+
+    from paper_2512_01283_gb300 import multigpu as MG
+
+    model = W.disk(n=24)
+    run = W.disk_run(n_packets=20_000, n_cam=2, npix=16)
+    ref = gpu_run(model, run, "fp32")
+    mods, S_sum, A_sum = [], None, None
+    for r in range(2):
+        m = M.Model(model)
+        MG.rank_launch(lambda rr, acc: M.launch(m, rr, precision="fp32", accumulate=acc), run, r, 2)
+        S = torch.empty((m.ncell, 2, 4), dtype=torch.float64, device="cuda")
+        A = torch.empty((m.ncell,), dtype=torch.float64, device="cuda")
+        m.tallies_into(S, A)
+        S_sum = S if S_sum is None else S_sum + S
+        A_sum = A if A_sum is None else A_sum + A
+        mods.append(m)
+    m0 = mods[0]
+    m0.set_tallies(S_sum, A_sum)
+    S0, A0 = m0.tallies(2)
+    assert np.allclose(S0, ref["S"], rtol=1e-9, atol=1e-12 * np.abs(ref["S"]).max())
+    # absorbed: same-cell lanes of a warp are pre-summed in FP32 before the FP64 atomic, and
+    # which packets share a warp differs between one launch and two shares
+    assert np.allclose(A0, ref["absorbed"], rtol=1e-6, atol=1e-9 * np.abs(ref["absorbed"]).max())
+    for k in range(2):
+        out = np.zeros((4, 16, 16))
+        m0.image(k, out)
+        assert np.allclose(out, ref["images"][k], rtol=1e-9, atol=1e-12 * np.abs(ref["images"][k]).max())
+    for m in mods:
+        m.close()
