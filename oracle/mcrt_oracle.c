@@ -82,6 +82,16 @@ typedef struct {
     int32_t npix[2];    /* nx, ny */
 } orc_camera;
 
+/* A statically refined patch: the root cells of `box` (root-cell indices i0, j0, k0,
+ * i1, j1, k1, half-open) are replaced by a uniform grid of `factor` cells per root cell
+ * along each axis, with its own arrays [nz][ny][nx] (bfield and emissivity as the
+ * root's: NULL when the root's are). */
+typedef struct {
+    int32_t box[6];
+    int32_t factor;
+    const float *kappa_abs, *kappa_sca, *bfield, *emissivity;
+} orc_patch;
+
 typedef struct {
     int32_t n[3];
     double lo[3], hi[3];
@@ -111,6 +121,10 @@ typedef struct {
     double eps_re, eps_im;    /* scat_model 2: dielectric function of the grain material */
     double aspect;            /* scat_model 2: equatorial over symmetry semi-axis (> 1 oblate) */
     double size_x;            /* scat_model 2: size parameter 2 pi a_eff / lambda */
+    int32_t n_patches;        /* static mesh refinement: patches of the root grid (one level,
+                                 disjoint boxes); the root arrays' values in covered cells
+                                 are not used */
+    const orc_patch *patches;
 } orc_problem;
 
 typedef struct {
@@ -686,6 +700,247 @@ static int cross_face(const int n3[3], const double lo[3], const double hi[3], i
     return cross_face_p(n3, lo, hi, idx, p, n, ell, axis, 0);
 }
 
+/* ------------------------------------------------------------------------- */
+/* Composite grid: the root grid and its statically refined patches (Sec. 2:  */
+/* a composite mesh with optional static mesh refinement).                    */
+/* ------------------------------------------------------------------------- */
+/* Cells are numbered root first ([z][y][x]), then each patch in order ([z][y][x]
+ * within the patch).  A position in the grid is (g, idx): g = -1 for the root grid,
+ * else the patch number. */
+typedef struct {
+    int g;
+    int idx[3];
+} where_t;
+
+static int64_t root_cells(const orc_problem *P) { return (int64_t)P->n[0] * P->n[1] * P->n[2]; }
+
+static void patch_dims(const orc_problem *P, int q, int n3[3])
+{
+    const orc_patch *Q = &P->patches[q];
+    for (int a = 0; a < 3; ++a) n3[a] = (Q->box[3 + a] - Q->box[a]) * Q->factor;
+}
+
+static int64_t patch_offset(const orc_problem *P, int q)
+{
+    int64_t off = root_cells(P);
+    for (int k = 0; k < q; ++k) {
+        int m[3];
+        patch_dims(P, k, m);
+        off += (int64_t)m[0] * m[1] * m[2];
+    }
+    return off;
+}
+
+int64_t orc_n_cells(const orc_problem *P) { return patch_offset(P, P->n_patches); }
+
+/* Cell counts and box of grid g (root or patch). */
+static void grid_geom(const orc_problem *P, int g, int n3[3], double lo[3], double hi[3])
+{
+    if (g < 0) {
+        for (int a = 0; a < 3; ++a) {
+            n3[a] = P->n[a];
+            lo[a] = P->lo[a];
+            hi[a] = P->hi[a];
+        }
+        return;
+    }
+    patch_dims(P, g, n3);
+    for (int a = 0; a < 3; ++a) {
+        double d = (P->hi[a] - P->lo[a]) / P->n[a];
+        lo[a] = P->lo[a] + P->patches[g].box[a] * d;
+        hi[a] = P->lo[a] + P->patches[g].box[3 + a] * d;
+    }
+}
+
+static int64_t cell_index(const orc_problem *P, const where_t *w)
+{
+    int n3[3];
+    double lo[3], hi[3];
+    grid_geom(P, w->g, n3, lo, hi);
+    int64_t local = ((int64_t)w->idx[2] * n3[1] + w->idx[1]) * n3[0] + w->idx[0];
+    return w->g < 0 ? local : patch_offset(P, w->g) + local;
+}
+
+static void cell_where(const orc_problem *P, int64_t c, where_t *w)
+{
+    w->g = -1;
+    for (int q = P->n_patches - 1; q >= 0; --q)
+        if (c >= patch_offset(P, q)) {
+            w->g = q;
+            c -= patch_offset(P, q);
+            break;
+        }
+    int n3[3];
+    double lo[3], hi[3];
+    grid_geom(P, w->g, n3, lo, hi);
+    w->idx[0] = (int)(c % n3[0]);
+    w->idx[1] = (int)((c / n3[0]) % n3[1]);
+    w->idx[2] = (int)(c / ((int64_t)n3[0] * n3[1]));
+}
+
+static double grid_cell_volume(const orc_problem *P, int g)
+{
+    int n3[3];
+    double lo[3], hi[3];
+    grid_geom(P, g, n3, lo, hi);
+    return (hi[0] - lo[0]) / n3[0] * (hi[1] - lo[1]) / n3[1] * (hi[2] - lo[2]) / n3[2];
+}
+
+/* Cell data of composite cell c. */
+static const float *cell_array(const orc_problem *P, int64_t c, int which, int64_t *local)
+{
+    *local = c;
+    if (c < root_cells(P)) {
+        const float *root[4] = {P->kappa_abs, P->kappa_sca, P->bfield, P->emissivity};
+        return root[which];
+    }
+    for (int q = P->n_patches - 1; q >= 0; --q) {
+        int64_t off = patch_offset(P, q);
+        if (c >= off) {
+            const orc_patch *Q = &P->patches[q];
+            const float *arr[4] = {Q->kappa_abs, Q->kappa_sca, Q->bfield, Q->emissivity};
+            *local = c - off;
+            return arr[which];
+        }
+    }
+    return NULL;
+}
+
+static double cell_ka(const orc_problem *P, int64_t c)
+{
+    int64_t l;
+    return cell_array(P, c, 0, &l)[l];
+}
+
+static double cell_ks(const orc_problem *P, int64_t c)
+{
+    int64_t l;
+    return cell_array(P, c, 1, &l)[l];
+}
+
+static double cell_em(const orc_problem *P, int64_t c)
+{
+    int64_t l;
+    const float *e = cell_array(P, c, 3, &l);
+    return e ? e[l] : 0.0;
+}
+
+/* Field direction of cell c; 0 when the model has no field. */
+static int cell_field(const orc_problem *P, int64_t c, double b[3])
+{
+    int64_t l;
+    const float *f = cell_array(P, c, 2, &l);
+    if (!f) return 0;
+    b[0] = f[3 * l];
+    b[1] = f[3 * l + 1];
+    b[2] = f[3 * l + 2];
+    return 1;
+}
+
+/* Patch covering root cell ridx, or -1. */
+static int covering_patch(const orc_problem *P, const int ridx[3])
+{
+    for (int q = 0; q < P->n_patches; ++q) {
+        const int32_t *b = P->patches[q].box;
+        if (ridx[0] >= b[0] && ridx[0] < b[3] && ridx[1] >= b[1] && ridx[1] < b[4] && ridx[2] >= b[2] &&
+            ridx[2] < b[5])
+            return q;
+    }
+    return -1;
+}
+
+/* Root cell ridx entered at p along n: the cell itself, or the cell of the patch that
+ * covers it, found like locate (a point on a face belongs to the cell n points into)
+ * and clamped to the patch. */
+static void enter_root_cell(const orc_problem *P, const int ridx[3], const double p[3], const double n[3],
+                            where_t *w)
+{
+    int q = covering_patch(P, ridx);
+    w->g = q;
+    if (q < 0) {
+        for (int a = 0; a < 3; ++a) w->idx[a] = ridx[a];
+        return;
+    }
+    int n3[3];
+    double lo[3], hi[3];
+    grid_geom(P, q, n3, lo, hi);
+    for (int a = 0; a < 3; ++a) {
+        double d = (hi[a] - lo[a]) / n3[a];
+        double x = (p[a] - lo[a]) / d;
+        int i = (int)floor(x);
+        if ((double)i == x && n[a] < 0.0) i -= 1;
+        if (i < 0) i = 0;
+        if (i >= n3[a]) i = n3[a] - 1;
+        w->idx[a] = i;
+    }
+}
+
+static int composite_locate(const orc_problem *P, const double p[3], const double n[3], where_t *w)
+{
+    int ridx[3];
+    if (!locate(P->n, P->lo, P->hi, p, n, ridx)) return 0;
+    enter_root_cell(P, ridx, p, n, w);
+    return 1;
+}
+
+static double composite_exit(const orc_problem *P, const where_t *w, const double p[3], const double n[3],
+                             int *axis)
+{
+    int n3[3];
+    double lo[3], hi[3];
+    grid_geom(P, w->g, n3, lo, hi);
+    return exit_distance(n3, lo, hi, w->idx, p, n, axis);
+}
+
+/* Move p to the exit face of the current cell and into the next cell of the composite
+ * grid; 0 when the packet leaves the grid.  Leaving a patch leads to the root cell
+ * beyond its face (or, through a periodic face of the root box, the one on the
+ * opposite side), which may itself be covered by a patch. */
+static int composite_cross(const orc_problem *P, where_t *w, double p[3], const double n[3], double ell, int axis,
+                           int periodic)
+{
+    int n3[3];
+    double lo[3], hi[3];
+    grid_geom(P, w->g, n3, lo, hi);
+    if (w->g < 0) {
+        if (!cross_face_p(n3, lo, hi, w->idx, p, n, ell, axis, periodic)) return 0;
+        int ridx[3] = {w->idx[0], w->idx[1], w->idx[2]};
+        enter_root_cell(P, ridx, p, n, w);
+        return 1;
+    }
+    if (cross_face_p(n3, lo, hi, w->idx, p, n, ell, axis, 0)) return 1;
+    const orc_patch *Q = &P->patches[w->g];
+    int ridx[3];
+    for (int a = 0; a < 3; ++a) ridx[a] = Q->box[a] + w->idx[a] / Q->factor;
+    ridx[axis] = n[axis] > 0.0 ? Q->box[3 + axis] : Q->box[axis] - 1;
+    if (ridx[axis] < 0 || ridx[axis] >= P->n[axis]) {
+        if (!((periodic >> axis) & 1)) return 0;
+        ridx[axis] = ridx[axis] < 0 ? P->n[axis] - 1 : 0;
+        p[axis] = ridx[axis] == 0 ? P->lo[axis] : P->hi[axis];
+    }
+    enter_root_cell(P, ridx, p, n, w);
+    return 1;
+}
+
+/* Composite cells and chord lengths along a ray from p0 (for the refinement pins). */
+int64_t orc_dda_walk_composite(const orc_problem *P, const double p0[3], const double n[3], int64_t max_cells,
+                               int64_t *cells, double *lengths)
+{
+    where_t w;
+    double p[3] = {p0[0], p0[1], p0[2]};
+    if (!composite_locate(P, p, n, &w)) return 0;
+    int64_t k = 0;
+    while (k < max_cells) {
+        int axis;
+        double ell = composite_exit(P, &w, p, n, &axis);
+        cells[k] = cell_index(P, &w);
+        lengths[k] = ell;
+        ++k;
+        if (!composite_cross(P, &w, p, n, ell, axis, 0)) break;
+    }
+    return k;
+}
+
 /* Brute list of cells and chord lengths along a ray (for the DDA pins). */
 int64_t orc_dda_walk(const int32_t n3[3], const double lo[3], const double hi[3], const double p0[3],
                      const double n[3], int64_t max_cells, int64_t *cells, double *lengths)
@@ -723,11 +978,12 @@ typedef struct {
 
 static void cell_quaternion(const orc_problem *P, int64_t c, double q[4])
 {
-    if (!P->bfield) {
+    double b[3];
+    if (!cell_field(P, c, b)) {
         q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
         return;
     }
-    orc_grain_quaternion(P->bfield[3 * c], P->bfield[3 * c + 1], P->bfield[3 * c + 2], q);
+    orc_grain_quaternion(b[0], b[1], b[2], q);
 }
 
 static void make_local_frame(const orc_problem *P, int64_t c, const double n[3], local_frame *F)
@@ -745,7 +1001,7 @@ static void make_local_frame(const orc_problem *P, int64_t c, const double n[3],
     F->thetap = acos(cz);
     const double zg[3] = {0.0, 0.0, 1.0};
     orc_to_lab(q, zg, F->axis);
-    double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+    double ka = cell_ka(P, c), ks = cell_ks(P, c);
     double kext = ka + ks;
     double omega = kext > 0.0 ? ks / kext : 0.0;
     if (P->scat_model == 2) {
@@ -851,11 +1107,11 @@ static void isotropic(double u_cos, double u_phi, double n[3])
 /* Packet birth, event 0 (Sec. 2.2): position, direction and Stokes vector in the
  * lab basis of n.  Slot 0 = (tau, cos theta, phi, cell), slot 1 = (x, y, z, -). */
 static int emit_packet(const run_ctx *C, int64_t pid, int s, double eps, double p[3], double n[3],
-                       double X[4], int idx[3], double *tau)
+                       double X[4], where_t *w, double *tau)
 {
     const orc_problem *P = C->P;
     const orc_source *src = &P->sources[s];
-    const int64_t ncell = (int64_t)P->n[0] * P->n[1] * P->n[2];
+    const int64_t ncell = orc_n_cells(P);
     double u0[4], u1[4];
     draw4(P, pid, 0, 0, u0);
     draw4(P, pid, 0, 1, u1);
@@ -864,13 +1120,13 @@ static int emit_packet(const run_ctx *C, int64_t pid, int s, double eps, double 
     if (src->type == 0) {
         p[0] = src->pos[0]; p[1] = src->pos[1]; p[2] = src->pos[2];
         isotropic(u0[1], u0[2], n);
-        inside = locate(P->n, P->lo, P->hi, p, n, idx);
+        inside = composite_locate(P, p, n, w);
     } else if (src->type == 1) {
         p[0] = P->lo[0] + u1[0] * (P->hi[0] - P->lo[0]);
         p[1] = P->lo[1] + u1[1] * (P->hi[1] - P->lo[1]);
         p[2] = src->beam_dir > 0 ? P->lo[2] : P->hi[2];
         n[0] = 0.0; n[1] = 0.0; n[2] = src->beam_dir > 0 ? 1.0 : -1.0;
-        inside = locate(P->n, P->lo, P->hi, p, n, idx);
+        inside = composite_locate(P, p, n, w);
     } else {
         /* thermal: first cell whose cumulative weight exceeds u * total */
         double target = u0[3] * C->cdf_total;
@@ -880,10 +1136,11 @@ static int emit_packet(const run_ctx *C, int64_t pid, int s, double eps, double 
             if (C->cdf[mid] > target) hi = mid; else lo = mid + 1;
         }
         int64_t c = lo;
-        idx[0] = (int)(c % P->n[0]);
-        idx[1] = (int)((c / P->n[0]) % P->n[1]);
-        idx[2] = (int)(c / ((int64_t)P->n[0] * P->n[1]));
-        for (int a = 0; a < 3; ++a) p[a] = P->lo[a] + (idx[a] + u1[a]) * cell_size(P, a);
+        cell_where(P, c, w);
+        int n3[3];
+        double glo[3], ghi[3];
+        grid_geom(P, w->g, n3, glo, ghi);
+        for (int a = 0; a < 3; ++a) p[a] = glo[a] + (w->idx[a] + u1[a]) * ((ghi[a] - glo[a]) / n3[a]);
         isotropic(u0[1], u0[2], n);
         inside = 1;
         /* emission alpha_abs B with alpha_abs the absorption part of K acting on
@@ -891,7 +1148,7 @@ static int emit_packet(const run_ctx *C, int64_t pid, int s, double eps, double 
          * mean over directions (mean alpha1 - omega) */
         local_frame F;
         make_local_frame(P, c, n, &F);
-        double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+        double ka = cell_ka(P, c), ks = cell_ks(P, c);
         double omega = (ka + ks) > 0.0 ? ks / (ka + ks) : 0.0;
         /* absorption part of K's first row along n */
         double kab1 = F.alpha[0] - F.sca[0], kab2 = F.alpha[1] - F.sca[1];
@@ -1019,8 +1276,8 @@ static void transport_packet(run_ctx *C, int64_t pid)
     double eps = source_luminosity(C, s) / (double)src->n_packets;
 
     double p[3], n[3], X[4], tau_rem;
-    int idx[3];
-    int inside = emit_packet(C, pid, s, eps, p, n, X, idx, &tau_rem);
+    where_t w;
+    int inside = emit_packet(C, pid, s, eps, p, n, X, &w, &tau_rem);
     double I_birth = X[0];
     C->stats[ST_EMITTED_E] += X[0];
     C->stats[ST_EMITTED_N] += 1.0;
@@ -1035,11 +1292,11 @@ static void transport_packet(run_ctx *C, int64_t pid)
             flag = 3;
             break;
         }
-        int64_t c = ((int64_t)idx[2] * P->n[1] + idx[1]) * P->n[0] + idx[0];
-        double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+        int64_t c = cell_index(P, &w);
+        double ka = cell_ka(P, c), ks = cell_ks(P, c);
         double kext = ka + ks;
         int axis;
-        double ell_exit = exit_distance(P->n, P->lo, P->hi, idx, p, n, &axis);
+        double ell_exit = composite_exit(P, &w, p, n, &axis);
         local_frame F;
         if (kext > 0.0) make_local_frame(P, c, n, &F);
         /* scattering optical depth sampled along n: kappa_sca for Theta-only optics, the
@@ -1098,7 +1355,7 @@ static void transport_packet(run_ctx *C, int64_t pid)
 
         if (!scatter_here) {
             tau_rem -= dtau_sca_exit;
-            if (!cross_face_p(P->n, P->lo, P->hi, idx, p, n, ell_exit, axis, P->periodic)) {
+            if (!composite_cross(P, &w, p, n, ell_exit, axis, P->periodic)) {
                 flag = 1;
                 break;
             }
@@ -1168,8 +1425,9 @@ static void *thread_main(void *arg)
     return NULL;
 }
 
-/* Thermal source set-up: cell weights kappa_ext (mean alpha1 - omega) B V and the
- * luminosity 4 pi sum of them. */
+/* Thermal source set-up: cell weights kappa_ext (mean alpha1 - omega) B V (V the cell's
+ * own volume; root cells covered by a patch weigh 0) and the luminosity 4 pi sum of
+ * them. */
 static int thermal_setup(run_ctx *C)
 {
     const orc_problem *P = C->P;
@@ -1180,16 +1438,17 @@ static int thermal_setup(run_ctx *C)
     C->alpha1_mean = P->scat_model == 2 ? 1.0 : kext_alpha1_mean(P);
     if (!need) return 0;
     if (!P->emissivity) return -1;
-    const int64_t ncell = (int64_t)P->n[0] * P->n[1] * P->n[2];
-    const double V = cell_size(P, 0) * cell_size(P, 1) * cell_size(P, 2);
+    const int64_t ncell = orc_n_cells(P);
     double *cdf = (double *)malloc(sizeof(double) * ncell);
     double acc = 0.0;
     for (int64_t c = 0; c < ncell; ++c) {
-        double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+        where_t wh;
+        cell_where(P, c, &wh);
+        double ka = cell_ka(P, c), ks = cell_ks(P, c);
         double kext = ka + ks;
         double omega = kext > 0.0 ? ks / kext : 0.0;
-        double w = kext * (C->alpha1_mean - omega) * P->emissivity[c] * V;
-        if (w < 0.0) w = 0.0;
+        double w = kext * (C->alpha1_mean - omega) * cell_em(P, c) * grid_cell_volume(P, wh.g);
+        if (w < 0.0 || (wh.g < 0 && covering_patch(P, wh.idx) >= 0)) w = 0.0;
         acc += w;
         cdf[c] = acc;
     }
@@ -1259,9 +1518,6 @@ int orc_transport(const orc_problem *P, orc_result *R)
 int orc_image(const orc_problem *P, const double *S, int cam, double scale_S, double *out)
 {
     const orc_camera *K = &P->cams[cam];
-    const int64_t ncell = (int64_t)P->n[0] * P->n[1] * P->n[2];
-    (void)ncell;
-    const double V = cell_size(P, 0) * cell_size(P, 1) * cell_size(P, 2);
     double Om[3] = {K->dir[0], K->dir[1], K->dir[2]};
     double cth[3], cph[3];
     orc_stokes_basis(Om, cth, cph);
@@ -1290,7 +1546,8 @@ int orc_image(const orc_problem *P, const double *S, int cam, double scale_S, do
             double X[4] = {0.0, 0.0, 0.0, 0.0};
             if (!miss && tin < tout) {
                 double p[3];
-                int idx[3];
+                int ridx[3];
+                where_t w;
                 for (int d = 0; d < 3; ++d) p[d] = o[d] + tin * Om[d];
                 for (int d = 0; d < 3; ++d) {
                     double dd = cell_size(P, d);
@@ -1299,19 +1556,21 @@ int orc_image(const orc_problem *P, const double *S, int cam, double scale_S, do
                     if ((double)ii == x && Om[d] < 0.0) ii -= 1;
                     if (ii < 0) ii = 0;
                     if (ii >= P->n[d]) ii = P->n[d] - 1;
-                    idx[d] = ii;
+                    ridx[d] = ii;
                 }
+                enter_root_cell(P, ridx, p, Om, &w);
                 for (;;) {
                     int axis;
-                    double ell = exit_distance(P->n, P->lo, P->hi, idx, p, Om, &axis);
-                    int64_t c = ((int64_t)idx[2] * P->n[1] + idx[1]) * P->n[0] + idx[0];
-                    double ka = P->kappa_abs[c], ks = P->kappa_sca[c];
+                    double ell = composite_exit(P, &w, p, Om, &axis);
+                    int64_t c = cell_index(P, &w);
+                    double ka = cell_ka(P, c), ks = cell_ks(P, c);
                     double kext = ka + ks;
                     if (kext > 0.0 && ell > 0.0) {
                         double omega = ks / kext;
+                        double V = grid_cell_volume(P, w.g);
                         local_frame F;
                         make_local_frame(P, c, Om, &F);
-                        double Bc = P->emissivity ? P->emissivity[c] : 0.0;
+                        double Bc = cell_em(P, c);
                         double Sg[4] = {(F.alpha[0] - F.sca[0]) * Bc, (F.alpha[1] - F.sca[1]) * Bc, 0.0, 0.0};
                         if (S && ks > 0.0) {
                             double Sc[4], Sgs[4];
@@ -1325,7 +1584,7 @@ int orc_image(const orc_problem *P, const double *S, int cam, double scale_S, do
                         orc_cell_solution(Xg, F.alpha[0], F.alpha[1], F.alpha[2], Sg, kext * ell, Yg);
                         orc_change_basis(Yg, F.gth, F.gph, F.th, F.ph, X);
                     }
-                    if (!cross_face(P->n, P->lo, P->hi, idx, p, Om, ell, axis)) break;
+                    if (!composite_cross(P, &w, p, Om, ell, axis, 0)) break;
                 }
             }
             for (int e = 0; e < 4; ++e) out[((size_t)e * ny + j) * nx + i] = X[e];
@@ -1352,8 +1611,8 @@ int orc_emit(const orc_problem *P, int64_t pid, double out[13])
     }
     double eps = source_luminosity(&C, s) / (double)P->sources[s].n_packets;
     double p[3], n[3], X[4], tau;
-    int idx[3];
-    int inside = emit_packet(&C, pid, s, eps, p, n, X, idx, &tau);
+    where_t w;
+    int inside = emit_packet(&C, pid, s, eps, p, n, X, &w, &tau);
     for (int a = 0; a < 3; ++a) { out[a] = p[a]; out[3 + a] = n[a]; }
     for (int e = 0; e < 4; ++e) out[6 + e] = X[e];
     out[10] = tau; out[11] = inside; out[12] = s;

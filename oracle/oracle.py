@@ -46,6 +46,11 @@ _f32p = C.POINTER(C.c_float)
 _f64p = C.POINTER(C.c_double)
 
 
+class Patch(C.Structure):
+    _fields_ = [("box", C.c_int32 * 6), ("factor", C.c_int32), ("kappa_abs", _f32p), ("kappa_sca", _f32p),
+                ("bfield", _f32p), ("emissivity", _f32p)]
+
+
 class Problem(C.Structure):
     _fields_ = [("n", C.c_int32 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("kappa_abs", _f32p), ("kappa_sca", _f32p), ("bfield", _f32p), ("emissivity", _f32p),
@@ -58,7 +63,8 @@ class Problem(C.Structure):
                 ("roulette_threshold", C.c_double), ("roulette_survival", C.c_double),
                 ("max_events", C.c_int64), ("max_trials", C.c_int32), ("n_threads", C.c_int32),
                 ("n_trace", C.c_int64), ("periodic", C.c_int32),
-                ("eps_re", C.c_double), ("eps_im", C.c_double), ("aspect", C.c_double), ("size_x", C.c_double)]
+                ("eps_re", C.c_double), ("eps_im", C.c_double), ("aspect", C.c_double), ("size_x", C.c_double),
+                ("n_patches", C.c_int32), ("patches", C.POINTER(Patch))]
 
 
 class Result(C.Structure):
@@ -105,6 +111,11 @@ def lib():
                                       _f64p]
             L.orc_scatter.restype = C.c_int
             L.orc_frame.argtypes = [C.POINTER(Problem), C.c_int64, _f64p, _f64p]
+            L.orc_n_cells.argtypes = [C.POINTER(Problem)]
+            L.orc_n_cells.restype = C.c_int64
+            L.orc_dda_walk_composite.argtypes = [C.POINTER(Problem), _f64p, _f64p, C.c_int64,
+                                                 C.POINTER(C.c_int64), _f64p]
+            L.orc_dda_walk_composite.restype = C.c_int64
             L.orc_spheroid_L.argtypes = [C.c_double]
             L.orc_spheroid_L.restype = C.c_double
             L.orc_dipole_constants.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _f64p]
@@ -328,8 +339,37 @@ def make_problem(model: dict, run: dict):
     P.n_threads = int(run.get("n_threads", 1))
     P.n_trace = int(run.get("n_trace", 0))
     P.periodic = int(model.get("periodic", 0))  # bit a: axis a periodic
+    patches = model.get("refine", [])
+    parr = (Patch * max(1, len(patches)))()
+    for i, q in enumerate(patches):
+        parr[i].box = (C.c_int32 * 6)(*q["box"])
+        parr[i].factor = int(q["factor"])
+        parr[i].kappa_abs = f32("pka%d" % i, q["kappa_abs"])
+        parr[i].kappa_sca = f32("pks%d" % i, q["kappa_sca"])
+        parr[i].bfield = f32("pbf%d" % i, q.get("bfield"))
+        parr[i].emissivity = f32("pem%d" % i, q.get("emissivity"))
+    keep.patches = parr
+    P.n_patches = len(patches)
+    P.patches = parr
     keep.P = P
     return keep
+
+
+def n_cells(model: dict) -> int:
+    """Cells of the composite grid: the root's, then each refined patch's."""
+    keep = make_problem(model, {"sources": [], "cameras": []})
+    return int(lib().orc_n_cells(C.byref(keep.P)))
+
+
+def dda_walk_composite(model: dict, p0, n, max_cells=100000):
+    """Composite cells and chord lengths along a ray through a refined grid."""
+    keep = make_problem(model, {"sources": [], "cameras": []})
+    p0, n = _d(p0, 3), _d(n, 3)
+    cells = np.zeros(max_cells, dtype=np.int64)
+    lens = np.zeros(max_cells)
+    k = lib().orc_dda_walk_composite(C.byref(keep.P), _pd(p0), _pd(n), max_cells,
+                                     cells.ctypes.data_as(C.POINTER(C.c_int64)), _pd(lens))
+    return cells[:k].copy(), lens[:k].copy()
 
 
 def transport(model: dict, run: dict):
@@ -337,7 +377,7 @@ def transport(model: dict, run: dict):
     [ncell], trace [n_trace][16] and stats."""
     keep = make_problem(model, run)
     P = keep.P
-    ncell = P.n[0] * P.n[1] * P.n[2]
+    ncell = int(lib().orc_n_cells(C.byref(P)))
     S = np.zeros((ncell, max(1, P.n_cam), 4))
     absorbed = np.zeros(ncell)
     trace = np.zeros((max(1, P.n_trace), 16))

@@ -27,6 +27,9 @@ Workloads (sizes as stated):
                     atmosphere test of Sec. 3.4), periodic in x and y, field along x,
                     thermal emission, cameras at 45 deg inclination and a range of
                     azimuths.
+  disk_refined      the flared disk on a 128^3 root grid with one statically refined patch
+                    (4x) over the inner quarter in x, y and the middle eighth in z, the
+                    fields evaluated at the patch's own cell centres.
   sweep             batched sweep: 32 models with edges drawn uniformly in 32..192, clumpy
                     log-normal density (sigma_ln = 1), mean optical depth log-uniform in
                     [1, 100], times 8 wavelengths 0.5-3 um (kappa ~ lambda^-1.5); central
@@ -272,11 +275,9 @@ def twisted_slab(tau, p0=0.01, nz_per_tau=200, nxy=2, coupling=True):
             "emissivity": None, "optics": {"model": "rayleigh", "kext": kext_constant(-p0, a3)}}
 
 
-def disk(n=192, tau_mid=1e3, r_in=0.1, r_out=1.0, albedo=0.6, pitch_deg=30.0, T0=1000.0,
-         lam_um=1.0, n_bins=8, p_max=0.05):
-    """Flared disk; see the module docstring."""
-    lo, hi = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
-    x, y, z = cell_centres((n, n, n), lo, hi)
+def _disk_fields(x, y, z, tau_mid, r_in, r_out, albedo, pitch_deg, T0, lam_um):
+    """Cell arrays of the flared disk at cell centres (x, y, z): kappa_abs, kappa_sca,
+    field, unnormalised emissivity."""
     R = np.sqrt(x * x + y * y) + 0.0 * z
     H = 0.1 * np.maximum(R, 1e-30) ** 1.25
     rho = np.where((R >= r_in) & (R <= r_out), np.maximum(R, 1e-30) ** -1.0 * np.exp(-z * z / (2 * H * H)), 0.0)
@@ -286,16 +287,71 @@ def disk(n=192, tau_mid=1e3, r_in=0.1, r_out=1.0, albedo=0.6, pitch_deg=30.0, T0
     ka = (kext - ks).astype(np.float32)
     pitch = math.radians(pitch_deg)
     Rs = np.maximum(R, 1e-30)
-    bf = np.zeros((n, n, n, 3), dtype=np.float32)
+    bf = np.zeros(np.broadcast(x, y, z).shape + (3,), dtype=np.float32)
     bf[..., 0] = (math.cos(pitch) * (-y / Rs)) * (R > 0)
     bf[..., 1] = (math.cos(pitch) * (x / Rs)) * (R > 0)
     bf[..., 2] = math.sin(pitch)
     T = T0 * Rs ** -0.5
     hc_k = 14387.77 / lam_um
     em = np.where(rho > 0, 1.0 / np.expm1(np.minimum(hc_k / T, 700.0)), 0.0)
+    return ka, ks, bf, em
+
+
+def disk(n=192, tau_mid=1e3, r_in=0.1, r_out=1.0, albedo=0.6, pitch_deg=30.0, T0=1000.0,
+         lam_um=1.0, n_bins=8, p_max=0.05):
+    """Flared disk; see the module docstring."""
+    lo, hi = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    x, y, z = cell_centres((n, n, n), lo, hi)
+    ka, ks, bf, em = _disk_fields(x, y, z, tau_mid, r_in, r_out, albedo, pitch_deg, T0, lam_um)
     em = (em / max(em.max(), 1e-300)).astype(np.float32)
     return {"lo": lo, "hi": hi, "kappa_abs": ka, "kappa_sca": ks, "bfield": bf, "emissivity": em,
             "optics": table_optics(n_bins, p_max)}
+
+
+def disk_refined(n=128, box=None, factor=4, tau_mid=1e3, r_in=0.1, r_out=1.0, albedo=0.6, pitch_deg=30.0,
+                 T0=1000.0, lam_um=1.0, n_bins=8, p_max=0.05):
+    """Flared disk on a composite grid: an n^3 root grid plus one statically refined
+    patch over root-cell box `box` (default: the inner quarter of x and y, the middle
+    eighth of z) with `factor` cells per root cell, the disk's fields evaluated at the
+    patch's own cell centres (emissivity normalised like the root's)."""
+    lo, hi = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
+    if box is None:
+        q, e = n // 2 - n // 8, n // 2 - n // 16
+        box = (q, q, e, n - q, n - q, n - e)
+    x, y, z = cell_centres((n, n, n), lo, hi)
+    ka, ks, bf, em = _disk_fields(x, y, z, tau_mid, r_in, r_out, albedo, pitch_deg, T0, lam_um)
+    norm = max(em.max(), 1e-300)
+    d = [(h - l) / n for l, h in zip(lo, hi)]
+    plo = [l + b * dd for l, b, dd in zip(lo, box[:3], d)]
+    phi = [l + b * dd for l, b, dd in zip(lo, box[3:], d)]
+    shape = tuple((box[3 + a] - box[a]) * factor for a in (2, 1, 0))
+    px, py, pz = cell_centres(shape, plo, phi)
+    pka, pks, pbf, pem = _disk_fields(px, py, pz, tau_mid, r_in, r_out, albedo, pitch_deg, T0, lam_um)
+    patch = {"box": tuple(int(b) for b in box), "factor": int(factor), "kappa_abs": pka, "kappa_sca": pks,
+             "bfield": pbf, "emissivity": (pem / norm).astype(np.float32)}
+    return {"lo": lo, "hi": hi, "kappa_abs": ka, "kappa_sca": ks, "bfield": bf,
+            "emissivity": (em / norm).astype(np.float32), "optics": table_optics(n_bins, p_max), "refine": [patch]}
+
+
+def refine_uniform(model, patches):
+    """The same model on a composite grid: each (box, factor) of `patches` becomes a
+    refined patch whose cells copy their parent root cell's values (a finer grid of the
+    same medium)."""
+    out = dict(model)
+    out["refine"] = []
+    for box, f in patches:
+        i0, j0, k0, i1, j1, k1 = box
+        rep = {}
+        for key in ("kappa_abs", "kappa_sca", "bfield", "emissivity"):
+            a = model.get(key)
+            if a is None:
+                rep[key] = None
+                continue
+            sub = np.asarray(a)[k0:k1, j0:j1, i0:i1]
+            sub = np.repeat(np.repeat(np.repeat(sub, f, axis=0), f, axis=1), f, axis=2)
+            rep[key] = np.ascontiguousarray(sub, dtype=np.float32)
+        out["refine"].append(dict(rep, box=tuple(box), factor=int(f)))
+    return out
 
 
 def disk_run(n_packets=100_000_000, seed=2, n_cam=8, npix=256, star_luminosity=1.0):
