@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-plane-parallel", action="store_true")
     ap.add_argument("--no-spheroids", action="store_true", help="skip the aligned-spheroid line")
+    ap.add_argument("--no-refined", action="store_true", help="skip the static-mesh-refinement line")
     ap.add_argument("--inline-tally", action="store_true",
                     help="table path: tally inside the transport kernel instead of a tally kernel per round")
     ap.add_argument("--tally-bps", type=int, default=0,
@@ -243,6 +244,31 @@ def run_spheroids(M, W, torch):
             "energy_balance_rel": (bal - st["emitted_energy"]) / st["emitted_energy"],
             "image_x": {"I": float(img[0].sum()), "Q_over_I": float(img[1].sum() / img[0].sum()),
                         "V_over_I": float(img[3].sum() / img[0].sum())}}
+
+
+def run_refined(M, W, torch):
+    """Static mesh refinement: the flared disk on a 128^3 root grid with a 4x refined
+    patch over the inner quarter in x, y and the middle eighth in z (1.05e6 patch cells,
+    the fields at their own centres), star + thermal, 1e7 packets, 8 cameras at 256^2,
+    FP32 with the in-place tally (refined grids do not run in rounds)."""
+    model = W.disk_refined(n=128, factor=4)
+    run = W.disk_run(n_packets=10_000_000)
+    m = M.Model(model)
+    M.launch(m, dict(run, seed=94), precision="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = M.launch(m, dict(run, seed=95), precision="fp32")
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    S, _ = m.tallies(len(run["cameras"]))
+    m.close()
+    nroot = 128 ** 3
+    bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
+    return {"workload": "flared disk, 128^3 root grid + 4x refined inner patch (1.05e6 cells), star + thermal, "
+                        "1e7 packets, 8 cameras at 256^2, in-place tally",
+            "value": st["events"] / wall, "unit": UNIT, "events": st["events"], "seconds": wall,
+            "patch_tally_share": float(np.abs(S[nroot:]).sum() / max(np.abs(S).sum(), 1e-300)),
+            "energy_balance_rel": abs(bal - st["emitted_energy"]) / st["emitted_energy"]}
 
 
 def image_diff(a, b):
@@ -540,6 +566,9 @@ def main():
 
     if not args.no_spheroids and world == 1:
         line["spheroids"] = run_spheroids(M, W, torch)
+
+    if not args.no_refined and world == 1:
+        line["refined"] = run_refined(M, W, torch)
 
     if not args.no_surrogate and world == 1:
         table_imgs = imgs.cpu().numpy()

@@ -193,6 +193,37 @@ MCRT_API mcrt_status mcrt_create_grid(mcrt_ctx **out, int32_t nx, int32_t ny, in
                              void *cuda_stream);
 
 /*
+ * A statically refined patch of the root grid (Sec. 2: a composite mesh, optionally with
+ * static mesh refinement).  The root cells of `box` (root-cell indices i0, j0, k0, i1,
+ * j1, k1, half-open, inside the root grid) are replaced by a uniform grid with `factor`
+ * cells per root cell along each axis, nx = (i1 - i0) factor and so on.
+ *   kappa_abs, kappa_sca  [nz][ny][nx] FP32 of the patch, host or device
+ *   bfield, emissivity    as the root grid's: given exactly when the root's are
+ */
+typedef struct {
+    int32_t box[6];
+    int32_t factor;  /* 2..16 */
+    const float *kappa_abs, *kappa_sca, *bfield, *emissivity;
+} mcrt_patch;
+
+/*
+ * mcrt_create_grid with static mesh refinement: up to 64 patches (disjoint boxes, one
+ * level).  Cells are numbered root first ([z][y][x]), then each patch in order
+ * ([z][y][x] within the patch); tallies (mcrt_get_tallies) use that numbering and hold
+ * zeros for covered root cells, whose root values are not used.  Packets descend into
+ * a patch on entering a covered root cell and return to the root cell beyond the
+ * patch face they leave through; step 2 marches through the same cells.  Refined
+ * models take Rayleigh, table or dipole optics in single-model launches (in-place
+ * tally); batched, surrogate and no-allocation launches refuse them.
+ * Errors: as mcrt_create_grid, and MCRT_E_INVAL for overlapping or out-of-range boxes,
+ * bad factors, or field/emission arrays present on one level only.
+ */
+MCRT_API mcrt_status mcrt_create_grid_refined(mcrt_ctx **out, int32_t nx, int32_t ny, int32_t nz, const double lo[3],
+                                     const double hi[3], const float *kappa_abs, const float *kappa_sca,
+                                     const float *bfield, const float *emissivity, int32_t boundary,
+                                     int32_t n_patches, const mcrt_patch *patches, void *cuda_stream);
+
+/*
  * Grain optics (Sec. 2.2: the Mueller matrix and cross sections are user-defined,
  * as analytic forms or tables; App. A: extinction elements alpha_i).
  *   model    MCRT_SCAT_RAYLEIGH: dipole scattering matrix (n_bins, mueller and

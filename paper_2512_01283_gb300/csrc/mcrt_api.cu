@@ -24,6 +24,7 @@ struct mcrt_ctx {
     int device = 0;
     int n_sm = 0;
     float4* d_cells = nullptr;
+    PatchDev* d_patches = nullptr;  // static mesh refinement
     bool has_emissivity = false;
     // optics
     bool tables_set = false;
@@ -201,76 +202,143 @@ extern "C" {
 
 const char* mcrt_last_error(const mcrt_ctx* ctx) { return ctx ? ctx->err : g_err; }
 
-mcrt_status mcrt_create_grid(mcrt_ctx** out, int32_t nx, int32_t ny, int32_t nz, const double lo[3],
-                             const double hi[3], const float* kappa_abs, const float* kappa_sca, const float* bfield,
-                             const float* emissivity, int32_t boundary, void* cuda_stream) {
-    if (!out) return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: out is NULL");
+// Grid creation with an optional list of refined patches (validated here).
+static mcrt_status create_grid(const char* me, mcrt_ctx** out, int32_t nx, int32_t ny, int32_t nz, const double lo[3],
+                               const double hi[3], const float* kappa_abs, const float* kappa_sca, const float* bfield,
+                               const float* emissivity, int32_t boundary, int32_t n_patches,
+                               const mcrt_patch* patches, void* cuda_stream) {
+    if (!out) return fail(nullptr, MCRT_E_INVAL, "%s: out is NULL", me);
     *out = nullptr;
-    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: bad shape %d %d %d", nx, ny, nz);
-    const long long ncell = (long long)nx * ny * nz;
-    if (ncell >= (1ll << 31)) return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: %lld cells exceed 2^31", ncell);
-    if (!lo || !hi) return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: lo/hi is NULL");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, MCRT_E_INVAL, "%s: bad shape %d %d %d", me, nx, ny, nz);
+    const long long nroot = (long long)nx * ny * nz;
+    if (!lo || !hi) return fail(nullptr, MCRT_E_INVAL, "%s: lo/hi is NULL", me);
     for (int a = 0; a < 3; ++a)
         if (!(hi[a] > lo[a]) || !std::isfinite(lo[a]) || !std::isfinite(hi[a]))
-            return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: empty or non-finite box on axis %d", a);
-    if (!kappa_abs || !kappa_sca) return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: kappa_abs/kappa_sca is NULL");
+            return fail(nullptr, MCRT_E_INVAL, "%s: empty or non-finite box on axis %d", me, a);
+    if (!kappa_abs || !kappa_sca) return fail(nullptr, MCRT_E_INVAL, "%s: kappa_abs/kappa_sca is NULL", me);
     if (boundary < 0 || boundary > (MCRT_BOUNDARY_PERIODIC_X | MCRT_BOUNDARY_PERIODIC_Y | MCRT_BOUNDARY_PERIODIC_Z))
-        return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: boundary must be an MCRT_BOUNDARY_* mask");
+        return fail(nullptr, MCRT_E_INVAL, "%s: boundary must be an MCRT_BOUNDARY_* mask", me);
+    if (n_patches < 0 || n_patches > kMaxPatches || (n_patches > 0 && !patches))
+        return fail(nullptr, MCRT_E_INVAL, "%s: need 0..%d patches", me, kMaxPatches);
+    const int root_n[3] = {nx, ny, nz};
+    std::vector<PatchDev> hp((size_t)n_patches);
+    long long ncell = nroot;
+    for (int q = 0; q < n_patches; ++q) {
+        const mcrt_patch& Q = patches[q];
+        if (Q.factor < 2 || Q.factor > 16) return fail(nullptr, MCRT_E_INVAL, "%s: patch %d: factor must be 2..16", me, q);
+        if (!Q.kappa_abs || !Q.kappa_sca) return fail(nullptr, MCRT_E_INVAL, "%s: patch %d: kappa arrays are NULL", me, q);
+        if ((Q.bfield != nullptr) != (bfield != nullptr) || (Q.emissivity != nullptr) != (emissivity != nullptr))
+            return fail(nullptr, MCRT_E_INVAL, "%s: patch %d: field and emission arrays must match the root's", me, q);
+        PatchDev& P = hp[q];
+        for (int a = 0; a < 3; ++a) {
+            if (Q.box[a] < 0 || Q.box[3 + a] > root_n[a] || Q.box[3 + a] <= Q.box[a])
+                return fail(nullptr, MCRT_E_INVAL, "%s: patch %d: box outside the root grid or empty", me, q);
+            P.box[a] = Q.box[a];
+            P.box[3 + a] = Q.box[3 + a];
+            P.n[a] = (Q.box[3 + a] - Q.box[a]) * Q.factor;
+            const double dr = (hi[a] - lo[a]) / root_n[a];
+            P.lo[a] = lo[a] + Q.box[a] * dr;
+            P.d[a] = dr / Q.factor;
+            P.lo_f[a] = (float)P.lo[a];
+            P.d_f[a] = (float)P.d[a];
+        }
+        P.factor = Q.factor;
+        P.offset = ncell;
+        ncell += (long long)P.n[0] * P.n[1] * P.n[2];
+        for (int k = 0; k < q; ++k) {
+            bool overlap = true;
+            for (int a = 0; a < 3; ++a)
+                overlap = overlap && hp[k].box[a] < P.box[3 + a] && P.box[a] < hp[k].box[3 + a];
+            if (overlap) return fail(nullptr, MCRT_E_INVAL, "%s: patches %d and %d overlap", me, k, q);
+        }
+    }
+    if (ncell >= (1ll << 31)) return fail(nullptr, MCRT_E_INVAL, "%s: %lld cells exceed 2^31", me, ncell);
 
     mcrt_ctx* c = new (std::nothrow) mcrt_ctx();
-    if (!c) return fail(nullptr, MCRT_E_NOMEM, "mcrt_create_grid: host allocation failed");
+    if (!c) return fail(nullptr, MCRT_E_NOMEM, "%s: host allocation failed", me);
     c->stream = (cudaStream_t)cuda_stream;
-    c->g.n[0] = nx;
-    c->g.n[1] = ny;
-    c->g.n[2] = nz;
     for (int a = 0; a < 3; ++a) {
+        c->g.n[a] = root_n[a];
         c->g.lo[a] = lo[a];
         c->g.hi[a] = hi[a];
         c->g.d[a] = (hi[a] - lo[a]) / c->g.n[a];
     }
     c->g.ncell = ncell;
+    c->g.ncell_root = nroot;
     c->g.periodic = boundary;
     c->has_emissivity = emissivity != nullptr;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_cells, (size_t)ncell * 2 * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_work, kWorkBytes);
+    if (e == cudaSuccess && n_patches > 0) e = cudaMalloc(&c->d_patches, hp.size() * sizeof(PatchDev));
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     if (e != cudaSuccess) {
-        mcrt_status st = fail(nullptr, e == cudaErrorMemoryAllocation ? MCRT_E_NOMEM : MCRT_E_CUDA,
-                              "mcrt_create_grid: %s", cudaGetErrorString(e));
+        mcrt_status st = fail(nullptr, e == cudaErrorMemoryAllocation ? MCRT_E_NOMEM : MCRT_E_CUDA, "%s: %s", me,
+                              cudaGetErrorString(e));
         mcrt_destroy(c);
         return st;
     }
     c->g.cells = c->d_cells;
+    c->g.n_patches = n_patches;
+    c->g.patches = c->d_patches;
     unsigned bad = 0;
-    {
+    e = cudaMemsetAsync(c->d_work, 0, kWorkBytes, c->stream);
+    // cell records of one level: its arrays staged on the device, then k_setup_cells
+    auto level = [&](const float* ka_in, const float* ks_in, const float* bf_in, const float* em_in, long long count,
+                     float4* dst) {
         DevIn ka, ks, bf, em;
-        const size_t fb = (size_t)ncell * sizeof(float);
-        e = stage(ka, kappa_abs, fb, c->stream);
-        if (e == cudaSuccess) e = stage(ks, kappa_sca, fb, c->stream);
-        if (e == cudaSuccess) e = stage(bf, bfield, 3 * fb, c->stream);
-        if (e == cudaSuccess) e = stage(em, emissivity, fb, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_work, 0, kWorkBytes, c->stream);
-        if (e == cudaSuccess)
-            e = launch_setup_cells((const float*)ka.ptr, (const float*)ks.ptr, (const float*)bf.ptr,
-                                   (const float*)em.ptr, ncell, c->d_cells, (unsigned*)c->d_work, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, c->d_work, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        const size_t fb = (size_t)count * sizeof(float);
+        cudaError_t r = stage(ka, ka_in, fb, c->stream);
+        if (r == cudaSuccess) r = stage(ks, ks_in, fb, c->stream);
+        if (r == cudaSuccess) r = stage(bf, bf_in, 3 * fb, c->stream);
+        if (r == cudaSuccess) r = stage(em, em_in, fb, c->stream);
+        if (r == cudaSuccess)
+            r = launch_setup_cells((const float*)ka.ptr, (const float*)ks.ptr, (const float*)bf.ptr,
+                                   (const float*)em.ptr, count, dst, (unsigned*)c->d_work, c->stream);
+        // the staged copies are freed when this returns: finish the kernel first
+        if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
+        return r;
+    };
+    if (e == cudaSuccess) e = level(kappa_abs, kappa_sca, bfield, emissivity, nroot, c->d_cells);
+    for (int q = 0; q < n_patches && e == cudaSuccess; ++q) {
+        const mcrt_patch& Q = patches[q];
+        const long long cnt = (long long)hp[q].n[0] * hp[q].n[1] * hp[q].n[2];
+        e = level(Q.kappa_abs, Q.kappa_sca, Q.bfield, Q.emissivity, cnt, c->d_cells + 2 * hp[q].offset);
     }
+    if (e == cudaSuccess && n_patches > 0)
+        e = cudaMemcpyAsync(c->d_patches, hp.data(), hp.size() * sizeof(PatchDev), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && n_patches > 0) e = launch_mark_covered(c->g, hp.data(), c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, c->d_work, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess && bad) {
         mcrt_destroy(c);
-        return fail(nullptr, MCRT_E_INVAL, "mcrt_create_grid: negative or non-finite values in the input grids");
+        return fail(nullptr, MCRT_E_INVAL, "%s: negative or non-finite values in the input grids", me);
     }
     if (e != cudaSuccess) {
-        mcrt_status st = fail(nullptr, e == cudaErrorMemoryAllocation ? MCRT_E_NOMEM : MCRT_E_CUDA,
-                              "mcrt_create_grid: %s", cudaGetErrorString(e));
+        mcrt_status st = fail(nullptr, e == cudaErrorMemoryAllocation ? MCRT_E_NOMEM : MCRT_E_CUDA, "%s: %s", me,
+                              cudaGetErrorString(e));
         mcrt_destroy(c);
         return st;
     }
     *out = c;
     return MCRT_OK;
+}
+
+mcrt_status mcrt_create_grid(mcrt_ctx** out, int32_t nx, int32_t ny, int32_t nz, const double lo[3],
+                             const double hi[3], const float* kappa_abs, const float* kappa_sca, const float* bfield,
+                             const float* emissivity, int32_t boundary, void* cuda_stream) {
+    return create_grid("mcrt_create_grid", out, nx, ny, nz, lo, hi, kappa_abs, kappa_sca, bfield, emissivity, boundary,
+                       0, nullptr, cuda_stream);
+}
+
+mcrt_status mcrt_create_grid_refined(mcrt_ctx** out, int32_t nx, int32_t ny, int32_t nz, const double lo[3],
+                                     const double hi[3], const float* kappa_abs, const float* kappa_sca,
+                                     const float* bfield, const float* emissivity, int32_t boundary,
+                                     int32_t n_patches, const mcrt_patch* patches, void* cuda_stream) {
+    return create_grid("mcrt_create_grid_refined", out, nx, ny, nz, lo, hi, kappa_abs, kappa_sca, bfield, emissivity,
+                       boundary, n_patches, patches, cuda_stream);
 }
 
 mcrt_status mcrt_set_dust_tables(mcrt_ctx* ctx, int32_t model, int32_t n_bins, int32_t n_theta, const float* mueller,
@@ -624,8 +692,11 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
     if (st != MCRT_OK) return st;
     const bool sur = d->optics == MCRT_OPTICS_SURROGATE;
     if (sur && !ctx->sur_set) return fail(ctx, MCRT_E_STATE, "mcrt_launch_packets: no surrogate attached (mcrt_set_surrogate)");
-    // FP32 table launches tally in a kernel of their own unless asked not to
-    const bool deferred_table = !sur && ctx->t.model == MCRT_SCAT_TABLE && d->precision == MCRT_FP32 &&
+    if (sur && ctx->g.n_patches > 0)
+        return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: refined grids take table, Rayleigh or dipole optics");
+    // FP32 table launches tally in a kernel of their own unless asked not to (refined grids:
+    // in place, the composite walk lives in the single-model kernels)
+    const bool deferred_table = !sur && ctx->g.n_patches == 0 && ctx->t.model == MCRT_SCAT_TABLE && d->precision == MCRT_FP32 &&
                                 d->n_cameras > 0 && !(d->time_budget_s > 0.0) && !(d->flags & MCRT_FLAG_INLINE_TALLY);
     const bool rounds = sur || deferred_table;
     TransportParams P{};
@@ -912,6 +983,7 @@ mcrt_status mcrt_destroy(mcrt_ctx* ctx) {
     if (!ctx) return MCRT_OK;
     free_tables(ctx);
     cudaFree(ctx->d_cells);
+    cudaFree(ctx->d_patches);
     cudaFree(ctx->d_cdf);
     cudaFree(ctx->d_block_sums);
     cudaFree(ctx->d_guide);
@@ -1014,6 +1086,8 @@ mcrt_status batch_build(mcrt_batch** out, mcrt_ctx* const* models, int32_t n_mod
             return fail(nullptr, MCRT_E_INVAL, "batch: all models need the same scattering model");
         if (models[m]->t.model == MCRT_SCAT_DIPOLE)
             return fail(nullptr, MCRT_E_INVAL, "batch: aligned-spheroid optics are a single-model option");
+        if (models[m]->g.n_patches > 0)
+            return fail(nullptr, MCRT_E_INVAL, "batch: refined grids are a single-model option");
     }
     mcrt_batch* b = new (std::nothrow) mcrt_batch();
     if (!b) return fail(nullptr, MCRT_E_NOMEM, "batch: host allocation failed");

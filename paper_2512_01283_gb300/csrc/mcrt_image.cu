@@ -8,6 +8,7 @@
 
 #include "mcrt_device.cuh"
 #include "mcrt_internal.h"
+#include "mcrt_refine.cuh"
 
 namespace mcrt {
 
@@ -81,13 +82,34 @@ template <typename T> __global__ void __launch_bounds__(128) k_image(const __gri
             i = i < 0 ? 0 : (i >= g.n[d] ? g.n[d] - 1 : i);
             idx[d] = i;
         }
-        const T inv_vol = T(1.0 / (P.g.d[0] * P.g.d[1] * P.g.d[2]));
-        const long long max_steps = (long long)g.n[0] + g.n[1] + g.n[2] + 3;
+        const T inv_vol_root = T(1.0 / (P.g.d[0] * P.g.d[1] * P.g.d[2]));
+        T inv_vol = inv_vol_root;
+        // composite grid: the current level's geometry (root, or the patch the ray is in)
+        GridT<T> gc = g;
+        int lvl = 0;
+        auto descend = [&]() {
+            const long long rc = ((long long)idx[2] * g.n[1] + idx[1]) * g.n[0] + idx[0];
+            const int q = covering_patch(P.g.cells[2 * rc + 1]);
+            if (q < 0) return;
+            const PatchDev& pq = P.g.patches[q];
+            lvl = q + 1;
+            for (int a = 0; a < 3; ++a) {
+                gc.n[a] = pq.n[a];
+                gc.lo[a] = patch_lo<T>(pq, a);
+                gc.d[a] = patch_d<T>(pq, a);
+            }
+            inv_vol = T(1.0 / (pq.d[0] * pq.d[1] * pq.d[2]));
+            patch_locate<T>(pq, p[0], p[1], p[2], dir[0], dir[1], dir[2], idx);
+        };
+        if (P.g.n_patches > 0) descend();
+        const long long max_steps =
+            (long long)(g.n[0] + g.n[1] + g.n[2]) * (P.g.n_patches > 0 ? 3 * 16 + 1 : 1) + 3;
         for (long long step = 0; step < max_steps; ++step) {
             int axis;
-            const T ell = exit_distance(g, idx, p, dir, axis);
+            const T ell = exit_distance(gc, idx, p, dir, axis);
             if (axis < 0) break;
-            const long long c = ((long long)idx[2] * g.n[1] + idx[1]) * g.n[0] + idx[0];
+            const long long c = lvl == 0 ? ((long long)idx[2] * g.n[1] + idx[1]) * g.n[0] + idx[0]
+                                         : patch_cell(P.g.patches[lvl - 1], idx[0], idx[1], idx[2]);
             const float4 r = P.g.cells[2 * c + 1];
             const T ks = T(r.y);
             const T kext = T(r.x) + ks;
@@ -131,7 +153,20 @@ template <typename T> __global__ void __launch_bounds__(128) k_image(const __gri
                 cell_step(X, a1, a2, a3, S, kext * ell);
                 rotate_qu(X[1], X[2], c2, -s2);
             }
-            if (!cross_face(g, idx, p, dir, ell, axis)) break;
+            if (lvl == 0) {
+                if (!cross_face(g, idx, p, dir, ell, axis)) break;
+                if (P.g.n_patches > 0) descend();
+            } else if (!cross_face(gc, idx, p, dir, ell, axis)) {
+                // out of the patch: the root cell beyond its face
+                const PatchDev& pq = P.g.patches[lvl - 1];
+                for (int a = 0; a < 3; ++a) idx[a] = pq.box[a] + (a == axis ? 0 : idx[a] / pq.factor);
+                idx[axis] = dir[axis] > T(0) ? pq.box[3 + axis] : pq.box[axis] - 1;
+                lvl = 0;
+                gc = g;
+                inv_vol = inv_vol_root;
+                if (idx[axis] < 0 || idx[axis] >= g.n[axis]) break;
+                descend();
+            }
         }
     }
     for (int e = 0; e < 4; ++e) P.out[((size_t)e * ny + iy) * nx + ix] = (double)X[e];
@@ -243,6 +278,7 @@ constexpr int kScanBlock = 256;
 constexpr int kScanItems = 16;
 
 __global__ void k_scan_local(const float4* __restrict__ cells, long long ncell, double alpha1_mean, double vol,
+                             long long ncell_root, int n_patches, const PatchDev* __restrict__ patches,
                              double* __restrict__ cdf, double* __restrict__ block_sums) {
     __shared__ double sh[kScanBlock];
     const long long base = (long long)blockIdx.x * kScanBlock * kScanItems + (long long)threadIdx.x * kScanItems;
@@ -255,7 +291,14 @@ __global__ void k_scan_local(const float4* __restrict__ cells, long long ncell, 
             const float4 r = cells[2 * c + 1];
             const double kext = (double)r.x + (double)r.y;
             const double omega = kext > 0.0 ? (double)r.y / kext : 0.0;
-            w = kext * (alpha1_mean - omega) * (double)r.z * vol;
+            double v = vol;  // the cell's own volume; covered root cells hold no emission
+            if (c >= ncell_root)
+                for (int q = n_patches - 1; q >= 0; --q)
+                    if (c >= patches[q].offset) {
+                        v = patches[q].d[0] * patches[q].d[1] * patches[q].d[2];
+                        break;
+                    }
+            w = kext * (alpha1_mean - omega) * (double)r.z * v;
             if (w < 0.0) w = 0.0;
         }
         run += w;
@@ -446,6 +489,34 @@ __global__ void k_dipole_setup(double eps_re, double eps_im, double aspect, doub
 
 }  // namespace
 
+// Root cells of a patch's box: q_B = 1, no opacity or emission, patch + 1 in the last word.
+__global__ void k_mark_covered(float4* __restrict__ cells, int nx, int ny, int i0, int j0, int k0, int ni, int nj,
+                               int nk, unsigned tag) {
+    const long long total = (long long)ni * nj * nk;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = i0 + (int)(t % ni), j = j0 + (int)((t / ni) % nj), k = k0 + (int)(t / ((long long)ni * nj));
+        const long long c = ((long long)k * ny + j) * nx + i;
+        cells[2 * c] = make_float4(1.f, 0.f, 0.f, 0.f);
+        cells[2 * c + 1] = make_float4(0.f, 0.f, 0.f, __uint_as_float(tag));
+    }
+}
+
+cudaError_t launch_mark_covered(const GridDev& g, const PatchDev* hp, cudaStream_t s) {
+    (void)cudaGetLastError();  // report these launches' errors only
+    for (int q = 0; q < g.n_patches; ++q) {
+        const PatchDev& P = hp[q];
+        const int ni = P.box[3] - P.box[0], nj = P.box[4] - P.box[1], nk = P.box[5] - P.box[2];
+        const long long total = (long long)ni * nj * nk;
+        const unsigned grid = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+        k_mark_covered<<<grid, 256, 0, s>>>(const_cast<float4*>(g.cells), g.n[0], g.n[1], P.box[0], P.box[1],
+                                            P.box[2], ni, nj, nk, (unsigned)(q + 1));
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_dipole_setup(double eps_re, double eps_im, double aspect, double x, double* out, cudaStream_t s) {
     (void)cudaGetLastError();  // report this launch's error only
     k_dipole_setup<<<1, 32, 0, s>>>(eps_re, eps_im, aspect, x, out);
@@ -490,7 +561,9 @@ cudaError_t launch_thermal_cdf(const GridDev& g, double alpha1_mean, double* cdf
                                cudaStream_t s) {
     const double vol = g.d[0] * g.d[1] * g.d[2];
     (void)cudaGetLastError();  // report these launches' errors only
-    k_scan_local<<<n_blocks, kScanBlock, 0, s>>>(g.cells, g.ncell, alpha1_mean, vol, cdf, block_sums);
+    k_scan_local<<<n_blocks, kScanBlock, 0, s>>>(g.cells, g.ncell, alpha1_mean, vol,
+                                                 g.n_patches > 0 ? g.ncell_root : g.ncell, g.n_patches, g.patches,
+                                                 cdf, block_sums);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_scan_sums<<<1, 32, 0, s>>>(block_sums, n_blocks);

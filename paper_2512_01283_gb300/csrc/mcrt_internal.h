@@ -10,6 +10,7 @@
 
 namespace mcrt {
 
+constexpr int kMaxPatches = 64;
 constexpr int kMaxCams = MCRT_MAX_CAMERAS;
 constexpr int kMaxSources = MCRT_MAX_SOURCES;
 // scattering-model id of the transport instantiation that defers the optics to the
@@ -25,12 +26,27 @@ constexpr int kRecordF4 = 4;        // tally record: 4 float4 (64 bytes)
 
 // Cell record, 32 bytes = one DRAM sector: q_B (float4) then
 // (kappa_abs, kappa_sca, emissivity, 0).
-struct GridDev {
+// A statically refined patch of the root grid (one level of a composite mesh): the
+// root cells of `box` (half-open, root-cell indices) are replaced by a uniform grid of
+// `factor` cells per root cell along each axis, numbered from `offset` on.
+struct PatchDev {
+    int box[6];
+    int factor;
     int n[3];
+    long long offset;
+    double lo[3], d[3];
+    float lo_f[3], d_f[3];
+};
+
+struct GridDev {
+    int n[3];      // root grid
     int periodic;  // bit a: axis a periodic (MCRT_BOUNDARY_PERIODIC_*)
     double lo[3], hi[3], d[3];
-    long long ncell;
-    const float4* cells;  // [ncell][2]
+    long long ncell;       // all cells: the root's, then each patch's
+    long long ncell_root;  // root cells
+    const float4* cells;   // [ncell][2]; a covered root cell holds (1,0,0,0), (0, 0, 0, patch + 1 as bits)
+    int n_patches;
+    const PatchDev* patches;  // [n_patches], device
 };
 
 // Aligned dipole spheroids (MCRT_SCAT_DIPOLE): index 0 a principal axis perpendicular
@@ -190,6 +206,8 @@ int thermal_cdf_blocks(long long ncell);
 cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* guide, long long n_guide,
                                  cudaStream_t s);
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s);
+// marks the root cells covered by patches (records of patch p + 1, zero opacity and emission)
+cudaError_t launch_mark_covered(const GridDev& g, const PatchDev* host_patches, cudaStream_t s);
 // one-thread kernel: the 16 constants of mcrt_dipole_constants into out (device)
 cudaError_t launch_dipole_setup(double eps_re, double eps_im, double aspect, double x, double* out, cudaStream_t s);
 // round-based paths (mcrt_wave.cu): the transport loop of one launch with the tally

@@ -89,6 +89,7 @@ template <typename T> struct Packet {
     const JobDev* job;  // batched launches: the packet's job
     unsigned events, n_seg, n_sca, n_tally, n_abs, trials;
     int ix, iy, iz, src;
+    int lvl;        // composite grids: 0 in the root grid, p + 1 in patch p
     float4 cq, cr;  // record of the current cell: q_B and (kappa_abs, kappa_sca, B, 0)
 };
 

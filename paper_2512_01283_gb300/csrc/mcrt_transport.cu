@@ -20,6 +20,7 @@
 #include "mcrt_device.cuh"
 #include "mcrt_internal.h"
 #include "mcrt_packet.cuh"
+#include "mcrt_refine.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -127,6 +128,9 @@ template <typename T> struct JobRef<T, false> {
     __device__ __forceinline__ const long long* guide() const { return P.thermal_guide; }
     __device__ __forceinline__ long long n_guide() const { return P.n_guide; }
     __device__ __forceinline__ unsigned index() const { return 0u; }
+    __device__ __forceinline__ int n_patches() const { return P.g.n_patches; }
+    __device__ __forceinline__ const PatchDev* patches() const { return P.g.patches; }
+    __device__ __forceinline__ long long ncell_root() const { return P.g.ncell_root; }
 };
 
 template <typename T> struct JobRef<T, true> {
@@ -151,6 +155,10 @@ template <typename T> struct JobRef<T, true> {
     __device__ __forceinline__ const long long* guide() const { return j->thermal_guide; }
     __device__ __forceinline__ long long n_guide() const { return j->n_guide; }
     __device__ __forceinline__ unsigned index() const { return j->index; }
+    // batched launches refuse refined grids
+    __device__ __forceinline__ int n_patches() const { return 0; }
+    __device__ __forceinline__ const PatchDev* patches() const { return nullptr; }
+    __device__ __forceinline__ long long ncell_root() const { return j->ncell; }
 };
 
 template <typename T, bool B>
@@ -167,6 +175,47 @@ __device__ __forceinline__ void load_cell(const J& job, int ix, int iy, int iz, 
     const long long c = ((long long)iz * job.n(1) + iy) * job.n(0) + ix;
     q = __ldg(&job.cells()[2 * c]);
     r = __ldg(&job.cells()[2 * c + 1]);
+}
+
+// Composite grids: a packet that has just entered a root cell covered by a patch moves
+// into the patch cell that holds its position (entry cell for its direction).
+template <typename T, typename J> __device__ __forceinline__ void descend(const J& job, Packet<T>& pk) {
+    const int q = covering_patch(pk.cr);
+    if (q < 0) return;
+    const PatchDev& pq = job.patches()[q];
+    int idx[3];
+    patch_locate<T>(pq, pk.px, pk.py, pk.pz, pk.nx, pk.ny, pk.nz, idx);
+    pk.ix = idx[0];
+    pk.iy = idx[1];
+    pk.iz = idx[2];
+    pk.lvl = q + 1;
+    const long long c = patch_cell(pq, idx[0], idx[1], idx[2]);
+    pk.cq = __ldg(&job.cells()[2 * c]);
+    pk.cr = __ldg(&job.cells()[2 * c + 1]);
+}
+
+// Exit of the current patch cell along n (as exit_face, with the patch's geometry).
+template <typename T>
+__device__ __forceinline__ T exit_face_patch(const PatchDev& q, const Packet<T>& pk, int& axis, T& face) {
+    T best = T(INFINITY);
+    axis = -1;
+    face = T(0);
+    const T p[3] = {pk.px, pk.py, pk.pz}, n[3] = {pk.nx, pk.ny, pk.nz};
+    const int id[3] = {pk.ix, pk.iy, pk.iz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (n[a] != T(0)) {
+            const T f = patch_lo<T>(q, a) + T(n[a] > T(0) ? id[a] + 1 : id[a]) * patch_d<T>(q, a);
+            T t = t_div(f - p[a], n[a]);
+            t = t < T(0) ? T(0) : t;
+            if (t < best) {
+                best = t;
+                axis = a;
+                face = f;
+            }
+        }
+    }
+    return best;
 }
 
 
@@ -211,7 +260,8 @@ template <typename J> __device__ __forceinline__ long long thermal_cell(const J&
 // Packet birth, event 0: slot 0 = (tau, cos theta, phi, cell), slot 1 = (x, y, z, -).
 // pid is the packet id within its model.  Returns false when the packet starts
 // outside the grid (it is then finished).
-template <typename T, bool B>
+// WP: the instantiation walks composite grids (births in patch cells).
+template <typename T, bool B, bool WP>
 __device__ bool emit(const TransportParams& P, const JobRef<T, B>& job, long long pid, Packet<T>& pk, BlockTotals& bt) {
     int s = 0;
     while (s < P.n_src - 1 && pid >= P.src[s].start + P.src[s].count) ++s;
@@ -229,21 +279,39 @@ __device__ bool emit(const TransportParams& P, const JobRef<T, B>& job, long lon
     pk.X0 = eps;
     pk.X1 = pk.X2 = pk.X3 = T(0);
     bool inside;
+    pk.lvl = 0;
     if (src.type == MCRT_SRC_THERMAL) {
         const long long c = thermal_cell(job, (double)u0.d);
-        pk.ix = (int)(c % job.n(0));
-        pk.iy = (int)((c / job.n(0)) % job.n(1));
-        pk.iz = (int)(c / ((long long)job.n(0) * job.n(1)));
-        pk.px = job.lo(0) + (T(pk.ix) + u1.a) * job.d(0);
-        pk.py = job.lo(1) + (T(pk.iy) + u1.b) * job.d(1);
-        pk.pz = job.lo(2) + (T(pk.iz) + u1.c) * job.d(2);
+        if (WP && job.n_patches() > 0 && c >= job.ncell_root()) {
+            // a cell of a refined patch
+            int q = job.n_patches() - 1;
+            while (q > 0 && job.patches()[q].offset > c) --q;
+            const PatchDev& pq = job.patches()[q];
+            const long long l = c - pq.offset;
+            pk.ix = (int)(l % pq.n[0]);
+            pk.iy = (int)((l / pq.n[0]) % pq.n[1]);
+            pk.iz = (int)(l / ((long long)pq.n[0] * pq.n[1]));
+            pk.px = patch_lo<T>(pq, 0) + (T(pk.ix) + u1.a) * patch_d<T>(pq, 0);
+            pk.py = patch_lo<T>(pq, 1) + (T(pk.iy) + u1.b) * patch_d<T>(pq, 1);
+            pk.pz = patch_lo<T>(pq, 2) + (T(pk.iz) + u1.c) * patch_d<T>(pq, 2);
+            pk.lvl = q + 1;
+            pk.cq = __ldg(&job.cells()[2 * c]);
+            pk.cr = __ldg(&job.cells()[2 * c + 1]);
+        } else {
+            pk.ix = (int)(c % job.n(0));
+            pk.iy = (int)((c / job.n(0)) % job.n(1));
+            pk.iz = (int)(c / ((long long)job.n(0) * job.n(1)));
+            pk.px = job.lo(0) + (T(pk.ix) + u1.a) * job.d(0);
+            pk.py = job.lo(1) + (T(pk.iy) + u1.b) * job.d(1);
+            pk.pz = job.lo(2) + (T(pk.iz) + u1.c) * job.d(2);
+            load_cell(job, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
+        }
         T n[3];
         iso_dir(u0.b, u0.c, n);
         pk.nx = n[0];
         pk.ny = n[1];
         pk.nz = n[2];
         inside = true;
-        load_cell(job, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
         // emission alpha_abs B (1,0,0,0) in the grain-meridian basis, with alpha_abs the
         // absorption part of K (K minus its scattering part (s11, s12)); weight
         // alpha_abs,11(theta') over its mean over directions (mean alpha1 - omega)
@@ -300,6 +368,8 @@ __device__ bool emit(const TransportParams& P, const JobRef<T, B>& job, long lon
         pk.iy = idx[1];
         pk.iz = idx[2];
         if (inside) load_cell(job, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
+        if constexpr (WP)
+            if (inside && job.n_patches() > 0) descend(job, pk);
     }
     pk.tau = -(double)t_log(u0.a);
     pk.I_birth = pk.X0;
@@ -349,6 +419,9 @@ __device__ __forceinline__ T exit_face(const J& job, const Packet<T>& pk, int& a
 
 __host__ __device__ constexpr bool table_optics(int scat) { return scat == MCRT_SCAT_TABLE || scat == kScatTableDeferred; }
 __host__ __device__ constexpr bool round_based(int scat) { return scat == kScatSurrogate || scat == kScatTableDeferred; }
+// instantiations that walk composite grids (static mesh refinement): single-model launches
+// with the in-place tally
+__host__ __device__ constexpr bool walks_patches(int scat, bool batch) { return !batch && !round_based(scat); }
 
 // Round-based paths: the packet leaves this launch for the suspend buffer (one slot per
 // work item of the launch, so it cannot run over), waiting for its scattering
@@ -381,12 +454,17 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     const bool capped = pk.events >= (unsigned)P.max_events;
     int axis;
     T face;
-    const T ell_exit = exit_face(job, pk, axis, face);
+    // composite grids: the patch the packet is in (nullptr in the root grid)
+    const PatchDev* pt = nullptr;
+    if constexpr (walks_patches(SCAT, B))
+        if (pk.lvl > 0) pt = &job.patches()[pk.lvl - 1];
+    const T ell_exit = pt ? exit_face_patch(*pt, pk, axis, face) : exit_face(job, pk, axis, face);
     // a packet without a finite exit (non-finite direction) ends as escaped
     const bool lost = !capped && axis < 0;
     const bool want_A = !capped && !lost && kext > T(0);
     const bool want_S = want_A && ks > T(0) && P.n_cam > 0;
-    const unsigned c32 = (unsigned)(((long long)pk.iz * job.n(1) + pk.iy) * job.n(0) + pk.ix);
+    const unsigned c32 = pt ? (unsigned)patch_cell(*pt, pk.ix, pk.iy, pk.iz)
+                            : (unsigned)(((long long)pk.iz * job.n(1) + pk.iy) * job.n(0) + pk.ix);
     // converged point: same-cell groups (of the same model) for the aggregated
     // tallies; lanes that leave below are outside actA / actS
     const unsigned long long key = ((unsigned long long)job.index() << 32) | c32;
@@ -426,16 +504,25 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     if (!scatter_here) {
         int* ni = axis == 0 ? &nix : (axis == 1 ? &niy : &niz);
         const T na = axis == 0 ? pk.nx : (axis == 1 ? pk.ny : pk.nz);
-        const int nn = job.n(axis);
+        const int nn = pt ? pt->n[axis] : job.n(axis);
         *ni += na > T(0) ? 1 : -1;
         next_in = *ni >= 0 && *ni < nn;
-        if (!next_in && ((job.periodic() >> axis) & 1)) {
-            // a periodic axis: the packet re-enters on the opposite face
-            face = na > T(0) ? job.lo(axis) : job.lo(axis) + T(nn) * job.d(axis);
-            *ni = na > T(0) ? 0 : nn - 1;
-            next_in = true;
+        if (pt) {
+            // within the patch; leaving it is resolved below, once the packet is on the face
+            if (next_in) {
+                const long long c = patch_cell(*pt, nix, niy, niz);
+                nq = __ldg(&job.cells()[2 * c]);
+                nr = __ldg(&job.cells()[2 * c + 1]);
+            }
+        } else {
+            if (!next_in && ((job.periodic() >> axis) & 1)) {
+                // a periodic axis: the packet re-enters on the opposite face
+                face = na > T(0) ? job.lo(axis) : job.lo(axis) + T(nn) * job.d(axis);
+                *ni = na > T(0) ? 0 : nn - 1;
+                next_in = true;
+            }
+            if (next_in) load_cell(job, nix, niy, niz, nq, nr);
         }
-        if (next_in) load_cell(job, nix, niy, niz, nq, nr);
     }
 
     const V3<T> n{pk.nx, pk.ny, pk.nz};
@@ -593,6 +680,32 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             pk.py = face;
         else
             pk.pz = face;
+        if constexpr (walks_patches(SCAT, B)) {
+            if (pt && !next_in) {
+                // out of the patch: the root cell beyond its face (across a periodic face
+                // of the root box, the one on the opposite side)
+                const T na = axis == 0 ? pk.nx : (axis == 1 ? pk.ny : pk.nz);
+                int r[3] = {pt->box[0] + nix / pt->factor, pt->box[1] + niy / pt->factor, pt->box[2] + niz / pt->factor};
+                r[axis] = na > T(0) ? pt->box[3 + axis] : pt->box[axis] - 1;
+                next_in = r[axis] >= 0 && r[axis] < job.n(axis);
+                if (!next_in && ((job.periodic() >> axis) & 1)) {
+                    r[axis] = na > T(0) ? 0 : job.n(axis) - 1;
+                    const T f = na > T(0) ? job.lo(axis) : job.lo(axis) + T(job.n(axis)) * job.d(axis);
+                    if (axis == 0)
+                        pk.px = f;
+                    else if (axis == 1)
+                        pk.py = f;
+                    else
+                        pk.pz = f;
+                    next_in = true;
+                }
+                nix = r[0];
+                niy = r[1];
+                niz = r[2];
+                pk.lvl = 0;
+                if (next_in) load_cell(job, nix, niy, niz, nq, nr);
+            }
+        }
         pk.ix = nix;
         pk.iy = niy;
         pk.iz = niz;
@@ -603,6 +716,8 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         }
         pk.cq = nq;
         pk.cr = nr;
+        if constexpr (walks_patches(SCAT, B))
+            if (pk.lvl == 0 && job.n_patches() > 0) descend(job, pk);
         return;
     }
 
@@ -862,7 +977,7 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
                     }
                 } else if (idx - w_resume < w_new) {
                     const long long pid = P.pid_begin + (long long)(w_next + (idx - w_resume));
-                    alive = emit<T, false>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
+                    alive = emit<T, false, false>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
                     pk.park = false;
                 } else {
                     pool_done = true;
@@ -892,9 +1007,9 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
                     pk.job = &P.jobs[job_index(P, pid)];
                     local = pid - pk.job->pid_start;
                 }
-                alive = emit<T, true>(P, JobRef<T, true>{pk.job}, local, pk, bt);
+                alive = emit<T, true, false>(P, JobRef<T, true>{pk.job}, local, pk, bt);
             } else {
-                alive = emit<T, false>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
+                alive = emit<T, false, walks_patches(SCAT, false)>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
             }
         }
         const unsigned pend = __ballot_sync(kFull, alive && pk.pending);

@@ -73,6 +73,11 @@ class TuneReport(C.Structure):
                 ("blocks_per_sm", C.c_int32 * 16), ("interleave", C.c_int32 * 16), ("events_per_s", C.c_double * 16)]
 
 
+class Patch(C.Structure):
+    _fields_ = [("box", C.c_int32 * 6), ("factor", C.c_int32), ("kappa_abs", C.c_void_p), ("kappa_sca", C.c_void_p),
+                ("bfield", C.c_void_p), ("emissivity", C.c_void_p)]
+
+
 class NoAllocProblem(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("lo", C.c_double * 3),
                 ("hi", C.c_double * 3), ("kappa_abs", C.c_void_p), ("kappa_sca", C.c_void_p),
@@ -91,7 +96,7 @@ SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "m
            "mcrt_surrogate_create", "mcrt_surrogate_train", "mcrt_surrogate_eval", "mcrt_surrogate_labels",
            "mcrt_surrogate_grad", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy",
            "mcrt_surrogate_error_map", "mcrt_set_surrogate", "mcrt_surrogate_eval_engine", "mcrt_set_dust_dipole",
-           "mcrt_dipole_constants", "mcrt_set_tallies"]
+           "mcrt_dipole_constants", "mcrt_set_tallies", "mcrt_create_grid_refined"]
 
 
 def lib():
@@ -105,6 +110,8 @@ def lib():
     L = C.CDLL(LIB_PATH)
     vp, i32, i64, dp, fp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.c_void_p
     L.mcrt_create_grid.argtypes = [C.POINTER(C.c_void_p), i32, i32, i32, dp, dp, fp, fp, fp, fp, i32, vp]
+    L.mcrt_create_grid_refined.argtypes = [C.POINTER(C.c_void_p), i32, i32, i32, dp, dp, fp, fp, fp, fp, i32, i32,
+                                           C.POINTER(Patch), vp]
     L.mcrt_set_dust_tables.argtypes = [vp, i32, i32, i32, fp, fp, i32, fp]
     L.mcrt_launch_packets.argtypes = [C.POINTER(C.c_void_p), i32, C.POINTER(LaunchDesc), C.POINTER(Stats)]
     L.mcrt_image_stokes.argtypes = [vp, i32, vp]
@@ -199,8 +206,23 @@ class Model:
         lo = (C.c_double * 3)(*model["lo"])
         hi = (C.c_double * 3)(*model["hi"])
         h = C.c_void_p()
-        st = L.mcrt_create_grid(C.byref(h), nx, ny, nz, lo, hi, pk, ps, pb, pe, int(model.get("periodic", 0)),
-                                _stream_handle(stream))
+        patches = model.get("refine") or []
+        self.ncell = nx * ny * nz
+        if patches:
+            arr = (Patch * len(patches))()
+            for i, q in enumerate(patches):
+                arr[i].box = (C.c_int32 * 6)(*q["box"])
+                arr[i].factor = int(q["factor"])
+                for key in ("kappa_abs", "kappa_sca", "bfield", "emissivity"):
+                    ptr, k = _ptr(q.get(key), np.float32)
+                    keep.append(k)
+                    setattr(arr[i], key, ptr)
+                self.ncell += int(np.prod([(q["box"][3 + a] - q["box"][a]) * q["factor"] for a in range(3)]))
+            st = L.mcrt_create_grid_refined(C.byref(h), nx, ny, nz, lo, hi, pk, ps, pb, pe, int(model.get("periodic", 0)),
+                                            len(patches), arr, _stream_handle(stream))
+        else:
+            st = L.mcrt_create_grid(C.byref(h), nx, ny, nz, lo, hi, pk, ps, pb, pe, int(model.get("periodic", 0)),
+                                    _stream_handle(stream))
         _check(st)
         self.h = h
         try:

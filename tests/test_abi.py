@@ -54,10 +54,10 @@ def test_struct_layout_matches_c():
     #include <stddef.h>
     #include "mcrt.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcrt_source), sizeof(mcrt_camera),
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(mcrt_source), sizeof(mcrt_camera),
              sizeof(mcrt_launch_desc), sizeof(mcrt_stats), offsetof(mcrt_launch_desc, pid_begin),
              offsetof(mcrt_launch_desc, time_budget_s), offsetof(mcrt_launch_desc, trace),
-             offsetof(mcrt_camera, npix));
+             offsetof(mcrt_camera, npix), sizeof(mcrt_patch), offsetof(mcrt_patch, kappa_abs));
       return 0;
     }
     """
@@ -69,7 +69,7 @@ def test_struct_layout_matches_c():
         vals = [int(x) for x in subprocess.check_output([exe]).split()]
     py = [C.sizeof(M.Source), C.sizeof(M.Camera), C.sizeof(M.LaunchDesc), C.sizeof(M.Stats),
           M.LaunchDesc.pid_begin.offset, M.LaunchDesc.time_budget_s.offset, M.LaunchDesc.trace.offset,
-          M.Camera.npix.offset]
+          M.Camera.npix.offset, C.sizeof(M.Patch), M.Patch.kappa_abs.offset]
     assert vals == py
 
 
