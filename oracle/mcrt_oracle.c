@@ -1441,16 +1441,29 @@ static int thermal_setup(run_ctx *C)
     const int64_t ncell = orc_n_cells(P);
     double *cdf = (double *)malloc(sizeof(double) * ncell);
     double acc = 0.0;
-    for (int64_t c = 0; c < ncell; ++c) {
-        where_t wh;
-        cell_where(P, c, &wh);
-        double ka = cell_ka(P, c), ks = cell_ks(P, c);
-        double kext = ka + ks;
-        double omega = kext > 0.0 ? ks / kext : 0.0;
-        double w = kext * (C->alpha1_mean - omega) * cell_em(P, c) * grid_cell_volume(P, wh.g);
-        if (w < 0.0 || (wh.g < 0 && covering_patch(P, wh.idx) >= 0)) w = 0.0;
-        acc += w;
-        cdf[c] = acc;
+    int64_t c = 0;
+    /* level by level: the root grid, then each patch, each with its cells' volume */
+    for (int g = -1; g < P->n_patches; ++g) {
+        int n3[3];
+        double glo[3], ghi[3];
+        grid_geom(P, g, n3, glo, ghi);
+        const double V = grid_cell_volume(P, g);
+        const float *ka = g < 0 ? P->kappa_abs : P->patches[g].kappa_abs;
+        const float *ks = g < 0 ? P->kappa_sca : P->patches[g].kappa_sca;
+        const float *em = g < 0 ? P->emissivity : P->patches[g].emissivity;
+        const int64_t count = (int64_t)n3[0] * n3[1] * n3[2];
+        for (int64_t l = 0; l < count; ++l, ++c) {
+            double kext = (double)ka[l] + (double)ks[l];
+            double omega = kext > 0.0 ? ks[l] / kext : 0.0;
+            double w = kext * (C->alpha1_mean - omega) * (em ? em[l] : 0.0) * V;
+            if (w < 0.0) w = 0.0;
+            if (g < 0 && P->n_patches > 0) {
+                int ridx[3] = {(int)(l % n3[0]), (int)((l / n3[0]) % n3[1]), (int)(l / ((int64_t)n3[0] * n3[1]))};
+                if (covering_patch(P, ridx) >= 0) w = 0.0;
+            }
+            acc += w;
+            cdf[c] = acc;
+        }
     }
     C->cdf = cdf;
     C->cdf_total = acc;

@@ -751,7 +751,7 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
     if (block % 32 != 0 || block > 128)
         return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: block_size must be a multiple of 32, <= 128");
     const size_t smem = transport_smem_bytes(P, d->precision, block);
-    int bps = transport_max_blocks_per_sm(d->precision, P.t.model, false, block, smem);
+    int bps = transport_max_blocks_per_sm(d->precision, P.t.model, false, block, smem, P.g.n_patches > 0);
     if (d->blocks_per_sm > 0 && d->blocks_per_sm < bps) bps = d->blocks_per_sm;
     const long long work = pe - pb;
     long long grid = (long long)ctx->n_sm * bps;

@@ -242,9 +242,10 @@ __device__ __forceinline__ void transfer(const T X[4], T a, T a2, T a3, T dtau, 
                                          T wscale) {
     const T xa = a * dtau, xb = a2 * dtau, ya = a3 * dtau;
     const T xp = xa + xb, xm = xa - xb;
+    const T ea = t_exp(-xa);
     if (fabs(xb) <= T(10)) {
-        const T ea = t_exp(-xa);
-        const T e1p = t_expm1(xb), e1m = t_expm1(-xb);
+        // e^{-xb} - 1 = -m / (1 + m) with m = e^{xb} - 1: no cancellation, one expm1
+        const T e1p = t_expm1(xb), e1m = -e1p * t_rcp(T(1) + e1p);
         const T sh = T(0.5) * (e1p - e1m), ch = T(1) + T(0.5) * (e1p + e1m);
         Y[0] = ea * (ch * X[0] - sh * X[1]);
         Y[1] = ea * (ch * X[1] - sh * X[0]);
@@ -254,7 +255,6 @@ __device__ __forceinline__ void transfer(const T X[4], T a, T a2, T a3, T dtau, 
         Y[0] = T(0.5) * (ep * sp + em * sm);
         Y[1] = T(0.5) * (ep * sp - em * sm);
     }
-    const T ea = t_exp(-xa);
     T s3 = T(0), c3 = T(1);
     if (ya != T(0)) t_sincos(ya, &s3, &c3);
     Y[2] = ea * (c3 * X[2] - s3 * X[3]);

@@ -190,8 +190,8 @@ struct ImageParams {
 
 // launchers (defined in the .cu files)
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s);
-const void* transport_kernel(int precision, int model, bool batch);
-int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem);
+const void* transport_kernel(int precision, int model, bool batch, bool refined = false);
+int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem, bool refined = false);
 size_t transport_smem_bytes(const TransportParams& p, int precision, int block);
 cudaError_t launch_image(const ImageParams& p, int precision, cudaStream_t s);
 cudaError_t launch_setup_cells(const float* ka, const float* ks, const float* bf, const float* em, long long ncell,

@@ -119,6 +119,23 @@ __device__ __forceinline__ double widen(float f) {
     const unsigned lo = e == 0u ? 0u : (u << 29);
     return __hiloint2double((int)hi, (int)lo);
 }
+
+// The remaining optical depth is an FP64 running sum (FP32 steps widened exactly).
+__device__ __forceinline__ void tau_set(double& t, float v) { t = (double)v; }
+__device__ __forceinline__ void tau_set(double& t, double v) { t = v; }
+__device__ __forceinline__ bool tau_below(double t, float d) { return t < widen(d); }
+__device__ __forceinline__ bool tau_below(double t, double d) { return t < d; }
+__device__ __forceinline__ void tau_sub(double& t, float d) { t -= widen(d); }
+__device__ __forceinline__ void tau_sub(double& t, double d) { t -= d; }
+__device__ __forceinline__ double tau_value(double t) { return t; }
+// 8 bytes of the waiting form of a packet
+__device__ __forceinline__ void tau_pack(double t, float& a, float& b) {
+    a = __int_as_float(__double2loint(t));
+    b = __int_as_float(__double2hiint(t));
+}
+__device__ __forceinline__ void tau_unpack(double& t, float a, float b) {
+    t = __hiloint2double(__float_as_int(b), __float_as_int(a));
+}
 __device__ __forceinline__ double widen(double d) { return d; }
 
 // Packet end: optional trace record, then the packet's totals into the block's.
@@ -225,8 +242,9 @@ __device__ __forceinline__ void store_state(float4* d, const Packet<float>& pk, 
     d[1] = make_float4(pk.nx, pk.ny, pk.nz, pk.X1);
     d[2] = make_float4(pk.X2, pk.X3, pk.I_birth, pk.e_abs);
     d[3] = make_float4(pk.e_gain, pk.s_flight, __int_as_float(pk.src), 0.f);
-    d[4] = make_float4(__uint_as_float((unsigned)(pid & 0xffffffffull)), __uint_as_float((unsigned)(pid >> 32)),
-                       __int_as_float(__double2loint(pk.tau)), __int_as_float(__double2hiint(pk.tau)));
+    float ta, tb;
+    tau_pack(pk.tau, ta, tb);
+    d[4] = make_float4(__uint_as_float((unsigned)(pid & 0xffffffffull)), __uint_as_float((unsigned)(pid >> 32)), ta, tb);
     d[5] = make_float4(__uint_as_float(pk.events), __uint_as_float(pk.n_seg), __uint_as_float(pk.n_sca),
                        __uint_as_float(pk.n_tally));
     d[6] = make_float4(__uint_as_float(pk.n_abs), __uint_as_float(pk.trials), __int_as_float(pk.ix),
@@ -252,7 +270,7 @@ __device__ __forceinline__ void load_state(const float4* d, Packet<float>& pk) {
     pk.s_flight = e.y;
     pk.src = __float_as_int(e.z);
     pk.pid = (long long)(((unsigned long long)__float_as_uint(f.y) << 32) | (unsigned long long)__float_as_uint(f.x));
-    pk.tau = __hiloint2double(__float_as_int(f.w), __float_as_int(f.z));
+    tau_unpack(pk.tau, f.z, f.w);
     pk.events = __float_as_uint(g.x);
     pk.n_seg = __float_as_uint(g.y);
     pk.n_sca = __float_as_uint(g.z);

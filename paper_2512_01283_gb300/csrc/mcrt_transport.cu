@@ -371,7 +371,7 @@ __device__ bool emit(const TransportParams& P, const JobRef<T, B>& job, long lon
         if constexpr (WP)
             if (inside && job.n_patches() > 0) descend(job, pk);
     }
-    pk.tau = -(double)t_log(u0.a);
+    tau_set(pk.tau, -t_log(u0.a));
     pk.I_birth = pk.X0;
     if (!inside) finish(P, pk, 1, bt);
     return inside;
@@ -419,8 +419,9 @@ __device__ __forceinline__ T exit_face(const J& job, const Packet<T>& pk, int& a
 
 __host__ __device__ constexpr bool table_optics(int scat) { return scat == MCRT_SCAT_TABLE || scat == kScatTableDeferred; }
 __host__ __device__ constexpr bool round_based(int scat) { return scat == kScatSurrogate || scat == kScatTableDeferred; }
-// instantiations that walk composite grids (static mesh refinement): single-model launches
-// with the in-place tally
+// instantiations that may walk composite grids (static mesh refinement): single-model
+// launches with the in-place tally; the kernels for grids with patches (R) are
+// instantiated apart, so that plain grids keep the plain walk
 __host__ __device__ constexpr bool walks_patches(int scat, bool batch) { return !batch && !round_based(scat); }
 
 // Round-based paths: the packet leaves this launch for the suspend buffer (one slot per
@@ -444,7 +445,7 @@ template <typename T> __device__ __forceinline__ void park_packet(const Transpor
 
 // One event of a live packet: a cell segment, then a scattering when the sampled
 // optical depth runs out inside the cell.  `work` = live lanes of the warp.
-template <typename T, int SCAT, bool B>
+template <typename T, int SCAT, bool B, bool R>
 __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm, Packet<T>& pk, bool& alive,
                                      BlockTotals& bt, unsigned work) {
     const JobRef<T, B> job = job_of<T, B>(P, sm, pk);
@@ -456,7 +457,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     T face;
     // composite grids: the patch the packet is in (nullptr in the root grid)
     const PatchDev* pt = nullptr;
-    if constexpr (walks_patches(SCAT, B))
+    if constexpr (R)
         if (pk.lvl > 0) pt = &job.patches()[pk.lvl - 1];
     const T ell_exit = pt ? exit_face_patch(*pt, pk, axis, face) : exit_face(job, pk, axis, face);
     // a packet without a finite exit (non-finite direction) ends as escaped
@@ -494,8 +495,8 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     }
     const T omega = kext > T(0) ? t_div(ks_n, kext) : T(0);
     const T dsca_exit = ks_n * ell_exit;
-    const bool scatter_here = (ks_n > T(0)) && (pk.tau < widen(dsca_exit));
-    const T ell = scatter_here ? T(pk.tau) / ks_n : ell_exit;
+    const bool scatter_here = (ks_n > T(0)) && tau_below(pk.tau, dsca_exit);
+    const T ell = scatter_here ? T(tau_value(pk.tau)) / ks_n : ell_exit;
 
     // the next cell's record is requested before the segment arithmetic
     int nix = pk.ix, niy = pk.iy, niz = pk.iz;
@@ -670,7 +671,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     pk.events++;
 
     if (!scatter_here) {
-        pk.tau -= widen(dsca_exit);
+        tau_sub(pk.tau, dsca_exit);
         pk.px += ell_exit * pk.nx;
         pk.py += ell_exit * pk.ny;
         pk.pz += ell_exit * pk.nz;
@@ -680,7 +681,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             pk.py = face;
         else
             pk.pz = face;
-        if constexpr (walks_patches(SCAT, B)) {
+        if constexpr (R) {
             if (pt && !next_in) {
                 // out of the patch: the root cell beyond its face (across a periodic face
                 // of the root box, the one on the opposite side)
@@ -716,7 +717,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         }
         pk.cq = nq;
         pk.cr = nr;
-        if constexpr (walks_patches(SCAT, B))
+        if constexpr (R)
             if (pk.lvl == 0 && job.n_patches() > 0) descend(job, pk);
         return;
     }
@@ -808,7 +809,7 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
         pk.nx = n2.x;
         pk.ny = n2.y;
         pk.nz = n2.z;
-        pk.tau = -(double)t_log(us.a);
+        tau_set(pk.tau, -t_log(us.a));
         return;
     }
     int bin = 0;
@@ -886,7 +887,7 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
     pk.nx = n2.x;
     pk.ny = n2.y;
     pk.nz = n2.z;
-    pk.tau = -(double)t_log(us.a);
+    tau_set(pk.tau, -t_log(us.a));
 }
 
 // Job of a batch packet index: the last job whose first index is <= gpid.
@@ -912,7 +913,7 @@ constexpr int min_blocks() {
     return sizeof(T) != 4 ? 1 : (SCAT == kScatTableDeferred ? MCRT_ROUND_MIN_BLOCKS : MCRT_MIN_BLOCKS);
 }
 
-template <typename T, int SCAT, bool B>
+template <typename T, int SCAT, bool B, bool R>
 __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
     k_transport(const __grid_constant__ TransportParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1009,7 +1010,7 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
                 }
                 alive = emit<T, true, false>(P, JobRef<T, true>{pk.job}, local, pk, bt);
             } else {
-                alive = emit<T, false, walks_patches(SCAT, false)>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
+                alive = emit<T, false, R>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
             }
         }
         const unsigned pend = __ballot_sync(kFull, alive && pk.pending);
@@ -1028,7 +1029,7 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
             }
             continue;
         }
-        if (alive && !pk.pending) step<T, SCAT, B>(P, sm, pk, alive, bt, work);
+        if (alive && !pk.pending) step<T, SCAT, B, R>(P, sm, pk, alive, bt, work);
     }
 
     bulk_wait_all();  // this thread's reductions have completed before the block ends
@@ -1056,32 +1057,33 @@ size_t transport_smem_bytes(const TransportParams& p, int precision, int block) 
     return kx + mix + cams + stage;
 }
 
-const void* transport_kernel(int precision, int model, bool batch) {
+template <typename T, int SCAT, bool B> const void* kernel_of(bool refined) {
+    if constexpr (walks_patches(SCAT, B))
+        if (refined) return (const void*)k_transport<T, SCAT, B, true>;
+    return (const void*)k_transport<T, SCAT, B, false>;
+}
+
+template <typename T> const void* kernel_of_model(int model, bool batch, bool refined) {
     if (model == MCRT_SCAT_DIPOLE)  // single-model launches only
-        return precision == MCRT_FP64 ? (const void*)k_transport<double, MCRT_SCAT_DIPOLE, false>
-                                      : (const void*)k_transport<float, MCRT_SCAT_DIPOLE, false>;
-    if (precision == MCRT_FP64) {
-        if (model == MCRT_SCAT_TABLE)
-            return batch ? (const void*)k_transport<double, MCRT_SCAT_TABLE, true>
-                         : (const void*)k_transport<double, MCRT_SCAT_TABLE, false>;
-        return batch ? (const void*)k_transport<double, MCRT_SCAT_RAYLEIGH, true>
-                     : (const void*)k_transport<double, MCRT_SCAT_RAYLEIGH, false>;
-    }
+        return kernel_of<T, MCRT_SCAT_DIPOLE, false>(refined);
     if (model == MCRT_SCAT_TABLE)
-        return batch ? (const void*)k_transport<float, MCRT_SCAT_TABLE, true>
-                     : (const void*)k_transport<float, MCRT_SCAT_TABLE, false>;
-    return batch ? (const void*)k_transport<float, MCRT_SCAT_RAYLEIGH, true>
-                 : (const void*)k_transport<float, MCRT_SCAT_RAYLEIGH, false>;
+        return batch ? kernel_of<T, MCRT_SCAT_TABLE, true>(false) : kernel_of<T, MCRT_SCAT_TABLE, false>(refined);
+    return batch ? kernel_of<T, MCRT_SCAT_RAYLEIGH, true>(false) : kernel_of<T, MCRT_SCAT_RAYLEIGH, false>(refined);
+}
+
+const void* transport_kernel(int precision, int model, bool batch, bool refined) {
+    return precision == MCRT_FP64 ? kernel_of_model<double>(model, batch, refined)
+                                  : kernel_of_model<float>(model, batch, refined);
 }
 
 const void* transport_kernel_rounds(int model) {
-    return model == kScatSurrogate ? (const void*)k_transport<float, kScatSurrogate, false>
-                                   : (const void*)k_transport<float, kScatTableDeferred, false>;
+    return model == kScatSurrogate ? (const void*)k_transport<float, kScatSurrogate, false, false>
+                                   : (const void*)k_transport<float, kScatTableDeferred, false, false>;
 }
 
-int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem) {
+int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem, bool refined) {
     int nb = 0;
-    const void* k = round_based(model) ? transport_kernel_rounds(model) : transport_kernel(precision, model, batch);
+    const void* k = round_based(model) ? transport_kernel_rounds(model) : transport_kernel(precision, model, batch, refined);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
@@ -1090,7 +1092,7 @@ int transport_max_blocks_per_sm(int precision, int model, bool batch, int block,
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s) {
     const size_t smem = transport_smem_bytes(p, precision, block);
     const void* k = p.sur.deferred ? transport_kernel_rounds(p.sur.deferred)
-                                   : transport_kernel(precision, p.t.model, p.jobs != nullptr);
+                                   : transport_kernel(precision, p.t.model, p.jobs != nullptr, p.g.n_patches > 0);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

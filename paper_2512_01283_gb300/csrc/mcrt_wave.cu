@@ -567,7 +567,7 @@ __global__ void __launch_bounds__(kWaveBlock, 1) k_sur_scatter(const __grid_cons
             pk.nx = n2s.x;
             pk.ny = n2s.y;
             pk.nz = n2s.z;
-            pk.tau = -(double)logf(us_a);
+            tau_set(pk.tau, -logf(us_a));
             pk.s_flight = flight_size(tabs, us_d);
             cg::coalesced_group grp = cg::coalesced_threads();
             unsigned long long base = 0;
@@ -641,9 +641,14 @@ __global__ void __launch_bounds__(kTabBlock) k_tab_tally(const __grid_constant__
                 table_matrix(s_mix, P.t.n_theta, dot(n, Om), Pm);
                 const PlaneRot<float> pr = plane_rotation(n, th, ph, Om, thc, phc);
                 apply_plane(pr, Pm, W, Y);
+                // lanes 4-7 of each group of 8 store their second half first, so that each
+                // quarter-warp phase of 16-byte stores covers the 8 bank groups once
                 double2* d2 = reinterpret_cast<double2*>(stage + lane * 4);
-                d2[0] = make_double2(widen(Y[0]), widen(Y[1]));
-                d2[1] = make_double2(widen(Y[2]), widen(Y[3]));
+                const double2 lo2 = make_double2(widen(Y[0]), widen(Y[1]));
+                const double2 hi2 = make_double2(widen(Y[2]), widen(Y[3]));
+                const int h = (lane >> 2) & 1;
+                d2[h] = h ? hi2 : lo2;
+                d2[1 - h] = h ? lo2 : hi2;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
         }
