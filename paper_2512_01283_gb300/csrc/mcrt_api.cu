@@ -762,7 +762,10 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
         // capacity of a round: up to 2^21 packets in flight, 32 tally records each
         unsigned long long cap = work < (1ll << 21) ? (unsigned long long)(work > 0 ? work : 1) : (1ull << 21);
         // soft limit: room for one more record per thread of the transport grid
-        const unsigned long long margin = (unsigned long long)ctx->n_sm * 16ull * 128ull;
+        // slots taken past the soft limit: one record per resident thread, plus (chunked
+        // reservation) one chunk per resident warp
+        const unsigned long long margin =
+            (unsigned long long)ctx->n_sm * (16ull * 128ull + 64ull * 32ull * (unsigned long long)MCRT_REC_CHUNK);
         unsigned long long rec_cap = cap * 32ull;
         if (rec_cap < 4 * margin) rec_cap = 4 * margin;
         if (!ctx->d_wave) CK(ctx, cudaMalloc(&ctx->d_wave, sizeof(WaveCtl)));

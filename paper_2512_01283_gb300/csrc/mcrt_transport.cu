@@ -61,7 +61,10 @@ template <typename T> struct Smem {
     const float4* mix;   // [n_theta][2]
     const float4* kext;  // [n_ktheta]
     double* stage;       // [blockDim][kStageDoubles]
+    unsigned long long* chunk;  // round-based paths: per warp, next and end of its record slots
 };
+
+constexpr unsigned kRecChunk = 32u * MCRT_REC_CHUNK;
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -443,6 +446,14 @@ template <typename T> __device__ __forceinline__ void park_packet(const Transpor
     alive = false;
 }
 
+// A tally-record slot that holds no record (skipped by the tally kernels).
+template <int SCAT> __device__ __forceinline__ void empty_record(const TransportParams& P, unsigned long long k) {
+    if constexpr (SCAT == kScatSurrogate)
+        P.sur.records[k * kRecordF4 + 3] = make_float4(__uint_as_float(0xffffffffu), 0.f, 0.f, 0.f);
+    else
+        P.sur.records[k * kTableRecordF4 + 1] = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
+}
+
 // One event of a live packet: a cell segment, then a scattering when the sampled
 // optical depth runs out inside the cell.  `work` = live lanes of the warp.
 template <typename T, int SCAT, bool B, bool R>
@@ -584,10 +595,40 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
                 const int lead = __ffs(actS) - 1;
                 const unsigned cnt = (unsigned)__popc(actS);
                 unsigned long long base = 0;
-                if (lane == lead) base = atomicAdd(&P.sur.ctl->n_rec[P.sur.rec_slot], (unsigned long long)cnt);
-                base = __shfl_sync(actS, base, lead);
-                const unsigned long long idx = base + (unsigned)__popc(actS & ((1u << lane) - 1u));
-                queued = base + cnt <= P.sur.rec_cap;
+                const unsigned rank = (unsigned)__popc(actS & ((1u << lane) - 1u));
+                unsigned long long idx, last;  // this lane's slot; the step's highest slot
+                if constexpr (kRecChunk > 0) {
+                    // slots from the warp's chunk; when it runs out, the first lanes take its
+                    // rest and the others the start of a new chunk
+                    unsigned long long* ch = sm.chunk + 2 * (threadIdx.x >> 5);
+                    unsigned long long next = ch[0], end = ch[1];
+                    const unsigned long long rest = end - next;
+                    if (rest >= cnt) {
+                        idx = next + rank;
+                        last = next + cnt - 1;
+                        next += cnt;
+                    } else {
+                        unsigned long long nb = 0;
+                        if (lane == lead) nb = atomicAdd(&P.sur.ctl->n_rec[P.sur.rec_slot], (unsigned long long)kRecChunk);
+                        nb = __shfl_sync(actS, nb, lead);
+                        idx = rank < rest ? next + rank : nb + (rank - rest);
+                        last = nb + (cnt - rest) - 1;
+                        next = nb + (cnt - rest);
+                        end = nb + kRecChunk;
+                    }
+                    __syncwarp(actS);
+                    if (lane == lead) {
+                        ch[0] = next;
+                        ch[1] = end;
+                    }
+                    __syncwarp(actS);
+                } else {
+                    if (lane == lead) base = atomicAdd(&P.sur.ctl->n_rec[P.sur.rec_slot], (unsigned long long)cnt);
+                    base = __shfl_sync(actS, base, lead);
+                    idx = base + rank;
+                    last = base + cnt - 1;
+                }
+                queued = last < P.sur.rec_cap;
                 if (idx < P.sur.rec_cap) {
                     if constexpr (SCAT == kScatSurrogate) {
                         float4* r = P.sur.records + idx * kRecordF4;
@@ -615,7 +656,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
                 // at most one record beyond it and the queue cannot run over (the in-place
                 // tally below is a guard that stays unused)
                 if (idx >= P.sur.rec_soft) pk.park = true;
-                if (lane == lead && base + cnt > P.sur.rec_soft) atomicExch(&P.sur.ctl->full, 1ull);
+                if (lane == lead && last >= P.sur.rec_soft) atomicExch(&P.sur.ctl->full, 1ull);
                 if (!queued && lane == lead) atomicAdd(&P.sur.ctl->cnt[kCntOverflow], (unsigned long long)cnt);
             }
         }
@@ -918,6 +959,7 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
     k_transport(const __grid_constant__ TransportParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockTotals bt;
+    __shared__ unsigned long long s_chunk[2 * (kDefaultBlock / 32)];
     // shared layout: kext table and mixture table (single model, TABLE), cameras,
     // tally staging
     float4* s_kext = reinterpret_cast<float4*>(smem_raw);
@@ -936,10 +978,11 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
     }
     if (threadIdx.x < 6) bt.e[threadIdx.x] = 0.0;
     if (threadIdx.x < 10) bt.n[threadIdx.x] = 0ull;
+    if (threadIdx.x < 2 * (kDefaultBlock / 32)) s_chunk[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) bt.status = 0u;
     __syncthreads();
 
-    const Smem<T> sm{s_cam, s_mix, s_kext, s_stage};
+    const Smem<T> sm{s_cam, s_mix, s_kext, s_stage, s_chunk};
     Packet<T> pk;
     pk.job = nullptr;
     bool alive = false, pool_done = false;
@@ -1032,6 +1075,13 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
         if (alive && !pk.pending) step<T, SCAT, B, R>(P, sm, pk, alive, bt, work);
     }
 
+    if constexpr (round_based(SCAT) && kRecChunk > 0) {
+        // the warp's unused record slots hold no record
+        __syncwarp();
+        const unsigned long long next = s_chunk[2 * (threadIdx.x >> 5)], end = s_chunk[2 * (threadIdx.x >> 5) + 1];
+        for (unsigned long long k = next + (threadIdx.x & 31); k < end && k < P.sur.rec_cap; k += 32)
+            empty_record<SCAT>(P, k);
+    }
     bulk_wait_all();  // this thread's reductions have completed before the block ends
     __syncthreads();
     if (threadIdx.x < 6) {

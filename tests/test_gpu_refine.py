@@ -146,3 +146,25 @@ def test_refined_grid_errors():
     assert e.value.status == M.MCRT_E_INVAL
     good.close()
     other.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_refined_spheroid_sphere_parity(prec):
+    """Aligned dipole spheroids on a refined grid: a 2x patch over the centre of the
+    spheroid sphere, central star, two cameras."""
+    base = W.spheroid_sphere(n=12, tau=1.5, albedo=0.6, b=(0.6, 0.0, 0.8))
+    m = W.refine_uniform(base, [((3, 3, 3, 9, 9, 9), 2)])
+    run = {"sources": [{"type": "point", "pos": (0.05, -0.02, 0.01), "luminosity": 1.0, "n_packets": 10_000}],
+           "cameras": [W.camera((1, 0, 0), (12, 12), (2.0, 2.0)), W.camera((0.3, 0.4, 0.866), (12, 12), (2.0, 2.0))],
+           "seed": 6, "roulette_threshold": 1e-4, "roulette_survival": 0.1}
+    o = oracle_run(m, run, n_trace=10_000)
+    g = gpu_run(m, run, prec, n_trace=10_000)
+    frac = trace_match_fraction(g["trace"], o["trace"], 1e-4)
+    assert frac >= (0.999 if prec == "fp64" else 0.99), frac
+    tol = 1e-7 if prec == "fp64" else 2e-3
+    dS = np.linalg.norm(g["S"] - o["S"]) / np.linalg.norm(o["S"])
+    assert dS < tol, dS
+    for k in range(2):
+        Itot = o["images"][k][0].sum()
+        for e in range(4):
+            assert abs(g["images"][k][e].sum() - o["images"][k][e].sum()) < max(tol, 1e-9) * Itot, (k, e)
