@@ -65,6 +65,13 @@ template <typename T> struct Smem {
 };
 
 constexpr unsigned kRecChunk = 32u * MCRT_REC_CHUNK;
+// Same-cell lanes of a warp pre-sum their absorbed energy before one FP64 atomic (1), or
+// every lane adds its own (0, round-based kernels only: there is no in-place tally
+// needing the same-cell groups).  Packets of a warp rarely share a cell: without the
+// match the table-round transport takes 852 ms per 1e8-packet disk step, 909 ms with it.
+#ifndef MCRT_ABS_GROUPS
+#define MCRT_ABS_GROUPS 0
+#endif
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -479,8 +486,9 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
                             : (unsigned)(((long long)pk.iz * job.n(1) + pk.iy) * job.n(0) + pk.ix);
     // converged point: same-cell groups (of the same model) for the aggregated
     // tallies; lanes that leave below are outside actA / actS
+    constexpr bool kGroups = MCRT_ABS_GROUPS || !round_based(SCAT);
     const unsigned long long key = ((unsigned long long)job.index() << 32) | c32;
-    const unsigned peers = __match_any_sync(work, key);
+    const unsigned peers = kGroups ? __match_any_sync(work, key) : (1u << (threadIdx.x & 31));
     const unsigned actA = __ballot_sync(work, want_A);
     const unsigned actS = __ballot_sync(work, want_S);
     if (capped || lost) {
@@ -573,7 +581,7 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         rotate_qu(Yg[1], Yg[2], c2, -s2);
         // absorbed energy, one FP64 atomic per same-cell group
         {
-            const unsigned gmax = __reduce_max_sync(actA, (unsigned)__popc(group));
+            const unsigned gmax = kGroups ? __reduce_max_sync(actA, (unsigned)__popc(group)) : 1u;
             T dI = pk.X0 - Yg[0];
             // aligned spheroids: the decrease of I also holds kappa_ext s12 int Q dl, which the
             // scattering weight returns in expectation; the absorbed energy is int (K_abs X)_0 dl
