@@ -382,7 +382,9 @@ def test_table_rounds_equal_the_in_place_tally():
         assert g["stats"]["wave_iterations"] >= 1
         assert trace_match_fraction(g["trace"], ref["trace"], 1e-6) >= 0.999
         assert np.linalg.norm(g["S"] - ref["S"]) < 1e-6 * np.linalg.norm(ref["S"])
-        assert np.linalg.norm(g["absorbed"] - ref["absorbed"]) < 1e-9 * np.linalg.norm(ref["absorbed"])
+        # absorbed: the in-place kernel pre-sums same-cell lanes in FP32 before widening, the
+        # round kernels widen each lane's term
+        assert np.linalg.norm(g["absorbed"] - ref["absorbed"]) < 1e-7 * np.linalg.norm(ref["absorbed"])
         for k in range(4):
             assert np.linalg.norm(g["images"][k] - ref["images"][k]) < 1e-6 * np.linalg.norm(ref["images"][k])
 
