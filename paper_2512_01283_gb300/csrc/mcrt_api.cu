@@ -61,6 +61,7 @@ struct mcrt_ctx {
     cudaStream_t tally_stream = nullptr;  // table rounds: tally kernels beside the next transport
     float4* d_records = nullptr;
     unsigned long long rec_cap = 0;
+    size_t rec_bytes = 0;  // size of the tally-record queue allocation
     float4 *d_susp = nullptr, *d_res = nullptr;
     unsigned long long wave_cap = 0;
     // work area: counter (8 B), stats (16 x 8 B), status (8 B)
@@ -163,6 +164,7 @@ void free_wave(mcrt_ctx* c) {
     c->d_records = nullptr;
     c->d_susp = c->d_res = nullptr;
     c->rec_cap = c->wave_cap = 0;
+    c->rec_bytes = 0;
 }
 
 void free_tables(mcrt_ctx* c) {
@@ -766,7 +768,12 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
         // reservation) one chunk per resident warp
         const unsigned long long margin =
             (unsigned long long)ctx->n_sm * (16ull * 128ull + 64ull * 32ull * (unsigned long long)MCRT_REC_CHUNK);
-        unsigned long long rec_cap = cap * 32ull;
+        // queue: 32 records per packet in flight for the network's 64-byte records,
+        // MCRT_TABLE_ROUND_RECORDS for the tables' 32-byte records, two slots of them (the
+        // overlapped rounds fill one while the tally reads the other)
+        const unsigned long long per_packet = sur ? 32ull : (unsigned long long)MCRT_TABLE_ROUND_RECORDS;
+        const size_t rec_bytes = (size_t)(sur ? kRecordF4 : 2 * kTableRecordF4) * sizeof(float4);
+        unsigned long long rec_cap = cap * per_packet;
         if (rec_cap < 4 * margin) rec_cap = 4 * margin;
         if (!ctx->d_wave) CK(ctx, cudaMalloc(&ctx->d_wave, sizeof(WaveCtl)));
         if (ctx->wave_cap < cap) {
@@ -782,17 +789,18 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
             }
             ctx->wave_cap = cap;
         }
-        if (ctx->rec_cap < rec_cap) {
+        if (ctx->rec_bytes < (size_t)rec_cap * rec_bytes) {
             cudaFree(ctx->d_records);
             ctx->d_records = nullptr;
-            ctx->rec_cap = 0;
-            cudaError_t e = cudaMalloc(&ctx->d_records, (size_t)rec_cap * kRecordF4 * sizeof(float4));
+            ctx->rec_bytes = 0;
+            cudaError_t e = cudaMalloc(&ctx->d_records, (size_t)rec_cap * rec_bytes);
             if (e != cudaSuccess) {
                 (void)cudaGetLastError();
                 return fail(ctx, MCRT_E_NOMEM, "mcrt_launch_packets: surrogate tally queue: %s", cudaGetErrorString(e));
             }
-            ctx->rec_cap = rec_cap;
+            ctx->rec_bytes = (size_t)rec_cap * rec_bytes;
         }
+        ctx->rec_cap = rec_cap;
         P.sur.image = ctx->d_sur_image;
         P.sur.image_tc = ctx->d_sur_image_tc;
         P.sur.tally_engine = (d->flags & MCRT_FLAG_MMA_SYNC_TALLY) ? MCRT_ENGINE_MMA_SYNC : MCRT_ENGINE_TCGEN05;

@@ -18,6 +18,12 @@ constexpr int kMaxPatches = 64;
 #ifndef MCRT_REC_CHUNK
 #define MCRT_REC_CHUNK 4
 #endif
+// Table rounds: tally records of queue per packet in flight (2^21 packets per round).
+// On the 192^3 disk, 32 (107 rounds per 1e8-packet step) beat 64 and 128 (65 and 48
+// rounds): the transport took 853, 862 and 906 ms.
+#ifndef MCRT_TABLE_ROUND_RECORDS
+#define MCRT_TABLE_ROUND_RECORDS 32
+#endif
 constexpr int kMaxCams = MCRT_MAX_CAMERAS;
 constexpr int kMaxSources = MCRT_MAX_SOURCES;
 // scattering-model id of the transport instantiation that defers the optics to the
