@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-plane-parallel", action="store_true")
     ap.add_argument("--no-spheroids", action="store_true", help="skip the aligned-spheroid line")
     ap.add_argument("--no-refined", action="store_true", help="skip the static-mesh-refinement line")
+    ap.add_argument("--no-microbench", action="store_true", help="skip the FP64 reduction microbenchmark")
     ap.add_argument("--inline-tally", action="store_true",
                     help="table path: tally inside the transport kernel instead of a tally kernel per round")
     ap.add_argument("--tally-bps", type=int, default=0,
@@ -269,6 +270,26 @@ def run_refined(M, W, torch):
             "value": st["events"] / wall, "unit": UNIT, "events": st["events"], "seconds": wall,
             "patch_tally_share": float(np.abs(S[nroot:]).sum() / max(np.abs(S).sum(), 1e-300)),
             "energy_balance_rel": abs(bal - st["emitted_energy"]) / st["emitted_energy"]}
+
+
+def run_reduction_peaks(M):
+    """Throughput of the FP64 reductions the tallies are made of (mcrt_microbench): scalar
+    atomic adds and 256-byte bulk reduce-adds at spread positions, into 32 MB (inside the
+    L2) and 8 GB (far beyond it).  For comparison with the tally kernel, the bulk rate is
+    also given as read-modify-write bytes (2 x 256 B per row), the way its algorithmic
+    bytes count the source rows."""
+    out = {}
+    for tag, nbytes in (("l2", 32 << 20), ("dram", 8 << 30)):
+        n_red = 1 << 28
+        ms = M.microbench(0, nbytes, n_red)
+        out["f64_atomic_per_s_" + tag] = n_red / (ms * 1e-3)
+        n_rows = 1 << 24
+        ms = M.microbench(1, nbytes, n_rows)
+        out["bulk_rows_per_s_" + tag] = n_rows / (ms * 1e-3)
+        out["bulk_rmw_GBs_" + tag] = n_rows * 512.0 / (ms * 1e-3) / 1e9
+    out["note"] = ("scalar atomics: 2^28 FP64 adds; bulk: 2^24 rows of 32 doubles (cp.reduce.async.bulk add.f64); "
+                   "positions spread by a multiplicative hash")
+    return out
 
 
 def image_diff(a, b):
@@ -569,6 +590,13 @@ def main():
 
     if not args.no_refined and world == 1:
         line["refined"] = run_refined(M, W, torch)
+
+    if not args.no_microbench and world == 1:
+        red = run_reduction_peaks(M)
+        line["reduction_peaks"] = red
+        if "tally" in line.get("roofline_kernels", {}):
+            tk = line["roofline_kernels"]["tally"]
+            tk["frac_of_bulk_reduction_dram"] = tk["achieved"] / red["bulk_rmw_GBs_dram"]
 
     if not args.no_surrogate and world == 1:
         table_imgs = imgs.cpu().numpy()

@@ -316,6 +316,17 @@ MCRT_API mcrt_status mcrt_image_stokes(mcrt_ctx *ctx, int32_t camera, double *ou
 MCRT_API mcrt_status mcrt_get_tallies(mcrt_ctx *ctx, double *source, double *absorbed);
 
 /*
+ * Throughput of the FP64 reductions the step-1 tallies are made of, on the current
+ * device: n_ops additions into a zeroed device buffer of `bytes` bytes at spread
+ * positions (a multiplicative hash of the op index).
+ *   kind 0: scalar FP64 atomic adds without return value (one double per op)
+ *   kind 1: 256-byte bulk reduce-adds of FP64 rows from shared memory (one row per op)
+ * One untimed launch, then *ms_out = the CUDA-event time of one launch of n_ops ops.
+ * Errors: MCRT_E_INVAL (kind, or bytes < 256), MCRT_E_NOMEM, MCRT_E_CUDA.
+ */
+MCRT_API mcrt_status mcrt_microbench(int32_t kind, uint64_t bytes, uint64_t n_ops, double *ms_out);
+
+/*
  * Replace the step-1 tallies of the last launch (layouts as in mcrt_get_tallies), e.g.
  * with their sum over ranks that each ran a share of the packet ids: step 2 is linear
  * in the tallies (Sec. 2.3), so images of the summed tallies are the images of all

@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmcrt.so")
-SOURCES = ["mcrt_api.cu", "mcrt_transport.cu", "mcrt_image.cu", "mcrt_noalloc.cu", "mcrt_mlp.cu", "mcrt_wave.cu"]
+SOURCES = ["mcrt_api.cu", "mcrt_transport.cu", "mcrt_image.cu", "mcrt_noalloc.cu", "mcrt_mlp.cu", "mcrt_wave.cu",
+           "mcrt_microbench.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include"), "-I", CSRC]

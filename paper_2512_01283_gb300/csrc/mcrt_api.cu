@@ -947,6 +947,35 @@ mcrt_status mcrt_get_tallies(mcrt_ctx* ctx, double* source, double* absorbed) {
     return MCRT_OK;
 }
 
+mcrt_status mcrt_microbench(int32_t kind, uint64_t bytes, uint64_t n_ops, double* ms_out) {
+    if ((kind != 0 && kind != 1) || bytes < 256 || !ms_out) return fail(nullptr, MCRT_E_INVAL, "mcrt_microbench: bad arguments");
+    int dev = 0, n_sm = 0;
+    CK(nullptr, cudaGetDevice(&dev));
+    CK(nullptr, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    DevIn buf;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&buf.owned, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        return fail(nullptr, MCRT_E_NOMEM, "mcrt_microbench: %llu bytes", (unsigned long long)bytes);
+    }
+    if (e == cudaSuccess) e = cudaMemset(buf.owned, 0, bytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = launch_microbench(kind, (double*)buf.owned, bytes, n_ops, n_sm, nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+    if (e == cudaSuccess) e = launch_microbench(kind, (double*)buf.owned, bytes, n_ops, n_sm, nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(nullptr, MCRT_E_CUDA, "mcrt_microbench: %s", cudaGetErrorString(e));
+    *ms_out = ms;
+    return MCRT_OK;
+}
+
 mcrt_status mcrt_set_tallies(mcrt_ctx* ctx, const double* source, const double* absorbed) {
     if (!ctx) return fail(nullptr, MCRT_E_INVAL, "mcrt_set_tallies: ctx is NULL");
     if (!ctx->launched) return fail(ctx, MCRT_E_STATE, "mcrt_set_tallies: no launch yet");

@@ -219,6 +219,9 @@ int thermal_cdf_blocks(long long ncell);
 cudaError_t launch_thermal_guide(const double* cdf, long long ncell, long long* guide, long long n_guide,
                                  cudaStream_t s);
 cudaError_t launch_unit_eval(int fn, int precision, long long n, const double* in, double* out, cudaStream_t s);
+// FP64 reduction throughput kernels (kind 0 scalar atomics, 1 bulk 256-byte rows)
+cudaError_t launch_microbench(int kind, double* buf, unsigned long long bytes, unsigned long long n_ops, int n_sm,
+                              cudaStream_t s);
 // marks the root cells covered by patches (records of patch p + 1, zero opacity and emission)
 cudaError_t launch_mark_covered(const GridDev& g, const PatchDev* host_patches, cudaStream_t s);
 // one-thread kernel: the 16 constants of mcrt_dipole_constants into out (device)

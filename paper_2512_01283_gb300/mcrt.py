@@ -96,7 +96,7 @@ SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "m
            "mcrt_surrogate_create", "mcrt_surrogate_train", "mcrt_surrogate_eval", "mcrt_surrogate_labels",
            "mcrt_surrogate_grad", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy",
            "mcrt_surrogate_error_map", "mcrt_set_surrogate", "mcrt_surrogate_eval_engine", "mcrt_set_dust_dipole",
-           "mcrt_dipole_constants", "mcrt_set_tallies", "mcrt_create_grid_refined"]
+           "mcrt_dipole_constants", "mcrt_set_tallies", "mcrt_create_grid_refined", "mcrt_microbench"]
 
 
 def lib():
@@ -117,6 +117,7 @@ def lib():
     L.mcrt_image_stokes.argtypes = [vp, i32, vp]
     L.mcrt_get_tallies.argtypes = [vp, vp, vp]
     L.mcrt_set_tallies.argtypes = [vp, vp, vp]
+    L.mcrt_microbench.argtypes = [i32, C.c_uint64, C.c_uint64, C.POINTER(C.c_double)]
     L.mcrt_destroy.argtypes = [vp]
     L.mcrt_last_error.argtypes = [vp]
     L.mcrt_last_error.restype = C.c_char_p
@@ -176,6 +177,14 @@ def _stream_handle(stream):
 
 DIPOLE_KEYS = ["L0", "L1", "al0_re", "al0_im", "al1_re", "al1_im", "q_ext0", "q_ext1", "q_sca0", "q_sca1",
                "q_abs0", "q_abs1", "rho_re", "rho_im", "zn", "env"]
+
+
+def microbench(kind, nbytes, n_ops):
+    """mcrt_microbench: CUDA-event milliseconds of n_ops FP64 reductions (kind 0 scalar
+    atomics, 1 bulk 256-byte rows) into a buffer of nbytes."""
+    ms = C.c_double()
+    _check(lib().mcrt_microbench(int(kind), int(nbytes), int(n_ops), C.byref(ms)))
+    return ms.value
 
 
 def dipole_constants(eps, aspect, x):

@@ -490,3 +490,13 @@ def test_rank_shares_and_the_tally_exchange():
         assert np.allclose(out, ref["images"][k], rtol=1e-9, atol=1e-12 * np.abs(ref["images"][k]).max())
     for m in mods:
         m.close()
+
+
+def test_reduction_microbench_runs_and_checks_arguments():
+    """mcrt_microbench: both reduction forms run on a small buffer; bad arguments are refused."""
+    for kind in (0, 1):
+        assert M.microbench(kind, 1 << 20, 1 << 16) > 0.0
+    for bad in ((2, 1 << 20, 10), (0, 64, 10)):
+        with pytest.raises(M.McrtError) as e:
+            M.microbench(*bad)
+        assert e.value.status == M.MCRT_E_INVAL
