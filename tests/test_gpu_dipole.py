@@ -226,3 +226,20 @@ def test_invalid_dipole_arguments_and_unsupported_paths():
     m2.close()
     with pytest.raises(M.McrtError):
         M.dipole_constants(complex(2.0, -1.0), 1.0, 0.1)
+
+
+@pytest.mark.parametrize("grain", [(EPS, 0.5, 0.2), (EPS, 1.0, 0.3), (complex(3.0, 2.0), 4.0, 0.05)],
+                         ids=["prolate", "sphere", "absorbing-flat"])
+def test_spheroid_shapes_parity_fp32(grain):
+    """Prolate, spherical and strongly absorbing flat grains: FP32 traces and tallies
+    against the oracle (the sphere case is Rayleigh scattering with the dipole code)."""
+    eps, s, x = grain
+    model = W.spheroid_sphere(n=12, tau=1.0, albedo=0.6, b=(0.3, 0.5, 0.81), optics=W.dipole_optics(eps, s, x))
+    run = {"sources": [{"type": "point", "pos": (0.02, 0.03, -0.01), "luminosity": 1.0, "n_packets": 8000}],
+           "cameras": [W.camera((0.2, 0.9, 0.39), (13, 13), (2.0, 2.0))], "seed": 12,
+           "roulette_threshold": 1e-4, "roulette_survival": 0.1}
+    o = oracle_run(model, run, n_trace=8000)
+    g = gpu_run(model, run, "fp32", n_trace=8000)
+    assert trace_match_fraction(g["trace"], o["trace"], 1e-4) >= 0.99
+    assert np.linalg.norm(g["S"] - o["S"]) < 2e-3 * np.linalg.norm(o["S"])
+    assert np.linalg.norm(g["absorbed"] - o["absorbed"]) < 2e-3 * np.linalg.norm(o["absorbed"])

@@ -169,3 +169,29 @@ def test_refined_spheroid_sphere_parity(prec):
         Itot = o["images"][k][0].sum()
         for e in range(4):
             assert abs(g["images"][k][e].sum() - o["images"][k][e].sum()) < max(tol, 1e-9) * Itot, (k, e)
+
+
+def test_many_patches_largest_factor_parity():
+    """The limits of a composite grid: 64 single-cell patches of factor 2 over a 8x8
+    plane of a slab, one patch of factor 16 and patches on every face; FP64 traces and
+    tallies against the oracle."""
+    base = W.dichroic_slab(n=10, tau=1.5, p=0.05, b_angle_deg=35.0, albedo=0.7, emissivity=1.0)
+    base["optics"] = W.table_optics(n_bins=2)
+    patches = [((i, j, 4, i + 1, j + 1, 5), 2) for i in range(1, 9) for j in range(1, 9)]
+    assert len(patches) == 64
+    m = W.refine_uniform(base, patches[:60] + [((0, 0, 0, 1, 1, 1), 16), ((9, 9, 9, 10, 10, 10), 3),
+                                               ((0, 5, 8, 10, 6, 10), 2), ((4, 0, 0, 6, 10, 2), 2)])
+    run = {"sources": [{"type": "point", "pos": (0.31, 0.42, 0.47), "luminosity": 1.0, "n_packets": 6000},
+                       {"type": "thermal", "luminosity": 0.0, "n_packets": 6000}],
+           "cameras": [W.camera((0.3, 0.2, 0.93), (11, 11), (1.2, 1.2), center=(0.5, 0.5, 0.5))], "seed": 14,
+           "roulette_threshold": 1e-4, "roulette_survival": 0.1}
+    o = oracle_run(m, run, n_trace=12_000)
+    g = gpu_run(m, run, "fp64", n_trace=12_000)
+    assert trace_match_fraction(g["trace"], o["trace"], 1e-4) >= 0.999
+    assert np.linalg.norm(g["S"] - o["S"]) < 1e-7 * np.linalg.norm(o["S"])
+    Itot = o["images"][0][0].sum()
+    for e in range(4):
+        assert abs(g["images"][0][e].sum() - o["images"][0][e].sum()) < 1e-7 * Itot
+    # a 65th patch is refused
+    with pytest.raises(M.McrtError):
+        M.Model(W.refine_uniform(base, patches + [((0, 0, 9, 1, 1, 10), 2)]))
