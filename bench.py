@@ -251,23 +251,29 @@ def run_refined(M, W, torch):
     """Static mesh refinement: the flared disk on a 128^3 root grid with a 4x refined
     patch over the inner quarter in x, y and the middle eighth in z (1.05e6 patch cells,
     the fields at their own centres), star + thermal, 1e7 packets, 8 cameras at 256^2,
-    FP32 with the in-place tally (refined grids do not run in rounds)."""
+    FP32: in rounds with the tally kernel (the default, as on plain grids) and, for
+    comparison, with the in-place tally."""
     model = W.disk_refined(n=128, factor=4)
     run = W.disk_run(n_packets=10_000_000)
     m = M.Model(model)
-    M.launch(m, dict(run, seed=94), precision="fp32")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    st = M.launch(m, dict(run, seed=95), precision="fp32")
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
+    out = {}
+    for name, kw in (("rounds", {}), ("in_place", {"inline_tally": True})):
+        M.launch(m, dict(run, seed=94), precision="fp32", **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = M.launch(m, dict(run, seed=95), precision="fp32", **kw)
+        torch.cuda.synchronize()
+        out[name] = (st, time.perf_counter() - t0)
     S, _ = m.tallies(len(run["cameras"]))
     m.close()
+    st, wall = out["rounds"]
     nroot = 128 ** 3
     bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
     return {"workload": "flared disk, 128^3 root grid + 4x refined inner patch (1.05e6 cells), star + thermal, "
-                        "1e7 packets, 8 cameras at 256^2, in-place tally",
+                        "1e7 packets, 8 cameras at 256^2, table rounds (transport + tally kernel)",
             "value": st["events"] / wall, "unit": UNIT, "events": st["events"], "seconds": wall,
+            "rounds": st["wave_iterations"], "kernel_ms": {"transport": st["ms_transport"], "tally": st["ms_tally"]},
+            "in_place_tally_value": out["in_place"][0]["events"] / out["in_place"][1],
             "patch_tally_share": float(np.abs(S[nroot:]).sum() / max(np.abs(S).sum(), 1e-300)),
             "energy_balance_rel": abs(bal - st["emitted_energy"]) / st["emitted_energy"]}
 

@@ -213,8 +213,9 @@ typedef struct {
  * zeros for covered root cells, whose root values are not used.  Packets descend into
  * a patch on entering a covered root cell and return to the root cell beyond the
  * patch face they leave through; step 2 marches through the same cells.  Refined
- * models take Rayleigh, table or dipole optics in single-model launches (in-place
- * tally); batched, surrogate and no-allocation launches refuse them.
+ * models take Rayleigh, table or dipole optics in single-model launches (FP32 table
+ * launches run in rounds with the tally kernel, as on plain grids); batched, surrogate
+ * and no-allocation launches refuse them.
  * Errors: as mcrt_create_grid, and MCRT_E_INVAL for overlapping or out-of-range boxes,
  * bad factors, or field/emission arrays present on one level only.
  */

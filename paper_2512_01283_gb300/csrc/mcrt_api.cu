@@ -696,9 +696,8 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
     if (sur && !ctx->sur_set) return fail(ctx, MCRT_E_STATE, "mcrt_launch_packets: no surrogate attached (mcrt_set_surrogate)");
     if (sur && ctx->g.n_patches > 0)
         return fail(ctx, MCRT_E_INVAL, "mcrt_launch_packets: refined grids take table, Rayleigh or dipole optics");
-    // FP32 table launches tally in a kernel of their own unless asked not to (refined grids:
-    // in place, the composite walk lives in the single-model kernels)
-    const bool deferred_table = !sur && ctx->g.n_patches == 0 && ctx->t.model == MCRT_SCAT_TABLE && d->precision == MCRT_FP32 &&
+    // FP32 table launches tally in a kernel of their own unless asked not to
+    const bool deferred_table = !sur && ctx->t.model == MCRT_SCAT_TABLE && d->precision == MCRT_FP32 &&
                                 d->n_cameras > 0 && !(d->time_budget_s > 0.0) && !(d->flags & MCRT_FLAG_INLINE_TALLY);
     const bool rounds = sur || deferred_table;
     TransportParams P{};
@@ -827,7 +826,7 @@ static mcrt_status launch_one(mcrt_ctx* ctx, const mcrt_launch_desc* d, mcrt_sta
             // the transport leaves room on every SM for the tally kernels of the round before
             P.sur.deferred = kScatTableDeferred;
             const size_t tsm = transport_smem_bytes(P, MCRT_FP32, 128);
-            const int bmax = transport_max_blocks_per_sm(MCRT_FP32, kScatTableDeferred, false, 128, tsm);
+            const int bmax = transport_max_blocks_per_sm(MCRT_FP32, kScatTableDeferred, false, 128, tsm, P.g.n_patches > 0);
             int tbps = d->blocks_per_sm > 0 ? d->blocks_per_sm : (bmax > 2 ? bmax - 2 : 1);
             if (tbps > bmax) tbps = bmax;
             const int abps = d->tally_blocks_per_sm;

@@ -234,7 +234,7 @@ __device__ __forceinline__ void apply_plane_full(const PlaneRot<float>& r, float
 }
 
 // A packet waiting between kernels: 8 float4 (128 bytes); its cell record is
-// reloaded from (ix, iy, iz) when it resumes.  parked = 1: stopped inside its flight
+// reloaded from (ix, iy, iz) and its level (root grid or patch) when it resumes.  parked = 1: stopped inside its flight
 // (nothing to do before it resumes), 0: waiting for its scattering.
 __device__ __forceinline__ void store_state(float4* d, const Packet<float>& pk, unsigned parked = 0u) {
     const unsigned long long pid = (unsigned long long)pk.pid;
@@ -249,7 +249,7 @@ __device__ __forceinline__ void store_state(float4* d, const Packet<float>& pk, 
                        __uint_as_float(pk.n_tally));
     d[6] = make_float4(__uint_as_float(pk.n_abs), __uint_as_float(pk.trials), __int_as_float(pk.ix),
                        __int_as_float(pk.iy));
-    d[7] = make_float4(__int_as_float(pk.iz), __uint_as_float(parked), 0.f, 0.f);
+    d[7] = make_float4(__int_as_float(pk.iz), __uint_as_float(parked), __int_as_float(pk.lvl), 0.f);
 }
 
 __device__ __forceinline__ void load_state(const float4* d, Packet<float>& pk) {
@@ -280,6 +280,7 @@ __device__ __forceinline__ void load_state(const float4* d, Packet<float>& pk) {
     pk.ix = __float_as_int(h.z);
     pk.iy = __float_as_int(h.w);
     pk.iz = __float_as_int(k.x);
+    pk.lvl = __float_as_int(k.z);
     pk.job = nullptr;
     pk.park = false;
     pk.pending = false;

@@ -437,9 +437,9 @@ __device__ __forceinline__ T exit_face(const J& job, const Packet<T>& pk, int& a
 __host__ __device__ constexpr bool table_optics(int scat) { return scat == MCRT_SCAT_TABLE || scat == kScatTableDeferred; }
 __host__ __device__ constexpr bool round_based(int scat) { return scat == kScatSurrogate || scat == kScatTableDeferred; }
 // instantiations that may walk composite grids (static mesh refinement): single-model
-// launches with the in-place tally; the kernels for grids with patches (R) are
-// instantiated apart, so that plain grids keep the plain walk
-__host__ __device__ constexpr bool walks_patches(int scat, bool batch) { return !batch && !round_based(scat); }
+// launches with the in-place tally or the table rounds; the kernels for grids with
+// patches (R) are instantiated apart, so that plain grids keep the plain walk
+__host__ __device__ constexpr bool walks_patches(int scat, bool batch) { return !batch && scat != kScatSurrogate; }
 
 // Round-based paths: the packet leaves this launch for the suspend buffer (one slot per
 // work item of the launch, so it cannot run over), waiting for its scattering
@@ -1028,15 +1028,23 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
                 // next round without a segment
                 const bool full = *reinterpret_cast<volatile unsigned long long*>(&P.sur.ctl->full) != 0ull;
                 pk.park = false;
+                const JobRef<T, false> jr{P, sm.kext, sm.mix};
                 if (idx < w_resume) {
                     if constexpr (sizeof(T) == 4) {
                         load_state(P.sur.resume + idx * kStateF4, pk);
-                        load_cell(JobRef<T, false>{P, sm.kext, sm.mix}, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
+                        if constexpr (!R) pk.lvl = 0;  // plain grids: the root level throughout
+                        if (R && pk.lvl > 0) {  // a cell of a refined patch
+                            const long long c = patch_cell(jr.patches()[pk.lvl - 1], pk.ix, pk.iy, pk.iz);
+                            pk.cq = __ldg(&jr.cells()[2 * c]);
+                            pk.cr = __ldg(&jr.cells()[2 * c + 1]);
+                        } else {
+                            load_cell(jr, pk.ix, pk.iy, pk.iz, pk.cq, pk.cr);
+                        }
                         alive = true;
                     }
                 } else if (idx - w_resume < w_new) {
                     const long long pid = P.pid_begin + (long long)(w_next + (idx - w_resume));
-                    alive = emit<T, false, false>(P, JobRef<T, false>{P, sm.kext, sm.mix}, pid, pk, bt);
+                    alive = emit<T, false, R>(P, jr, pid, pk, bt);
                     pk.park = false;
                 } else {
                     pool_done = true;
@@ -1141,14 +1149,16 @@ const void* transport_kernel(int precision, int model, bool batch, bool refined)
                                   : kernel_of_model<float>(model, batch, refined);
 }
 
-const void* transport_kernel_rounds(int model) {
-    return model == kScatSurrogate ? (const void*)k_transport<float, kScatSurrogate, false, false>
-                                   : (const void*)k_transport<float, kScatTableDeferred, false, false>;
+const void* transport_kernel_rounds(int model, bool refined) {
+    if (model == kScatSurrogate) return (const void*)k_transport<float, kScatSurrogate, false, false>;
+    return refined ? (const void*)k_transport<float, kScatTableDeferred, false, true>
+                   : (const void*)k_transport<float, kScatTableDeferred, false, false>;
 }
 
 int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem, bool refined) {
     int nb = 0;
-    const void* k = round_based(model) ? transport_kernel_rounds(model) : transport_kernel(precision, model, batch, refined);
+    const void* k = round_based(model) ? transport_kernel_rounds(model, refined)
+                                        : transport_kernel(precision, model, batch, refined);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess) return 1;
     return nb > 0 ? nb : 1;
@@ -1156,7 +1166,7 @@ int transport_max_blocks_per_sm(int precision, int model, bool batch, int block,
 
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s) {
     const size_t smem = transport_smem_bytes(p, precision, block);
-    const void* k = p.sur.deferred ? transport_kernel_rounds(p.sur.deferred)
+    const void* k = p.sur.deferred ? transport_kernel_rounds(p.sur.deferred, p.g.n_patches > 0)
                                    : transport_kernel(precision, p.t.model, p.jobs != nullptr, p.g.n_patches > 0);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -692,7 +692,7 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
     const unsigned long long total = (unsigned long long)(p.pid_end - p.pid_begin);
     const int block = 128;
     const size_t tsmem = transport_smem_bytes(p, MCRT_FP32, block);
-    const int bps = transport_max_blocks_per_sm(MCRT_FP32, model, false, block, tsmem);
+    const int bps = transport_max_blocks_per_sm(MCRT_FP32, model, false, block, tsmem, p.g.n_patches > 0);
     const int tgrid = n_sm * bps;
     float4* const bufs[2] = {p_in.sur.resume, p_in.sur.suspend};
     cudaEvent_t e0 = nullptr, e1 = nullptr, ek[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -26,10 +26,10 @@ def _gpu():
     M.lib()
 
 
-def gpu_run(model, run, precision, n_trace=0):
+def gpu_run(model, run, precision, n_trace=0, **kw):
     m = M.Model(model)
     trace = np.zeros((max(1, n_trace), 16))
-    st = M.launch(m, run, precision=precision, trace=trace if n_trace else None, n_trace=n_trace)
+    st = M.launch(m, run, precision=precision, trace=trace if n_trace else None, n_trace=n_trace, **kw)
     n_cam = len(run.get("cameras", []))
     S, A = m.tallies(n_cam)
     imgs = []
@@ -82,6 +82,34 @@ def test_refined_disk_parity(refined_disk, prec):
         for e in range(4):
             assert abs(g["images"][k][e].sum() - o["images"][k][e].sum()) < max(tol, 1e-9) * Itot, (k, e)
     assert g["stats"]["emitted_energy"] == pytest.approx(o["stats"]["emitted_energy"], rel=1e-6)
+
+
+def test_refined_table_rounds_equal_the_in_place_tally():
+    """FP32 table launches on a refined grid run in rounds like plain grids: the same
+    packets and tallies as the in-place tally, over several rounds between which packets
+    wait, some of them inside patches."""
+    model = W.disk_refined(n=48, factor=3)
+    run = W.disk_run(n_packets=4_000_000, n_cam=4, npix=16)
+    ref = gpu_run(model, run, "fp32", n_trace=200_000, inline_tally=True)
+    assert ref["stats"]["wave_iterations"] == 0
+    g = gpu_run(model, run, "fp32", n_trace=200_000)
+    assert g["stats"]["wave_iterations"] >= 2  # packets parked and resumed
+    assert g["stats"]["events"] == ref["stats"]["events"]
+    assert trace_match_fraction(g["trace"], ref["trace"], 1e-6) >= 0.999
+    assert np.linalg.norm(g["S"] - ref["S"]) < 1e-6 * np.linalg.norm(ref["S"])
+    assert np.abs(g["S"][48 ** 3:]).sum() > 0.05 * np.abs(g["S"]).sum()
+    assert np.linalg.norm(g["absorbed"] - ref["absorbed"]) < 1e-6 * np.linalg.norm(ref["absorbed"])
+    for k in range(4):
+        assert np.linalg.norm(g["images"][k] - ref["images"][k]) < 1e-6 * np.linalg.norm(ref["images"][k])
+    # the packet ids split over three launches that add to the same tallies
+    m = M.Model(model)
+    M.launch(m, dict(run, pid_end=1_300_001), precision="fp32")
+    M.launch(m, dict(run, pid_begin=1_300_001, pid_end=2_633_333), precision="fp32", accumulate=1)
+    M.launch(m, dict(run, pid_begin=2_633_333), precision="fp32", accumulate=1)
+    S, A = m.tallies(4)
+    m.close()
+    assert np.linalg.norm(S - ref["S"]) < 1e-6 * np.linalg.norm(ref["S"])
+    assert np.linalg.norm(A - ref["absorbed"]) < 1e-6 * np.linalg.norm(ref["absorbed"])
 
 
 def test_refined_copy_equals_the_plain_grid_on_gpu():
