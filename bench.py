@@ -97,23 +97,38 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel, units_per_launch):
-    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu summary of
-    the disk workload: bytes per unit (segment of the transport kernel, record of the
-    tally kernel) of the captured small launch times this launch's units; None when
-    the kernel sources changed since the capture."""
+def profiled_fields():
+    """The key: value lines of the committed ncu summary of the disk workload's table
+    rounds, or {} when the kernel sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "rounds_disk192.md")
     if not os.path.exists(path):
-        return None
+        return {}
     fields = {}
     for line in open(path):
         if ":" in line and not line.startswith(("|", "#", "`")):
             k, v = line.split(":", 1)
             fields[k.strip()] = v.strip()
-    key = "%s_traffic_bytes_per_unit" % kernel
-    if fields.get("kernel_source_sha") != kernel_source_sha() or key not in fields:
+    return fields if fields.get("kernel_source_sha") == kernel_source_sha() else {}
+
+
+def profiled_traffic(kernel, units_per_launch):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu summary of
+    the disk workload: bytes per unit (segment of the transport kernel, record of the
+    tally kernel) of the captured small launch times this launch's units; None when
+    the kernel sources changed since the capture."""
+    v = profiled_fields().get("%s_traffic_bytes_per_unit" % kernel)
+    return None if v is None else float(v) * units_per_launch
+
+
+def profiled_issue(kernel):
+    """Issue utilisation of `kernel` in the same capture (duration-weighted over its
+    launches): share of cycles an instruction issued, and active threads per warp
+    instruction; None when the kernel sources changed since the capture."""
+    f = profiled_fields()
+    a, t = f.get("%s_issue_active_pct" % kernel), f.get("%s_threads_per_warp_instruction" % kernel)
+    if a is None or t is None:
         return None
-    return float(fields[key]) * units_per_launch
+    return {"issue_active": float(a) / 100.0, "threads_per_warp_instruction": float(t), "source": "ncu"}
 
 
 class ClockSampler:
@@ -525,11 +540,13 @@ def main():
         kernels["transport"] = {"kernel": "k_transport<float, table rounds>", "bound": "hbm",
                                 "achieved": b_t / (t_ms * 1e-3) / 1e9, "ms_per_step": t_ms / args.steps,
                                 "bytes_per_unit": "32 cell + 16 absorbed RMW (absorbing) + 32 record (tallying) per segment",
-                                "traffic": profiled_traffic("transport", seg / args.steps)}
+                                "traffic": profiled_traffic("transport", seg / args.steps),
+                                "issue": profiled_issue("transport")}
         kernels["tally"] = {"kernel": "k_tab_tally", "bound": "hbm", "achieved": b_a / (a_ms * 1e-3) / 1e9,
                             "ms_per_step": a_ms / args.steps,
                             "bytes_per_unit": "32 record + 64 x n_cam source RMW per tallying segment",
-                            "traffic": profiled_traffic("tally", tal / args.steps)}
+                            "traffic": profiled_traffic("tally", tal / args.steps),
+                            "issue": profiled_issue("tally")}
         for k in kernels.values():
             k.update({"peak": peak, "unit": "GB/s", "frac": k["achieved"] / peak, "peak_source": src})
         dom = kernels["transport"] if t_ms >= a_ms else kernels["tally"]
