@@ -326,6 +326,45 @@ def test_empty_and_degenerate_inputs():
     m.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_eight_sources_with_empty_and_single_packet_sources(prec):
+    """The most sources a launch takes (8): point, beam and thermal sources mixed, two
+    with no packets and one with a single packet, against the oracle (packet ids run
+    through the sources in order, each source's energy split over its own packets); a
+    ninth source is refused."""
+    model = W.dichroic_slab(n=8, tau=1.5, p=0.05, b_angle_deg=35.0, albedo=0.6, emissivity=1.0)
+    model["optics"] = W.table_optics(n_bins=2)
+    sources = [{"type": "point", "pos": (0.3, 0.6, 0.5), "luminosity": 2.0, "n_packets": 0},
+               {"type": "beam", "beam_dir": 1, "luminosity": 1.0, "n_packets": 1},
+               {"type": "point", "pos": (0.5, 0.5, 0.5), "luminosity": 0.7, "n_packets": 337},
+               {"type": "thermal", "luminosity": 0.0, "n_packets": 0},
+               {"type": "beam", "beam_dir": -1, "luminosity": 0.4, "n_packets": 95},
+               {"type": "point", "pos": (0.81, 0.22, 0.13), "luminosity": 1.3, "n_packets": 1000},
+               {"type": "thermal", "luminosity": 0.0, "n_packets": 640},
+               {"type": "point", "pos": (0.05, 0.95, 0.5), "luminosity": 0.1, "n_packets": 3}]
+    n = sum(s["n_packets"] for s in sources)
+    run = {"sources": sources, "cameras": [W.camera((0.3, 0.2, 0.93), (9, 9), (1.2, 1.2), center=(0.5, 0.5, 0.5))],
+           "seed": 21, "roulette_threshold": 1e-4, "roulette_survival": 0.1}
+    o = oracle_run(model, run, n_trace=n, n_threads=4)
+    g = gpu_run(model, run, prec, n_trace=n)
+    # every packet is born at the source its id falls in
+    assert np.array_equal(g["trace"][:, 14], o["trace"][:, 14])
+    assert np.array_equal(np.bincount(g["trace"][:, 14].astype(int), minlength=8),
+                          [s["n_packets"] for s in sources])
+    assert trace_match_fraction(g["trace"], o["trace"], 1e-4) >= (0.999 if prec == "fp64" else 0.99)
+    tol = 1e-7 if prec == "fp64" else 2e-3
+    assert np.linalg.norm(g["S"] - o["S"]) < tol * np.linalg.norm(o["S"])
+    assert g["stats"]["emitted_energy"] == pytest.approx(o["stats"]["emitted_energy"], rel=1e-6)
+    Itot = o["images"][0][0].sum()
+    for e in range(4):
+        assert abs(g["images"][0][e].sum() - o["images"][0][e].sum()) < max(tol, 1e-9) * Itot
+    m = M.Model(model)
+    with pytest.raises(M.McrtError) as err:
+        M.launch(m, dict(run, sources=sources + [sources[2]]))
+    assert err.value.status == M.MCRT_E_INVAL
+    m.close()
+
+
 def test_ragged_packet_counts_and_resume():
     """Odd packet counts (not multiples of a warp) and a launch split into two id
     ranges with accumulate give the same tallies as one launch."""
