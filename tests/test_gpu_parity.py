@@ -365,6 +365,36 @@ def test_eight_sources_with_empty_and_single_packet_sources(prec):
     m.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step2_images_pixelwise_on_the_oracle_tallies(prec):
+    """Step 2 alone: the oracle's step-1 tallies set into the GPU model (mcrt_set_tallies)
+    and imaged by both sides, pixel by pixel.  Cameras with non-square pixel counts and
+    fields of view, one looking down -z (the pole of the Stokes basis), one along +y, one
+    oblique with an off-centre image centre, and a single pixel."""
+    model = W.disk(n=16)
+    cams = [W.camera((0, 0, -1), (7, 5), (1.7, 1.1)),
+            W.camera((0, 1, 0), (6, 9), (2.0, 1.3)),
+            W.camera((0.4, -0.3, 0.6), (11, 4), (1.4, 0.6), center=(0.1, -0.2, 0.05)),
+            W.camera((0.2, 0.7, -0.3), (1, 1), (0.3, 0.3))]
+    run = dict(W.disk_run(n_packets=6000), cameras=cams)
+    r = dict(run, n_threads=4)
+    o = O.transport(model, r)
+    m = M.Model(model)
+    M.launch(m, run, precision=prec)
+    m.set_tallies(np.ascontiguousarray(o["S"]), np.ascontiguousarray(o["absorbed"]))
+    # FP64: the cell record keeps the grain quaternion in FP32, which the oracle does not
+    tol = 1e-7 if prec == "fp64" else 2e-5
+    for k, c in enumerate(cams):
+        ref = O.image(model, r, o["S"], k)
+        out = np.zeros((4, c["npix"][1], c["npix"][0]))
+        m.image(k, out)
+        assert out.shape == ref.shape
+        scale = np.abs(ref[0]).max()
+        assert scale > 0
+        assert np.abs(out - ref).max() < tol * scale, (k, np.abs(out - ref).max() / scale)
+    m.close()
+
+
 def test_ragged_packet_counts_and_resume():
     """Odd packet counts (not multiples of a warp) and a launch split into two id
     ranges with accumulate give the same tallies as one launch."""
