@@ -365,18 +365,33 @@ def test_eight_sources_with_empty_and_single_packet_sources(prec):
     m.close()
 
 
+def _step2_model(kind):
+    if kind == "disk":
+        return W.disk(n=16), {}
+    if kind == "refined disk":
+        return W.disk_refined(n=16, factor=2), {}
+    # aligned dipole spheroids with a central star (imaging adds their own emission); 10
+    # cells, so that no pixel ray runs along a cell face, where the two precisions may
+    # image different neighbours
+    m = W.spheroid_sphere(n=10, tau=1.5, albedo=0.6, b=(0.6, 0.0, 0.8))
+    m["emissivity"] = np.full(m["kappa_abs"].shape, 0.3, dtype=np.float32)
+    return m, {"sources": [{"type": "point", "pos": (0.05, -0.02, 0.01), "luminosity": 1.0, "n_packets": 6000}]}
+
+
+@pytest.mark.parametrize("kind", ["disk", "refined disk", "spheroids"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_step2_images_pixelwise_on_the_oracle_tallies(prec):
+def test_step2_images_pixelwise_on_the_oracle_tallies(kind, prec):
     """Step 2 alone: the oracle's step-1 tallies set into the GPU model (mcrt_set_tallies)
-    and imaged by both sides, pixel by pixel.  Cameras with non-square pixel counts and
-    fields of view, one looking down -z (the pole of the Stokes basis), one along +y, one
-    oblique with an off-centre image centre, and a single pixel."""
-    model = W.disk(n=16)
+    and imaged by both sides, pixel by pixel, on a plain grid with tables, a composite
+    grid and aligned spheroids.  Cameras with non-square pixel counts and fields of
+    view, one looking down -z (the pole of the Stokes basis), one along +y, one oblique
+    with an off-centre image centre, and a single pixel."""
+    model, extra = _step2_model(kind)
     cams = [W.camera((0, 0, -1), (7, 5), (1.7, 1.1)),
             W.camera((0, 1, 0), (6, 9), (2.0, 1.3)),
             W.camera((0.4, -0.3, 0.6), (11, 4), (1.4, 0.6), center=(0.1, -0.2, 0.05)),
             W.camera((0.2, 0.7, -0.3), (1, 1), (0.3, 0.3))]
-    run = dict(W.disk_run(n_packets=6000), cameras=cams)
+    run = dict(W.disk_run(n_packets=6000), cameras=cams, **extra)
     r = dict(run, n_threads=4)
     o = O.transport(model, r)
     m = M.Model(model)
