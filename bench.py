@@ -323,7 +323,42 @@ def image_diff(a, b):
     return {"I_rel_l2": float(dI.mean()), "QU_rel_l2": float(dP.mean()), "I_total_rel_max": float(tot.max())}
 
 
-def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_value):
+def map_d2(a, b, ref):
+    """Mean over cameras of the squared L2 difference of the I maps and of the (Q, U)
+    maps of two image stacks [cam][4][ny][nx], relative to the I maps of `ref`."""
+    a, b, ref = np.asarray(a), np.asarray(b), np.asarray(ref)
+    nI = np.sum(ref[:, 0] ** 2, axis=(1, 2))
+    dI = np.sum((a[:, 0] - b[:, 0]) ** 2, axis=(1, 2)) / nI
+    dP = np.sum((a[:, 1:3] - b[:, 1:3]) ** 2, axis=(1, 2, 3)) / nI
+    return float(dI.mean()), float(dP.mean())
+
+
+def fixed_error(t1, t2, s1, s2, packets, table_s, sur_s, targets=(0.01, 0.02, 0.05)):
+    """Table and surrogate paths at a fixed map error.  From two seeds of each path at
+    `packets` packets: the Monte-Carlo variance of a map, sigma^2 = d^2(seed 1, seed 2) / 2,
+    for each path, and the surrogate's systematic difference from the table path,
+    b^2 = d^2(s1, t1) - sigma_s^2 - sigma_t^2.  A path's error after N packets against the
+    table method's expected map is then eps^2 = b^2 + sigma^2 packets / N, which gives the
+    packets, and with each path's measured time per packet the seconds, to reach eps."""
+    out = {"packets_per_run": packets, "seconds_per_run": {"table": table_s, "surrogate": sur_s}}
+    for name, k in (("I", 0), ("QU", 1)):
+        vt = map_d2(t1, t2, t1)[k] / 2.0
+        vs = map_d2(s1, s2, t1)[k] / 2.0
+        b2 = max(0.0, map_d2(s1, t1, t1)[k] - vs - vt)
+        rows = []
+        for eps in targets:
+            nt = packets * vt / eps ** 2
+            ns = packets * vs / (eps ** 2 - b2) if eps ** 2 > b2 else None
+            st = nt / packets * table_s
+            ss = ns / packets * sur_s if ns is not None else None
+            rows.append({"eps": eps, "table_packets": nt, "table_s": st, "surrogate_packets": ns, "surrogate_s": ss,
+                         "table_over_surrogate_time": st / ss if ss else None})
+        out[name] = {"sigma_table": vt ** 0.5, "sigma_surrogate": vs ** 0.5, "bias_surrogate": b2 ** 0.5,
+                     "targets": rows}
+    return out
+
+
+def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_value, table_step_s):
     """The same disk with the grain optics from the MLP surrogate: trained here on the
     tables (2e7 samples), table fallback above the error-map bound; throughput and
     the images' difference from the table path's, next to the table path's own
@@ -369,6 +404,11 @@ def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_v
         peak_bf16 = 1700.0
     other = np.zeros_like(imgs)
     table_step(2000 + args.steps, other)
+    # a second surrogate seed (untimed) for the fixed-error comparison
+    imgs2 = np.zeros_like(imgs)
+    M.launch(mdl, dict(run, seed=6000), precision="fp32", optics="surrogate")
+    for c in range(n_cam):
+        mdl.image(c, imgs2[c])
     out = {"workload": "flared disk %d^3 as the table line, grain optics from the MLP surrogate (7 -> 128 x 4 -> 20, "
                        "SiLU, BF16 weights, FP32 accumulation; tally on tcgen05, rejection trials on mma.sync), "
                        "trained on %.0e samples from the "
@@ -395,7 +435,10 @@ def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_v
                         "traffic": None, "peak_source": "measured bf16_tflops_sustained (kernel inside a long step)",
                         "flop_per_row": flop_row},
            "image_error": {"surrogate_vs_table": image_diff(imgs, table_imgs),
-                           "table_vs_table_other_seed": image_diff(other, table_imgs)},
+                           "table_vs_table_other_seed": image_diff(other, table_imgs),
+                           "surrogate_vs_surrogate_other_seed": image_diff(imgs2, imgs)},
+           "fixed_error": fixed_error(table_imgs, other, imgs, imgs2, args.packets, table_step_s,
+                                      wall / args.sur_steps),
            "gpu_launches_per_step": int(st["wave_iterations"]) * 4 + n_cam}
     sur.close()
     mdl.close()
@@ -629,7 +672,8 @@ def main():
             for k in range(n_cam):
                 mdl.image(k, out[k])
 
-        line["surrogate"] = run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, value)
+        line["surrogate"] = run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, value,
+                                          ms_max / args.steps * 1e-3)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
