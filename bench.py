@@ -526,12 +526,26 @@ def main():
             MG.combine_tallies(S_sum, A_sum, dist)
             m_.set_tallies(S_sum, A_sum)
 
+    my_cams = MG.rank_cameras(n_cam, rank, world)
+
+    def image_step(m_, host=None):
+        # step 2 split by camera over ranks, the images gathered (one all-reduce)
+        if world == 1:
+            for k in my_cams:
+                m_.image(k, host[k] if host is not None else imgs[k])
+            return
+        imgs.zero_()
+        for k in my_cams:
+            m_.image(k, imgs[k])
+        MG.combine_images(imgs, dist)
+        if host is not None:
+            host[:] = imgs.cpu().numpy()
+
     def step(seed):
         st = launch_share(mdl, seed, inline_tally=args.inline_tally, tally_blocks_per_sm=args.tally_bps,
                           blocks_per_sm=args.transport_bps)
         exchange(mdl)
-        for k in range(n_cam):
-            mdl.image(k, imgs[k])
+        image_step(mdl)
         return st
 
     for w in range(args.warmup):
@@ -610,7 +624,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args),
             "roofline": roofline, "roofline_kernels": kernels, "roofline_step": roofline_step,
-            "gpu_launches": int(sum(3 * s["wave_iterations"] if s["wave_iterations"] else 1 for s in stats) + args.steps * n_cam),
+            "gpu_launches": int(sum(3 * s["wave_iterations"] if s["wave_iterations"] else 1 for s in stats)
+                                + args.steps * len(my_cams)),
             "clocks": cs.summary(),
             "detail": {"events_per_step": events / args.steps, "segments_per_step": seg / args.steps,
                        "scatterings_per_step": sum(s["scatterings"] for s in stats) / args.steps,
@@ -635,15 +650,14 @@ def main():
             m2 = M.Model(model)
             st = launch_share(m2, 3000 + s)
             exchange(m2)
-            for k in range(n_cam):
-                m2.image(k, host_imgs[k])
+            image_step(m2, host_imgs)
             m2.close()
             torch.cuda.synchronize()
             e_t += time.perf_counter() - t0
             e_ev += st["events"]
         e_val = e_ev / e_t
         line["e2e"] = {"value": e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
-        line["gpu_launches_e2e_per_step"] = int(3 * st["wave_iterations"]) + n_cam + 5
+        line["gpu_launches_e2e_per_step"] = int(3 * st["wave_iterations"]) + len(my_cams) + 5
 
     if not args.no_sweep:
         line["batched_sweep"] = run_sweep(args, M, W, torch)

@@ -7,6 +7,8 @@ are split into `world` consecutive shares, so every rank runs the same mix of so
 A combined image needs one exchange: the FP64 source and absorbed tallies summed over
 ranks, after which step 2 (linear in the tallies, Sec. 2.3) runs on the summed
 tallies.  Summed tallies equal the single run's up to the order of the FP64 additions.
+Step 2 is then split by camera (each camera's image depends only on the summed
+tallies): rank r images cameras r, r + world, ..., and the images are gathered.
 
 Throughput over ranks (weak scaling): events summed, time the maximum over ranks.
 """
@@ -67,6 +69,21 @@ def combine_tallies(source, absorbed, dist=None):
         if t is not None:
             dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return source, absorbed
+
+
+def rank_cameras(n_cam: int, rank: int, world: int):
+    """Cameras that `rank` images in step 2: rank, rank + world, ..."""
+    return list(range(rank, n_cam, world))
+
+
+def combine_images(images, dist=None):
+    """Gather the images of all ranks in place (torch FP64 tensor [camera][4][ny][nx]
+    holding this rank's cameras and zeros elsewhere; one sum all-reduce).  Without a
+    process group: unchanged."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return images
+    dist.all_reduce(images, op=dist.ReduceOp.SUM)
+    return images
 
 
 def reduce_timing(ms: float, events: float, dist=None, device="cpu"):

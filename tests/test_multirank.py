@@ -1,8 +1,9 @@
 """Two ranks on the CPU (gloo): the packet sharding of the multi-GPU path and its one
 exchange.  Each rank transports its share of every source's packet ids with the
 oracle; after the all-reduce sum the tallies equal those of one run over all ids (to
-the order of FP64 additions), and the throughput reduction takes the slowest rank's
-time and all events.  No GPU is used."""
+the order of FP64 additions); step 2 split by camera and gathered gives the single
+run's images; and the throughput reduction takes the slowest rank's time and all
+events.  No GPU is used."""
 import os
 
 import numpy as np
@@ -40,9 +41,15 @@ def _worker(rank, world, port, q):
     S, A, ev = _oracle_ranges(model, run, MG.rank_ranges(run, rank, world))
     S, A = torch.tensor(S, dtype=torch.float64), torch.tensor(A, dtype=torch.float64)
     MG.combine_tallies(S, A, dist)
+    # step 2 split by camera, the images gathered
+    n_cam, npix = len(run["cameras"]), run["cameras"][0]["npix"]
+    imgs = torch.zeros((n_cam, 4, npix[1], npix[0]), dtype=torch.float64)
+    for k in MG.rank_cameras(n_cam, rank, world):
+        imgs[k] = torch.from_numpy(O.image(model, run, S.numpy(), k))
+    MG.combine_images(imgs, dist)
     ms, ev_all = MG.reduce_timing(10.0 + rank, ev, dist)
     if rank == 0:
-        q.put((S.numpy(), A.numpy(), ms, ev_all))
+        q.put((S.numpy(), A.numpy(), ms, ev_all, imgs.numpy()))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -56,7 +63,7 @@ def test_two_ranks_sum_to_the_single_run():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    S, A, ms, ev = q.get(timeout=300)
+    S, A, ms, ev, imgs = q.get(timeout=300)
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
@@ -66,6 +73,17 @@ def test_two_ranks_sum_to_the_single_run():
     assert np.allclose(A, o["absorbed"], rtol=1e-12, atol=1e-14 * np.abs(o["absorbed"]).max())
     assert ms == 11.0
     assert ev == o["stats"]["events"]
+    for k in range(len(run["cameras"])):
+        ref = O.image(model, run, o["S"], k)
+        assert np.allclose(imgs[k], ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
+def test_rank_cameras_cover_every_camera_once():
+    for n_cam in (0, 1, 3, 8, 16):
+        for world in (1, 2, 3, 4, 8):
+            got = sorted(k for r in range(world) for k in MG.rank_cameras(n_cam, r, world))
+            assert got == list(range(n_cam))
+            assert max(len(MG.rank_cameras(n_cam, r, world)) for r in range(world)) <= -(-n_cam // world)
 
 
 def test_rank_ranges_cover_every_source_once():
