@@ -86,14 +86,30 @@ def oracle_sample(model, run, seconds, n_threads, pid_offset=0):
     return events, wall, packets
 
 
-def kernel_source_sha():
+KERNEL_SOURCES = ("paper_2512_01283_gb300/csrc/mcrt_transport.cu", "paper_2512_01283_gb300/csrc/mcrt_device.cuh",
+                  "paper_2512_01283_gb300/csrc/mcrt_internal.h", "paper_2512_01283_gb300/csrc/mcrt_packet.cuh",
+                  "paper_2512_01283_gb300/csrc/mcrt_wave.cu")
+
+
+def code_only(text):
+    """C++ source without its comments and blank space, so that a comment edit does not
+    mark a profile of the same code as stale."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_source_sha(read=None):
+    """Hash of the code (comments and blank space dropped) of the table-round kernels'
+    sources; `read(path)` gives a file's text (default: the working tree)."""
     import hashlib
 
+    read = read or (lambda f: open(os.path.join(ROOT, f), encoding="utf-8").read())
     h = hashlib.sha256()
-    for f in ("paper_2512_01283_gb300/csrc/mcrt_transport.cu", "paper_2512_01283_gb300/csrc/mcrt_device.cuh",
-              "paper_2512_01283_gb300/csrc/mcrt_internal.h", "paper_2512_01283_gb300/csrc/mcrt_packet.cuh",
-              "paper_2512_01283_gb300/csrc/mcrt_wave.cu"):
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(code_only(read(f)).encode())
     return h.hexdigest()[:16]
 
 

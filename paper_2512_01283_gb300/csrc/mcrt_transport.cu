@@ -2,19 +2,19 @@
 // Sec. 2.2-2.3): persistent, thread-per-packet Monte-Carlo transport of Stokes
 // packets through the grid.
 //
-// Design (GB300): one warp holds 32 independent packets in registers; a lane whose
-// packet ends takes the next packet id from a global counter (one atomic per warp,
-// via a coalesced group) and is reborn in place, so warps stay full until the pool
-// drains.  Each loop iteration moves every live packet by one cell segment (DDA),
-// applies the in-cell analytic extinction (App. A) in the grain-meridian basis
-// (eq. rotation-angle / stokes-rotation, quaternions of eq. grain-quaternion), and
-// adds the segment's path integral through Z(Omega_cam; Omega_pp) to the FP64
-// source tally of every camera (eq. scat-disc-sum).  Lanes of a warp in the same
-// cell are found with __match_any_sync and their tally contributions are summed in
-// registers before one FP64 atomic per group.  Scattering events draw a new
-// direction by rejection sampling of the polarization-aware cross section.
-// Per-step arithmetic runs in T (float or double); the remaining scattering optical
-// depth and all tallies are FP64.
+// Design (GB300): one warp holds 32 independent packets in registers; lanes whose
+// packets end take the next packet ids from a global counter (one atomic per group
+// of lanes, via a coalesced group) and are reborn in place, so warps stay full until
+// the pool drains.  Each loop iteration moves every live packet by one cell segment
+// (DDA), applies the in-cell analytic extinction (App. A) in the grain-meridian basis
+// (eq. rotation-angle / stokes-rotation, quaternions of eq. grain-quaternion), adds
+// its absorbed energy with one FP64 atomic, and tallies the segment's path integral
+// through Z(Omega_cam; Omega_pp) for every camera (eq. scat-disc-sum): in place, one
+// FP64 bulk reduction of the cell's camera rows per lane, or (table rounds and the
+// surrogate) as a record that a tally kernel of its own adds.  Scatterings draw a new
+// direction by rejection sampling of the polarization-aware cross section, for the
+// warp's waiting lanes together.  Per-step arithmetic runs in T (float or double);
+// the remaining scattering optical depth and all tallies are FP64.
 #include <cooperative_groups.h>
 
 #include "mcrt_device.cuh"
