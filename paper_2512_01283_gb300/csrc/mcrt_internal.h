@@ -13,8 +13,8 @@ namespace mcrt {
 constexpr int kMaxPatches = 64;
 // Round-based paths: a warp reserves its tally-record slots in chunks of this many per
 // lane (one atomic per chunk instead of one per tallying step); 0 reserves per step.
-// On the 192^3 disk the table-round transport takes 910 ms per 1e8-packet step with 4
-// or 8, 924 ms with 16 and 1027 ms per step without chunks.
+// Measured when introduced, on the 192^3 disk: table-round transport 910 ms per 1e8-packet
+// step with 4 or 8, 924 ms with 16 and 1027 ms per step without chunks.
 #ifndef MCRT_REC_CHUNK
 #define MCRT_REC_CHUNK 4
 #endif

@@ -1,15 +1,18 @@
-// mcrt_wave.cu -- the surrogate path: step 1 of the two-step scheme (Sec. 2.2-2.3)
-// with the grain optics of Sec. 2.2 taken from the network of mcrt_mlp.cu instead of
-// the tables.
+// mcrt_wave.cu -- round-based step 1 of the two-step scheme (Sec. 2.2-2.3): the
+// surrogate path, with the grain optics of Sec. 2.2 taken from the network of
+// mcrt_mlp.cu instead of the tables, and the table rounds (FP32 table launches),
+// whose transport kernel scatters in place and leaves 32-byte records that
+// k_tab_tally adds for every camera with one FP64 bulk reduction per record.
 //
 // The network is a dense contraction, so it runs where the rows are dense: the
 // transport kernel (k_transport, surrogate instantiation) moves every packet in
 // flight to its next scattering, applies extinction, and leaves one 64-byte record
 // per tallying segment (direction, flight size, path integral, grain quaternion,
 // cell); at the scattering the packet itself waits in a 128-byte slot.  Then
-//  - k_sur_tally evaluates the network for every (record, camera) row, 16 rows per
-//    warp through mcrt_mlp_infer.cuh, and adds Z W to the FP64 source tally with
-//    TMA bulk reductions;
+//  - k_sur_tally_tc evaluates the network for every (record, camera) row on the
+//    5th-generation tensor cores (mcrt_mlp_tc.cuh, 128-row tiles), or k_sur_tally on
+//    mma.sync, 16 rows per warp (mcrt_mlp_infer.cuh), and adds Z W to the FP64
+//    source tally with TMA bulk reductions;
 //  - k_sur_scatter runs the rejection sampling of the waiting packets, each warp
 //    evaluating up to 16 trials at once (trials of the same packet in order, the
 //    first accepted one wins, which is exactly the sequential rule);
