@@ -476,6 +476,14 @@ mcrt_status mcrt_set_dust_dipole(mcrt_ctx* ctx, double eps_re, double eps_im, do
     t.dip.ca[1] = c[17];
     t.dip.cs[0] = c[18];
     t.dip.cs[1] = c[19];
+    t.dip.f_rho_re = (float)t.dip.rho_re;
+    t.dip.f_rho_im = (float)t.dip.rho_im;
+    t.dip.f_zn = (float)t.dip.zn;
+    t.dip.f_env = (float)t.dip.env;
+    for (int k = 0; k < 2; ++k) {
+        t.dip.f_ca[k] = (float)t.dip.ca[k];
+        t.dip.f_cs[k] = (float)t.dip.cs[k];
+    }
     ctx->t = t;
     ctx->tables_set = true;
     return MCRT_OK;

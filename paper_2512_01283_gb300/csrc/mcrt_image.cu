@@ -121,8 +121,8 @@ template <typename T> __global__ void __launch_bounds__(128) k_image(const __gri
                     const GrainFrame<T> f = grain_frame(P.g.cells[2 * c], Om, phc);
                     c2 = f.c2;
                     s2 = f.s2;
-                    const DipoleDev& dp = P.t.dip;
-                    dipole_K(T(dp.ca[0]), T(dp.ca[1]), T(dp.cs[0]), T(dp.cs[1]), T(r.x) / kext, omega, f.cos_tp, a1,
+                    const DipoleConst<T> dp = dipole_const<T>(P.t.dip);
+                    dipole_K(dp.ca0, dp.ca1, dp.cs0, dp.cs1, T(r.x) / kext, omega, f.cos_tp, a1,
                              a2, s11, s12);
                     a3 = T(0);
                 } else if (P.t.k_iso) {

@@ -69,7 +69,22 @@ struct DipoleDev {
     double ca[2], cs[2];    // absorption and scattering cross sections over their orientation averages
     double zn;              // Zhat = zn M(J), 1/sr
     double env;             // bound of (Zhat X)_0 / I
+    // the same constants rounded once to FP32 on the host, for the FP32 kernels (no FP64
+    // conversion per segment on GB300's narrow FP64 pipe)
+    float f_rho_re, f_rho_im, f_ca[2], f_cs[2], f_zn, f_env;
 };
+
+// Dipole constants in the kernel's arithmetic type.
+template <typename T> struct DipoleConst {
+    T rho_re, rho_im, ca0, ca1, cs0, cs1, zn, env;
+};
+template <typename T> __host__ __device__ inline DipoleConst<T> dipole_const(const DipoleDev& d);
+template <> __host__ __device__ inline DipoleConst<float> dipole_const<float>(const DipoleDev& d) {
+    return DipoleConst<float>{d.f_rho_re, d.f_rho_im, d.f_ca[0], d.f_ca[1], d.f_cs[0], d.f_cs[1], d.f_zn, d.f_env};
+}
+template <> __host__ __device__ inline DipoleConst<double> dipole_const<double>(const DipoleDev& d) {
+    return DipoleConst<double>{d.rho_re, d.rho_im, d.ca[0], d.ca[1], d.cs[0], d.cs[1], d.zn, d.env};
+}
 
 struct TablesDev {
     int model;            // MCRT_SCAT_*

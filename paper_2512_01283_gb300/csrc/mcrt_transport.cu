@@ -341,7 +341,8 @@ __device__ bool emit(const TransportParams& P, const JobRef<T, B>& job, long lon
         const TablesDev& tb = job.t();
         T a1, a2, a3, s11 = omega, s12 = T(0);
         if (tb.model == MCRT_SCAT_DIPOLE) {
-            dipole_K(T(tb.dip.ca[0]), T(tb.dip.ca[1]), T(tb.dip.cs[0]), T(tb.dip.cs[1]), T(pk.cr.x) / kext, omega,
+            const DipoleConst<T> dc = dipole_const<T>(tb.dip);
+            dipole_K(dc.ca0, dc.ca1, dc.cs0, dc.cs1, T(pk.cr.x) / kext, omega,
                      f.cos_tp, a1, a2, s11, s12);
             a3 = T(0);
         } else {
@@ -515,8 +516,8 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             dip_f = grain_frame(pk.cq, n0, ph0);
             T S2 = (T(1) - dip_f.cos_tp) * (T(1) + dip_f.cos_tp);
             S2 = S2 > T(0) ? S2 : T(0);
-            const T c0 = T(tabs.dip.cs[0]);
-            ks_n = ks * (c0 + (T(tabs.dip.cs[1]) - c0) * T(0.5) * S2);
+            const DipoleConst<T> dc = dipole_const<T>(tabs.dip);
+            ks_n = ks * (dc.cs0 + (dc.cs1 - dc.cs0) * T(0.5) * S2);
         }
     }
     const T omega = kext > T(0) ? t_div(ks_n, kext) : T(0);
@@ -566,7 +567,8 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
             c2 = dip_f.c2;
             s2 = dip_f.s2;
             T s11;
-            dipole_K(T(tabs.dip.ca[0]), T(tabs.dip.ca[1]), T(tabs.dip.cs[0]), T(tabs.dip.cs[1]),
+            const DipoleConst<T> dc = dipole_const<T>(tabs.dip);
+            dipole_K(dc.ca0, dc.ca1, dc.cs0, dc.cs1,
                      t_div(T(pk.cr.x), kext), t_div(ks, kext), dip_f.cos_tp, a1, a2, s11, s12);
             a3 = T(0);
         } else if (tabs.k_iso) {
@@ -693,7 +695,8 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
                     load_camera(sm.cam + 12 * (k0 + k), Om, thc, phc);
                     T sv[4];
                     if constexpr (SCAT == MCRT_SCAT_DIPOLE) {
-                        dipole_apply(T(tabs.dip.rho_re), T(tabs.dip.rho_im), T(tabs.dip.zn), ax, th, ph, thc, phc, Wg,
+                        const DipoleConst<T> dc = dipole_const<T>(tabs.dip);
+                        dipole_apply(dc.rho_re, dc.rho_im, dc.zn, ax, th, ph, thc, phc, Wg,
                                      sv);
                     } else {
                         const T mu = dot(n, Om);
@@ -824,17 +827,17 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
         // aligned spheroid: isotropic proposal, envelope env I >= (Zhat X)_0; the new
         // Stokes vector is Zhat X (K_sca X)_0 / (s11 (Zhat X)_0), i.e. Zhat X renormalised
         // to I + (s12 / s11) Q with Q in the grain-meridian basis
-        const DipoleDev& dp = tabs.dip;
+        const DipoleConst<T> dp = dipole_const<T>(tabs.dip);
         const V3<T> ax = quat_to_lab(pk.cq, V3<T>{T(0), T(0), T(1)});
         const GrainFrame<T> f = grain_frame(pk.cq, n, ph);
         T Qg = pk.X1, Ug = pk.X2;
         rotate_qu(Qg, Ug, f.c2, f.s2);
         T S2 = (T(1) - f.cos_tp) * (T(1) + f.cos_tp);
         S2 = S2 > T(0) ? S2 : T(0);
-        const T hs = (T(dp.cs[1]) - T(dp.cs[0])) * T(0.5) * S2;
-        const T Iw = pk.X0 + t_div(hs, T(dp.cs[0]) + hs) * Qg;
+        const T hs = (dp.cs1 - dp.cs0) * T(0.5) * S2;
+        const T Iw = pk.X0 + t_div(hs, dp.cs0 + hs) * Qg;
         const T X[4] = {pk.X0, pk.X1, pk.X2, pk.X3};
-        const T rho_re = T(dp.rho_re), rho_im = T(dp.rho_im), zn = T(dp.zn), env = T(dp.env);
+        const T rho_re = dp.rho_re, rho_im = dp.rho_im, zn = dp.zn, env = dp.env;
         V3<T> n2;
         T Y[4];
         bool accepted = false;
