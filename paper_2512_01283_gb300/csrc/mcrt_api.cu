@@ -390,9 +390,10 @@ mcrt_status mcrt_set_dust_tables(mcrt_ctx* ctx, int32_t model, int32_t n_bins, i
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_alpha1, sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_mix, (size_t)nt * 2 * sizeof(float4));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_bins, (size_t)nb * nt * 2 * sizeof(float4));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_env_cdf, (size_t)nb * nint * sizeof(double));
+    // cumulative tables: FP64, then their FP32 copies
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_env_cdf, (size_t)nb * nint * (sizeof(double) + sizeof(float)));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_env, (size_t)nb * nint * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_bin_cdf, (size_t)nb * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_bin_cdf, (size_t)nb * (sizeof(double) + sizeof(float)));
     if (e != cudaSuccess) {
         free_tables(ctx);
         return fail(ctx, MCRT_E_NOMEM, "mcrt_set_dust_tables: %s", cudaGetErrorString(e));
@@ -427,6 +428,8 @@ mcrt_status mcrt_set_dust_tables(mcrt_ctx* ctx, int32_t model, int32_t n_bins, i
     t.env_cdf = ctx->d_env_cdf;
     t.env = ctx->d_env;
     t.bin_cdf = ctx->d_bin_cdf;
+    t.env_cdf_f = reinterpret_cast<const float*>(ctx->d_env_cdf + (size_t)nb * nint);
+    t.bin_cdf_f = reinterpret_cast<const float*>(ctx->d_bin_cdf + nb);
     t.kext = ctx->d_kext;
     t.alpha1_mean = a1m;
     ctx->tables_set = true;

@@ -214,7 +214,9 @@ __global__ void k_setup_cells(const float* __restrict__ ka, const float* __restr
 
 // Table preparation (one block): mixture matrix for the tally, per-bin rows,
 // piecewise-constant envelope of P11 with its normalised cumulative weights,
-// cumulative bin weights, extinction rows and the sphere average of alpha1.
+// cumulative bin weights, extinction rows and the sphere average of alpha1.  The two
+// cumulative tables are followed by their FP32 copies (env_cdf holds n_bins (n_theta - 1)
+// doubles and as many floats, bin_cdf n_bins doubles and n_bins floats).
 __global__ void k_prepare_tables(int model, int n_bins, int n_theta, int n_ktheta, const float* __restrict__ mueller,
                                  const float* __restrict__ bin_weight, const float* __restrict__ kext,
                                  float4* __restrict__ mix, float4* __restrict__ bins, double* __restrict__ env_cdf,
@@ -270,6 +272,12 @@ __global__ void k_prepare_tables(int model, int n_bins, int n_theta, int n_kthet
         }
         for (int j = 0; j < nint; ++j) env_cdf[(size_t)k * nint + j] /= tot;
     }
+    // FP32 copies after the FP64 tables
+    __syncthreads();
+    float* env_cdf_f = reinterpret_cast<float*>(env_cdf + (size_t)n_bins * nint);
+    float* bin_cdf_f = reinterpret_cast<float*>(bin_cdf + n_bins);
+    for (int i = threadIdx.x; i < n_bins * nint; i += blockDim.x) env_cdf_f[i] = (float)env_cdf[i];
+    for (int k = threadIdx.x; k < n_bins; k += blockDim.x) bin_cdf_f[k] = (float)bin_cdf[k];
 }
 
 // Thermal emission weights kappa_ext (mean alpha1 - omega) B V and their inclusive

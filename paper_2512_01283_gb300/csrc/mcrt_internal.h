@@ -96,10 +96,19 @@ struct TablesDev {
     const double* env_cdf;  // [n_bins][n_theta-1] normalised cumulative envelope weights
     const float* env;     // [n_bins][n_theta-1] envelope max(P11_j, P11_j+1)
     const double* bin_cdf;  // [n_bins] normalised cumulative bin weights
+    // the two cumulative weights rounded to FP32 once (stored after the FP64 ones), for
+    // the FP32 kernels, which compare in FP32: no FP64 conversion per search step
+    const float* env_cdf_f;
+    const float* bin_cdf_f;
     const float4* kext;   // [n_ktheta] (alpha1, alpha2, alpha3, 0)
     double alpha1_mean;
     DipoleDev dip;        // MCRT_SCAT_DIPOLE constants
 };
+
+// Entry i of a cumulative weight table in the kernel's arithmetic type.
+template <typename T> __device__ __forceinline__ T cdf_at(const double* d, const float* f, size_t i);
+template <> __device__ __forceinline__ float cdf_at<float>(const double*, const float* f, size_t i) { return f[i]; }
+template <> __device__ __forceinline__ double cdf_at<double>(const double* d, const float*, size_t i) { return d[i]; }
 
 struct SourceDev {
     int type, beam_dir;

@@ -36,9 +36,9 @@ constexpr size_t kOffCells = 0;
 constexpr size_t kOffMix = kOffCells + round256((size_t)kMaxCells * 2 * sizeof(float4));
 constexpr size_t kOffBins = kOffMix + round256((size_t)kMaxTheta * 2 * sizeof(float4));
 constexpr size_t kOffEnvCdf = kOffBins + round256((size_t)kMaxBins * kMaxTheta * 2 * sizeof(float4));
-constexpr size_t kOffEnv = kOffEnvCdf + round256((size_t)kMaxBins * (kMaxTheta - 1) * sizeof(double));
+constexpr size_t kOffEnv = kOffEnvCdf + round256((size_t)kMaxBins * (kMaxTheta - 1) * (sizeof(double) + sizeof(float)));
 constexpr size_t kOffBinCdf = kOffEnv + round256((size_t)kMaxBins * (kMaxTheta - 1) * sizeof(float));
-constexpr size_t kOffKext = kOffBinCdf + round256((size_t)kMaxBins * sizeof(double));
+constexpr size_t kOffKext = kOffBinCdf + round256((size_t)kMaxBins * (sizeof(double) + sizeof(float)));
 constexpr size_t kOffWork = kOffKext + round256((size_t)kMaxTheta * sizeof(float4));
 // work area: packet counter (8 B), 16 totals (128 B), status (8 B), alpha1 mean (8 B),
 // invalid-input flag (8 B)
@@ -202,6 +202,9 @@ extern "C" mcrt_status mcrt_launch_packets_noalloc(const mcrt_noalloc_problem* p
     t.env_cdf = reinterpret_cast<const double*>(base + kOffEnvCdf);
     t.env = reinterpret_cast<const float*>(base + kOffEnv);
     t.bin_cdf = reinterpret_cast<const double*>(base + kOffBinCdf);
+    // the FP32 copies follow the FP64 tables (as k_prepare_tables writes them)
+    t.env_cdf_f = reinterpret_cast<const float*>(t.env_cdf + (size_t)t.n_bins * (t.n_theta > 1 ? t.n_theta - 1 : 0));
+    t.bin_cdf_f = reinterpret_cast<const float*>(t.bin_cdf + t.n_bins);
     t.kext = reinterpret_cast<const float4*>(base + kOffKext);
     t.alpha1_mean = 1.0;  // used by thermal sources only, which are not accepted here
 

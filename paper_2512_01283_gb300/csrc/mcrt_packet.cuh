@@ -189,7 +189,7 @@ template <typename T> __device__ __forceinline__ T flight_size(const TablesDev& 
     if (t.n_bins <= 1) return T(0);
     int bin = t.n_bins - 1;
     for (int k = 0; k < t.n_bins; ++k)
-        if (u < T(t.bin_cdf[k])) {
+        if (u < cdf_at<T>(t.bin_cdf, t.bin_cdf_f, k)) {
             bin = k;
             break;
         }

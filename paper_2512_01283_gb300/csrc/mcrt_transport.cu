@@ -876,7 +876,7 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
     if (table_optics(SCAT)) {
         bin = tabs.n_bins - 1;
         for (int k = 0; k < tabs.n_bins; ++k)
-            if (us.c < T(tabs.bin_cdf[k])) {
+            if (us.c < cdf_at<T>(tabs.bin_cdf, tabs.bin_cdf_f, k)) {
                 bin = k;
                 break;
             }
@@ -899,11 +899,11 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
         } else {
             // interval j of the piecewise-constant envelope of P11: first j with u < cdf_j
             const int nint = tabs.n_theta - 1;
-            const double* cdf = tabs.env_cdf + (size_t)bin * nint;
+            const size_t c0i = (size_t)bin * nint;
             int lo = 0, hi = nint - 1;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (ut.a < T(cdf[mid]))
+                if (ut.a < cdf_at<T>(tabs.env_cdf, tabs.env_cdf_f, c0i + mid))
                     hi = mid;
                 else
                     lo = mid + 1;

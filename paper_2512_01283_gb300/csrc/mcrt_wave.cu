@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kWaveBlock, 1) k_sur_scatter(const __grid_cons
             if (live) {
                 bin = tabs.n_bins - 1;
                 for (int k = 0; k < tabs.n_bins; ++k)
-                    if (us.c < (float)tabs.bin_cdf[k]) {
+                    if (us.c < tabs.bin_cdf_f[k]) {
                         bin = k;
                         break;
                     }
@@ -461,11 +461,11 @@ __global__ void __launch_bounds__(kWaveBlock, 1) k_sur_scatter(const __grid_cons
                     const Draw4<float> ut = draw4<float>(opid, onsca, 1u + (unsigned)ot, P.seed, P.stream);
                     // interval of the piecewise-constant envelope of bin obin, then the
                     // angle inside it and the azimuth (as the table path)
-                    const double* cdf = tabs.env_cdf + (size_t)obin * nint;
+                    const float* cdf = tabs.env_cdf_f + (size_t)obin * nint;
                     int lo = 0, hi = nint - 1;
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
-                        if (ut.a < (float)cdf[mid])
+                        if (ut.a < cdf[mid])
                             hi = mid;
                         else
                             lo = mid + 1;
