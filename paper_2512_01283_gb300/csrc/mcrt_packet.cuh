@@ -120,18 +120,10 @@ __device__ __forceinline__ double widen(float f) {
     return __hiloint2double((int)hi, (int)lo);
 }
 
-// The remaining optical depth is an FP64 running sum (FP32 steps widened exactly).  Both
-// it and a segment's optical depth are zeros or positive and not NaN, and such IEEE
-// doubles, once the sign bit is cleared (a distance can be -0, which equals +0), order as
-// their bit patterns do as unsigned integers: the FP32 kernels compare them with one
-// 64-bit integer comparison (off GB300's narrow FP64 pipe), the same decision.
-__device__ __forceinline__ void tau_set(double& t, float v) { t = widen(v); }
+// The remaining optical depth is an FP64 running sum (FP32 steps widened exactly).
+__device__ __forceinline__ void tau_set(double& t, float v) { t = (double)v; }
 __device__ __forceinline__ void tau_set(double& t, double v) { t = v; }
-__device__ __forceinline__ bool tau_below(double t, float d) {
-    constexpr unsigned long long kMag = 0x7fffffffffffffffull;
-    return ((unsigned long long)__double_as_longlong(t) & kMag) <
-           ((unsigned long long)__double_as_longlong(widen(d)) & kMag);
-}
+__device__ __forceinline__ bool tau_below(double t, float d) { return t < widen(d); }
 __device__ __forceinline__ bool tau_below(double t, double d) { return t < d; }
 __device__ __forceinline__ void tau_sub(double& t, float d) { t -= widen(d); }
 __device__ __forceinline__ void tau_sub(double& t, double d) { t -= d; }
