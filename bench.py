@@ -581,8 +581,12 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     stats = []
-    clocks_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
-    os.makedirs(os.path.dirname(clocks_path), exist_ok=True)
+    # the raw nvidia-smi samples (their summary goes into the JSON line); MCRT_CLOCKS_DIR keeps them
+    import tempfile
+
+    clocks_dir = os.environ.get("MCRT_CLOCKS_DIR", tempfile.gettempdir())
+    clocks_path = os.path.join(clocks_dir, "bench_clocks_rank%d.csv" % rank)
+    os.makedirs(clocks_dir, exist_ok=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(clocks_path) as cs:
         e0.record()
