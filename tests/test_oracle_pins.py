@@ -267,6 +267,34 @@ def test_inclined_disk_polarization(incl_deg):
     assert abs(tot[2] / tot[0]) < 1e-13
 
 
+def test_single_scattering_tally_of_a_thin_slab():
+    """eq. (scat-disc-sum) in the single-scattering limit: an unpolarized beam along +z
+    through a thin Rayleigh slab (tau = 1e-3, albedo 1, no dichroism).  Between events
+    the packet is attenuated by K - omega 1 = 0 and leaves the beam where it scatters,
+    so the tally of a z-layer of thickness dz starting at z is, in expectation,
+    L Z(Omega_c; z-hat) (1, 0, 0, 0) (e^{-kappa z} - e^{-kappa (z + dz)}) / kappa, with
+    Z the Rayleigh matrix 3/(16 pi) (1 + mu^2, mu^2 - 1) at mu = Omega_c . z-hat; scattered
+    packets add O(tau).  With Omega_c in the x-z plane the camera's theta-hat lies in the
+    scattering plane, so the light, polarized across it, has Q = Z21 I < 0 and U = V = 0."""
+    n, tau = 6, 1e-3
+    model = W.dichroic_slab(n=n, tau=tau, p=0.0, albedo=1.0)
+    angles = [math.radians(d) for d in (30.0, 90.0, 150.0)]
+    cams = [W.camera((math.sin(a), 0.0, math.cos(a)), (2, 2), (1.0, 1.0)) for a in angles]
+    run = dict(W.beam_run(4000, cameras=cams), n_threads=4)
+    o = O.transport(model, run)
+    S = o["S"].reshape(n, n, n, len(cams), 4)  # [z][y][x][camera][I,Q,U,V]
+    dz = 1.0 / n
+    for c, a in enumerate(angles):
+        mu = math.cos(a)
+        z11, z21 = 3.0 / (16.0 * math.pi) * (1.0 + mu * mu), 3.0 / (16.0 * math.pi) * (mu * mu - 1.0)
+        for k in range(n):
+            w = (math.exp(-tau * k * dz) - math.exp(-tau * (k + 1) * dz)) / tau
+            layer = S[k].sum(axis=(0, 1))[c]
+            assert abs(layer[0] - z11 * w) < 3e-3 * z11 * w, (a, k, layer)
+            assert abs(layer[1] - z21 * w) < 3e-3 * z11 * w, (a, k, layer)
+            assert abs(layer[2]) < 3e-3 * z11 * w and abs(layer[3]) < 1e-12 * z11 * w, (a, k, layer)
+
+
 # ---------------------------------------------------------------------------------
 # Rejection sampling of the polarization-aware cross section
 # ---------------------------------------------------------------------------------
