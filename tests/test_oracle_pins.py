@@ -295,6 +295,31 @@ def test_single_scattering_tally_of_a_thin_slab():
             assert abs(layer[2]) < 3e-3 * z11 * w and abs(layer[3]) < 1e-12 * z11 * w, (a, k, layer)
 
 
+def test_thin_slab_image_carries_the_scattered_power():
+    """Step 2's normalisation end to end (S = omega / V * tally per unit extinction optical
+    depth, Sec. 2.3 and App. A): for the thin slab above, the image summed over pixels
+    times the pixel area is the power scattered per steradian toward the camera,
+    L omega (1 - e^{-tau}) Z11(Theta) for I and L omega (1 - e^{-tau}) Z21(Theta) for Q (the
+    beam decays with the extinction, a fraction omega of it scattered), up to the slab's
+    own extinction of the scattered light and multiple scattering, both O(tau).  Albedo
+    0.5, so that a dropped or doubled omega shows."""
+    n, tau, omega = 6, 1e-3, 0.5
+    model = W.dichroic_slab(n=n, tau=tau, p=0.0, albedo=omega)
+    for deg in (30.0, 90.0, 150.0):
+        a = math.radians(deg)
+        cam = W.camera((math.sin(a), 0.0, math.cos(a)), (90, 90), (3.0, 3.0), center=(0.5, 0.5, 0.5))
+        run = dict(W.beam_run(4000, cameras=[cam]), n_threads=4)
+        o = O.transport(model, run)
+        img = O.image(model, run, o["S"], 0)
+        apix = (3.0 / 90) ** 2
+        mu = math.cos(a)
+        z11, z21 = 3.0 / (16.0 * math.pi) * (1.0 + mu * mu), 3.0 / (16.0 * math.pi) * (mu * mu - 1.0)
+        scat = omega * (1.0 - math.exp(-tau))
+        assert img[0].sum() * apix == pytest.approx(scat * z11, rel=3e-3), deg
+        assert img[1].sum() * apix == pytest.approx(scat * z21, rel=4e-3), deg
+        assert abs(img[2].sum() * apix) < 1e-3 * scat * z11 and np.all(img[3] == 0.0), deg
+
+
 # ---------------------------------------------------------------------------------
 # Rejection sampling of the polarization-aware cross section
 # ---------------------------------------------------------------------------------
