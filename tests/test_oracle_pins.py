@@ -295,6 +295,34 @@ def test_single_scattering_tally_of_a_thin_slab():
             assert abs(layer[2]) < 3e-3 * z11 * w and abs(layer[3]) < 1e-12 * z11 * w, (a, k, layer)
 
 
+def test_single_scattering_tally_with_a_bin_mixture():
+    """The same thin-slab limit with tabulated optics of three grain-size bins (Sec. 2.2,
+    Mueller elements linear in the scattering angle between tabulated angles): the layer
+    sums follow the weighted mixture sum_b w_b (P11_b, P12_b)(Theta) / sum_b w_b, the
+    tables interpolated here with numpy at angles between grid points."""
+    n, tau = 6, 1e-3
+    model = W.dichroic_slab(n=n, tau=tau, p=0.0, albedo=1.0)
+    model["optics"] = W.table_optics(n_bins=3, p_max=0.0)
+    tabs = np.asarray(model["optics"]["mueller"], dtype=np.float64)
+    w = np.asarray(model["optics"]["bin_weight"], dtype=np.float64)
+    w = w / w.sum()
+    grid = np.linspace(0.0, math.pi, tabs.shape[1])
+    angles = [math.radians(d) for d in (37.3, 90.4, 141.7)]
+    cams = [W.camera((math.sin(a), 0.0, math.cos(a)), (2, 2), (1.0, 1.0)) for a in angles]
+    run = dict(W.beam_run(4000, cameras=cams), n_threads=4)
+    o = O.transport(model, run)
+    S = o["S"].reshape(n, n, n, len(cams), 4)
+    dz = 1.0 / n
+    for c, a in enumerate(angles):
+        p11 = sum(w[b] * np.interp(a, grid, tabs[b, :, 0]) for b in range(3))
+        p12 = sum(w[b] * np.interp(a, grid, tabs[b, :, 1]) for b in range(3))
+        for k in range(n):
+            f = (math.exp(-tau * k * dz) - math.exp(-tau * (k + 1) * dz)) / tau
+            layer = S[k].sum(axis=(0, 1))[c]
+            assert abs(layer[0] - p11 * f) < 3e-3 * p11 * f, (a, k, layer)
+            assert abs(layer[1] - p12 * f) < 3e-3 * p11 * f, (a, k, layer)
+
+
 def test_thin_slab_image_carries_the_scattered_power():
     """Step 2's normalisation end to end (S = omega / V * tally per unit extinction optical
     depth, Sec. 2.3 and App. A): for the thin slab above, the image summed over pixels
