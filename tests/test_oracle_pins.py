@@ -554,6 +554,39 @@ def test_energy_balance_absorbing_disk_with_roulette():
     assert st["roulette_killed"] > 0 and st["scatterings"] > 0
 
 
+def test_point_and_beam_births_follow_their_definitions():
+    """Packet birth (Sec. 2.2): a point source emits unpolarized packets of energy L/N
+    from its position in isotropic directions (n_z and the azimuth uniform); a plane
+    beam enters uniformly over the face it starts on, along +z or -z.  Kolmogorov-
+    Smirnov distances against the uniform law (bound 1.63 / sqrt(N), the 1 % level)."""
+    from scipy import stats
+
+    model = W.dichroic_slab(n=4, tau=1.0, albedo=0.5)
+    N = 20000
+    crit = 1.63 / math.sqrt(N)
+    run = {"sources": [{"type": "point", "pos": (0.3, 0.6, 0.5), "luminosity": 2.0, "n_packets": N},
+                       {"type": "beam", "beam_dir": 1, "luminosity": 1.0, "n_packets": N},
+                       {"type": "beam", "beam_dir": -1, "luminosity": 3.0, "n_packets": N}], "seed": 17}
+    rows = O.emit(model, run, range(3 * N))
+    pt, up, down = rows[:N], rows[N:2 * N], rows[2 * N:]
+    assert np.all(pt[:, 12] == 0) and np.all(up[:, 12] == 1) and np.all(down[:, 12] == 2)
+    # point source: fixed position, energy L / N, unpolarized, isotropic
+    assert np.allclose(pt[:, 0:3], (0.3, 0.6, 0.5), atol=1e-15)
+    assert np.allclose(pt[:, 6], 2.0 / N, rtol=1e-14) and np.all(pt[:, 7:10] == 0.0)
+    assert np.allclose(np.linalg.norm(pt[:, 3:6], axis=1), 1.0, atol=1e-14)
+    assert stats.kstest((pt[:, 5] + 1) / 2, "uniform").statistic < crit
+    phi = (np.arctan2(pt[:, 4], pt[:, 3]) + math.pi) / (2 * math.pi)
+    assert stats.kstest(phi, "uniform").statistic < crit
+    # beams: on their face, uniform over it, along the axis, energy L / N
+    for b, z0, nz, L in ((up, 0.0, 1.0, 1.0), (down, 1.0, -1.0, 3.0)):
+        assert np.all(b[:, 2] == z0) and np.all(b[:, 5] == nz) and np.all(b[:, 3:5] == 0.0)
+        assert np.allclose(b[:, 6], L / N, rtol=1e-14) and np.all(b[:, 7:10] == 0.0)
+        for a in (0, 1):
+            assert stats.kstest(b[:, a], "uniform").statistic < crit
+    # the optical depth to the first scattering is exponential with mean 1
+    assert stats.kstest(pt[:, 10], "expon").statistic < crit
+
+
 def test_thermal_birth_polarization():
     """Thermal emission alpha_abs B: at birth the packet is polarized across the
     projected field with degree |alpha2| / (alpha1 - omega)."""
