@@ -30,6 +30,11 @@ Workloads (sizes as stated):
   disk_refined      the flared disk on a 128^3 root grid with one statically refined patch
                     (4x) over the inner quarter in x, y and the middle eighth in z, the
                     fields evaluated at the patch's own cell centres.
+  inclined_thin_disk  the inclined-disk scene of Sec. 3.1: a geometrically and optically
+                    thin annulus of Rayleigh grains (one cell layer |z| <= h, inner radius
+                    0.3, outer 1, radial optical depth 1e-3) around a central isotropic
+                    star, so that the light reaching the grains travels in the disk
+                    plane; field along x; cameras at inclinations 0..90 deg, 256^2.
   sweep             batched sweep: 32 models with edges drawn uniformly in 32..192, clumpy
                     log-normal density (sigma_ln = 1), mean optical depth log-uniform in
                     [1, 100], times 8 wavelengths 0.5-3 um (kappa ~ lambda^-1.5); central
@@ -125,6 +130,19 @@ def dipole_optics(eps=complex(2.30, 0.0228) ** 2, aspect=2.0, x=0.3):
 
 def rayleigh_optics():
     return {"model": "rayleigh", "kext": kext_isotropic()}
+
+
+def rayleigh_table(n_theta=N_THETA):
+    """The dipole-sphere (Rayleigh) scattering matrix as a one-bin table [1][n_theta][6]:
+    P11 = P22 = 1 + c^2, P12 = c^2 - 1, P33 = P44 = 2c, P34 = 0, normalised like
+    ``synthetic_bins`` (theta-linear interpolant of P11 integrating to 1)."""
+    c = np.cos(np.linspace(0.0, math.pi, n_theta))
+    tab = np.zeros((1, n_theta, 6))
+    tab[0, :, 0] = tab[0, :, 2] = 1 + c * c
+    tab[0, :, 1] = c * c - 1
+    tab[0, :, 3] = tab[0, :, 5] = 2 * c
+    tab /= _interp_norm(tab[0, :, 0], n_theta)
+    return tab.astype(np.float32)
 
 
 def table_optics(n_bins=8, p_max=0.05):
@@ -362,6 +380,36 @@ def disk_run(n_packets=100_000_000, seed=2, n_cam=8, npix=256, star_luminosity=1
                         {"type": "thermal", "luminosity": 0.0, "n_packets": n_packets - n_star}],
             "cameras": inclination_cameras(n_cam, npix, 2.0), "seed": seed,
             "roulette_threshold": 1e-4, "roulette_survival": 0.1}
+
+
+def inclined_thin_disk(n=64, h=0.01, r_in=0.3, r_out=1.0, tau=1e-3, table=False):
+    """Thin annulus of Rayleigh grains (Sec. 3.1, inclined-disk test): grid
+    [-1,1]^2 x [-h,h] with one cell layer of n x n cells; kappa_sca = tau / (r_out - r_in)
+    where the cell centre's cylindrical radius lies in [r_in, r_out] (radial scattering
+    optical depth tau), albedo 1; field along +x (the paper puts the grain frame's axis
+    along x in this test).  ``table``: the Rayleigh matrix as a 181-angle table
+    (MCRT_SCAT_TABLE) instead of the closed form."""
+    lo, hi = (-1.0, -1.0, -float(h)), (1.0, 1.0, float(h))
+    x, y, z = cell_centres((1, n, n), lo, hi)
+    R = np.sqrt(x * x + y * y) + 0.0 * z
+    ks = np.where((R >= r_in) & (R <= r_out), tau / (r_out - r_in), 0.0).astype(np.float32)
+    bf = np.zeros(ks.shape + (3,), dtype=np.float32)
+    bf[..., 0] = 1.0
+    optics = rayleigh_optics()
+    if table:
+        optics = {"model": "table", "mueller": rayleigh_table(), "bin_weight": np.ones(1, np.float32),
+                  "kext": kext_isotropic()}
+    return {"lo": lo, "hi": hi, "kappa_abs": np.zeros_like(ks), "kappa_sca": ks, "bfield": bf, "emissivity": None,
+            "optics": optics, "geometry": {"h": float(h), "r_in": float(r_in), "r_out": float(r_out)}}
+
+
+def thin_disk_run(n_packets, seed=6, npix=256, incl_deg=(0, 15, 30, 45, 60, 75, 90)):
+    """Central isotropic star (luminosity 1) and cameras at inclinations ``incl_deg``
+    from the disk axis toward +x, FOV 2 x 2; no roulette (albedo 1)."""
+    cams = [camera((math.sin(math.radians(a)), 0.0, math.cos(math.radians(a))), (npix, npix), (2.0, 2.0))
+            for a in incl_deg]
+    return {"sources": [{"type": "point", "pos": (0.0, 0.0, 0.0), "luminosity": 1.0, "n_packets": int(n_packets)}],
+            "cameras": cams, "seed": seed, "roulette_threshold": 0.0, "roulette_survival": 0.1}
 
 
 def clumpy_density(n, seed, smooth_cells=2.0):

@@ -627,6 +627,164 @@ def test_thermal_cell_selection_follows_weights():
     assert abs(L - 4 * math.pi * em.sum() * f32(1.0) * 0.125) < 1e-9
 
 
+# ---------------------------------------------------------------------------------
+# App. A and eq. polarized-rt with extinction elements that depend on theta'
+# ---------------------------------------------------------------------------------
+# alpha1..3 on 5 nodes theta'_j = 45 j deg; FP32 as the ABI takes them
+KEXT5 = np.array([[1.0, 0.0, 0.0], [1.3, -0.1, 0.02], [2.0, -0.3, 0.05], [1.5, -0.05, 0.01], [1.1, 0.0, 0.0]],
+                 dtype=np.float32)
+NODES5 = np.radians([0.0, 45.0, 90.0, 135.0, 180.0])
+
+
+def alpha_by_hand(thetap):
+    """alpha1..3 at theta', linear in theta' between the two nodes around it."""
+    return np.array([np.interp(thetap, NODES5, KEXT5[:, e].astype(np.float64)) for e in range(3)])
+
+
+def aligned_slab(tau, b, albedo=0.0, emissivity=None, n=4):
+    """[0,1]^3 slab, kappa_ext = tau, uniform field b, the 5-node extinction table."""
+    shape = (n, n, n)
+    kext = np.full(shape, tau, dtype=np.float32)
+    bf = np.zeros(shape + (3,), dtype=np.float32)
+    bf[...] = np.asarray(b, dtype=np.float32)
+    em = None if emissivity is None else np.full(shape, emissivity, dtype=np.float32)
+    return {"lo": (0.0, 0.0, 0.0), "hi": (1.0, 1.0, 1.0), "kappa_abs": (kext * (1 - albedo)).astype(np.float32),
+            "kappa_sca": (kext * albedo).astype(np.float32), "bfield": bf, "emissivity": em,
+            "optics": {"model": "rayleigh", "kext": KEXT5}}
+
+
+@pytest.mark.parametrize("theta_b,phi_b", [(30.0, 0.0), (30.0, 30.0), (100.0, -70.0), (160.0, 10.0)])
+def test_dichroic_slab_with_angle_dependent_extinction(theta_b, phi_b):
+    """App. A: an unpolarized beam along +z through a uniformly aligned slab with the
+    field at polar angle theta_B (so theta' = theta_B for every packet) leaves with
+    I/I0 = e^(-alpha1 tau) cosh(alpha2 tau) and degree tanh(|alpha2| tau) along the
+    projected field, alpha_i interpolated by hand linearly in theta' between the
+    table's nodes.  Interpolating in cos theta', or taking theta' from the lab polar
+    angle of n, gives other alphas."""
+    tau = 2.0
+    tb, pb = math.radians(theta_b), math.radians(phi_b)
+    b32 = np.array([math.sin(tb) * math.cos(pb), math.sin(tb) * math.sin(pb), math.cos(tb)], dtype=np.float32)
+    b = b32.astype(np.float64)
+    thetap = math.atan2(math.hypot(b[0], b[1]), b[2])
+    a1, a2, _ = alpha_by_hand(thetap)
+    t = f32(tau)
+    model = aligned_slab(tau, b32)
+    run = W.beam_run(4, seed=1)
+    run["n_trace"] = 4
+    out = O.transport(model, run)
+    tr = out["trace"]
+    I = tr[:, 0] / tr[:, 13]
+    ref_I = math.exp(-a1 * t) * math.cosh(a2 * t)
+    assert np.allclose(I, ref_I, rtol=1e-10), (I, ref_I)
+    # n = +z: theta-hat = x-hat, phi-hat = y-hat; the projected field is at angle phi_B
+    deg = math.tanh(abs(a2) * t)
+    chi = math.atan2(b[1], b[0])
+    assert np.allclose(tr[:, 1] / tr[:, 0], deg * math.cos(2 * chi), atol=1e-12)
+    assert np.allclose(tr[:, 2] / tr[:, 0], deg * math.sin(2 * chi), atol=1e-12)
+    assert np.all(np.abs(tr[:, 3] / tr[:, 0]) < 1e-15)
+    assert abs(out["stats"]["absorbed_energy"] - (1 - ref_I)) < 1e-10
+
+
+def alpha1_sphere_mean_by_quadrature():
+    """1/2 int_0^pi alpha1(theta') sin theta' dtheta' of the theta'-linear interpolant."""
+    f = lambda th: float(alpha_by_hand(th)[0]) * math.sin(th)
+    return 0.5 * sum(quad(f, NODES5[j], NODES5[j + 1], epsabs=1e-14, epsrel=1e-13)[0] for j in range(4))
+
+
+def test_thermal_luminosity_uses_the_sphere_average_of_alpha1():
+    """eq. polarized-rt: the emission alpha_abs B summed over directions is
+    4 pi kappa_ext (<alpha1> - omega) B per unit volume, <alpha1> the average of
+    alpha1(theta') over the sphere (scipy quadrature of the interpolant; its plain
+    mean over theta' would differ by 8 %)."""
+    for albedo in (0.0, 0.3):
+        model = aligned_slab(1.5, (0.6, 0.0, 0.8), albedo=albedo, emissivity=2.0)
+        run = {"sources": [{"type": "thermal", "n_packets": 10}], "seed": 9}
+        ka, ks = float(model["kappa_abs"][0, 0, 0]), float(model["kappa_sca"][0, 0, 0])
+        kext = ka + ks
+        omega = ks / kext
+        L = O.thermal_luminosity(model, run)
+        ref = 4 * math.pi * kext * (alpha1_sphere_mean_by_quadrature() - omega) * 2.0 * 1.0
+        assert abs(L - ref) < 1e-12 * ref, (L, ref)
+
+
+def test_thermal_births_with_angle_dependent_extinction():
+    """eq. polarized-rt with alpha_abs = K - omega 1 acting on (B,0,0,0): a packet
+    emitted along n carries weight (alpha1(theta') - omega) / (<alpha1> - omega) and
+    degree |alpha2(theta')| / (alpha1(theta') - omega) across the projected field,
+    theta' the angle between n and the field."""
+    albedo = 0.3
+    b32 = np.array([0.6, 0.0, 0.8], dtype=np.float32)
+    b = unit(b32.astype(np.float64))
+    model = aligned_slab(1.5, b32, albedo=albedo, emissivity=1.0)
+    N = 400
+    run = {"sources": [{"type": "thermal", "luminosity": 1.0, "n_packets": N}], "seed": 9}
+    rows = O.emit(model, run, range(N))
+    ka, ks = float(model["kappa_abs"][0, 0, 0]), float(model["kappa_sca"][0, 0, 0])
+    omega = ks / (ka + ks)
+    mean1 = alpha1_sphere_mean_by_quadrature()
+    eps = 1.0 / N
+    thetaps = []
+    for r in rows:
+        n, X = r[3:6], r[6:10]
+        thetap = math.acos(max(-1.0, min(1.0, float(np.dot(n, b)))))
+        thetaps.append(thetap)
+        a1, a2, _ = alpha_by_hand(thetap)
+        assert abs(X[0] / eps - (a1 - omega) / (mean1 - omega)) < 1e-9
+        th, ph = O.stokes_basis(n)
+        bperp = b - np.dot(b, n) * n
+        chi = math.atan2(np.dot(bperp, ph), np.dot(bperp, th))
+        deg = abs(a2) / (a1 - omega)
+        assert abs(X[1] / X[0] - deg * math.cos(2 * chi + math.pi)) < 1e-9
+        assert abs(X[2] / X[0] - deg * math.sin(2 * chi + math.pi)) < 1e-9
+    # the draw covers several table intervals
+    assert len(np.unique(np.digitize(thetaps, NODES5))) >= 4
+
+
+# ---------------------------------------------------------------------------------
+# Sec. 3.1: the inclined-disk test through step 1 and step 2
+# ---------------------------------------------------------------------------------
+def stokes_sums_by_batch(model, run, nb, per, n_threads):
+    """Transport nb batches of `per` packet ids (one run of nb * per ids) and image
+    every camera: sums [nb][n_cam][4] of each batch's images, scaled by nb."""
+    out = np.zeros((nb, len(run["cameras"]), 4))
+    for b in range(nb):
+        r = dict(run, pid_begin=b * per, pid_end=(b + 1) * per, n_threads=n_threads)
+        o = O.transport(model, r)
+        for k in range(len(run["cameras"])):
+            out[b, k] = O.image(model, r, o["S"], k).sum(axis=(1, 2)) * nb
+    return out
+
+
+def test_inclined_thin_disk_through_both_steps():
+    """Sec. 3.1 (Yang et al. 2016): light of a central star reaching a geometrically and
+    optically thin annulus of Rayleigh grains travels in the disk plane; scattered once
+    and imaged at inclination i its integrated Q/I is sin^2 i / (2 + sin^2 i) and U/I = 0.
+    Step 1 (tally) and step 2 (images) of the oracle, 32 M packets in 16 batches; the
+    gate is 4 batch sigma plus 3e-4 for the pixel quadrature of the images.  The light
+    is in the plane only to h / r_in: the expectation includes its <k_z^2>."""
+    import closed_forms as CF
+
+    model = W.inclined_thin_disk()
+    g = model["geometry"]
+    kz2 = CF.thin_annulus_kz2(g["h"], g["r_in"], g["r_out"])
+    assert kz2 < 2e-4
+    nb, per = 16, 2_000_000
+    run = W.thin_disk_run(nb * per)
+    sums = stokes_sums_by_batch(model, run, nb, per, os.cpu_count() or 1)
+    tot = sums.mean(axis=0)
+    for k, a in enumerate((0, 15, 30, 45, 60, 75, 90)):
+        i = math.radians(a)
+        q = sums[:, k, 1] / sums[:, k, 0]
+        u = sums[:, k, 2] / sums[:, k, 0]
+        sq, su = q.std(ddof=1) / math.sqrt(nb), u.std(ddof=1) / math.sqrt(nb)
+        p = CF.inclined_disk_p(i, kz2)
+        assert abs(tot[k, 1] / tot[k, 0] - p) < 4 * sq + 3e-4, (a, tot[k, 1] / tot[k, 0], p, sq)
+        assert abs(tot[k, 2] / tot[k, 0]) < 4 * su + 3e-4, (a, tot[k, 2] / tot[k, 0], su)
+        assert abs(tot[k, 3]) < 1e-12 * tot[k, 0]
+    # the expectation moves with i as the paper's curve: 0 face-on, 1/3 edge-on
+    assert CF.inclined_disk_p(0.0) == 0.0 and abs(CF.inclined_disk_p(math.pi / 2) - 1 / 3) < 1e-15
+
+
 def test_sweep_generator_statistics():
     """Batched-sweep inputs: ln rho has unit variance (sigma_ln = 1) and <rho> ~ 1;
     kappa scales as lambda^-1.5 between the wavelengths of one model."""
