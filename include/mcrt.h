@@ -521,12 +521,20 @@ MCRT_API mcrt_status mcrt_set_surrogate(mcrt_ctx *ctx, mcrt_surrogate *s, double
  * Limits (MCRT_E_INVAL beyond them): at most MCRT_NOALLOC_MAX_CELLS cells,
  * MCRT_NOALLOC_MAX_BINS grain bins, MCRT_NOALLOC_MAX_THETA angles per table; point
  * and beam sources only (thermal sources need per-cell emission scratch).
- * The first call on a device looks up the array's device address (this can load
- * the library's device code); make that first call before any stream capture.
+ * Every call looks up the array's device address on the current device (the first
+ * lookup on a device can load the library's device code); make the first call on a
+ * device before any stream capture.  Inputs, outputs and the trace must be memory of
+ * the current device (or managed memory); memory of another GPU is refused.
  * All calls share the one array, so calls whose GPU work overlaps (different
  * streams or host threads without ordering between them) race on it; each call
- * clears what must start at zero.  Work runs on prob->cuda_stream; out_stats
- * (nullable, host) is filled after that stream has been synchronized.
+ * clears what must start at zero.  Work runs on prob->cuda_stream, and the call
+ * synchronizes that stream three times before it returns: after copying the kext
+ * rows to the host for their checks, after the set-up kernels' check of the grids,
+ * and after the transport, to read the launch's status word.  It therefore blocks
+ * the calling host thread until all work queued on the stream has finished.  The
+ * status is read whether or not out_stats is given: MCRT_E_EVENT_CAP or
+ * MCRT_E_TIMEOUT report packets cut by the caps or the time budget (the outputs hold
+ * the rest).  out_stats (nullable, host) receives the launch totals.
  */
 enum { MCRT_NOALLOC_MAX_CELLS = 131072, MCRT_NOALLOC_MAX_BINS = 8, MCRT_NOALLOC_MAX_THETA = 181 };
 

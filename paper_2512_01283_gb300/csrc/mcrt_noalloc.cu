@@ -16,7 +16,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "mcrt.h"
 #include "mcrt_internal.h"
@@ -47,28 +46,20 @@ constexpr size_t kScratchBytes = kOffWork + round256(kWorkBytes);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device, looked up once per
-// device (the first call on a device does this; it may load the module).
+// Device address of the scratch array on the current device, looked up on every call
+// with that device current: after a cudaDeviceReset, or in another context on the same
+// device, the module is loaded anew and the array can sit elsewhere, so no address is
+// kept between calls.  The first lookup on a device may load the library's device code.
 cudaError_t scratch_address(unsigned char** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev] = p;
-    }
-    *out = static_cast<unsigned char*>(g_addr[dev]);
+    *out = static_cast<unsigned char*>(p);
     return cudaSuccess;
 }
 
+// Device memory of the current device (or managed memory): the kernels read and write
+// these buffers directly, so memory of another GPU is refused.
 bool on_device(const void* p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -76,7 +67,13 @@ bool on_device(const void* p) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 void basis(const double n[3], double th[3], double ph[3]) {
@@ -282,32 +279,35 @@ extern "C" mcrt_status mcrt_launch_packets_noalloc(const mcrt_noalloc_problem* p
     const long long need = (nwork + block - 1) / block;
     if (need < grid) grid = need > 0 ? need : 1;
     if (nwork > 0) NA_CK(launch_transport(P, d->precision, block, (int)grid, s));
-    if (!out_stats) return MCRT_OK;
 
+    // the launch's status word is always read (event or trial cap, time budget), the
+    // totals when out_stats is given
     double raw[16];
     unsigned status = 0;
-    NA_CK(cudaMemcpyAsync(raw, work + 8, sizeof raw, cudaMemcpyDeviceToHost, s));
+    if (out_stats) NA_CK(cudaMemcpyAsync(raw, work + 8, sizeof raw, cudaMemcpyDeviceToHost, s));
     NA_CK(cudaMemcpyAsync(&status, work + 136, sizeof status, cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
-    std::memset(out_stats, 0, sizeof(*out_stats));
-    const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(raw + 6);
-    out_stats->emitted_energy = raw[0];
-    out_stats->escaped_energy = raw[1];
-    out_stats->absorbed_energy = raw[2];
-    out_stats->roulette_lost = raw[3];
-    out_stats->roulette_gain = raw[4];
-    out_stats->cap_lost = raw[5];
-    out_stats->events = (double)cnt[0];
-    out_stats->segments = (double)cnt[1];
-    out_stats->scatterings = (double)cnt[2];
-    out_stats->emitted = (double)cnt[3];
-    out_stats->escaped = (double)cnt[4];
-    out_stats->roulette_killed = (double)cnt[5];
-    out_stats->cap_hits = (double)cnt[6];
-    out_stats->trials = (double)cnt[7];
-    out_stats->tally_segments = (double)cnt[8];
-    out_stats->absorb_segments = (double)cnt[9];
-    out_stats->status_bits = (double)status;
+    if (out_stats) {
+        std::memset(out_stats, 0, sizeof(*out_stats));
+        const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(raw + 6);
+        out_stats->emitted_energy = raw[0];
+        out_stats->escaped_energy = raw[1];
+        out_stats->absorbed_energy = raw[2];
+        out_stats->roulette_lost = raw[3];
+        out_stats->roulette_gain = raw[4];
+        out_stats->cap_lost = raw[5];
+        out_stats->events = (double)cnt[0];
+        out_stats->segments = (double)cnt[1];
+        out_stats->scatterings = (double)cnt[2];
+        out_stats->emitted = (double)cnt[3];
+        out_stats->escaped = (double)cnt[4];
+        out_stats->roulette_killed = (double)cnt[5];
+        out_stats->cap_hits = (double)cnt[6];
+        out_stats->trials = (double)cnt[7];
+        out_stats->tally_segments = (double)cnt[8];
+        out_stats->absorb_segments = (double)cnt[9];
+        out_stats->status_bits = (double)status;
+    }
     if (status & MCRT_STATUS_TIMEOUT) return mcrt_fail_noctx(MCRT_E_TIMEOUT, "%s: time budget exhausted", me);
     if (status & (MCRT_STATUS_EVENT_CAP | MCRT_STATUS_TRIAL_CAP))
         return mcrt_fail_noctx(MCRT_E_EVENT_CAP, "%s: packets reached the event or trial cap", me);

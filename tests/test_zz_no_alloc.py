@@ -90,6 +90,69 @@ def test_noalloc_matches_allocating_entry_point(torch_cuda, name, make, precisio
         assert np.linalg.norm(A - ref_A) <= 1e-9 * max(np.linalg.norm(ref_A), 1e-300), call
 
 
+def test_noalloc_beam_source_fp32(torch_cuda):
+    """A plane beam into a scattering, absorbing slab with aligned grains (FP32,
+    Rayleigh, two cameras), twice in a row, against the allocating entry point."""
+    torch = torch_cuda
+    model = W.dichroic_slab(n=16, tau=2.0, albedo=0.5)
+    run = W.beam_run(30_000, seed=3, cameras=[W.camera((0, 0, 1), (8, 8), (1.0, 1.0)),
+                                              W.camera((0.6, 0, 0.8), (8, 8), (1.0, 1.0))])
+    ref_st, ref_S, ref_A = reference(model, run, "fp32")
+    dev = to_device(torch, model)
+    source = torch.empty((model["kappa_abs"].size, 2, 4), dtype=torch.float64, device="cuda")
+    absorbed = torch.empty(model["kappa_abs"].size, dtype=torch.float64, device="cuda")
+    for call in range(2):
+        source.fill_(5.0)
+        absorbed.fill_(5.0)
+        st = M.launch_noalloc(dev, run, source, absorbed, precision="fp32")
+        assert st["status"] == M.MCRT_OK
+        for key in ("emitted", "escaped", "events", "scatterings", "tally_segments"):
+            assert st[key] == ref_st[key], (call, key)
+        S, A = source.cpu().numpy(), absorbed.cpu().numpy()
+        assert np.linalg.norm(S - ref_S) <= 1e-6 * np.linalg.norm(ref_S), call
+        assert np.linalg.norm(A - ref_A) <= 1e-6 * np.linalg.norm(ref_A), call
+
+
+def test_noalloc_half_ranges_accumulate_to_one_call(torch_cuda):
+    """Two calls over the halves of the packet ids, the second with accumulate = 1 (the
+    outputs kept while the shared scratch's counters start again at zero), equal one
+    allocating call over all ids."""
+    torch = torch_cuda
+    model = W.disk(n=24)
+    run = dict(W.disk_run(20_000, n_cam=2, npix=8),
+               sources=[{"type": "point", "pos": (0.0, 0.0, 0.0), "luminosity": 1.0, "n_packets": 20_000}])
+    ref_st, ref_S, ref_A = reference(model, run, "fp32")
+    dev = to_device(torch, model)
+    source = torch.full((model["kappa_abs"].size, 2, 4), 9.0, dtype=torch.float64, device="cuda")
+    absorbed = torch.full((model["kappa_abs"].size,), 9.0, dtype=torch.float64, device="cuda")
+    st1 = M.launch_noalloc(dev, dict(run, pid_begin=0, pid_end=10_000), source, absorbed, precision="fp32")
+    st2 = M.launch_noalloc(dev, dict(run, pid_begin=10_000, pid_end=20_000), source, absorbed, precision="fp32",
+                           accumulate=1)
+    for key in ("emitted", "escaped", "events", "segments", "scatterings", "tally_segments"):
+        assert st1[key] + st2[key] == ref_st[key], key
+    S, A = source.cpu().numpy(), absorbed.cpu().numpy()
+    assert np.linalg.norm(S - ref_S) <= 1e-6 * np.linalg.norm(ref_S)
+    assert np.linalg.norm(A - ref_A) <= 1e-6 * np.linalg.norm(ref_A)
+
+
+def test_noalloc_without_cameras(torch_cuda):
+    """No camera and no source-tally buffer: only the absorbed tally is written."""
+    torch = torch_cuda
+    model = W.disk(n=24)
+    run = dict(W.disk_run(10_000, n_cam=0),
+               sources=[{"type": "point", "pos": (0.0, 0.0, 0.0), "luminosity": 1.0, "n_packets": 10_000}])
+    run["cameras"] = []
+    ref_st, _, ref_A = reference(model, run, "fp32")
+    dev = to_device(torch, model)
+    absorbed = torch.full((model["kappa_abs"].size,), -1.0, dtype=torch.float64, device="cuda")
+    st = M.launch_noalloc(dev, run, None, absorbed, precision="fp32")
+    assert st["events"] == ref_st["events"] and st["tally_segments"] == 0
+    A = absorbed.cpu().numpy()
+    assert np.linalg.norm(A - ref_A) <= 1e-6 * np.linalg.norm(ref_A)
+    # the absorbed total sums each packet's FP32 absorbed energy, the tally widened terms
+    assert abs(A.sum() - st["absorbed_energy"]) <= 1e-7 * st["emitted_energy"]
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit(torch_cuda):
     torch = torch_cuda
     model = W.rayleigh_sphere(n=4)
