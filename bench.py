@@ -35,11 +35,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--packets", type=float, default=1e8)
     ap.add_argument("--grid", type=int, default=192)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--cpu-chunks", type=int, default=CPU_CHUNKS, help="chunks of packet ids in the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
-    ap.add_argument("--sweep-packets", type=float, default=1e6, help="packets per job of the batched sweep")
+    ap.add_argument("--sweep-packets", type=float, default=1e7, help="packets per job of the batched sweep")
+    ap.add_argument("--sweep-runs", type=int, default=1, help="timed graph replays of the batched sweep")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-plane-parallel", action="store_true")
     ap.add_argument("--no-spheroids", action="store_true", help="skip the aligned-spheroid line")
@@ -64,26 +65,42 @@ def workload_config(args):
             "l2": "no flush: the source tally (1.81 GB) and grid (226 MB) exceed the 129 MB L2"}
 
 
-def oracle_sample(model, run, seconds, n_threads, pid_offset=0):
-    """Oracle on growing pid samples (half star ids, half thermal ids) until about
-    ``seconds`` of wall time; returns (events, wall, packets)."""
+CPU_CHUNK = 8192  # packet ids per source half in one chunk of the oracle baseline
+CPU_CHUNKS = 48   # chunks of the GPU arm's baseline (about 13 s of loop time); the reference arm cycles through them
+
+
+def oracle_sample(model, run, chunks, n_threads, bufs=None):
+    """The FP64 oracle on chunks of the workload's packet ids: chunk c is ids
+    [c * CPU_CHUNK, (c + 1) * CPU_CHUNK) of the star half and the same offsets into
+    the thermal half, each half one oracle call over all host threads.  The time is the
+    packet loops' alone, measured inside the oracle: its per-call set-up (problem
+    marshalling, the thermal emission CDF over all cells) is excluded, and the tally
+    buffers are allocated and touched once beforehand.  Returns (events, seconds,
+    packets, bufs)."""
     from oracle import oracle as O
 
+    if bufs is None:
+        ncell = O.n_cells(model)
+        bufs = (np.zeros((ncell, max(1, len(run["cameras"])), 4)), np.zeros(ncell))
+        for b in bufs:
+            b.fill(0.0)
     n_star = run["sources"][0]["n_packets"]
-    chunk, events, wall, packets = 256, 0.0, 0.0, 0
-    start = pid_offset
-    while wall < seconds:
-        for base in (start, n_star + start):
-            t0 = time.perf_counter()
-            out = O.transport(model, dict(run, pid_begin=base, pid_end=base + chunk, n_threads=n_threads,
-                                          cameras=run["cameras"]))
-            wall += time.perf_counter() - t0
+    events = wall = 0.0
+    packets = 0
+    for c in chunks:
+        for base in (c * CPU_CHUNK, n_star + c * CPU_CHUNK):
+            out = O.transport(model, dict(run, pid_begin=base, pid_end=base + CPU_CHUNK, n_threads=n_threads),
+                              S_out=bufs[0], absorbed_out=bufs[1])
             events += out["stats"]["events"]
-            packets += chunk
-        start += chunk
-        if wall < seconds / 4:
-            chunk *= 2
-    return events, wall, packets
+            wall += out["stats"]["loop_seconds"]
+            packets += CPU_CHUNK
+    return events, wall, packets, bufs
+
+
+def oracle_sample_text(chunks, packets, total):
+    return ("chunks %s of %d star + %d thermal packet ids (chunk c: ids from c x %d in each half) of the "
+            "%.0e-packet workload, %d packets; packet loops timed inside the oracle, its set-up excluded"
+            % (chunks, CPU_CHUNK, CPU_CHUNK, CPU_CHUNK, total, packets))
 
 
 KERNEL_SOURCES = ("paper_2512_01283_gb300/csrc/mcrt_transport.cu", "paper_2512_01283_gb300/csrc/mcrt_device.cuh",
@@ -203,10 +220,10 @@ def run_sweep(args, M, W, torch, rank=0, world=1, dist=None):
     batch = M.Batch(mdls, run, precision="fp32")
     tune = batch.tune(packets_per_job=max(1000, int(args.sweep_packets) // 100))
     setup_s = time.perf_counter() - t0
-    batch.launch(seed=10)
+    # the tuner's trial launches ran the same kernels: no separate warm-up replay
     torch.cuda.synchronize()
     runs = []
-    for s in range(2):
+    for s in range(args.sweep_runs):
         t1 = time.perf_counter()
         st = batch.launch(seed=11 + s)
         runs.append((st, time.perf_counter() - t1))
@@ -472,7 +489,9 @@ def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_v
 
 
 def run_reference(args, rank):
-    """Reference arm: the FP64 CPU oracle timed on bounded samples of the workload."""
+    """Reference arm: the FP64 CPU oracle, each step one chunk of the workload's packet
+    ids (steps cycle through the chunks the GPU arm's cpu_baseline times), the packet
+    loops timed inside the oracle."""
     if rank != 0:
         return
     from paper_2512_01283_gb300 import workloads as W
@@ -480,22 +499,23 @@ def run_reference(args, rank):
     model = W.disk(n=args.grid)
     run = W.disk_run(n_packets=int(args.packets))
     cores = os.cpu_count() or 1
-    per_step = max(2.0, 90.0 / max(1, args.steps + args.warmup))
-    vals = []
+    bufs = None
+    ev = wall = 0.0
+    npk = 0
+    timed = []
     for s in range(args.warmup + args.steps):
-        ev, wall, npk = oracle_sample(model, run, per_step, cores, pid_offset=s * 100000)
+        c = s % CPU_CHUNKS
+        e, w, n, bufs = oracle_sample(model, run, [c], cores, bufs)
         if s >= args.warmup:
-            vals.append((ev, wall, npk))
-    ev = sum(v[0] for v in vals)
-    wall = sum(v[1] for v in vals)
+            ev, wall, npk = ev + e, wall + w, npk + n
+            timed.append(c)
     value = ev / wall
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d packets per step (half star, half thermal ids) of the %.0e-packet "
-                                       "workload" % (vals[0][2], args.packets)},
+                             "sample": oracle_sample_text(sorted(set(timed)), npk, args.packets)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -536,21 +556,17 @@ def main():
     npix = run["cameras"][0]["npix"]
     mdl = M.Model(model)
     imgs = torch.empty((n_cam, 4, npix[1], npix[0]), dtype=torch.float64, device="cuda")
-    S_sum = A_sum = None
-    if world > 1:
-        S_sum = torch.empty((mdl.ncell, n_cam, 4), dtype=torch.float64, device="cuda")
-        A_sum = torch.empty((mdl.ncell,), dtype=torch.float64, device="cuda")
 
     def launch_share(m_, seed, **kw):
         return MG.rank_launch(lambda r, acc: M.launch(m_, dict(r, seed=seed), precision="fp32", accumulate=acc, **kw),
                               run, rank, world)
 
     def exchange(m_):
-        # the one exchange of a sharded run: FP64 tallies summed over ranks before step 2
+        # the one exchange of a sharded run: FP64 tallies summed over ranks before step 2,
+        # in place on the library's own buffers (no copy out and back)
         if world > 1:
-            m_.tallies_into(S_sum, A_sum)
-            MG.combine_tallies(S_sum, A_sum, dist)
-            m_.set_tallies(S_sum, A_sum)
+            src, ab = m_.tally_tensors(n_cam)
+            MG.combine_tallies(src, ab, dist)
 
     my_cams = MG.rank_cameras(n_cam, rank, world)
 
@@ -601,12 +617,16 @@ def main():
     events = sum(s["events"] for s in stats)
     ms_max, ev_all = MG.reduce_timing(ms, events, dist, device="cuda")
     value = ev_all / (ms_max * 1e-3)
+    _, tal_all = MG.reduce_timing(ms, sum(s["tally_segments"] for s in stats), dist, device="cuda")
 
-    # rooflines: algorithmic bytes of each kernel over its CUDA-event time measured
-    # inside the library on the launching stream.  FP32 table launches run in rounds:
-    # the transport kernel (32 B cell + 16 B absorbed RMW per absorbing segment + 32 B
-    # record per tallying segment) and the tally kernel (32 B record + 64 B source RMW
-    # per camera and record); the dominant one (longer time) is `roofline`.
+    # rooflines: the method's algorithmic bytes (per segment: 4 B kappa + 16 B grain
+    # quaternion read; 8 B absorbed-energy read + write per absorbing segment; 4 Stokes x
+    # 8 B read + write per camera per tallying segment, the source tally being far larger
+    # than L2) over each kernel's CUDA-event time measured inside the library on its
+    # launching stream.  FP32 table launches run in rounds: the transport kernel carries
+    # the kappa, quaternion and absorbed bytes, the tally kernel the source bytes; the
+    # longer of the two is `roofline`.  The bytes this design moves besides (32-byte cell
+    # records, 32-byte tally records between the kernels) are given as design_bytes.
     seg = sum(s["segments"] for s in stats)
     tal = sum(s["tally_segments"] for s in stats)
     ab = sum(s["absorb_segments"] for s in stats)
@@ -620,35 +640,40 @@ def main():
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     src = "measured" if "hbm_gbs" in peaks else "fallback"
+    alg_t = 20.0 * seg + 16.0 * ab
+    alg_a = 64.0 * n_cam * tal
     kernels = {}
     if t_ms > 0 and a_ms > 0:
-        b_t = 32.0 * seg + 16.0 * ab + 32.0 * tal
-        b_a = (32.0 + 64.0 * n_cam) * tal
         kernels["transport"] = {"kernel": "k_transport<float, table rounds>", "bound": "hbm",
-                                "achieved": b_t / (t_ms * 1e-3) / 1e9, "ms_per_step": t_ms / args.steps,
-                                "bytes_per_unit": "32 cell + 16 absorbed RMW (absorbing) + 32 record (tallying) per segment",
+                                "achieved": alg_t / (t_ms * 1e-3) / 1e9, "ms_per_step": t_ms / args.steps,
+                                "bytes_per_unit": "4 kappa + 16 quaternion per segment, + 16 absorbed read/write "
+                                                  "per absorbing segment",
+                                "design_bytes_per_unit": "32 cell record per segment + 16 absorbed per absorbing "
+                                                         "segment + 32 tally record per tallying segment",
+                                "design_GBs": (32.0 * seg + 16.0 * ab + 32.0 * tal) / (t_ms * 1e-3) / 1e9,
                                 "traffic": profiled_traffic("transport", seg / args.steps),
                                 "issue": profiled_issue("transport")}
-        kernels["tally"] = {"kernel": "k_tab_tally", "bound": "hbm", "achieved": b_a / (a_ms * 1e-3) / 1e9,
+        kernels["tally"] = {"kernel": "k_tab_tally", "bound": "hbm", "achieved": alg_a / (a_ms * 1e-3) / 1e9,
                             "ms_per_step": a_ms / args.steps,
-                            "bytes_per_unit": "32 record + 64 x n_cam source RMW per tallying segment",
+                            "bytes_per_unit": "n_cam x 4 Stokes x 8 B, read + write, per tallying segment",
+                            "design_bytes_per_unit": "32 tally record + n_cam x 64 source read/write per record",
+                            "design_GBs": (32.0 + 64.0 * n_cam) * tal / (a_ms * 1e-3) / 1e9,
                             "traffic": profiled_traffic("tally", tal / args.steps),
                             "issue": profiled_issue("tally")}
         for k in kernels.values():
             k.update({"peak": peak, "unit": "GB/s", "frac": k["achieved"] / peak, "peak_source": src})
+            k["traffic_per_launch_note"] = "ncu dram bytes of a 2e6-packet capture, scaled to the step's units"
         dom = kernels["transport"] if t_ms >= a_ms else kernels["tally"]
         roofline = dict(dom)
-        alg_step = b_t + b_a
     else:
-        alg_step = 32.0 * seg + 16.0 * ab + 64.0 * n_cam * tal
-        achieved = alg_step / (kms * 1e-3) / 1e9
+        achieved = (alg_t + alg_a) / (kms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": None, "peak_source": src, "kernel": "k_transport<float, table> (tally in place)",
-                    "bytes_per_unit": "32 cell + 16 absorbed RMW (if absorbing) + 64 x n_cam source RMW (if "
-                                      "scattering) per segment"}
+                    "bytes_per_unit": "20 per segment + 16 per absorbing segment + 64 x n_cam per tallying segment"}
+    alg_step = alg_t + alg_a
     roofline_step = {"achieved": alg_step / (ms_max * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": alg_step / (ms_max * 1e-3) / 1e9 / peak,
-                     "note": "all algorithmic bytes of step 1 over the whole step time (images included)"}
+                     "frac": alg_step / (ms_max * 1e-3) / 1e9 / peak, "bytes_per_step": alg_step / args.steps,
+                     "note": "the method's bytes of step 1 (as roofline) over the whole step time, images included"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -657,6 +682,7 @@ def main():
             "gpu_launches": int(sum(3 * s["wave_iterations"] if s["wave_iterations"] else 1 for s in stats)
                                 + args.steps * len(my_cams)),
             "clocks": cs.summary(),
+            "tally_segments_per_s": tal_all / (ms_max * 1e-3),
             "detail": {"events_per_step": events / args.steps, "segments_per_step": seg / args.steps,
                        "scatterings_per_step": sum(s["scatterings"] for s in stats) / args.steps,
                        "tally_segments_per_step": tal / args.steps,
@@ -721,10 +747,10 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        ev, wall, npk = oracle_sample(model, run, args.cpu_seconds, cores)
+        chunks = list(range(args.cpu_chunks))
+        ev, wall, npk, _ = oracle_sample(model, run, chunks, cores)
         line["cpu_baseline"] = {"value": ev / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "%d packets (first ids of the star and of the thermal halves) of the "
-                                          "%.0e-packet workload, %.1f s" % (npk, args.packets, wall)}
+                                "sample": oracle_sample_text(chunks, npk, args.packets), "seconds": wall}
     mdl.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

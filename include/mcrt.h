@@ -337,6 +337,21 @@ MCRT_API mcrt_status mcrt_microbench(int32_t kind, uint64_t bytes, uint64_t n_op
  */
 MCRT_API mcrt_status mcrt_set_tallies(mcrt_ctx *ctx, const double *source, const double *absorbed);
 
+/*
+ * Device addresses of the step-1 tallies of the last launch, owned by the library
+ * (layouts as in mcrt_get_tallies), for collectives that work on them in place: the
+ * sum over ranks of a sharded run (Sec. 2.3: step 2 is linear in the tallies) can run
+ * directly on these buffers instead of a copy out and back.  Writes through them
+ * replace the tallies as mcrt_set_tallies does.  The caller orders its work on them
+ * after the launch and before the next call that uses ctx (the launch has
+ * synchronized ctx's stream when it returned with out_stats; otherwise synchronize
+ * that stream first).  Valid until the next launch or mcrt_destroy of ctx.  Any
+ * output pointer may be NULL; source is NULL (count 0) when the launch had no camera.
+ * Errors: MCRT_E_INVAL, MCRT_E_STATE (no launch yet).
+ */
+MCRT_API mcrt_status mcrt_tally_buffers(mcrt_ctx *ctx, double **source, double **absorbed, int64_t *source_count,
+                                        int64_t *absorbed_count);
+
 /* Release the context and its device memory; NULL is accepted. */
 MCRT_API mcrt_status mcrt_destroy(mcrt_ctx *ctx);
 
@@ -444,6 +459,16 @@ MCRT_API mcrt_status mcrt_surrogate_eval(mcrt_surrogate *s, int64_t n, const flo
 MCRT_API mcrt_status mcrt_surrogate_labels(mcrt_surrogate *s, int64_t n, const float *inputs, float *labels);
 MCRT_API mcrt_status mcrt_surrogate_grad(mcrt_surrogate *s, int64_t n, const float *inputs, const float *targets,
                                          const float *loss_weights, float *grads, double *loss);
+/*
+ * The FP32 mode of mcrt_surrogate_grad, for checking the backward pass at FP32
+ * accuracy: the same loss and gradient with FP32 operands, activations and gradients
+ * throughout (FP32 FMA on the CUDA cores, no BF16 rounding; the inputs enter as FP32
+ * without high and low parts) and the FP32 master weights as they are.  Allocates
+ * its activation buffers for the duration of the call.  Same arguments and errors.
+ */
+MCRT_API mcrt_status mcrt_surrogate_grad_fp32(mcrt_surrogate *s, int64_t n, const float *inputs,
+                                              const float *targets, const float *loss_weights, float *grads,
+                                              double *loss);
 MCRT_API mcrt_status mcrt_surrogate_params(mcrt_surrogate *s, float *params, int32_t set);
 MCRT_API int64_t mcrt_surrogate_param_count(void);
 MCRT_API mcrt_status mcrt_surrogate_destroy(mcrt_surrogate *s); /* NULL-safe */

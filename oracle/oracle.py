@@ -73,7 +73,7 @@ class Result(C.Structure):
 
 STAT_NAMES = ["emitted_energy", "escaped_energy", "absorbed_energy", "roulette_lost", "roulette_gain",
               "cap_lost", "events", "segments", "scatterings", "emitted", "escaped", "roulette_killed",
-              "cap_hits", "trials", "status", "spare"]
+              "cap_hits", "trials", "status", "loop_seconds"]
 
 
 def lib():
@@ -372,14 +372,19 @@ def dda_walk_composite(model: dict, p0, n, max_cells=100000):
     return cells[:k].copy(), lens[:k].copy()
 
 
-def transport(model: dict, run: dict):
+def transport(model: dict, run: dict, S_out=None, absorbed_out=None):
     """Step 1 (Sec. 2.2, 2.3).  Returns dict with S [ncell][n_cam][4], absorbed
-    [ncell], trace [n_trace][16] and stats."""
+    [ncell], trace [n_trace][16] and stats.  S_out / absorbed_out: FP64 buffers of
+    those shapes to add the tallies to instead of fresh zeroed ones (a timing loop
+    reuses them, so that first-touch page faults stay out of the packet loop)."""
     keep = make_problem(model, run)
     P = keep.P
     ncell = int(lib().orc_n_cells(C.byref(P)))
-    S = np.zeros((ncell, max(1, P.n_cam), 4))
-    absorbed = np.zeros(ncell)
+    S = np.zeros((ncell, max(1, P.n_cam), 4)) if S_out is None else S_out
+    absorbed = np.zeros(ncell) if absorbed_out is None else absorbed_out
+    for a, shape in ((S, (ncell, max(1, P.n_cam), 4)), (absorbed, (ncell,))):
+        if a.shape != shape or a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise ValueError("tally buffer of shape %s, contiguous float64, expected" % (shape,))
     trace = np.zeros((max(1, P.n_trace), 16))
     R = Result()
     R.S = _pd(S)

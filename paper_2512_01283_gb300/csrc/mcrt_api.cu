@@ -999,6 +999,17 @@ mcrt_status mcrt_set_tallies(mcrt_ctx* ctx, const double* source, const double* 
     return MCRT_OK;
 }
 
+mcrt_status mcrt_tally_buffers(mcrt_ctx* ctx, double** source, double** absorbed, int64_t* source_count,
+                               int64_t* absorbed_count) {
+    if (!ctx) return fail(nullptr, MCRT_E_INVAL, "mcrt_tally_buffers: ctx is NULL");
+    if (!ctx->launched) return fail(ctx, MCRT_E_STATE, "mcrt_tally_buffers: no launch yet");
+    if (source) *source = ctx->n_cam > 0 ? ctx->d_S : nullptr;
+    if (absorbed) *absorbed = ctx->d_absorbed;
+    if (source_count) *source_count = ctx->n_cam > 0 ? (int64_t)ctx->g.ncell * ctx->n_cam * 4 : 0;
+    if (absorbed_count) *absorbed_count = (int64_t)ctx->g.ncell;
+    return MCRT_OK;
+}
+
 mcrt_status mcrt_set_surrogate(mcrt_ctx* ctx, mcrt_surrogate* s, double bound) {
     if (!ctx || !s) return fail(ctx, MCRT_E_INVAL, "mcrt_set_surrogate: ctx or surrogate is NULL");
     if (!ctx->tables_set || ctx->t.model != MCRT_SCAT_TABLE)

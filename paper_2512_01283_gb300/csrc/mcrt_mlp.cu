@@ -297,6 +297,140 @@ template <int EPI> cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------
+// FP32 mode of the training passes, for gradient checks at FP32 accuracy: the same
+// layers and fused epilogues with FP32 operands and activations on the FP32 pipe (no
+// BF16 rounding anywhere), C[m][n] = sum_k A(m,k) B(k,n) with the index rules of
+// GemmArgs.  Block tile 64x64x16, 256 threads of 4x4 outputs each.
+// ---------------------------------------------------------------------------------
+struct GemmArgs32 {
+    int M, N, K;
+    const float* A;
+    int lda, a_t;
+    const float* B;
+    int ldb, b_kn;
+    const float* bias;
+    float* Zout;
+    int ldz;
+    float* Hout;
+    int ldh;
+    const float* Zprev;
+};
+
+constexpr int kT32 = 64, kK32 = 16;
+
+template <int EPI> __global__ void __launch_bounds__(256) k_gemm32(const GemmArgs32 g) {
+    __shared__ float As[kK32][kT32 + 4];  // [k][m]
+    __shared__ float Bs[kK32][kT32 + 4];  // [k][n]
+    const int m0 = blockIdx.y * kT32, n0 = blockIdx.x * kT32;
+    const int tid = threadIdx.x, tm = (tid / 16) * 4, tn = (tid % 16) * 4;
+    float acc[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    int kb = 0, ke = g.K;
+    if (EPI == EPI_DW && gridDim.z > 1) {
+        const int per = ((g.K + gridDim.z - 1) / gridDim.z + kK32 - 1) / kK32 * kK32;
+        kb = blockIdx.z * per;
+        ke = kb + per < g.K ? kb + per : g.K;
+    }
+    for (int k0 = kb; k0 < ke; k0 += kK32) {
+        for (int i = tid; i < kT32 * kK32; i += blockDim.x) {
+            const int r = i / kK32, kk = i % kK32, k = k0 + kk;
+            const int m = m0 + r, n = n0 + r;
+            float a = 0.f, b = 0.f;
+            if (m < g.M && k < ke) a = g.a_t ? g.A[(size_t)k * g.lda + m] : g.A[(size_t)m * g.lda + k];
+            if (n < g.N && k < ke) b = g.b_kn ? g.B[(size_t)k * g.ldb + n] : g.B[(size_t)n * g.ldb + k];
+            As[kk][r] = a;
+            Bs[kk][r] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kK32; ++kk) {
+            float a[4], b[4];
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tm + i];
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tn + j];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + tm + i, n = n0 + tn + j;
+            if (m >= g.M || n >= g.N) continue;
+            const float v = acc[i][j];
+            if (EPI == EPI_HIDDEN) {
+                const float z = v + g.bias[n];
+                g.Zout[(size_t)m * g.ldz + n] = z;
+                g.Hout[(size_t)m * g.ldh + n] = silu_f(z);
+            } else if (EPI == EPI_OUT) {
+                g.Zout[(size_t)m * g.ldz + n] = v + g.bias[n];
+            } else if (EPI == EPI_DX) {
+                g.Hout[(size_t)m * g.ldh + n] = v * silu_grad_f(g.Zprev[(size_t)m * g.ldz + n]);
+            } else {
+                if (gridDim.z > 1)
+                    atomicAdd(&g.Zout[(size_t)m * g.ldz + n], v);
+                else
+                    g.Zout[(size_t)m * g.ldz + n] = v;
+            }
+        }
+}
+
+template <int EPI> cudaError_t gemm32(const GemmArgs32& g, cudaStream_t s) {
+    (void)cudaGetLastError();
+    dim3 grid((g.N + kT32 - 1) / kT32, (g.M + kT32 - 1) / kT32);
+    if (EPI == EPI_DW) {
+        int z = 256 / (int)(grid.x * grid.y);
+        const int kmax = (g.K + 4 * kK32 - 1) / (4 * kK32);
+        z = z < kmax ? z : kmax;
+        grid.z = z > 1 ? z : 1;
+    }
+    k_gemm32<EPI><<<grid, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+// FP32 inputs [n][7] as the first 7 of 16 columns (the rest zero): in FP32 the input
+// needs no high and low parts.
+__global__ void k_pack_inputs32(int n, const float* __restrict__ in, float* __restrict__ X) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < kInPad; ++c) X[(size_t)i * kInPad + c] = c < kIn ? in[(size_t)i * kIn + c] : 0.f;
+}
+
+// dY = 2 w (Y - T) / (B * 20) in FP32 and the loss sum (the FP32 twin of k_loss_grad).
+__global__ void k_loss_grad32(int B, const float* __restrict__ Y, const float* __restrict__ T,
+                              const float* __restrict__ w, float* __restrict__ dY, double* __restrict__ loss) {
+    __shared__ double part[256];
+    double acc = 0.0;
+    const float scale = 2.f / ((float)B * (float)kOut);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < B * kOutPad; i += gridDim.x * blockDim.x) {
+        const int b = i / kOutPad, o = i % kOutPad;
+        float d = 0.f;
+        if (o < kOut) {
+            const float r = Y[(size_t)b * kOutPad + o] - T[(size_t)b * kOut + o];
+            acc += (double)(w[o] * r * r);
+            d = scale * w[o] * r;
+        }
+        dY[i] = d;
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) part[threadIdx.x] += part[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, part[0] / ((double)B * kOut));
+}
+
+// db[n] = sum over rows of dZ[b][n] (FP32 input).
+__global__ void k_colsum32(int B, int N, const float* __restrict__ dZ, float* __restrict__ db) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int b = blockIdx.y; b < B; b += gridDim.y) s += dZ[(size_t)b * N + n];
+    atomicAdd(&db[n], s);
+}
+
 // dY = 2 w (Y - T) / (B * 20) (BF16, zero in the padding columns) and the loss sum.
 __global__ void k_loss_grad(int B, const float* __restrict__ Y, const float* __restrict__ T,
                             const float* __restrict__ w, bf16* __restrict__ dY, double* __restrict__ loss) {
@@ -1079,6 +1213,123 @@ mcrt_status mcrt_surrogate_grad(mcrt_surrogate* s, int64_t n, const float* input
     SK(cudaMemcpyAsync(s->d_w, ones.data(), sizeof(float) * kOut, cudaMemcpyHostToDevice, s->stream));
     SK(cudaStreamSynchronize(s->stream));
     if (loss) *loss = l;
+    return MCRT_OK;
+}
+
+// The FP32 mode of mcrt_surrogate_grad: forward, loss gradient and backward with FP32
+// operands, activations and gradients (k_gemm32), the FP32 master weights as they
+// are.  Its buffers live for the call only.
+mcrt_status mcrt_surrogate_grad_fp32(mcrt_surrogate* s, int64_t n, const float* inputs, const float* targets,
+                                     const float* loss_weights, float* grads, double* loss) {
+    if (!s || n < 1 || n > (1 << 20) || !inputs || !targets || !grads)
+        return mcrt_fail_noctx(MCRT_E_INVAL, "mcrt_surrogate_grad_fp32: bad arguments");
+    mcrt_status st = stage_inputs(s, inputs, n);
+    if (st != MCRT_OK) return st;
+    const int B = (int)n;
+    // x [B][16], z and h [4][B][128], y [B][24], t [B][20], dy [B][24], dz [2][B][128]
+    const size_t nx = (size_t)B * kInPad, nh = (size_t)B * kHid, ny = (size_t)B * kOutPad;
+    const size_t total = nx + 8 * nh + ny + (size_t)B * kOut + ny + 2 * nh;
+    float* base = nullptr;
+    SK(cudaMalloc(&base, total * sizeof(float)));
+    float* x = base;
+    float* z[4];
+    float* h[4];
+    for (int i = 0; i < 4; ++i) {
+        z[i] = x + nx + (size_t)(2 * i) * nh;
+        h[i] = z[i] + nh;
+    }
+    float* y = x + nx + 8 * nh;
+    float* t = y + ny;
+    float* dy = t + (size_t)B * kOut;
+    float* dzb[2] = {dy + ny, dy + ny + nh};
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    k_pack_inputs32<<<(unsigned)((n + 127) / 128), 128, 0, s->stream>>>(B, s->d_in, x);
+    ck(cudaGetLastError());
+    ck(cudaMemcpyAsync(t, targets, (size_t)n * kOut * sizeof(float), cudaMemcpyDefault, s->stream));
+    std::vector<float> w(kOut, 1.f);
+    if (loss_weights) std::memcpy(w.data(), loss_weights, sizeof(float) * kOut);
+    ck(cudaMemcpyAsync(s->d_w, w.data(), sizeof(float) * kOut, cudaMemcpyHostToDevice, s->stream));
+    for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+        GemmArgs32 g{};
+        g.M = B;
+        g.N = layer_out(l);
+        g.K = layer_in(l);
+        g.A = l == 0 ? x : h[l - 1];
+        g.lda = layer_in(l);
+        g.B = s->d_params + layer_offset(l);
+        g.ldb = layer_in(l);
+        g.bias = s->d_params + layer_offset(l) + layer_out(l) * layer_in(l);
+        if (l < kLayers - 1) {
+            g.Zout = z[l];
+            g.ldz = kHid;
+            g.Hout = h[l];
+            g.ldh = kHid;
+            ck(gemm32<EPI_HIDDEN>(g, s->stream));
+        } else {
+            g.Zout = y;
+            g.ldz = kOutPad;
+            ck(gemm32<EPI_OUT>(g, s->stream));
+        }
+    }
+    ck(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
+    if (e == cudaSuccess) {
+        k_loss_grad32<<<256, 256, 0, s->stream>>>(B, y, t, s->d_w, dy, s->d_loss);
+        ck(cudaGetLastError());
+    }
+    ck(cudaMemsetAsync(s->d_grads, 0, sizeof(float) * kParams, s->stream));
+    const float* dZ = dy;
+    int cur = 0;
+    for (int l = kLayers - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int no = layer_out(l), ni = layer_in(l);
+        GemmArgs32 gw{};
+        gw.M = no;
+        gw.N = ni;
+        gw.K = B;
+        gw.A = dZ;
+        gw.lda = no;
+        gw.a_t = 1;
+        gw.B = l == 0 ? x : h[l - 1];
+        gw.ldb = ni;
+        gw.b_kn = 1;
+        gw.Zout = s->d_grads + layer_offset(l);
+        gw.ldz = ni;
+        ck(gemm32<EPI_DW>(gw, s->stream));
+        k_colsum32<<<dim3((no + 127) / 128, 64), 128, 0, s->stream>>>(B, no, dZ,
+                                                                      s->d_grads + layer_offset(l) + no * ni);
+        ck(cudaGetLastError());
+        if (l == 0) break;
+        GemmArgs32 gx{};
+        gx.M = B;
+        gx.N = ni;
+        gx.K = no;
+        gx.A = dZ;
+        gx.lda = no;
+        gx.B = s->d_params + layer_offset(l);
+        gx.ldb = ni;
+        gx.b_kn = 1;
+        gx.Zprev = z[l - 1];
+        gx.ldz = kHid;
+        gx.Hout = dzb[cur];
+        gx.ldh = kHid;
+        ck(gemm32<EPI_DX>(gx, s->stream));
+        dZ = dzb[cur];
+        cur ^= 1;
+    }
+    double lv = 0.0;
+    ck(cudaMemcpyAsync(grads, s->d_grads, sizeof(float) * kParams, cudaMemcpyDefault, s->stream));
+    ck(cudaMemcpyAsync(&lv, s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    std::vector<float> ones(kOut, 1.f);
+    ck(cudaMemcpyAsync(s->d_w, ones.data(), sizeof(float) * kOut, cudaMemcpyHostToDevice, s->stream));
+    ck(cudaStreamSynchronize(s->stream));
+    cudaFree(base);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return mcrt_fail_noctx(MCRT_E_CUDA, "mcrt_surrogate_grad_fp32: %s", cudaGetErrorString(e));
+    }
+    if (loss) *loss = lv;
     return MCRT_OK;
 }
 

@@ -94,9 +94,9 @@ SYMBOLS = ["mcrt_create_grid", "mcrt_set_dust_tables", "mcrt_launch_packets", "m
            "mcrt_get_tallies", "mcrt_destroy", "mcrt_last_error", "mcrt_unit_eval", "mcrt_launch_packets_noalloc",
            "mcrt_batch_create", "mcrt_batch_run", "mcrt_batch_tune", "mcrt_batch_images", "mcrt_batch_destroy",
            "mcrt_surrogate_create", "mcrt_surrogate_train", "mcrt_surrogate_eval", "mcrt_surrogate_labels",
-           "mcrt_surrogate_grad", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy",
+           "mcrt_surrogate_grad", "mcrt_surrogate_grad_fp32", "mcrt_surrogate_params", "mcrt_surrogate_param_count", "mcrt_surrogate_destroy",
            "mcrt_surrogate_error_map", "mcrt_set_surrogate", "mcrt_surrogate_eval_engine", "mcrt_set_dust_dipole",
-           "mcrt_dipole_constants", "mcrt_set_tallies", "mcrt_create_grid_refined", "mcrt_microbench"]
+           "mcrt_dipole_constants", "mcrt_set_tallies", "mcrt_create_grid_refined", "mcrt_microbench", "mcrt_tally_buffers"]
 
 
 def lib():
@@ -117,6 +117,8 @@ def lib():
     L.mcrt_image_stokes.argtypes = [vp, i32, vp]
     L.mcrt_get_tallies.argtypes = [vp, vp, vp]
     L.mcrt_set_tallies.argtypes = [vp, vp, vp]
+    L.mcrt_tally_buffers.argtypes = [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64)]
     L.mcrt_microbench.argtypes = [i32, C.c_uint64, C.c_uint64, C.POINTER(C.c_double)]
     L.mcrt_destroy.argtypes = [vp]
     L.mcrt_last_error.argtypes = [vp]
@@ -133,6 +135,7 @@ def lib():
     L.mcrt_surrogate_eval.argtypes = [vp, i64, vp, vp]
     L.mcrt_surrogate_labels.argtypes = [vp, i64, vp, vp]
     L.mcrt_surrogate_grad.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.mcrt_surrogate_grad_fp32.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     L.mcrt_surrogate_params.argtypes = [vp, vp, i32]
     L.mcrt_surrogate_param_count.argtypes = []
     L.mcrt_surrogate_param_count.restype = C.c_int64
@@ -294,6 +297,28 @@ class Model:
         ps, ks = _ptr(source, np.float64)
         pa, ka = _ptr(absorbed, np.float64)
         _check(lib().mcrt_set_tallies(self.h, ps, pa), self.h)
+
+    def tally_tensors(self, n_cam: int):
+        """The library's own tally buffers of the last launch as CUDA torch tensors
+        (mcrt_tally_buffers; no copy): source [ncell][n_cam][4] (None without cameras)
+        and absorbed [ncell], FP64, valid until the next launch or close."""
+        import torch
+
+        ps, pa = C.c_void_p(), C.c_void_p()
+        ns, na = C.c_int64(), C.c_int64()
+        _check(lib().mcrt_tally_buffers(self.h, C.byref(ps), C.byref(pa), C.byref(ns), C.byref(na)), self.h)
+
+        class _View:  # a device buffer described by the CUDA array interface
+            def __init__(self, ptr, shape):
+                self.__cuda_array_interface__ = {"data": (ptr, False), "shape": shape, "typestr": "<f8",
+                                                 "version": 3, "strides": None, "stream": None}
+
+        src = None
+        if ns.value > 0:
+            assert ns.value == self.ncell * n_cam * 4
+            src = torch.as_tensor(_View(ps.value, (self.ncell, n_cam, 4)), device="cuda")
+        ab = torch.as_tensor(_View(pa.value, (na.value,)), device="cuda")
+        return src, ab
 
     def close(self):
         if getattr(self, "h", None):
@@ -524,15 +549,17 @@ class Surrogate:
                                            C.c_void_p(out.ctypes.data)))
         return out
 
-    def grad(self, inputs, targets, loss_weights=None):
+    def grad(self, inputs, targets, loss_weights=None, precision="bf16"):
+        """Loss and per-layer gradients (mcrt_surrogate_grad; precision "fp32":
+        mcrt_surrogate_grad_fp32)."""
+        fn = lib().mcrt_surrogate_grad_fp32 if precision == "fp32" else lib().mcrt_surrogate_grad
         x = np.ascontiguousarray(np.asarray(inputs, dtype=np.float32))
         t = np.ascontiguousarray(np.asarray(targets, dtype=np.float32))
         w = None if loss_weights is None else np.ascontiguousarray(np.asarray(loss_weights, dtype=np.float32))
         g = np.zeros(self.n_params, dtype=np.float32)
         loss = C.c_double()
-        _check(lib().mcrt_surrogate_grad(self.h, x.shape[0], C.c_void_p(x.ctypes.data), C.c_void_p(t.ctypes.data),
-                                         C.c_void_p(w.ctypes.data) if w is not None else None,
-                                         C.c_void_p(g.ctypes.data), C.byref(loss)))
+        _check(fn(self.h, x.shape[0], C.c_void_p(x.ctypes.data), C.c_void_p(t.ctypes.data),
+                  C.c_void_p(w.ctypes.data) if w is not None else None, C.c_void_p(g.ctypes.data), C.byref(loss)))
         return loss.value, self.unflatten(g)
 
     def error_map(self, n_samples=1 << 22):

@@ -43,7 +43,9 @@ Workloads (sizes as stated):
 The grain tables are synthetic (no measured optical constants are available): per bin
 a Henyey-Greenstein P11, P12/P11 = -p (1-c^2)/(1+c^2), P22 = P11,
 P33/P11 = P44/P11 = 2c/(1+c^2), P34 = 0, which is a realizable scattering matrix for
-0 <= p <= 1.
+0 <= p <= 1.  Their extinction has the dipole form alpha1 = 1, alpha2 = -p_max sin^2
+theta' with p_max from 0.1 (smallest bin) to 0.02 (largest); the mixture's table holds
+the extinction-weighted mean of the bins' p_max.
 """
 from __future__ import annotations
 
@@ -145,9 +147,19 @@ def rayleigh_table(n_theta=N_THETA):
     return tab.astype(np.float32)
 
 
-def table_optics(n_bins=8, p_max=0.05):
+def bin_p_max(n_bins=8):
+    """Dichroism of the synthetic size bins: p_max from 0.1 (smallest grains) to 0.02."""
+    return np.linspace(0.1, 0.02, n_bins)
+
+
+def table_optics(n_bins=8, p_max=None):
+    """Synthetic bin tables with the dipole extinction form.  ``p_max`` None: each bin
+    k has its own alpha2 = -p_max,k sin^2 theta' (``bin_p_max``); the table given is
+    that of the mixture, the bins weighted by their share of the extinction (all bins
+    share the cell's albedo, so that share is ``bin_weight``).  A number: one p_max."""
     tabs, w, _ = synthetic_bins(n_bins)
-    return {"model": "table", "mueller": tabs, "bin_weight": w, "kext": kext_dipole(p_max)}
+    p = float(np.dot(w.astype(np.float64), bin_p_max(n_bins))) if p_max is None else float(p_max)
+    return {"model": "table", "mueller": tabs, "bin_weight": w, "kext": kext_dipole(p)}
 
 
 # ----------------------------------------------------------------------------------
@@ -316,7 +328,7 @@ def _disk_fields(x, y, z, tau_mid, r_in, r_out, albedo, pitch_deg, T0, lam_um):
 
 
 def disk(n=192, tau_mid=1e3, r_in=0.1, r_out=1.0, albedo=0.6, pitch_deg=30.0, T0=1000.0,
-         lam_um=1.0, n_bins=8, p_max=0.05):
+         lam_um=1.0, n_bins=8, p_max=None):
     """Flared disk; see the module docstring."""
     lo, hi = (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0)
     x, y, z = cell_centres((n, n, n), lo, hi)
@@ -327,7 +339,7 @@ def disk(n=192, tau_mid=1e3, r_in=0.1, r_out=1.0, albedo=0.6, pitch_deg=30.0, T0
 
 
 def disk_refined(n=128, box=None, factor=4, tau_mid=1e3, r_in=0.1, r_out=1.0, albedo=0.6, pitch_deg=30.0,
-                 T0=1000.0, lam_um=1.0, n_bins=8, p_max=0.05):
+                 T0=1000.0, lam_um=1.0, n_bins=8, p_max=None):
     """Flared disk on a composite grid: an n^3 root grid plus one statically refined
     patch over root-cell box `box` (default: the inner quarter of x and y, the middle
     eighth of z) with `factor` cells per root cell, the disk's fields evaluated at the

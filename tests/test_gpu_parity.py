@@ -12,6 +12,7 @@ import math
 import numpy as np
 import pytest
 
+from accuracy_report import integrated_error, record
 from oracle import oracle as O
 from paper_2512_01283_gb300 import build as B
 from paper_2512_01283_gb300 import mcrt as M
@@ -170,13 +171,13 @@ def test_dichroic_slab_full_size(tau):
     tr = g["trace"]
     I = tr[:, 0] / tr[:, 13]
     ref_I = math.exp(-t) * math.cosh(p * t)
-    assert np.allclose(I, ref_I, rtol=2e-5)
+    assert np.allclose(I, ref_I, rtol=1e-5, atol=0.0)
     assert np.allclose(tr[:, 1] / tr[:, 0], math.tanh(p * t), rtol=1e-5, atol=64 * 2.0 ** -24)
     assert np.all(np.abs(tr[:, 2:4]) <= 1e-6 * tr[:, :1])
-    assert abs(st["escaped_energy"] - ref_I) < 2e-5 * ref_I + 1e-9
+    assert abs(st["escaped_energy"] - ref_I) < 1e-5 * ref_I
     assert abs(st["absorbed_energy"] + st["escaped_energy"] - 1.0) < 1e-5
     o = oracle_run(model, dict(run, pid_end=256), n_trace=256, images=False)
-    assert trace_match_fraction(tr, o["trace"], 2e-5) == 1.0
+    assert trace_match_fraction(tr, o["trace"], 1e-5) == 1.0
 
 
 # absolute floors in Q/I: FP32 = 64 cells x 2^-24 (one rounding of Q per cell),
@@ -262,17 +263,23 @@ def test_rayleigh_sphere_chi2_independent_seeds(sphere_oracle):
 # flared disk with grain tables, star + thermal emission
 # ---------------------------------------------------------------------------------
 def test_small_disk_parity():
+    """24^3 disk, star + thermal, 4 cameras, 1e5 packets: traces (>= 99.9 % FP64, 99 %
+    FP32: the optically thick disk flips more FP32 decisions), integrated image Stokes
+    within 1e-3 of the total I, energy balance."""
     model = W.disk(n=24)
-    run = W.disk_run(n_packets=20_000, n_cam=4, npix=32)
-    o = oracle_run(model, run, n_trace=20_000)
+    n = 100_000
+    run = W.disk_run(n_packets=n, n_cam=4, npix=32)
+    o = oracle_run(model, run, n_trace=n, n_threads=16)
     for prec in ("fp64", "fp32"):
-        g = gpu_run(model, run, prec, n_trace=20_000)
+        g = gpu_run(model, run, prec, n_trace=n)
         frac = trace_match_fraction(g["trace"], o["trace"], 1e-4)
         assert frac >= (0.999 if prec == "fp64" else 0.99), (prec, frac)
-        for k in range(4):
-            Itot = o["images"][k][0].sum()
-            for e in range(4):
-                assert abs(g["images"][k][e].sum() - o["images"][k][e].sum()) < 2e-3 * Itot, (prec, k, e)
+        err = integrated_error(g["images"], o["images"])
+        record("flared disk 24^3, star + thermal, 4 cameras, 1e5 packets, " + prec, "max integrated |dX|/I", err,
+               1e-3)
+        record("flared disk 24^3, star + thermal, 4 cameras, 1e5 packets, " + prec, "trace match fraction at 1e-4",
+               frac, 0.999 if prec == "fp64" else 0.99, "min")
+        assert err < (1e-9 if prec == "fp64" else 1e-3), (prec, err)
         st = g["stats"]
         bal = st["escaped_energy"] + st["absorbed_energy"] + st["roulette_lost"] - st["roulette_gain"] + st["cap_lost"]
         assert abs(bal - st["emitted_energy"]) < (1e-9 if prec == "fp64" else 1e-5) * st["emitted_energy"]
@@ -336,16 +343,16 @@ def test_eight_sources_with_empty_and_single_packet_sources(prec):
     model["optics"] = W.table_optics(n_bins=2)
     sources = [{"type": "point", "pos": (0.3, 0.6, 0.5), "luminosity": 2.0, "n_packets": 0},
                {"type": "beam", "beam_dir": 1, "luminosity": 1.0, "n_packets": 1},
-               {"type": "point", "pos": (0.5, 0.5, 0.5), "luminosity": 0.7, "n_packets": 337},
+               {"type": "point", "pos": (0.5, 0.5, 0.5), "luminosity": 0.7, "n_packets": 33_700},
                {"type": "thermal", "luminosity": 0.0, "n_packets": 0},
-               {"type": "beam", "beam_dir": -1, "luminosity": 0.4, "n_packets": 95},
-               {"type": "point", "pos": (0.81, 0.22, 0.13), "luminosity": 1.3, "n_packets": 1000},
-               {"type": "thermal", "luminosity": 0.0, "n_packets": 640},
+               {"type": "beam", "beam_dir": -1, "luminosity": 0.4, "n_packets": 9_500},
+               {"type": "point", "pos": (0.81, 0.22, 0.13), "luminosity": 1.3, "n_packets": 100_000},
+               {"type": "thermal", "luminosity": 0.0, "n_packets": 64_000},
                {"type": "point", "pos": (0.05, 0.95, 0.5), "luminosity": 0.1, "n_packets": 3}]
     n = sum(s["n_packets"] for s in sources)
     run = {"sources": sources, "cameras": [W.camera((0.3, 0.2, 0.93), (9, 9), (1.2, 1.2), center=(0.5, 0.5, 0.5))],
            "seed": 21, "roulette_threshold": 1e-4, "roulette_survival": 0.1}
-    o = oracle_run(model, run, n_trace=n, n_threads=4)
+    o = oracle_run(model, run, n_trace=n, n_threads=16)
     g = gpu_run(model, run, prec, n_trace=n)
     # every packet is born at the source its id falls in
     assert np.array_equal(g["trace"][:, 14], o["trace"][:, 14])
@@ -355,9 +362,10 @@ def test_eight_sources_with_empty_and_single_packet_sources(prec):
     tol = 1e-7 if prec == "fp64" else 2e-3
     assert np.linalg.norm(g["S"] - o["S"]) < tol * np.linalg.norm(o["S"])
     assert g["stats"]["emitted_energy"] == pytest.approx(o["stats"]["emitted_energy"], rel=1e-6)
-    Itot = o["images"][0][0].sum()
-    for e in range(4):
-        assert abs(g["images"][0][e].sum() - o["images"][0][e].sum()) < max(tol, 1e-9) * Itot
+    err = integrated_error(g["images"], o["images"])
+    record("eight sources, 8^3 slab, 2 bins, 2.07e5 packets, " + prec, "max integrated |dX|/I", err, 1e-3)
+    # FP64: the cell record keeps the grain quaternion of the 35-degree field in FP32
+    assert err < (1e-7 if prec == "fp64" else 1e-3), err
     m = M.Model(model)
     with pytest.raises(M.McrtError) as err:
         M.launch(m, dict(run, sources=sources + [sources[2]]))
@@ -571,6 +579,27 @@ def test_rank_shares_and_the_tally_exchange():
     for k in range(2):
         out = np.zeros((4, 16, 16))
         m0.image(k, out)
+        assert np.allclose(out, ref["images"][k], rtol=1e-9, atol=1e-12 * np.abs(ref["images"][k]).max())
+    for m in mods:
+        m.close()
+    # the same sum in place on the library's own buffers (mcrt_tally_buffers), as the
+    # NCCL all-reduce of a sharded run does it
+    mods = []
+    for r in range(2):
+        m = M.Model(model)
+        MG.rank_launch(lambda rr, acc: M.launch(m, rr, precision="fp32", accumulate=acc), run, r, 2)
+        mods.append(m)
+    (S0v, A0v), (S1v, A1v) = mods[0].tally_tensors(2), mods[1].tally_tensors(2)
+    assert S0v.shape == (mods[0].ncell, 2, 4) and A0v.shape == (mods[0].ncell,)
+    S0v.add_(S1v)
+    A0v.add_(A1v)
+    torch.cuda.synchronize()
+    S0, A0 = mods[0].tallies(2)
+    assert np.allclose(S0, ref["S"], rtol=1e-9, atol=1e-12 * np.abs(ref["S"]).max())
+    assert np.allclose(A0, ref["absorbed"], rtol=1e-6, atol=1e-9 * np.abs(ref["absorbed"]).max())
+    for k in range(2):
+        out = np.zeros((4, 16, 16))
+        mods[0].image(k, out)
         assert np.allclose(out, ref["images"][k], rtol=1e-9, atol=1e-12 * np.abs(ref["images"][k]).max())
     for m in mods:
         m.close()
