@@ -154,6 +154,8 @@ struct WaveCtl {
     unsigned long long n_resume;       // packets to resume in the current transport launch
     unsigned long long n_resume_next;  // packets written to the resume buffer by the scattering kernel
     unsigned long long n_suspend;      // packets suspended at a scattering by the current launch
+    unsigned long long n_born;         // table rounds: new packets the birth kernel stored after the
+                                       // resume list (packets born outside the grid are not stored)
     unsigned long long n_rec[2];       // tally records requested per record buffer (the table
                                        // rounds alternate two buffers; the surrogate uses [0])
     unsigned long long full;           // the record queue passed its soft limit: packets park
@@ -227,6 +229,9 @@ struct ImageParams {
 
 // launchers (defined in the .cu files)
 cudaError_t launch_transport(const TransportParams& p, int precision, int block, int grid, cudaStream_t s);
+// Births of a round of the FP32 table path (k_birth): the round's new packets in the
+// waiting form after the resume list, before the round's transport launch.
+cudaError_t launch_births(const TransportParams& p, int n_sm, cudaStream_t s);
 const void* transport_kernel(int precision, int model, bool batch, bool refined = false);
 int transport_max_blocks_per_sm(int precision, int model, bool batch, int block, size_t smem, bool refined = false);
 size_t transport_smem_bytes(const TransportParams& p, int precision, int block);

@@ -1008,7 +1008,10 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
     const unsigned long long t0 = global_ns();
     // surrogate path: packets resumed after their scattering, then new packets
     unsigned long long w_resume = 0, w_new = 0, w_next = 0;
-    if constexpr (round_based(SCAT)) {
+    if constexpr (SCAT == kScatTableDeferred) {
+        // table rounds: the birth kernel stored the round's new packets after the resume list
+        w_resume = P.sur.ctl->n_resume + P.sur.ctl->n_born;
+    } else if constexpr (round_based(SCAT)) {
         w_resume = P.sur.ctl->n_resume;
         w_new = P.sur.ctl->n_new;
         w_next = P.sur.ctl->next_pid;
@@ -1045,10 +1048,13 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
                         }
                         alive = true;
                     }
-                } else if (idx - w_resume < w_new) {
-                    const long long pid = P.pid_begin + (long long)(w_next + (idx - w_resume));
-                    alive = emit<T, false, R>(P, jr, pid, pk, bt);
-                    pk.park = false;
+                } else if (SCAT != kScatTableDeferred && idx - w_resume < w_new) {
+                    // the surrogate path emits here; the table rounds hold no birth code
+                    if constexpr (SCAT != kScatTableDeferred) {
+                        const long long pid = P.pid_begin + (long long)(w_next + (idx - w_resume));
+                        alive = emit<T, false, R>(P, jr, pid, pk, bt);
+                        pk.park = false;
+                    }
                 } else {
                     pool_done = true;
                 }
@@ -1120,7 +1126,59 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
     }
 }
 
+// Births of a round of the FP32 table path, in a kernel of their own: one thread per
+// new packet of the round (so births run with every lane busy and their thermal-cell
+// searches overlap), each born packet stored in the 128-byte waiting form after the
+// packets resumed from the previous round, where the round's transport kernel takes it
+// like a resumed one.  The transport kernel of the table rounds thus holds no birth
+// code.  The packet is the one emit() gives inside the transport kernel: the same
+// random numbers and FP32 values (the waiting form keeps them exactly), so the
+// trajectories do not change.  Packets that start outside the grid are finished here.
+constexpr int kBirthBlock = 256;
+
+template <bool R> __global__ void __launch_bounds__(kBirthBlock) k_birth(const __grid_constant__ TransportParams P) {
+    __shared__ BlockTotals bt;
+    if (threadIdx.x < 6) bt.e[threadIdx.x] = 0.0;
+    if (threadIdx.x < 10) bt.n[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) bt.status = 0u;
+    __syncthreads();
+    const unsigned long long n_new = P.sur.ctl->n_new, first = P.sur.ctl->n_resume, next = P.sur.ctl->next_pid;
+    const JobRef<float, false> jr{P, P.t.kext, P.t.mix};
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_new;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        Packet<float> pk;
+        pk.job = nullptr;
+        const long long pid = P.pid_begin + (long long)(next + i);
+        if (emit<float, false, R>(P, jr, pid, pk, bt)) {
+            cg::coalesced_group grp = cg::coalesced_threads();
+            unsigned long long base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->n_born, (unsigned long long)grp.size());
+            base = grp.shfl(base, 0);
+            store_state(P.sur.resume + (first + base + grp.thread_rank()) * kStateF4, pk, 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        if (bt.e[threadIdx.x] != 0.0) atomicAdd(&P.stats[threadIdx.x], bt.e[threadIdx.x]);
+    } else if (threadIdx.x < 16) {
+        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(P.stats + 6);
+        if (bt.n[threadIdx.x - 6]) atomicAdd(&cnt[threadIdx.x - 6], bt.n[threadIdx.x - 6]);
+    } else if (threadIdx.x == 16 && bt.status) {
+        atomicOr(P.status, bt.status);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_births(const TransportParams& p, int n_sm, cudaStream_t s) {
+    (void)cudaGetLastError();
+    const int grid = n_sm * 8;
+    if (p.g.n_patches > 0)
+        k_birth<true><<<grid, kBirthBlock, 0, s>>>(p);
+    else
+        k_birth<false><<<grid, kBirthBlock, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 size_t transport_smem_bytes(const TransportParams& p, int precision, int block) {
     const bool batch = p.jobs != nullptr;

@@ -98,6 +98,7 @@ __global__ void k_wave_begin(WaveCtl* c, unsigned long long total, unsigned long
     c->n_new = left < room ? left : room;
     c->claim = 0;
     c->n_suspend = 0;
+    c->n_born = 0;
     c->n_rec[slot] = 0;
     c->full = 0;
     c->cnt[kCntIterations] += 1;
@@ -645,10 +646,12 @@ __global__ void __launch_bounds__(kTabBlock) k_tab_tally(const __grid_constant__
                 const PlaneRot<float> pr = plane_rotation(n, th, ph, Om, thc, phc);
                 apply_plane(pr, Pm, W, Y);
                 // lanes 4-7 of each group of 8 store their second half first, so that each
-                // quarter-warp phase of 16-byte stores covers the 8 bank groups once
+                // quarter-warp phase of 16-byte stores covers the 8 bank groups once.  The
+                // FP32 -> FP64 conversions run on the FP64 pipe, idle in this kernel (the
+                // integer-only widening would add to its busiest pipes)
                 double2* d2 = reinterpret_cast<double2*>(stage + lane * 4);
-                const double2 lo2 = make_double2(widen(Y[0]), widen(Y[1]));
-                const double2 hi2 = make_double2(widen(Y[2]), widen(Y[3]));
+                const double2 lo2 = make_double2((double)Y[0], (double)Y[1]);
+                const double2 hi2 = make_double2((double)Y[2], (double)Y[3]);
                 const int h = (lane >> 2) & 1;
                 d2[h] = h ? hi2 : lo2;
                 d2[1 - h] = h ? lo2 : hi2;
@@ -722,6 +725,7 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
         k_wave_begin<<<1, 1, 0, s>>>(p.sur.ctl, total, C, sur ? 0 : 1, 0);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(ek[0], s);
+        if (e == cudaSuccess && !sur) e = launch_births(p, n_sm, s);
         if (e == cudaSuccess) e = launch_transport(p, MCRT_FP32, block, tgrid, s);
         if (e == cudaSuccess) e = cudaEventRecord(ek[1], s);
         if (e == cudaSuccess) {
@@ -839,6 +843,7 @@ cudaError_t run_table_rounds_overlapped(const TransportParams& p_in, int n_sm, u
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(tb, s);
+        if (e == cudaSuccess) e = launch_births(p, n_sm, s);
         if (e == cudaSuccess) e = launch_transport(p, MCRT_FP32, 128, tgrid, s);
         if (e == cudaSuccess) e = cudaEventRecord(te, s);
         // this round's tally runs beside the next round's transport
