@@ -36,12 +36,16 @@ constexpr int kDefaultBlock = 128;
 #define MCRT_MIN_BLOCKS 5
 #endif
 // lanes of a warp that wait before the warp runs the scattering code (or takes new
-// packets) for all of them at once.  Measured on GB300: the table rounds of the 192^3
-// disk run fastest with 4 and 4 (1.00 s per 1e8-packet step; 1.05 s with 8 and 4, 1.08 s
-// with 1 and 1), the batched launch of the 256-job sweep with 8 and 4 (9.4e9 events/s;
-// 8.7e9 with 4 and 4, 7.5e9 with 1 and 1)
+// packets) for all of them at once.  Measured on GB300: the in-place kernels run fastest
+// with 4 and 4; the table rounds of the 192^3 disk, whose births run in a kernel of their
+// own, with 6 scatterings (transport 718 ms per 1e8-packet step, against 728 with 4 and
+// 738 with 3) and 4 resumed packets (752 ms with 1 or 8); the batched launch of the
+// 256-job sweep with 8 and 4 (9.4e9 events/s; 8.7e9 with 4 and 4, 7.5e9 with 1 and 1)
 #ifndef MCRT_SCATTER_BATCH
 #define MCRT_SCATTER_BATCH 4
+#endif
+#ifndef MCRT_SCATTER_BATCH_ROUNDS
+#define MCRT_SCATTER_BATCH_ROUNDS 6
 #endif
 #ifndef MCRT_SCATTER_BATCH_JOBS
 #define MCRT_SCATTER_BATCH_JOBS 8
@@ -49,7 +53,9 @@ constexpr int kDefaultBlock = 128;
 #ifndef MCRT_REFILL_BATCH
 #define MCRT_REFILL_BATCH 4
 #endif
-template <bool B> constexpr int scatter_batch() { return B ? MCRT_SCATTER_BATCH_JOBS : MCRT_SCATTER_BATCH; }
+template <bool B, int SCAT> constexpr int scatter_batch() {
+    return B ? MCRT_SCATTER_BATCH_JOBS : (SCAT == kScatTableDeferred ? MCRT_SCATTER_BATCH_ROUNDS : MCRT_SCATTER_BATCH);
+}
 // per-thread staging slot for the TMA bulk reduction of one segment's source
 // contributions: up to 8 cameras x 4 Stokes FP64 (256 B), padded to 272 B so that
 // the 16-byte stores of a warp spread over all shared-memory banks
@@ -1095,7 +1101,7 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
             continue;
         }
         // scatterings of the warp run together once enough lanes wait for one
-        if (pend != 0u && (__popc(pend) >= scatter_batch<B>() || work == 0u)) {
+        if (pend != 0u && (__popc(pend) >= scatter_batch<B, SCAT>() || work == 0u)) {
             if constexpr (SCAT != kScatSurrogate) {  // the surrogate scatters in its own kernel
                 if (alive && pk.pending) {
                     pk.pending = false;
