@@ -597,10 +597,13 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
         // absorbed energy, one FP64 atomic per same-cell group
         {
             const unsigned gmax = kGroups ? __reduce_max_sync(actA, (unsigned)__popc(group)) : 1u;
+            // the absorbed energy is int (K_abs X)_0 dl = kappa_ext (a W_I + (a2 - s12) W_Q) over the
+            // segment, from the path integral where it is computed: I0 - I1 would cancel in
+            // optically thin cells (FP32: nothing absorbed below dtau ~ 6e-8).  For aligned
+            // spheroids the decrease of I also holds kappa_ext s12 int Q dl, which the scattering
+            // weight returns in expectation, hence a2 - s12.
             T dI = pk.X0 - Yg[0];
-            // aligned spheroids: the decrease of I also holds kappa_ext s12 int Q dl, which the
-            // scattering weight returns in expectation; the absorbed energy is int (K_abs X)_0 dl
-            if constexpr (SCAT == MCRT_SCAT_DIPOLE) dI -= kext * s12 * Wg[1];
+            if (want_S || SCAT == MCRT_SCAT_DIPOLE) dI = kext * (a * Wg[0] + (a2 - s12) * Wg[1]);
             pk.e_abs += dI;
             if (dI != T(0)) pk.n_abs++;
             if (gmax > 1u) dI = group_sum(actA, group, dI, gmax);

@@ -260,9 +260,12 @@ def test_disk64_table_rounds_accuracy(disk_oracle):
         c, dof = chi2(ind, orc, "S", e, mask)
         record(cfg, "chi2/dof per cell of the source tally, " + name, c, 1.2)
         assert c < 1.2, (name, c, dof)
+    # cells whose absorbed energy is known to 30 % and exceeds 1e-12 of the largest cell's:
+    # below that floor the absorption along a segment (dtau < 1e-16) vanishes in the FP64
+    # oracle's I0 - I1, while the kernels take it from the path integral
     va = ind.var_of_mean("A") + orc.var_of_mean("A")
     ma = 0.5 * (ind.mean("A") + orc.mean("A"))
-    m = (va > 0) & (np.sqrt(va) < 0.3 * ma)
+    m = (va > 0) & (np.sqrt(va) < 0.3 * ma) & (ma > 1e-12 * ma.max())
     ca = float(np.sum((ind.mean("A") - orc.mean("A"))[m] ** 2 / va[m]) / m.sum())
     record(cfg, "chi2/dof per cell of the absorbed tally", ca, 1.2)
     assert ca < 1.2, ca
