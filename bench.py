@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--sur-steps", type=int, default=1, help="timed launches of the surrogate path")
     ap.add_argument("--sur-train-samples", type=float, default=2e7, help="training samples of the network")
     ap.add_argument("--sur-bound", type=float, default=0.05, help="error-map bound of the table fallback")
+    ap.add_argument("--fixed-error-measured", action="store_true",
+                    help="surrogate line: run both paths to a fixed map error against a 10-launch table reference")
     return ap.parse_args()
 
 
@@ -401,7 +403,65 @@ def fixed_error(t1, t2, s1, s2, packets, table_s, sur_s, targets=(0.01, 0.02, 0.
     return out
 
 
-def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_value, table_step_s):
+def fixed_error_measured(M, torch, mdl_t, mdl_s, run, n_cam, npix, n_ref=10, targets=(0.05, 0.03), n_max=1.6e8):
+    """Both paths run to a fixed map error, measured: a reference of n_ref table launches
+    of the run's packets (seeds 7000 + k, 10^9 packets at the default size), then each
+    path at 1e7, 2e7, 4e7, ... packets (fresh seeds) until its I map is within the
+    smallest target of the reference.  The error of a map is the relative L2 difference
+    of its I maps (and of its Q, U maps against I) from the reference's, over the
+    cameras; the reference's own Monte-Carlo noise (its batch spread / sqrt(n_ref)) is
+    taken out in quadrature.  Seconds are each path's measured launch times."""
+    total = sum(int(src["n_packets"]) for src in run["sources"])
+
+    def images(m, r, optics):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        M.launch(m, r, precision="fp32", optics=optics)
+        out = np.zeros((n_cam, 4, npix[1], npix[0]))
+        for k in range(n_cam):
+            m.image(k, out[k])
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    refs = [images(mdl_t, dict(run, seed=7000 + k), "tables")[0] for k in range(n_ref)]
+    ref = np.mean(refs, axis=0)
+    nI = np.sum(ref[:, 0] ** 2, axis=(1, 2))
+    var_ref = np.var(refs, axis=0, ddof=1) / n_ref
+    noise_I = float(np.mean(np.sum(var_ref[:, 0], axis=(1, 2)) / nI))
+    noise_QU = float(np.mean(np.sum(var_ref[:, 1:3], axis=(1, 2, 3)) / nI))
+
+    def errors(img):
+        dI = float(np.mean(np.sum((img[:, 0] - ref[:, 0]) ** 2, axis=(1, 2)) / nI))
+        dQU = float(np.mean(np.sum((img[:, 1:3] - ref[:, 1:3]) ** 2, axis=(1, 2, 3)) / nI))
+        return max(0.0, dI - noise_I) ** 0.5, max(0.0, dQU - noise_QU) ** 0.5
+
+    out = {"reference": {"packets": n_ref * total, "I_noise": noise_I ** 0.5, "QU_noise": noise_QU ** 0.5}}
+    for name, m, optics in (("table", mdl_t, "tables"), ("surrogate", mdl_s, "surrogate")):
+        runs, n, k = [], 1e7, 0
+        while n <= n_max:
+            half = int(n) // 2
+            r = dict(run, seed=8000 + 100 * k + (0 if name == "table" else 50),
+                     sources=[dict(run["sources"][0], n_packets=half),
+                              dict(run["sources"][1], n_packets=int(n) - half)])
+            img, sec = images(m, r, optics)
+            eI, eQU = errors(img)
+            runs.append({"packets": int(n), "seconds": sec, "I_error": eI, "QU_error": eQU})
+            if eI <= min(targets) and eQU <= min(targets):
+                break
+            n *= 2
+            k += 1
+        reach = {}
+        for eps in targets:
+            hit = [x for x in runs if x["I_error"] <= eps and x["QU_error"] <= eps]
+            reach["%g" % eps] = hit[0] if hit else None
+        out[name] = {"runs": runs, "first_within": reach}
+    for eps in targets:
+        a, b = out["table"]["first_within"]["%g" % eps], out["surrogate"]["first_within"]["%g" % eps]
+        out["table_over_surrogate_time_%g" % eps] = (a["seconds"] / b["seconds"]) if (a and b) else None
+    return out
+
+
+def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_value, table_step_s, table_mdl=None):
     """The same disk with the grain optics from the MLP surrogate: trained here on the
     tables (2e7 samples), table fallback above the error-map bound; throughput and
     the images' difference from the table path's, next to the table path's own
@@ -482,6 +542,8 @@ def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_v
                            "surrogate_vs_surrogate_other_seed": image_diff(imgs2, imgs)},
            "fixed_error": fixed_error(table_imgs, other, imgs, imgs2, args.packets, table_step_s,
                                       wall / args.sur_steps),
+           "fixed_error_measured": (fixed_error_measured(M, torch, table_mdl, mdl, run, n_cam, npix)
+                                    if args.fixed_error_measured else None),
            "gpu_launches_per_step": int(st["wave_iterations"]) * 4 + n_cam}
     sur.close()
     mdl.close()
@@ -743,7 +805,7 @@ def main():
                 mdl.image(k, out[k])
 
         line["surrogate"] = run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, value,
-                                          ms_max / args.steps * 1e-3)
+                                          ms_max / args.steps * 1e-3, table_mdl=mdl)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1

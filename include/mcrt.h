@@ -74,8 +74,9 @@ enum { MCRT_OPTICS_TABLES = 0, MCRT_OPTICS_SURROGATE = 1 };
 enum {
     MCRT_FLAG_INLINE_TALLY = 1,  /* FP32 table launches: tally inside the transport kernel instead of the
                                     default rounds (transport, then a tally kernel over the queued segments) */
-    MCRT_FLAG_MMA_SYNC_TALLY = 2 /* surrogate launches: the network of the tally on warp-level mma.sync
-                                    instead of the default 5th-generation tensor cores (tcgen05) */
+    MCRT_FLAG_MMA_SYNC_TALLY = 2 /* surrogate launches: the network of the tally and of the rejection
+                                    trials on warp-level mma.sync instead of the default
+                                    5th-generation tensor cores (tcgen05) */
 };
 enum { MCRT_MAX_SOURCES = 8, MCRT_MAX_CAMERAS = 16 };
 

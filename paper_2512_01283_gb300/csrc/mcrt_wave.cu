@@ -595,6 +595,297 @@ __global__ void __launch_bounds__(kWaveBlock, 1) k_sur_scatter(const __grid_cons
     flush_counters(P.sur.ctl, s_cnt, v, 4, which);
 }
 
+// The rejection trials of the waiting packets on the 5th-generation tensor cores: a CTA
+// of kScatGroups groups of 128 threads (the engine of mcrt_mlp_tc.cuh, one weight copy per
+// CTA); a group takes 128 waiting packets at a time, thread k owning packet k.  Every
+// round the unresolved packets share the group's 128 trial rows -- packet k takes trials
+// t_k .. t_k + T - 1 with T = 128 / (unresolved packets), at most 8 -- each row a proposal with the
+// table path's Philox counters, envelope and angles, and the network evaluates all 128
+// rows in one tile; each packet then takes its first accepted trial in trial order,
+// which is the sequential rule.  The decisions are those of k_sur_scatter up to the FP32
+// summation order of the two tensor-core engines.
+constexpr int kScatGroups = 2;
+constexpr int kScatPk = tc::kRows;  // one packet per thread of the group
+struct ScatPkt {     // a waiting packet as its trial rows read it (shared memory)
+    float n[3], th[3], ph[3], g[3];  // direction, its Stokes basis, the direction in the grain frame
+    float4 q;                        // grain quaternion of the packet's cell
+    float X[4];
+    float sk;                        // size coordinate of the drawn bin
+    int bin, t_next, want;           // want: live and not yet resolved
+    int slot_owner;                  // entry k: the k-th unresolved packet
+    unsigned pid_lo, pid_hi, n_sca;
+};
+struct ScatRow {     // a trial's outcome (over the activation tile once the network is done)
+    float Y[4], n2[3];
+    int acc;
+};
+constexpr size_t kScatTcSmem = tc::smem_bytes(kScatGroups) + kScatGroups * kScatPk * sizeof(ScatPkt);
+static_assert(sizeof(ScatRow) * tc::kRows <= (size_t)tc::kActBytes, "trial rows fit in the activation tile");
+
+__global__ void __launch_bounds__(tc::kRows * kScatGroups, 1) k_sur_scatter_tc(const __grid_constant__ TransportParams P) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) unsigned long long mbar[kScatGroups];
+    __shared__ unsigned tmem_slot;
+    __shared__ BlockTotals bt;
+    __shared__ unsigned long long s_cnt[4];
+    __shared__ int n_unres[kScatGroups][tc::kRows / 32];
+    if (threadIdx.x < 6) bt.e[threadIdx.x] = 0.0;
+    if (threadIdx.x < 10) bt.n[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) bt.status = 0u;
+    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0ull;
+    const tc::Group g = tc::setup(kScatGroups, sm, P.sur.image_tc, mbar, &tmem_slot);  // ends with a barrier
+    const int t = g.t, gi = threadIdx.x / tc::kRows;
+    ScatPkt* pkt = reinterpret_cast<ScatPkt*>(sm + tc::smem_bytes(kScatGroups)) + gi * kScatPk;
+    ScatRow* rows = reinterpret_cast<ScatRow*>(g.act);
+    const TablesDev& tabs = P.t;
+    const int nint = tabs.n_theta - 1;
+    const float widen_env = 1.f + P.sur.env_margin;
+    const unsigned long long nsus = P.sur.ctl->n_suspend;
+    const unsigned long long nbatch = (nsus + kScatPk - 1) / kScatPk;
+    unsigned long long c_rows = 0, c_map = 0, c_real = 0, c_miss = 0;
+    unsigned phase = 0;
+    bool failed = false;
+    for (unsigned long long batch = (unsigned long long)blockIdx.x * kScatGroups + gi; batch < nbatch;
+         batch += (unsigned long long)gridDim.x * kScatGroups) {
+        Packet<float> pk;
+        pk.X0 = pk.X1 = pk.X2 = pk.X3 = 0.f;
+        pk.pid = 0;
+        pk.n_sca = 0;
+        bool live = false, resolved = false;
+        float us_a = 0.5f, us_d = 0.5f;
+        V3<float> n2s{0.f, 0.f, 1.f};
+        float Ys[4] = {0.f, 0.f, 0.f, 0.f};
+        if (t < kScatPk) {
+            const unsigned long long i = batch * kScatPk + (unsigned)t;
+            const bool parked = i < nsus && __float_as_uint(P.sur.suspend[i * kStateF4 + 7].y) != 0u;
+            if (parked) {
+                // stopped inside its flight: straight to the resume buffer
+                cg::coalesced_group grp = cg::coalesced_threads();
+                unsigned long long base = 0;
+                if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->n_resume_next, (unsigned long long)grp.size());
+                base = grp.shfl(base, 0);
+                const float4* src = P.sur.suspend + i * kStateF4;
+                float4* dst = P.sur.resume + (base + grp.thread_rank()) * kStateF4;
+#pragma unroll
+                for (int e = 0; e < kStateF4; ++e) dst[e] = src[e];
+            }
+            ScatPkt& sp = pkt[t];
+            sp.want = 0;
+            sp.t_next = 0;
+            if (i < nsus && !parked) {
+                load_state(P.sur.suspend + i * kStateF4, pk);
+                const Draw4<float> us = draw4<float>(pk.pid, pk.n_sca, 0u, P.seed, P.stream);
+                us_a = us.a;
+                us_d = us.d;
+                live = true;
+                if (P.roulette_thr > 0.0 && (double)pk.X0 < P.roulette_thr * (double)pk.I_birth) {
+                    if ((double)us.b < P.roulette_surv) {
+                        const float gmul = (float)(1.0 / P.roulette_surv);
+                        pk.e_gain += pk.X0 * (gmul - 1.f);
+                        pk.X0 *= gmul;
+                        pk.X1 *= gmul;
+                        pk.X2 *= gmul;
+                        pk.X3 *= gmul;
+                    } else {
+                        finish(P, pk, 2, bt);
+                        live = false;
+                    }
+                }
+                if (live) {
+                    int bin = tabs.n_bins - 1;
+                    for (int k = 0; k < tabs.n_bins; ++k)
+                        if (us.c < tabs.bin_cdf_f[k]) {
+                            bin = k;
+                            break;
+                        }
+                    const long long c = ((long long)pk.iz * P.g.n[1] + pk.iy) * P.g.n[0] + pk.ix;
+                    const float4 q = __ldg(&P.g.cells[2 * c]);
+                    const V3<float> n{pk.nx, pk.ny, pk.nz};
+                    V3<float> th, ph;
+                    stokes_basis(n, th, ph);
+                    const V3<float> gf = quat_to_grain(q, n);
+                    sp.n[0] = n.x; sp.n[1] = n.y; sp.n[2] = n.z;
+                    sp.th[0] = th.x; sp.th[1] = th.y; sp.th[2] = th.z;
+                    sp.ph[0] = ph.x; sp.ph[1] = ph.y; sp.ph[2] = ph.z;
+                    sp.g[0] = gf.x; sp.g[1] = gf.y; sp.g[2] = gf.z;
+                    sp.q = q;
+                    sp.X[0] = pk.X0; sp.X[1] = pk.X1; sp.X[2] = pk.X2; sp.X[3] = pk.X3;
+                    sp.bin = bin;
+                    sp.sk = tabs.n_bins > 1 ? -1.f + 2.f * (float)bin / (float)(tabs.n_bins - 1) : 0.f;
+                    sp.pid_lo = (unsigned)((unsigned long long)pk.pid & 0xffffffffull);
+                    sp.pid_hi = (unsigned)((unsigned long long)pk.pid >> 32);
+                    sp.n_sca = pk.n_sca;
+                    sp.want = 1;
+                }
+            }
+        }
+        tc::group_sync(g);
+        for (;;) {
+            // the unresolved packets in packet order (slot_owner) and their number, by warp
+            // ballots and the counts of the group's earlier warps
+            const bool want = pkt[t].want != 0;
+            const unsigned wb = __ballot_sync(0xffffffffu, want);
+            const int w = t >> 5, lane = t & 31;
+            if (lane == 0) n_unres[gi][w] = __popc(wb);
+            tc::group_sync(g);
+            int before = 0, nu = 0;
+            for (int k = 0; k < tc::kRows / 32; ++k) {
+                before += k < w ? n_unres[gi][k] : 0;
+                nu += n_unres[gi][k];
+            }
+            const int my_slot = before + __popc(wb & ((1u << lane) - 1u));
+            if (want) pkt[my_slot].slot_owner = t;
+            tc::group_sync(g);
+            if (nu == 0) break;  // the same in every thread of the group
+            const int T = tc::kRows / nu < 8 ? tc::kRows / nu : 8;
+            const int slot = t / T, j = t % T;
+            const int owner = slot < nu ? pkt[slot].slot_owner : 0;
+            const ScatPkt& o = pkt[owner];
+            const int ot = o.t_next + j;
+            const bool rowv = slot < nu && ot < P.max_trials;
+            float bound = 0.f, bmax = 0.f, mu = 1.f;
+            V3<float> n2{0.f, 0.f, 1.f};
+            PlaneRot<float> pr{1.f, 0.f, 1.f, 0.f};
+            bool fb = false;
+            float u[mlp::kIn] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const V3<float> on{o.n[0], o.n[1], o.n[2]}, oth{o.th[0], o.th[1], o.th[2]}, oph{o.ph[0], o.ph[1], o.ph[2]};
+            if (rowv) {
+                const long long opid = (long long)(((unsigned long long)o.pid_hi << 32) | (unsigned long long)o.pid_lo);
+                const Draw4<float> ut = draw4<float>(opid, o.n_sca, 1u + (unsigned)ot, P.seed, P.stream);
+                // interval of the piecewise-constant envelope of the drawn bin, then the angle
+                // inside it and the azimuth (as the table path)
+                const float* cdf = tabs.env_cdf_f + (size_t)o.bin * nint;
+                int lo = 0, hi = nint - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (ut.a < cdf[mid])
+                        hi = mid;
+                    else
+                        lo = mid + 1;
+                }
+                float s0, c0, s1, c1;
+                sincospif((float)lo / (float)nint, &s0, &c0);
+                sincospif((float)(lo + 1) / (float)nint, &s1, &c1);
+                mu = c0 - ut.b * (c0 - c1);
+                float sn = (1.f - mu) * (1.f + mu);
+                sn = sn > 0.f ? sqrtf(sn) : 0.f;
+                float sa, ca;
+                sincospif(2.f * ut.c, &sa, &ca);
+                n2 = V3<float>{mu * on.x + sn * (ca * oth.x + sa * oph.x), mu * on.y + sn * (ca * oth.y + sa * oph.y),
+                               mu * on.z + sn * (ca * oth.z + sa * oph.z)};
+                bmax = 2.f * tabs.env[(size_t)o.bin * nint + lo] * o.X[0] * widen_env;
+                bound = ut.d * bmax;
+                V3<float> th2, ph2;
+                stokes_basis(n2, th2, ph2);
+                pr = plane_rotation(on, oth, oph, n2, th2, ph2);
+                const V3<float> og{o.g[0], o.g[1], o.g[2]};
+                const V3<float> n2GF = quat_to_grain(o.q, n2);
+                u[0] = og.x;
+                u[1] = og.y;
+                u[2] = og.z;
+                u[3] = n2GF.x;
+                u[4] = n2GF.y;
+                u[5] = n2GF.z;
+                u[6] = o.sk;
+                fb = map_says_fallback(P.sur, og, n2GF, o.sk);
+            }
+            tc::store_input(g, u);
+            float y[24];
+            if (!tc::forward(g, y, phase, kTensorWaitNs)) {  // false in every thread of the group
+                failed = true;
+                break;
+            }
+            ScatRow r;
+            r.acc = 0;
+            r.Y[0] = r.Y[1] = r.Y[2] = r.Y[3] = 0.f;
+            r.n2[0] = n2.x;
+            r.n2[1] = n2.y;
+            r.n2[2] = n2.z;
+            if (rowv) {
+                float m[16];
+                const float oX[4] = {o.X[0], o.X[1], o.X[2], o.X[3]};
+                const bool real = realizable(y, m);
+                if (!fb && real) {
+                    apply_plane_full(pr, __expf(y[0]), m, oX, r.Y);
+                } else {
+                    float Pm[6];
+                    table_at(tabs, o.sk, mu, Pm);
+                    apply_plane(pr, Pm, oX, r.Y);
+                    if (fb)
+                        ++c_map;
+                    else
+                        ++c_real;
+                }
+                ++c_rows;
+                if (r.Y[0] > bmax) ++c_miss;
+                r.acc = bound < r.Y[0] ? 1 : 2;  // 1 accepted, 2 rejected, 0 no trial
+            }
+            rows[t] = r;
+            tc::group_sync(g);
+            if (want) {
+                // this packet's rows, in trial order: the first accepted one wins
+                const int sp = my_slot;
+                int examined = 0, src = -1;
+                for (int k = sp * T; k < sp * T + T; ++k) {
+                    if (rows[k].acc == 0) break;
+                    ++examined;
+                    if (rows[k].acc == 1) {
+                        src = k;
+                        break;
+                    }
+                }
+                pk.trials += (unsigned)examined;
+                pkt[t].t_next += T;
+                if (src >= 0) {
+                    resolved = true;
+                    for (int e = 0; e < 4; ++e) Ys[e] = rows[src].Y[e];
+                    n2s = V3<float>{rows[src].n2[0], rows[src].n2[1], rows[src].n2[2]};
+                    pkt[t].want = 0;
+                } else if (pkt[t].t_next >= P.max_trials) {
+                    finish(P, pk, 4, bt);
+                    live = false;
+                    pkt[t].want = 0;
+                }
+            }
+            tc::group_sync(g);
+        }
+        if (failed) break;
+        if (t < kScatPk && live && resolved) {
+            // Ys is in the lab basis of the new direction; the intensity is kept
+            const float norm = pk.X0 / Ys[0];
+            pk.X0 = Ys[0] * norm;
+            pk.X1 = Ys[1] * norm;
+            pk.X2 = Ys[2] * norm;
+            pk.X3 = Ys[3] * norm;
+            pk.nx = n2s.x;
+            pk.ny = n2s.y;
+            pk.nz = n2s.z;
+            tau_set(pk.tau, -logf(us_a));
+            pk.s_flight = flight_size(tabs, us_d);
+            cg::coalesced_group grp = cg::coalesced_threads();
+            unsigned long long base = 0;
+            if (grp.thread_rank() == 0) base = atomicAdd(&P.sur.ctl->n_resume_next, (unsigned long long)grp.size());
+            base = grp.shfl(base, 0);
+            store_state(P.sur.resume + (base + grp.thread_rank()) * kStateF4, pk);
+        }
+        tc::group_sync(g);  // the packet table is read before the next batch overwrites it
+    }
+    if (failed && t == 0) atomicOr(P.status, (unsigned)MCRT_STATUS_DEVICE_TIMEOUT);
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        if (bt.e[threadIdx.x] != 0.0) atomicAdd(&P.stats[threadIdx.x], bt.e[threadIdx.x]);
+    } else if (threadIdx.x < 16) {
+        unsigned long long* c = reinterpret_cast<unsigned long long*>(P.stats + 6);
+        if (bt.n[threadIdx.x - 6]) atomicAdd(&c[threadIdx.x - 6], bt.n[threadIdx.x - 6]);
+    } else if (threadIdx.x == 16 && bt.status) {
+        atomicOr(P.status, bt.status);
+    }
+    const unsigned long long v[4] = {c_rows, c_map, c_real, c_miss};
+    const int which[4] = {kCntScatRows, kCntFallbackMap, kCntFallbackReal, kCntEnvelopeMiss};
+    flush_counters(P.sur.ctl, s_cnt, v, 4, which);
+    tc::teardown(kScatGroups, g, failed, phase, kTensorWaitNs);
+}
+
 // Source tally of queued table-path segments: one (record, camera) row per lane,
 // the mixture table and the cameras in shared memory; a record's cameras are one
 // contiguous FP64 bulk reduction into S[cell].  Same arithmetic as the in-place
@@ -687,6 +978,8 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
             e = cudaFuncSetAttribute(k_sur_tally_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTallyTcSmem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_sur_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sur_scatter_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScatTcSmem);
     } else {
         if (tab_smem > 48 * 1024)
             e = cudaFuncSetAttribute(k_tab_tally, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_smem);
@@ -739,7 +1032,10 @@ cudaError_t run_round_transport(const TransportParams& p_in, int model, int n_sm
         }
         if (e == cudaSuccess) e = cudaEventRecord(ek[2], s);
         if (e == cudaSuccess && sur) {
-            k_sur_scatter<<<n_sm, kWaveBlock, kScatSmem, s>>>(p);
+            if (p.sur.tally_engine == MCRT_ENGINE_TCGEN05)
+                k_sur_scatter_tc<<<n_sm, tc::kRows * kScatGroups, kScatTcSmem, s>>>(p);
+            else
+                k_sur_scatter<<<n_sm, kWaveBlock, kScatSmem, s>>>(p);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaEventRecord(ek[3], s);

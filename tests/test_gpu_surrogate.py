@@ -286,9 +286,9 @@ def test_surrogate_path_against_table_path(disk_net):
 
 
 def test_tally_engines_agree(disk_net):
-    """The source tally of a surrogate launch on tcgen05 (default) and on mma.sync:
-    same records, same network, so the tallies and images agree up to FP32 rounding
-    (and rare BF16 activation flips); trajectories are identical."""
+    """A surrogate launch with the network on tcgen05 (default: tally and rejection
+    trials) and on mma.sync: the same network on the same rows, so the tallies and images
+    agree up to FP32 rounding and the rare trial whose acceptance flips with it."""
     model, s = disk_net
     run = W.disk_run(n_packets=20_000, n_cam=4, npix=32)
     out = {}
@@ -300,9 +300,35 @@ def test_tally_engines_agree(disk_net):
         out[eng] = (st, S, A)
         m.close()
     (st_t, S_t, A_t), (st_m, S_m, A_m) = out["tcgen05"], out["mma"]
-    assert st_t["events"] == st_m["events"] and st_t["mlp_tally_rows"] == st_m["mlp_tally_rows"]
-    assert np.linalg.norm(A_t - A_m) < 1e-9 * np.linalg.norm(A_m)  # FP64 atomics in another order
-    assert np.linalg.norm(S_t - S_m) < 2e-3 * np.linalg.norm(S_m)
+    assert abs(st_t["events"] - st_m["events"]) <= 1e-3 * st_m["events"]
+    assert np.linalg.norm(A_t - A_m) < 2e-3 * np.linalg.norm(A_m)
+    assert np.linalg.norm(S_t - S_m) < 5e-3 * np.linalg.norm(S_m)
+
+
+def test_rejection_trials_on_tcgen05_follow_the_mma_engine_exactly(disk_net):
+    """Validation mode (every evaluation from the tables): the rejection trials on the
+    5th-generation tensor cores (128-row tiles of trials, packets sharing them by the
+    sequential rule) give the same packets as those on mma.sync, trial for trial.  The
+    engines evaluate different numbers of speculative trials (rows of 128 against 16 per
+    tile), so only the network-row counts differ."""
+    model, s = disk_net
+    run = W.disk_run(n_packets=20_000, n_cam=2, npix=16)
+    out = {}
+    for eng in ("tcgen05", "mma"):
+        m = M.Model(model)
+        m.set_surrogate(s, -1.0)
+        tr = np.zeros((20_000, 16))
+        st = M.launch(m, run, precision="fp32", optics="surrogate", tally_engine=eng, trace=tr, n_trace=20_000)
+        out[eng] = (st, tr)
+        m.close()
+    (st_t, tr_t), (st_m, tr_m) = out["tcgen05"], out["mma"]
+    for key in ("events", "scatterings", "trials", "escaped", "roulette_killed"):
+        assert st_t[key] == st_m[key], key
+    assert np.array_equal(tr_t[:, 10:13], tr_m[:, 10:13])  # scatterings, segments, fate of every packet
+    # final Stokes vectors to FP32 rounding (the two kernels round the same expressions apart):
+    # within 1e-4 of I for 99.9 % of the packets, as FP32 traces are gated against the oracle
+    err = np.max(np.abs(tr_t[:, 0:4] - tr_m[:, 0:4]), axis=1) / (np.abs(tr_m[:, 0]) + 1e-300)
+    assert np.mean(err < 1e-4) >= 0.999, np.mean(err < 1e-4)
 
 
 def test_surrogate_path_odd_camera_count(disk_net):
