@@ -513,7 +513,7 @@ def run_surrogate(args, M, W, torch, model, run, table_imgs, table_step, table_v
     for c in range(n_cam):
         mdl.image(c, imgs2[c])
     out = {"workload": "flared disk %d^3 as the table line, grain optics from the MLP surrogate (7 -> 128 x 4 -> 20, "
-                       "SiLU, BF16 weights, FP32 accumulation; tally on tcgen05, rejection trials on mma.sync), "
+                       "SiLU, BF16 weights, FP32 accumulation; tally and rejection trials on tcgen05), "
                        "trained on %.0e samples from the "
                        "tables, table fallback above error bound %g; %.0e packets"
                        % (args.grid, n_train * 2048, args.sur_bound, args.packets),
