@@ -228,27 +228,78 @@ __device__ __forceinline__ bool layer_mma(const Group& g, unsigned a_addr, int K
 // TMEM address of row t's lane (warp w reaches lanes 32 (w mod 4) .. + 31)
 __device__ __forceinline__ unsigned lane_addr(const Group& g) { return g.tmem + ((unsigned)(g.t & ~31) << 16); }
 
-// SiLU(z) from h = z / 2 (the hidden layers' weights and biases are stored halved,
-// which is exact in BF16 and FP32): z sigma(z) = h + h tanh(h)
-__device__ __forceinline__ float silu_half(float h) { return fmaf(h, mlp::tanh_apx(h), h); }
 
-// Hidden-layer epilogue of row t: D + bias, SiLU, BF16, into the activation tile.
+// wait for this thread's TMEM loads, with the destination registers tied to the wait so
+// that no use of them is scheduled before it
+__device__ __forceinline__ void tmem_wait_ld32(float (&v)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                   "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15]),
+                   "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]), "+f"(v[22]), "+f"(v[23]),
+                   "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]), "+f"(v[29]), "+f"(v[30]), "+f"(v[31])
+                 :
+                 : "memory");
+}
+// packed FP32 pairs (add / fma .f32x2: one instruction for two lanes of arithmetic,
+// each rounded as the scalar operation)
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long d, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(d));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Hidden-layer epilogue of 32 columns of row t: D + bias, SiLU, BF16, into the
+// activation tile.  The hidden layers' weights and biases are stored halved (exact in
+// BF16 and FP32), so D + bias is h = z / 2 and SiLU(z) = z sigma(z) = h + h tanh(h).
+__device__ __forceinline__ void epi_chunk(const Group& g, const float* bias, int j, const float (&v)[32]) {
+    unsigned p[16];
+    const unsigned long long* b2 = reinterpret_cast<const unsigned long long*>(bias + j);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const unsigned long long h = f2_add(f2_pack(v[2 * i], v[2 * i + 1]), b2[i]);
+        float h0, h1;
+        f2_unpack(h, h0, h1);
+        const unsigned long long r = f2_fma(h, f2_pack(mlp::tanh_apx(h0), mlp::tanh_apx(h1)), h);
+        float r0, r1;
+        f2_unpack(r, r0, r1);
+        p[i] = mlp::pack_bf16(r0, r1);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4*>(g.act + core_off(g.t, j + 8 * c, 128)) =
+            make_uint4(p[4 * c], p[4 * c + 1], p[4 * c + 2], p[4 * c + 3]);
+}
+
+// Hidden-layer epilogue of row t, 128 columns: the next 32 columns are loaded from
+// tensor memory while the current ones are converted.
 __device__ __forceinline__ void hidden_epilogue(const Group& g, const float* bias) {
     const unsigned la = lane_addr(g);
-#pragma unroll 1
-    for (int j = 0; j < 128; j += 32) {
-        float v[32];
-        tmem_ld32(la + (unsigned)j, v);
-        tmem_wait_ld();
-        unsigned p[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-            p[i] = mlp::pack_bf16(silu_half(v[2 * i] + bias[j + 2 * i]), silu_half(v[2 * i + 1] + bias[j + 2 * i + 1]));
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            *reinterpret_cast<uint4*>(g.act + core_off(g.t, j + 8 * c, 128)) =
-                make_uint4(p[4 * c], p[4 * c + 1], p[4 * c + 2], p[4 * c + 3]);
-    }
+    float va[32], vb[32];
+    tmem_ld32(la, va);
+    tmem_wait_ld32(va);
+    tmem_ld32(la + 32u, vb);
+    epi_chunk(g, bias, 0, va);
+    tmem_wait_ld32(vb);
+    tmem_ld32(la + 64u, va);
+    epi_chunk(g, bias, 32, vb);
+    tmem_wait_ld32(va);
+    tmem_ld32(la + 96u, vb);
+    epi_chunk(g, bias, 64, va);
+    tmem_wait_ld32(vb);
+    epi_chunk(g, bias, 96, vb);
 }
 
 // The network on the group's 128 rows (inputs in a0): out[0..23] of row t.  All

@@ -807,6 +807,73 @@ __device__ __forceinline__ void step(const TransportParams& P, const Smem<T>& sm
     pk.pending = true;
 }
 
+// Russian roulette at a scattering of a packet whose intensity fell below the threshold
+// fraction of its birth intensity: it survives with probability surv, its Stokes
+// vector scaled by 1 / surv.  Returns false when the packet ends here.
+template <typename T>
+__device__ __forceinline__ bool roulette(const TransportParams& P, Packet<T>& pk, T u, BlockTotals& bt) {
+    if (P.roulette_thr > 0.0 && (double)pk.X0 < P.roulette_thr * (double)pk.I_birth) {
+        if ((double)u < P.roulette_surv) {
+            const T gmul = T(1.0 / P.roulette_surv);
+            pk.e_gain += pk.X0 * (gmul - T(1));
+            pk.X0 *= gmul;
+            pk.X1 *= gmul;
+            pk.X2 *= gmul;
+            pk.X3 *= gmul;
+        } else {
+            finish(P, pk, 2, bt);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Size bin of a scattering: the first bin whose cumulative weight exceeds u.
+template <typename T> __device__ __forceinline__ int size_bin(const TablesDev& tabs, T u) {
+    for (int k = 0; k < tabs.n_bins; ++k)
+        if (u < cdf_at<T>(tabs.bin_cdf, tabs.bin_cdf_f, k)) return k;
+    return tabs.n_bins - 1;
+}
+
+// One trial of the rejection sampling of a tabulated scattering (Sec. 2.2): a scattering
+// angle from the piecewise-constant envelope of P11 of the size bin (interval j with
+// probability proportional to its envelope mass, cos theta uniform inside it), an
+// azimuth uniform around n, accepted when u 2 env_j I lies below the scattered
+// intensity P11 I + P12 Q_s.  Returns the proposed direction n2, mu = cos theta and the
+// matrix at mu.
+template <typename T>
+__device__ __forceinline__ bool table_trial(const TablesDev& tabs, int bin, const Draw4<T>& ut, const V3<T>& n,
+                                            const V3<T>& th, const V3<T>& ph, const T X[4], V3<T>& n2, T& mu,
+                                            T Pm[6]) {
+    const float4* tab = tabs.bins + (size_t)bin * tabs.n_theta * 2;
+    // interval j of the envelope: first j with u < cdf_j
+    const int nint = tabs.n_theta - 1;
+    const size_t c0i = (size_t)bin * nint;
+    int lo = 0, hi = nint - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ut.a < cdf_at<T>(tabs.env_cdf, tabs.env_cdf_f, c0i + mid))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    const int j = lo;
+    T s0, c0, s1, c1;
+    t_sincospi(T(j) / T(nint), &s0, &c0);
+    t_sincospi(T(j + 1) / T(nint), &s1, &c1);
+    mu = c0 - ut.b * (c0 - c1);
+    T sn = (T(1) - mu) * (T(1) + mu);
+    sn = sn > T(0) ? t_sqrt(sn) : T(0);
+    T sa, ca;
+    t_sincospi(T(2) * ut.c, &sa, &ca);
+    n2 = V3<T>{mu * n.x + sn * (ca * th.x + sa * ph.x), mu * n.y + sn * (ca * th.y + sa * ph.y),
+               mu * n.z + sn * (ca * th.z + sa * ph.z)};
+    table_matrix(tab, tabs.n_theta, mu, Pm);
+    const T bound = ut.d * T(2) * T(tabs.env[c0i + j]) * X[0];
+    const T Qs = plane_Q(th, ph, n2, X);
+    return bound < Pm[0] * X[0] + Pm[1] * Qs;
+}
+
 // Scattering of a packet at its current position (Sec. 2.2): roulette, size bin, then
 // rejection sampling of the new direction; run for the warp's waiting lanes together.
 template <typename T, int SCAT, bool B>
@@ -818,19 +885,9 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
     V3<T> th, ph;
     stokes_basis(n, th, ph);
     const Draw4<T> us = draw4<T>(pk.pid, pk.n_sca, 0u, P.seed, job.stream());
-    if (P.roulette_thr > 0.0 && (double)pk.X0 < P.roulette_thr * (double)pk.I_birth) {
-        if ((double)us.b < P.roulette_surv) {
-            const T gmul = T(1.0 / P.roulette_surv);
-            pk.e_gain += pk.X0 * (gmul - T(1));
-            pk.X0 *= gmul;
-            pk.X1 *= gmul;
-            pk.X2 *= gmul;
-            pk.X3 *= gmul;
-        } else {
-            finish(P, pk, 2, bt);
-            alive = false;
-            return;
-        }
+    if (!roulette(P, pk, us.b, bt)) {
+        alive = false;
+        return;
     }
     if constexpr (SCAT == MCRT_SCAT_DIPOLE) {
         // aligned spheroid: isotropic proposal, envelope env I >= (Zhat X)_0; the new
@@ -880,17 +937,7 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
         tau_set(pk.tau, -t_log(us.a));
         return;
     }
-    int bin = 0;
-    const float4* tab = nullptr;
-    if (table_optics(SCAT)) {
-        bin = tabs.n_bins - 1;
-        for (int k = 0; k < tabs.n_bins; ++k)
-            if (us.c < cdf_at<T>(tabs.bin_cdf, tabs.bin_cdf_f, k)) {
-                bin = k;
-                break;
-            }
-        tab = tabs.bins + (size_t)bin * tabs.n_theta * 2;
-    }
+    const int bin = table_optics(SCAT) ? size_bin(tabs, us.c) : 0;
     const T X[4] = {pk.X0, pk.X1, pk.X2, pk.X3};
     V3<T> n2;
     T Pm[6];
@@ -898,41 +945,20 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
     for (int t = 0; t < P.max_trials; ++t) {
         const Draw4<T> ut = draw4<T>(pk.pid, pk.n_sca, 1u + (unsigned)t, P.seed, job.stream());
         pk.trials++;
-        T bound;
+        bool acc;
         if (SCAT == MCRT_SCAT_RAYLEIGH) {
             T g2[3];
             iso_dir(ut.a, ut.b, g2);
             n2 = quat_to_lab(pk.cq, V3<T>{g2[0], g2[1], g2[2]});
             rayleigh_matrix(dot(n, n2), Pm);
-            bound = ut.c * T(2) * T(0.11936620731892133) * X[0];  // 2 * 3/(8 pi)
+            const T bound = ut.c * T(2) * T(0.11936620731892133) * X[0];  // 2 * 3/(8 pi)
+            const T Qs = plane_Q(th, ph, n2, X);
+            acc = bound < Pm[0] * X[0] + Pm[1] * Qs;
         } else {
-            // interval j of the piecewise-constant envelope of P11: first j with u < cdf_j
-            const int nint = tabs.n_theta - 1;
-            const size_t c0i = (size_t)bin * nint;
-            int lo = 0, hi = nint - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (ut.a < cdf_at<T>(tabs.env_cdf, tabs.env_cdf_f, c0i + mid))
-                    hi = mid;
-                else
-                    lo = mid + 1;
-            }
-            const int j = lo;
-            T s0, c0, s1, c1;
-            t_sincospi(T(j) / T(nint), &s0, &c0);
-            t_sincospi(T(j + 1) / T(nint), &s1, &c1);
-            const T mu = c0 - ut.b * (c0 - c1);
-            T sn = (T(1) - mu) * (T(1) + mu);
-            sn = sn > T(0) ? t_sqrt(sn) : T(0);
-            T sa, ca;
-            t_sincospi(T(2) * ut.c, &sa, &ca);
-            n2 = V3<T>{mu * n.x + sn * (ca * th.x + sa * ph.x), mu * n.y + sn * (ca * th.y + sa * ph.y),
-                       mu * n.z + sn * (ca * th.z + sa * ph.z)};
-            table_matrix(tab, tabs.n_theta, mu, Pm);
-            bound = ut.d * T(2) * T(tabs.env[(size_t)bin * nint + j]) * X[0];
+            T mu;
+            acc = table_trial(tabs, bin, ut, n, th, ph, X, n2, mu, Pm);
         }
-        const T Qs = plane_Q(th, ph, n2, X);
-        if (bound < Pm[0] * X[0] + Pm[1] * Qs) {
+        if (acc) {
             accepted = true;
             break;
         }
@@ -956,6 +982,127 @@ __device__ __forceinline__ void scatter_event(const TransportParams& P, const Sm
     pk.ny = n2.y;
     pk.nz = n2.z;
     tau_set(pk.tau, -t_log(us.a));
+}
+
+// Lane of the k-th set bit of m (k < popc(m)), by halving.
+__device__ __forceinline__ int nth_set_lane(unsigned m, int k) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const unsigned lo = m & ((1u << w) - 1u);
+        const int c = __popc(lo);
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = lo;
+        }
+    }
+    return pos;
+}
+
+// Scatterings of the warp's waiting lanes with their rejection trials spread over all
+// 32 lanes (single-model launches with tabulated optics).  Each owner first takes its
+// roulette and size bin; then, round after round, every unresolved packet gets
+// floor(32 / unresolved) lanes that evaluate its next trials in trial order, and the
+// packet takes its first accepted trial.  Direction, matrix and trial count are thus
+// those of the sequential rule (same random numbers, same arithmetic).  All 32 lanes
+// call it.
+template <typename T>
+__device__ __forceinline__ void scatter_coop(const TransportParams& P, const Smem<T>& sm, Packet<T>& pk, bool& alive,
+                                             BlockTotals& bt) {
+    const int lane = threadIdx.x & 31;
+    const JobRef<T, false> job = job_of<T, false>(P, sm, pk);
+    const TablesDev& tabs = job.t();
+    bool live = false;
+    int bin = 0;
+    T u_tau = T(1);
+    if (alive && pk.pending) {
+        pk.pending = false;
+        const Draw4<T> us = draw4<T>(pk.pid, pk.n_sca, 0u, P.seed, job.stream());
+        live = roulette(P, pk, us.b, bt);
+        alive = live;
+        bin = size_bin(tabs, us.c);
+        u_tau = us.a;
+    }
+    unsigned todo = __ballot_sync(kFull, live);
+    int t_next = 0;          // owner: first trial of its next round
+    bool accepted = false;   // owner: a trial was accepted
+    V3<T> n2a{T(0), T(0), T(1)};
+    T mua = T(1);
+    while (todo != 0u) {
+        const int nu = __popc(todo);
+        const int per = 32 / nu;
+        const int k = lane / per;  // packet this lane evaluates (rank among the unresolved)
+        const int src = k < nu ? nth_set_lane(todo, k) : lane;
+        const V3<T> n{__shfl_sync(kFull, pk.nx, src), __shfl_sync(kFull, pk.ny, src), __shfl_sync(kFull, pk.nz, src)};
+        const T X[4] = {__shfl_sync(kFull, pk.X0, src), __shfl_sync(kFull, pk.X1, src),
+                        __shfl_sync(kFull, pk.X2, src), T(0)};
+        const long long pid = __shfl_sync(kFull, pk.pid, src);
+        const unsigned nsca = __shfl_sync(kFull, pk.n_sca, src);
+        const int tb = __shfl_sync(kFull, bin, src);
+        const int t = __shfl_sync(kFull, t_next, src) + lane % per;
+        bool acc = false;
+        V3<T> n2{T(0), T(0), T(1)};
+        T mu = T(1);
+        if (k < nu && t < P.max_trials) {
+            V3<T> th, ph;
+            stokes_basis(n, th, ph);
+            const Draw4<T> ut = draw4<T>(pid, nsca, 1u + (unsigned)t, P.seed, job.stream());
+            T Pm[6];
+            acc = table_trial(tabs, tb, ut, n, th, ph, X, n2, mu, Pm);
+        }
+        const unsigned am = __ballot_sync(kFull, acc);
+        // each owner: the first accepted trial among its lanes
+        const bool own = (todo >> lane) & 1u;
+        const int kr = __popc(todo & ((1u << lane) - 1u));
+        const unsigned seg = own ? (per >= 32 ? kFull : ((1u << per) - 1u) << (kr * per)) : 0u;
+        const unsigned hit = am & seg;
+        const int w = hit != 0u ? __ffs(hit) - 1 : lane;
+        n2.x = __shfl_sync(kFull, n2.x, w);
+        n2.y = __shfl_sync(kFull, n2.y, w);
+        n2.z = __shfl_sync(kFull, n2.z, w);
+        mu = __shfl_sync(kFull, mu, w);
+        if (own) {
+            if (hit != 0u) {
+                pk.trials += (unsigned)(w - kr * per + 1);
+                accepted = true;
+                n2a = n2;
+                mua = mu;
+            } else {
+                const int left = P.max_trials - t_next;
+                pk.trials += (unsigned)(left < per ? (left > 0 ? left : 0) : per);
+                t_next += per;
+            }
+        }
+        todo = __ballot_sync(kFull, own && hit == 0u && t_next < P.max_trials);
+    }
+    if (!live) return;
+    if (!accepted) {
+        finish(P, pk, 4, bt);
+        alive = false;
+        return;
+    }
+    const V3<T> n{pk.nx, pk.ny, pk.nz};
+    V3<T> th, ph, th2, ph2;
+    stokes_basis(n, th, ph);
+    stokes_basis(n2a, th2, ph2);
+    T Pm[6];
+    table_matrix(tabs.bins + (size_t)bin * tabs.n_theta * 2, tabs.n_theta, mua, Pm);
+    const PlaneRot<T> pr = plane_rotation(n, th, ph, n2a, th2, ph2);
+    const T X[4] = {pk.X0, pk.X1, pk.X2, pk.X3};
+    T Y[4];
+    apply_plane(pr, Pm, X, Y);
+    const T norm = X[0] / Y[0];
+    pk.X0 = Y[0] * norm;
+    pk.X1 = Y[1] * norm;
+    pk.X2 = Y[2] * norm;
+    pk.X3 = Y[3] * norm;
+    pk.nx = n2a.x;
+    pk.ny = n2a.y;
+    pk.nz = n2a.z;
+    tau_set(pk.tau, -t_log(u_tau));
 }
 
 // Job of a batch packet index: the last job whose first index is <= gpid.
@@ -1105,7 +1252,9 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
         }
         // scatterings of the warp run together once enough lanes wait for one
         if (pend != 0u && (__popc(pend) >= scatter_batch<B, SCAT>() || work == 0u)) {
-            if constexpr (SCAT != kScatSurrogate) {  // the surrogate scatters in its own kernel
+            if constexpr (table_optics(SCAT) && !B) {
+                scatter_coop<T>(P, sm, pk, alive, bt);  // every lane runs trials of the waiting packets
+            } else if constexpr (SCAT != kScatSurrogate) {  // the surrogate scatters in its own kernel
                 if (alive && pk.pending) {
                     pk.pending = false;
                     scatter_event<T, SCAT, B>(P, sm, pk, alive, bt);

@@ -78,7 +78,9 @@ def test_graph_batch_runs_tune_and_images(sweep):
         for m, mdl in enumerate(mdls):
             S, A = mdl.tallies(1)
             assert rel(S, ref[m][1]) < 1e-6, (rep, m)  # FP32 same-cell pre-sums
-            assert rel(imgs[m][0], ref[m][3]) < 1e-6, (rep, m)  # FP32 image arithmetic
+            # FP32 image arithmetic of two kernels compiled apart (the single-model kernels
+            # spread the rejection trials over the warp): a few ulp per operation
+            assert rel(imgs[m][0], ref[m][3]) < 2e-6, (rep, m)
     other = b.launch(seed=78)
     assert other["events"] != st["events"]
     rep = b.tune(packets_per_job=1000)
