@@ -133,11 +133,12 @@ __device__ V3<float> iso_unit(float ua, float ub) {
     return V3<float>{st * cp, st * sp, ct};
 }
 
-// Training batch of step `step`: inputs (zero-padded to 16, BF16) and targets.
-__global__ void k_gen_batch(LabelTables T, unsigned seed, unsigned step, int B, bf16* __restrict__ X,
-                            float* __restrict__ Y) {
+// Training batch of step step0 + *iter: inputs (zero-padded to 16, BF16) and targets.
+__global__ void k_gen_batch(LabelTables T, unsigned seed, unsigned step0, const unsigned* __restrict__ iter, int B,
+                            bf16* __restrict__ X, float* __restrict__ Y) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
+    const unsigned step = step0 + *iter;
     const Draw4<float> u0 = draw4<float>(i, step, 0x51u, seed, 0x5A17u);
     const Draw4<float> u1 = draw4<float>(i, step, 0x52u, seed, 0x5A17u);
     const V3<float> ni = iso_unit(u0.a, u0.b), ns = iso_unit(u0.c, u0.d);
@@ -431,9 +432,11 @@ __global__ void k_colsum32(int B, int N, const float* __restrict__ dZ, float* __
     atomicAdd(&db[n], s);
 }
 
-// dY = 2 w (Y - T) / (B * 20) (BF16, zero in the padding columns) and the loss sum.
+// dY = 2 w (Y - T) / (B * 20) (BF16, zero in the padding columns) and the loss sum,
+// added to loss[*iter] (loss[0] without an iteration counter).
 __global__ void k_loss_grad(int B, const float* __restrict__ Y, const float* __restrict__ T,
-                            const float* __restrict__ w, bf16* __restrict__ dY, double* __restrict__ loss) {
+                            const float* __restrict__ w, bf16* __restrict__ dY, double* __restrict__ loss,
+                            const unsigned* __restrict__ iter) {
     __shared__ double part[256];
     double acc = 0.0;
     const float scale = 2.f / ((float)B * (float)kOut);
@@ -453,7 +456,7 @@ __global__ void k_loss_grad(int B, const float* __restrict__ Y, const float* __r
         if (threadIdx.x < off) part[threadIdx.x] += part[threadIdx.x + off];
         __syncthreads();
     }
-    if (threadIdx.x == 0) atomicAdd(loss, part[0] / ((double)B * kOut));
+    if (threadIdx.x == 0) atomicAdd(loss + (iter ? *iter : 0u), part[0] / ((double)B * kOut));
 }
 
 // db[n] = sum over rows of dZ[b][n] (BF16 input, FP32 output).
@@ -465,9 +468,13 @@ __global__ void k_colsum(int B, int N, const bf16* __restrict__ dZ, float* __res
     atomicAdd(&db[n], s);
 }
 
-// Adam on the FP32 master parameters, then the BF16 copies of the weights.
+// Adam on the FP32 master parameters; the learning rate and the two bias corrections
+// of the iteration are sched[3 * *iter + 0..2].
 __global__ void k_adam(int P, float* __restrict__ p, const float* __restrict__ grad, float* __restrict__ m,
-                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       float* __restrict__ v, const float* __restrict__ sched, const unsigned* __restrict__ iter,
+                       float b1, float b2, float eps) {
+    const float* sc = sched + 3 * (size_t)*iter;
+    const float lr = sc[0], c1 = sc[1], c2 = sc[2];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P; i += gridDim.x * blockDim.x) {
         const float g = grad[i];
         const float mi = b1 * m[i] + (1.f - b1) * g;
@@ -479,8 +486,10 @@ __global__ void k_adam(int P, float* __restrict__ p, const float* __restrict__ g
 }
 
 // BF16 copies of the weights for the training GEMMs.  Layer 0 columns 7-13 repeat
-// columns 0-6 (they multiply the low parts of the split inputs).
-__global__ void k_pack_weights(const float* __restrict__ p, bf16* __restrict__ wbf) {
+// columns 0-6 (they multiply the low parts of the split inputs).  As the last kernel
+// of a training step it also advances the step's iteration counter (iter_inc).
+__global__ void k_pack_weights(const float* __restrict__ p, bf16* __restrict__ wbf, unsigned* __restrict__ iter_inc) {
+    if (iter_inc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(iter_inc, 1u);
     for (int l = 0; l < kLayers; ++l) {
         const int n = layer_out(l) * layer_in(l);
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1048,7 +1057,7 @@ mcrt_status mcrt_surrogate_create(mcrt_surrogate** out, const mcrt_ctx* optics, 
     if (e == cudaSuccess) {
         (void)cudaGetLastError();
         k_init_params<<<64, 256, 0, s->stream>>>(s->d_params, seed);
-        k_pack_weights<<<64, 256, 0, s->stream>>>(s->d_params, s->d_wbf);
+        k_pack_weights<<<64, 256, 0, s->stream>>>(s->d_params, s->d_wbf, nullptr);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -1061,35 +1070,81 @@ mcrt_status mcrt_surrogate_create(mcrt_surrogate** out, const mcrt_ctx* optics, 
 }
 
 mcrt_status mcrt_surrogate_train(mcrt_surrogate* s, int64_t n_steps, int32_t batch, double lr, double* loss_history) {
-    if (!s || n_steps < 0 || batch < 64 || batch > (1 << 20))
+    if (!s || n_steps < 0 || batch < 64 || batch > (1 << 20) || n_steps > (1ll << 31))
         return mcrt_fail_noctx(MCRT_E_INVAL, "mcrt_surrogate_train: bad arguments");
     SK(ensure_buffers(s->buf, batch));
     s->map_valid = false;
+    if (n_steps == 0) return MCRT_OK;
     const LabelTables T = tables_of(s);
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    // schedule of every step: cosine decay of the learning rate over the call's steps
+    // and Adam's bias corrections of the global step
+    std::vector<float> sched((size_t)n_steps * 3);
     for (long long it = 0; it < n_steps; ++it) {
-        const unsigned step = (unsigned)(s->step++);
-        (void)cudaGetLastError();
-        k_gen_batch<<<(batch + 127) / 128, 128, 0, s->stream>>>(T, s->seed, step, batch, s->buf.x0, s->buf.t);
-        SK(cudaGetLastError());
-        mcrt_status st = forward(s, batch);
-        if (st != MCRT_OK) return st;
-        SK(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
-        k_loss_grad<<<256, 256, 0, s->stream>>>(batch, s->buf.y, s->buf.t, s->d_w, s->buf.dy, s->d_loss);
-        SK(cudaGetLastError());
-        st = backward(s, batch);
-        if (st != MCRT_OK) return st;
-        // cosine decay of the learning rate over the call's steps
+        const unsigned step = (unsigned)(s->step + it);
         const double frac = n_steps > 1 ? (double)it / (double)(n_steps - 1) : 0.0;
-        const float lr_t = (float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.141592653589793 * frac))));
-        const float c1 = 1.f - std::pow(b1, (float)(step + 1)), c2 = 1.f - std::pow(b2, (float)(step + 1));
-        k_adam<<<128, 256, 0, s->stream>>>(kParams, s->d_params, s->d_grads, s->d_m, s->d_v, lr_t, b1, b2, eps, c1, c2);
-        k_pack_weights<<<64, 256, 0, s->stream>>>(s->d_params, s->d_wbf);
-        SK(cudaGetLastError());
-        if (loss_history) SK(cudaMemcpyAsync(&loss_history[it], s->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        sched[3 * it] = (float)(lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(3.141592653589793 * frac))));
+        sched[3 * it + 1] = 1.f - std::pow(b1, (float)(step + 1));
+        sched[3 * it + 2] = 1.f - std::pow(b2, (float)(step + 1));
     }
-    SK(cudaStreamSynchronize(s->stream));
-    return MCRT_OK;
+    // one allocation: loss per step (FP64), schedule, iteration counter
+    const size_t hist_bytes = (size_t)n_steps * sizeof(double), sched_bytes = sched.size() * sizeof(float);
+    unsigned char* work = nullptr;
+    SK(cudaMalloc(&work, hist_bytes + sched_bytes + 16));
+    double* d_hist = reinterpret_cast<double*>(work);
+    float* d_sched = reinterpret_cast<float*>(work + hist_bytes);
+    unsigned* d_iter = reinterpret_cast<unsigned*>(work + hist_bytes + sched_bytes);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto done = [&](mcrt_status st) {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamSynchronize(s->stream);
+        cudaFree(work);
+        return st;
+    };
+    cudaError_t e = cudaMemcpyAsync(d_sched, sched.data(), sched_bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_hist, 0, hist_bytes, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_iter, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // the schedule left the host buffer
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return done(mcrt_fail_noctx(MCRT_E_CUDA, "mcrt_surrogate_train: %s", cudaGetErrorString(e)));
+    }
+    // one training step, captured once and replayed: every launch of the step reads its
+    // iteration from d_iter, which the step's last kernel advances
+    (void)cudaGetLastError();
+    e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return done(mcrt_fail_noctx(MCRT_E_CUDA, "mcrt_surrogate_train: %s", cudaGetErrorString(e)));
+    mcrt_status st = MCRT_OK;
+    k_gen_batch<<<(batch + 127) / 128, 128, 0, s->stream>>>(T, s->seed, (unsigned)s->step, d_iter, batch, s->buf.x0,
+                                                            s->buf.t);
+    if (cudaGetLastError() != cudaSuccess) st = MCRT_E_CUDA;
+    if (st == MCRT_OK) st = forward(s, batch);
+    if (st == MCRT_OK) {
+        k_loss_grad<<<256, 256, 0, s->stream>>>(batch, s->buf.y, s->buf.t, s->d_w, s->buf.dy, d_hist, d_iter);
+        if (cudaGetLastError() != cudaSuccess) st = MCRT_E_CUDA;
+    }
+    if (st == MCRT_OK) st = backward(s, batch);
+    if (st == MCRT_OK) {
+        k_adam<<<128, 256, 0, s->stream>>>(kParams, s->d_params, s->d_grads, s->d_m, s->d_v, d_sched, d_iter, b1, b2,
+                                           eps);
+        k_pack_weights<<<64, 256, 0, s->stream>>>(s->d_params, s->d_wbf, d_iter);
+        if (cudaGetLastError() != cudaSuccess) st = MCRT_E_CUDA;
+    }
+    e = cudaStreamEndCapture(s->stream, &graph);
+    if (st != MCRT_OK) return done(mcrt_fail_noctx(MCRT_E_CUDA, "mcrt_surrogate_train: capture of the step failed"));
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    for (long long it = 0; it < n_steps && e == cudaSuccess; ++it) e = cudaGraphLaunch(exec, s->stream);
+    if (e == cudaSuccess && loss_history)
+        e = cudaMemcpyAsync(loss_history, d_hist, hist_bytes, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return done(mcrt_fail_noctx(MCRT_E_CUDA, "mcrt_surrogate_train: %s", cudaGetErrorString(e)));
+    }
+    s->step += n_steps;
+    return done(MCRT_OK);
 }
 
 mcrt_status mcrt_surrogate_eval(mcrt_surrogate* s, int64_t n, const float* inputs, float* outputs) {
@@ -1202,7 +1257,7 @@ mcrt_status mcrt_surrogate_grad(mcrt_surrogate* s, int64_t n, const float* input
     st = forward(s, (int)n);
     if (st != MCRT_OK) return st;
     SK(cudaMemsetAsync(s->d_loss, 0, sizeof(double), s->stream));
-    k_loss_grad<<<256, 256, 0, s->stream>>>((int)n, s->buf.y, s->buf.t, s->d_w, s->buf.dy, s->d_loss);
+    k_loss_grad<<<256, 256, 0, s->stream>>>((int)n, s->buf.y, s->buf.t, s->d_w, s->buf.dy, s->d_loss, nullptr);
     SK(cudaGetLastError());
     st = backward(s, (int)n);
     if (st != MCRT_OK) return st;
@@ -1339,7 +1394,7 @@ mcrt_status mcrt_surrogate_params(mcrt_surrogate* s, float* params, int32_t set)
         s->map_valid = false;
         SK(cudaMemcpyAsync(s->d_params, params, sizeof(float) * kParams, cudaMemcpyDefault, s->stream));
         (void)cudaGetLastError();
-        k_pack_weights<<<64, 256, 0, s->stream>>>(s->d_params, s->d_wbf);
+        k_pack_weights<<<64, 256, 0, s->stream>>>(s->d_params, s->d_wbf, nullptr);
         SK(cudaGetLastError());
     } else {
         SK(cudaMemcpyAsync(params, s->d_params, sizeof(float) * kParams, cudaMemcpyDefault, s->stream));
