@@ -906,59 +906,81 @@ __global__ void __launch_bounds__(kTabBlock) k_tab_tally(const __grid_constant__
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    double* stage = s_stage + (threadIdx.x >> 5) * 32 * 4;
+    double* const slots = s_stage + (threadIdx.x >> 5) * 2 * 32 * 4;  // two staging slots per warp
     const unsigned long long nreq = P.sur.ctl->n_rec[P.sur.rec_slot];
     const unsigned long long nrec = nreq < P.sur.rec_cap ? nreq : P.sur.rec_cap;
     const int ncam = P.n_cam;
     const int ncp = ncam <= 1 ? 1 : (ncam <= 2 ? 2 : (ncam <= 4 ? 4 : (ncam <= 8 ? 8 : 16)));
     const int per_tile = 32 / ncp;
+    const int cam = lane % ncp;
     const unsigned long long ntile = (nrec + per_tile - 1) / per_tile;
-    for (unsigned long long tile = (unsigned long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntile;
-         tile += (unsigned long long)gridDim.x * wpb) {
-        bulk_wait_read();  // this lane's reductions of the previous tile have read the staging rows
-        __syncwarp();
-        const int cam = lane % ncp;
-        const unsigned long long rec = tile * per_tile + (unsigned)(lane / ncp);
-        bool valid = false;
-        unsigned cell = 0;
-        if (rec < nrec) {
+    const unsigned long long stride = (unsigned long long)gridDim.x * wpb;
+    // the next tile's record is loaded while this one is converted, and each warp
+    // alternates two staging slots, so that a slot is rewritten only once the reduction
+    // issued from it two tiles before has read it (every lane commits one bulk group per
+    // tile, empty when it issues none, so "all but the newest group" is that reduction)
+    auto load = [&](unsigned long long t, float4& a, float4& b) {
+        const unsigned long long rec = t * per_tile + (unsigned)(lane / ncp);
+        if (t < ntile && rec < nrec) {
             const float4* r = P.sur.records + rec * kTableRecordF4;
-            const float4 r0 = r[0], r1 = r[1];
-            cell = __float_as_uint(r1.w);
-            valid = cam < ncam && cell != 0xffffffffu;
-            if (valid) {
-                const V3<float> n{r0.x, r0.y, r0.z};
-                const float W[4] = {r0.w, r1.x, r1.y, r1.z};
-                V3<float> th, ph, Om, thc, phc;
-                stokes_basis(n, th, ph);
-                load_camera(s_cam + 12 * cam, Om, thc, phc);
-                float Pm[6], Y[4];
-                table_matrix(s_mix, P.t.n_theta, dot(n, Om), Pm);
-                const PlaneRot<float> pr = plane_rotation(n, th, ph, Om, thc, phc);
-                apply_plane(pr, Pm, W, Y);
-                // lanes 4-7 of each group of 8 store their second half first, so that each
-                // quarter-warp phase of 16-byte stores covers the 8 bank groups once.  The
-                // FP32 -> FP64 conversions run on the FP64 pipe, idle in this kernel (the
-                // integer-only widening would add to its busiest pipes)
-                double2* d2 = reinterpret_cast<double2*>(stage + lane * 4);
-                const double2 lo2 = make_double2((double)Y[0], (double)Y[1]);
-                const double2 hi2 = make_double2((double)Y[2], (double)Y[3]);
-                const int h = (lane >> 2) & 1;
-                d2[h] = h ? hi2 : lo2;
-                d2[1 - h] = h ? lo2 : hi2;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            }
+            a = r[0];
+            b = r[1];
+        } else {
+            b.w = __uint_as_float(0xffffffffu);
+        }
+    };
+    float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+    unsigned long long tile = (unsigned long long)blockIdx.x * wpb + (threadIdx.x >> 5);
+    load(tile, n0, n1);
+    for (unsigned it = 0; tile < ntile; ++it, tile += stride) {
+        const float4 r0 = n0, r1 = n1;
+        load(tile + stride, n0, n1);
+        const unsigned cell = __float_as_uint(r1.w);
+        const bool valid = cam < ncam && cell != 0xffffffffu;
+        double2 lo2 = make_double2(0.0, 0.0), hi2 = lo2;
+        if (valid) {
+            const V3<float> n{r0.x, r0.y, r0.z};
+            const float W[4] = {r0.w, r1.x, r1.y, r1.z};
+            V3<float> th, ph, Om, thc, phc;
+            stokes_basis(n, th, ph);
+            load_camera(s_cam + 12 * cam, Om, thc, phc);
+            float Pm[6], Y[4];
+            table_matrix(s_mix, P.t.n_theta, dot(n, Om), Pm);
+            const PlaneRot<float> pr = plane_rotation(n, th, ph, Om, thc, phc);
+            apply_plane(pr, Pm, W, Y);
+            // the FP32 -> FP64 conversions run on the FP64 pipe, idle in this kernel (the
+            // integer-only widening would add to its busiest pipes)
+            lo2 = make_double2((double)Y[0], (double)Y[1]);
+            hi2 = make_double2((double)Y[2], (double)Y[3]);
+        }
+        double* stage = slots + (it & 1u) * 32 * 4;
+        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+        if (valid) {
+            // lanes 4-7 of each group of 8 store their second half first, so that each
+            // quarter-warp phase of 16-byte stores covers the 8 bank groups once
+            double2* d2 = reinterpret_cast<double2*>(stage + lane * 4);
+            const int h = (lane >> 2) & 1;
+            d2[h] = h ? hi2 : lo2;
+            d2[1 - h] = h ? lo2 : hi2;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         __syncwarp();
-        if (valid && cam == 0)
-            bulk_reduce_add_f64(P.S + (size_t)cell * (size_t)ncam * 4, stage + lane * 4, (unsigned)ncam * 32u);
+        if (valid && cam == 0) {
+            const unsigned src = (unsigned)__cvta_generic_to_shared(stage + lane * 4);
+            asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(
+                             P.S + (size_t)cell * (size_t)ncam * 4),
+                         "r"(src), "r"((unsigned)ncam * 32u)
+                         : "memory");
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
     bulk_wait_all();
 }
 
 size_t tab_tally_smem(const TransportParams& p) {
     return (size_t)2 * p.t.n_theta * sizeof(float4) + 12 * kMaxCams * sizeof(float) +
-           (size_t)(kTabBlock / 32) * 32 * 4 * sizeof(double);
+           (size_t)(kTabBlock / 32) * 2 * 32 * 4 * sizeof(double);
 }
 
 }  // namespace
