@@ -251,25 +251,39 @@ __global__ void __launch_bounds__(tc::kRows * kTcGroups, 1) k_sur_tally_tc(const
     unsigned long long c_rows = 0, c_map = 0, c_real = 0;
     unsigned phase = 0;
     bool failed = false;
-    for (unsigned long long tile = (unsigned long long)blockIdx.x * kTcGroups + gi; tile < ntile;
-         tile += (unsigned long long)gridDim.x * kTcGroups) {
+    const int cam = t % ncp;
+    const unsigned long long stride = (unsigned long long)gridDim.x * kTcGroups;
+    // row t's record of a tile (cell word 0xffffffff past the end); the next tile's is
+    // loaded while this tile runs through the network
+    auto load = [&](unsigned long long tl, float4 (&r)[4]) {
+        const unsigned long long rec = tl * per_tile + (unsigned)(t / ncp);
+        if (tl < ntile && rec < nrec) {
+            const float4* src = P.sur.records + rec * kRecordF4;
+            r[0] = src[0];
+            r[1] = src[1];
+            r[2] = src[2];
+            r[3] = src[3];
+        } else {
+            r[3].x = __uint_as_float(0xffffffffu);
+        }
+    };
+    float4 nxt[4];
+    unsigned long long tile = (unsigned long long)blockIdx.x * kTcGroups + gi;
+    load(tile, nxt);
+    for (; tile < ntile; tile += stride) {
         // the staging rows share the input tile: every reduction of the previous tile
         // has read them before any row is overwritten
         bulk_wait_read();
         tc::group_sync(g);
-        const int cam = t % ncp;
-        const unsigned long long rec = tile * per_tile + (unsigned)(t / ncp);
-        bool valid = false, fb = false;
-        unsigned cell = 0;
+        const float4 r0 = nxt[0], r1 = nxt[1], q = nxt[2];
+        const unsigned cell = __float_as_uint(nxt[3].x);
+        load(tile + stride, nxt);
+        bool valid = cam < ncam && cell != 0xffffffffu, fb = false;
         float s = 0.f, W[4] = {0.f, 0.f, 0.f, 0.f}, mu = 1.f;
         PlaneRot<float> pr{1.f, 0.f, 1.f, 0.f};
         float u[mlp::kIn] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (rec < nrec) {
-            const float4* r = P.sur.records + rec * kRecordF4;
-            cell = __float_as_uint(r[3].x);
-            valid = cam < ncam && cell != 0xffffffffu;
+        {
             if (valid) {
-                const float4 r0 = r[0], r1 = r[1], q = r[2];
                 const V3<float> n{r0.x, r0.y, r0.z};
                 s = r0.w;
                 W[0] = r1.x;
