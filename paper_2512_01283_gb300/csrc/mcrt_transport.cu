@@ -1003,23 +1003,24 @@ __device__ __forceinline__ int nth_set_lane(unsigned m, int k) {
 }
 
 // Scatterings of the warp's waiting lanes with their rejection trials spread over all
-// 32 lanes (single-model launches with tabulated optics).  Each owner first takes its
+// 32 lanes (launches with tabulated optics; in batched launches each trial lane reads
+// the tables of its packet's job).  Each owner first takes its
 // roulette and size bin; then, round after round, every unresolved packet gets
 // floor(32 / unresolved) lanes that evaluate its next trials in trial order, and the
 // packet takes its first accepted trial.  Direction, matrix and trial count are thus
 // those of the sequential rule (same random numbers, same arithmetic).  All 32 lanes
 // call it.
-template <typename T>
+template <typename T, bool B>
 __device__ __forceinline__ void scatter_coop(const TransportParams& P, const Smem<T>& sm, Packet<T>& pk, bool& alive,
                                              BlockTotals& bt) {
     const int lane = threadIdx.x & 31;
-    const JobRef<T, false> job = job_of<T, false>(P, sm, pk);
-    const TablesDev& tabs = job.t();
     bool live = false;
     int bin = 0;
     T u_tau = T(1);
     if (alive && pk.pending) {
         pk.pending = false;
+        const JobRef<T, B> job = job_of<T, B>(P, sm, pk);
+        const TablesDev& tabs = job.t();
         const Draw4<T> us = draw4<T>(pk.pid, pk.n_sca, 0u, P.seed, job.stream());
         live = roulette(P, pk, us.b, bt);
         alive = live;
@@ -1043,15 +1044,21 @@ __device__ __forceinline__ void scatter_coop(const TransportParams& P, const Sme
         const unsigned nsca = __shfl_sync(kFull, pk.n_sca, src);
         const int tb = __shfl_sync(kFull, bin, src);
         const int t = __shfl_sync(kFull, t_next, src) + lane % per;
+        // the packet's job (batched launches)
+        Packet<T> jp;
+        if constexpr (B)
+            jp.job = reinterpret_cast<const JobDev*>(
+                __shfl_sync(kFull, reinterpret_cast<unsigned long long>(pk.job), src));
         bool acc = false;
         V3<T> n2{T(0), T(0), T(1)};
         T mu = T(1);
         if (k < nu && t < P.max_trials) {
+            const JobRef<T, B> job = job_of<T, B>(P, sm, jp);
             V3<T> th, ph;
             stokes_basis(n, th, ph);
             const Draw4<T> ut = draw4<T>(pid, nsca, 1u + (unsigned)t, P.seed, job.stream());
             T Pm[6];
-            acc = table_trial(tabs, tb, ut, n, th, ph, X, n2, mu, Pm);
+            acc = table_trial(job.t(), tb, ut, n, th, ph, X, n2, mu, Pm);
         }
         const unsigned am = __ballot_sync(kFull, acc);
         // each owner: the first accepted trial among its lanes
@@ -1084,6 +1091,7 @@ __device__ __forceinline__ void scatter_coop(const TransportParams& P, const Sme
         alive = false;
         return;
     }
+    const TablesDev& tabs = job_of<T, B>(P, sm, pk).t();
     const V3<T> n{pk.nx, pk.ny, pk.nz};
     V3<T> th, ph, th2, ph2;
     stokes_basis(n, th, ph);
@@ -1252,8 +1260,8 @@ __global__ void __launch_bounds__(kDefaultBlock, (min_blocks<T, SCAT>()))
         }
         // scatterings of the warp run together once enough lanes wait for one
         if (pend != 0u && (__popc(pend) >= scatter_batch<B, SCAT>() || work == 0u)) {
-            if constexpr (table_optics(SCAT) && !B) {
-                scatter_coop<T>(P, sm, pk, alive, bt);  // every lane runs trials of the waiting packets
+            if constexpr (table_optics(SCAT)) {
+                scatter_coop<T, B>(P, sm, pk, alive, bt);  // every lane runs trials of the waiting packets
             } else if constexpr (SCAT != kScatSurrogate) {  // the surrogate scatters in its own kernel
                 if (alive && pk.pending) {
                     pk.pending = false;
