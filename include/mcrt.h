@@ -441,7 +441,10 @@ MCRT_API mcrt_status mcrt_batch_destroy(mcrt_batch *batch); /* NULL-safe */
  *   train:  n_steps Adam steps on fresh batches of `batch` samples generated on the
  *           GPU from the tables (uniform directions, uniform s); learning rate `lr`
  *           with cosine decay; loss_history (host, nullable) gets the mean squared
- *           error of each step.
+ *           error of each step.  One step is captured once as a CUDA graph on the
+ *           surrogate's own stream and replayed n_steps times; the call allocates
+ *           20 bytes of device memory per step (losses, schedule) for its duration
+ *           and returns when the steps have run.
  *   eval:   outputs [n][20] (host or device) for inputs [n][7].
  *   labels: the training targets [n][20] of inputs [n][7].
  *   grad:   loss sum_b sum_o w_o (y - t)^2 / (20 n) and its gradient with respect
