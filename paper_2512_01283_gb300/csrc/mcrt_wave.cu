@@ -900,18 +900,25 @@ __global__ void __launch_bounds__(tc::kRows * kScatGroups, 1) k_sur_scatter_tc(c
     tc::teardown(kScatGroups, g, failed, phase, kTensorWaitNs);
 }
 
-// Source tally of queued table-path segments: one (record, camera) row per lane,
-// the mixture table and the cameras in shared memory; a record's cameras are one
-// contiguous FP64 bulk reduction into S[cell].  Same arithmetic as the in-place
-// tally of k_transport (table_matrix, plane_rotation, apply_plane), with every
-// lane of the warp busy.
-constexpr int kTabBlock = 256;
+// Source tally of queued table-path segments: one record per lane, its cameras in
+// turn (the record's Stokes basis once, then per camera the matrix at the scattering
+// angle, the plane rotation and the Stokes product), the mixture table and the
+// cameras in shared memory.  Each lane stages its record's camera rows (32 B each) in
+// a row of its own and issues one contiguous FP64 bulk reduction into S[cell]; lanes
+// share nothing, so no lane waits for another.  Same arithmetic as the in-place tally
+// of k_transport (table_matrix, plane_rotation, apply_plane).
+constexpr int kTabBlock = 128;
+constexpr int kTabSlots = 2;  // staging rows per lane (1 or 2), alternated from tile to tile
+// a lane's staging row: the cameras' rows, padded by 16 B so that the 16-byte stores of
+// a quarter-warp's lanes (rows 8 c + 4 words apart) fall in different bank groups
+__host__ __device__ constexpr int tab_row_bytes(int ncam) { return ncam * 32 + 16; }
+
 __global__ void __launch_bounds__(kTabBlock) k_tab_tally(const __grid_constant__ TransportParams P) {
     extern __shared__ __align__(16) unsigned char sm[];
     float4* s_mix = reinterpret_cast<float4*>(sm);
     const int n_mix = 2 * P.t.n_theta;
     float* s_cam = reinterpret_cast<float*>(s_mix + n_mix);
-    double* s_stage = reinterpret_cast<double*>(s_cam + 12 * kMaxCams);
+    unsigned char* s_stage = reinterpret_cast<unsigned char*>(s_cam + 12 * kMaxCams);
     for (int i = threadIdx.x; i < n_mix; i += blockDim.x) s_mix[i] = P.t.mix[i];
     for (int i = threadIdx.x; i < 12 * P.n_cam; i += blockDim.x) {
         const CameraDev& cd = P.cam[i / 12];
@@ -920,21 +927,20 @@ __global__ void __launch_bounds__(kTabBlock) k_tab_tally(const __grid_constant__
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    double* const slots = s_stage + (threadIdx.x >> 5) * 2 * 32 * 4;  // two staging slots per warp
+    const int ncam = P.n_cam;
+    const int row = tab_row_bytes(ncam);
+    // row of (warp, slot, lane) at index (warp * kTabSlots + slot) * 32 + lane
+    unsigned char* const rows = s_stage + ((size_t)(threadIdx.x >> 5) * kTabSlots * 32 + lane) * row;
     const unsigned long long nreq = P.sur.ctl->n_rec[P.sur.rec_slot];
     const unsigned long long nrec = nreq < P.sur.rec_cap ? nreq : P.sur.rec_cap;
-    const int ncam = P.n_cam;
-    const int ncp = ncam <= 1 ? 1 : (ncam <= 2 ? 2 : (ncam <= 4 ? 4 : (ncam <= 8 ? 8 : 16)));
-    const int per_tile = 32 / ncp;
-    const int cam = lane % ncp;
-    const unsigned long long ntile = (nrec + per_tile - 1) / per_tile;
+    const unsigned long long ntile = (nrec + 31) / 32;
     const unsigned long long stride = (unsigned long long)gridDim.x * wpb;
-    // the next tile's record is loaded while this one is converted, and each warp
-    // alternates two staging slots, so that a slot is rewritten only once the reduction
-    // issued from it two tiles before has read it (every lane commits one bulk group per
-    // tile, empty when it issues none, so "all but the newest group" is that reduction)
+    // the next tile's record is loaded while this one is converted; a lane's two rows
+    // alternate, so that a row is rewritten only once the reduction issued from it two
+    // tiles before has read it (every lane commits one bulk group per tile, empty when
+    // it issues none, so "all but the newest group" is that reduction)
     auto load = [&](unsigned long long t, float4& a, float4& b) {
-        const unsigned long long rec = t * per_tile + (unsigned)(lane / ncp);
+        const unsigned long long rec = t * 32 + (unsigned)lane;
         if (t < ntile && rec < nrec) {
             const float4* r = P.sur.records + rec * kTableRecordF4;
             a = r[0];
@@ -950,38 +956,30 @@ __global__ void __launch_bounds__(kTabBlock) k_tab_tally(const __grid_constant__
         const float4 r0 = n0, r1 = n1;
         load(tile + stride, n0, n1);
         const unsigned cell = __float_as_uint(r1.w);
-        const bool valid = cam < ncam && cell != 0xffffffffu;
-        double2 lo2 = make_double2(0.0, 0.0), hi2 = lo2;
-        if (valid) {
+        if (cell != 0xffffffffu) {
+            unsigned char* const dst = rows + (size_t)(it % kTabSlots) * 32 * row;
+            if constexpr (kTabSlots == 1)
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            else
+                asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
             const V3<float> n{r0.x, r0.y, r0.z};
             const float W[4] = {r0.w, r1.x, r1.y, r1.z};
-            V3<float> th, ph, Om, thc, phc;
+            V3<float> th, ph;
             stokes_basis(n, th, ph);
-            load_camera(s_cam + 12 * cam, Om, thc, phc);
-            float Pm[6], Y[4];
-            table_matrix(s_mix, P.t.n_theta, dot(n, Om), Pm);
-            const PlaneRot<float> pr = plane_rotation(n, th, ph, Om, thc, phc);
-            apply_plane(pr, Pm, W, Y);
-            // the FP32 -> FP64 conversions run on the FP64 pipe, idle in this kernel (the
-            // integer-only widening would add to its busiest pipes)
-            lo2 = make_double2((double)Y[0], (double)Y[1]);
-            hi2 = make_double2((double)Y[2], (double)Y[3]);
-        }
-        double* stage = slots + (it & 1u) * 32 * 4;
-        asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-        __syncwarp();
-        if (valid) {
-            // lanes 4-7 of each group of 8 store their second half first, so that each
-            // quarter-warp phase of 16-byte stores covers the 8 bank groups once
-            double2* d2 = reinterpret_cast<double2*>(stage + lane * 4);
-            const int h = (lane >> 2) & 1;
-            d2[h] = h ? hi2 : lo2;
-            d2[1 - h] = h ? lo2 : hi2;
+            for (int k = 0; k < ncam; ++k) {
+                V3<float> Om, thc, phc;
+                load_camera(s_cam + 12 * k, Om, thc, phc);
+                float Pm[6], Y[4];
+                table_matrix(s_mix, P.t.n_theta, dot(n, Om), Pm);
+                const PlaneRot<float> pr = plane_rotation(n, th, ph, Om, thc, phc);
+                apply_plane(pr, Pm, W, Y);
+                // the FP32 -> FP64 conversions run on the FP64 pipe, idle in this kernel
+                double2* d2 = reinterpret_cast<double2*>(dst + 32 * k);
+                d2[0] = make_double2((double)Y[0], (double)Y[1]);
+                d2[1] = make_double2((double)Y[2], (double)Y[3]);
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        }
-        __syncwarp();
-        if (valid && cam == 0) {
-            const unsigned src = (unsigned)__cvta_generic_to_shared(stage + lane * 4);
+            const unsigned src = (unsigned)__cvta_generic_to_shared(dst);
             asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f64 [%0], [%1], %2;" ::"l"(
                              P.S + (size_t)cell * (size_t)ncam * 4),
                          "r"(src), "r"((unsigned)ncam * 32u)
@@ -994,7 +992,7 @@ __global__ void __launch_bounds__(kTabBlock) k_tab_tally(const __grid_constant__
 
 size_t tab_tally_smem(const TransportParams& p) {
     return (size_t)2 * p.t.n_theta * sizeof(float4) + 12 * kMaxCams * sizeof(float) +
-           (size_t)(kTabBlock / 32) * 2 * 32 * 4 * sizeof(double);
+           (size_t)(kTabBlock / 32) * kTabSlots * 32 * (size_t)tab_row_bytes(p.n_cam > 0 ? p.n_cam : 1);
 }
 
 }  // namespace
