@@ -1004,12 +1004,12 @@ __device__ __forceinline__ int nth_set_lane(unsigned m, int k) {
 
 // Scatterings of the warp's waiting lanes with their rejection trials spread over all
 // 32 lanes (launches with tabulated optics; in batched launches each trial lane reads
-// the tables of its packet's job).  Each owner first takes its
-// roulette and size bin; then, round after round, every unresolved packet gets
-// floor(32 / unresolved) lanes that evaluate its next trials in trial order, and the
-// packet takes its first accepted trial.  Direction, matrix and trial count are thus
-// those of the sequential rule (same random numbers, same arithmetic).  All 32 lanes
-// call it.
+// the tables of its packet's job).  Each owner first takes its roulette and size bin;
+// then, round after round, every unresolved packet gets floor(32 / unresolved) lanes
+// that evaluate its next trials in trial order, and the packet takes its first
+// accepted trial.  Direction, matrix and trial count are thus those of the sequential
+// rule (same random numbers, same arithmetic; the trial reads I, Q and U only, so V
+// is not passed).  All 32 lanes call it.
 template <typename T, bool B>
 __device__ __forceinline__ void scatter_coop(const TransportParams& P, const Smem<T>& sm, Packet<T>& pk, bool& alive,
                                              BlockTotals& bt) {
