@@ -372,7 +372,9 @@ def test_network_beats_a_table_of_equal_memory(disk_net):
     the grain frame and on the size (five coordinates), a table of the network's
     size (4 x 6 x 4 x 6 x 2 nodes of the same 20 FP32 outputs, 92 KB, multilinear)
     is far less accurate than the network (117 KB), judged on fresh inputs against
-    the FP64 labels of the oracle."""
+    the FP64 labels of the oracle.  The method's own tables for these optics depend on
+    the scattering angle alone (181 angles per size bin) and are exact there: against
+    them the network gains nothing, and the table path is the faster and exact one."""
     from scipy.interpolate import RegularGridInterpolator
 
     model, s = disk_net
